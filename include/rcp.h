@@ -1,0 +1,252 @@
+/*
+ * rcp.h -- C ABI of the GB300 (sm_103a) recursive-camera-painting renderer.
+ *
+ * Recursive Camera Painting (Akleman, Mullins, Morrison, Oh; arXiv 2312.12392)
+ * renders K passes. Pass n gives every pixel (u,v) its own camera, moved by a
+ * function of that pixel's value in the previous pass's image, and ray-traces
+ * the scene again:  I_n(u,v) = F(I_{n-1}(u,v), S(n))            (§2, Eq. 1)
+ * with I_0 = (0.5, 0.5, 0.5), so pass 1 is a plain ray-traced image (§3).
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned; nothing aborts or throws across the ABI. The
+ *    last error message of the calling thread is in rcp_last_error().
+ *  - Input arrays are copied; the caller keeps ownership. Output buffers are
+ *    allocated by the caller. "host" buffers are ordinary CPU memory; "device"
+ *    buffers are CUDA device pointers on the current device.
+ *  - Images are row-major, row 0 at the top. "rgbz" images hold 4 floats per
+ *    pixel: linear RGB in [0,1] and the hit distance t of the pixel's primary
+ *    ray (0 on a miss). "rgb" images hold 3 floats per pixel.
+ *  - Primitive ids: triangles 0..T-1, spheres T..T+S-1; -1 marks a miss.
+ *  - Valid arguments: 1 <= width, height <= 8192; 1 <= K <= 16; k >= 0;
+ *    focal_dist > 0; finite coordinates. Degenerate (zero-area) triangles are
+ *    accepted and never hit.
+ *  - A scene may be rendered from several threads at once; rcp_scene_update_*
+ *    must not run concurrently with renders of the same scene.
+ */
+#ifndef RCP_H
+#define RCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RCP_OK = 0,
+    RCP_ERR_ARG = -1,     /* an argument is out of range or NULL */
+    RCP_ERR_OOM = -2,     /* device or host allocation failed, or admission refused for good */
+    RCP_ERR_CUDA = -3,    /* a CUDA call failed (message says which) */
+    RCP_ERR_STACK = -4,   /* BVH deeper than the traversal stack */
+    RCP_ERR_TIMEOUT = -5, /* a bounded wait ran out */
+    RCP_ERR_STATE = -6    /* call not valid in the object's current state */
+} rcp_status;
+
+typedef enum { RCP_LIGHT_POINT = 0, RCP_LIGHT_DIRECTIONAL = 1 } rcp_light_type;
+
+/* v = light position (point) or direction towards the light (directional;
+ * normalised by the library). ambient = the ambient term a of the shading
+ * c = albedo * (a + (1 - a) * V * max(0, N.L)) (0.1 in the workloads). The
+ * paper does not define a shading model; this Lambert + shadow-ray model is the
+ * one the library implements. */
+typedef struct {
+    int32_t type;
+    float v[3];
+    float ambient;
+} rcp_light;
+
+/* Base pinhole camera: eye P_e, look-at point, up vector, vertical FOV. */
+typedef struct {
+    float eye[3];
+    float look_at[3];
+    float up[3];
+    float fov_y_deg;
+} rcp_camera;
+
+/* Colour-to-camera mapping (§2 Eq. 3-4 displacements V_e, V_p; §3 Eq. 5).
+ * With d = 2 * I_{n-1}(u,v) - 1 and V = k * (d.r * right + d.g * up +
+ * d.b * forward) in the base camera's frame:
+ *  RCP_MAP_EYE:    P'_e = P_e + V, ray re-aimed at the pixel's focal-plane point
+ *                  P_p (at focal_dist along the view axis).
+ *  RCP_MAP_TARGET: P'_e = P_e, P'_p = P_p + V (the paper's §3 example).
+ *  RCP_MAP_DEPTH:  P'_e = P_e, P'_p = P_p + |z - z0| * V, z = the previous
+ *                  pass's hit distance (§4, Eq. 7). */
+typedef enum { RCP_MAP_EYE = 0, RCP_MAP_TARGET = 1, RCP_MAP_DEPTH = 2 } rcp_mapping;
+
+typedef struct {
+    int32_t mapping;  /* rcp_mapping */
+    float k;          /* displacement strength lambda (world units) */
+    float focal_dist; /* distance f of the focal plane along the view axis */
+    float z0;         /* in-focus depth of RCP_MAP_DEPTH (ignored otherwise) */
+} rcp_params;
+
+typedef struct rcp_scene rcp_scene;
+
+/* Scene statistics (sizes, BVH shape, build time). */
+typedef struct {
+    int64_t n_tris, n_spheres;
+    int64_t n_nodes;      /* 8-wide BVH nodes (80 bytes each) */
+    int32_t depth;        /* levels of the 8-wide BVH */
+    int32_t max_leaf;     /* largest leaf (primitives) */
+    int64_t device_bytes; /* device memory held by the scene */
+    float diam;           /* diagonal of the scene's bounding box */
+    float build_ms;       /* last BVH build (or refit) time on the device */
+} rcp_scene_info;
+
+/* Build a scene and its BVH on the device (the scene S(n) of Eq. 1).
+ * tri_xyz: host, T*9 floats (v0 v1 v2 per triangle); spheres: host, S*4 floats
+ * (centre, radius), may be NULL when S == 0; albedo: host, (T+S)*3 floats,
+ * triangles first. The BVH is an LBVH (30-bit Morton codes, radix sort, Karras
+ * hierarchy, bottom-up refit) collapsed to a compressed 8-wide BVH. *out
+ * receives a handle owned by the library until rcp_scene_destroy. */
+rcp_status rcp_scene_create(const float* tri_xyz, int64_t T, const float* spheres, int64_t S,
+                            const float* albedo, const rcp_light* light, rcp_scene** out);
+
+/* Move the triangles' vertices (same count and order; host or device array of
+ * T*9 floats) and refit the BVH's boxes bottom-up without rebuilding its
+ * topology. The scene's diameter, t_min and shadow offset stay those of the
+ * original build. `stream` (cudaStream_t or NULL) orders the device variant. */
+rcp_status rcp_scene_update_vertices(rcp_scene* scene, const float* tri_xyz);
+rcp_status rcp_scene_update_vertices_device(rcp_scene* scene, const float* d_tri_xyz, void* stream);
+
+rcp_status rcp_scene_get_info(const rcp_scene* scene, rcp_scene_info* info);
+
+/* Check the BVH on the device: every primitive in exactly one leaf, every
+ * child box inside its quantised slot, every primitive inside its leaf box.
+ * RCP_OK when all hold; RCP_ERR_STATE with a message otherwise. */
+rcp_status rcp_scene_validate(const rcp_scene* scene);
+
+void rcp_scene_destroy(rcp_scene* scene);
+
+/* K passes I_1..I_K from I_0 = 0.5 (§2-§3); writes I_K's RGB to out_rgb (host,
+ * width*height*3 floats). Synchronous. */
+rcp_status rcp_render(const rcp_scene* scene, const rcp_camera* cam, int width, int height, int K,
+                      const rcp_params* params, float* out_rgb);
+
+/* One pass I_n = F(I_{n-1}, S): in_rgbz (host, width*height*4, NULL = I_0)
+ * -> out_rgbz (host, width*height*4); out_prim (host, width*height int32,
+ * nullable) receives each pixel's primary-hit id. Synchronous. */
+rcp_status rcp_render_pass(const rcp_scene* scene, const rcp_camera* cam, int width, int height,
+                           const rcp_params* params, const float* in_rgbz, float* out_rgbz,
+                           int32_t* out_prim);
+
+/* Device variant of both: K passes starting from d_in (device rgbz image, NULL =
+ * I_0), final image to d_out (device, width*height*4 floats; may equal d_in),
+ * last pass's hit ids to d_prim (device, nullable). Enqueued on `stream`
+ * (cudaStream_t, NULL = legacy default); the call returns once enqueued. The
+ * K-pass sequence is captured once per (scene, shape, K) in a CUDA graph and
+ * replayed. Intermediate images live in library-owned device memory. */
+rcp_status rcp_render_device(const rcp_scene* scene, const rcp_camera* cam, int width, int height,
+                             int K, const rcp_params* params, const float* d_in, float* d_out,
+                             int32_t* d_prim, void* stream);
+
+/* Many views of one scene in one persistent launch per pass (§2's per-(u,v)
+ * cameras for every view at once). cams, widths, heights: host arrays of
+ * n_views; d_outs: host array of n_views device pointers (rgbz, width*height*4
+ * floats each). All views run K passes; the K-pass recursion is captured in a
+ * CUDA graph keyed by the view shapes. Enqueued on `stream`. */
+rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rcp_camera* cams,
+                                   const int* widths, const int* heights, int K,
+                                   const rcp_params* params, float* const* d_outs, void* stream);
+
+/* Traversal tuning. block: threads per block (64, 128, 256); blocks_per_sm:
+ * resident blocks of the persistent launch (0 = occupancy maximum); chunk:
+ * pixels a warp claims per fetch (32 or 64); fused_camera: 1 = rays are made
+ * inside the trace kernel, 0 = a separate camera kernel writes a ray buffer;
+ * node_cache: top BVH nodes kept in shared memory (0, 64, 256). */
+typedef struct {
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t chunk;
+    int32_t fused_camera;
+    int32_t node_cache;
+} rcp_tuning;
+
+rcp_status rcp_get_tuning(const rcp_scene* scene, rcp_tuning* out);
+rcp_status rcp_set_tuning(rcp_scene* scene, const rcp_tuning* tuning);
+
+/* Time every tuning candidate on this scene and view, keep the fastest in the
+ * scene and return it. cache_path (nullable): a JSON file of earlier results,
+ * keyed by GPU name, scene size class and view size; read before and updated
+ * after the search. */
+rcp_status rcp_autotune(rcp_scene* scene, const rcp_camera* cam, int width, int height,
+                        const rcp_params* params, const char* cache_path, rcp_tuning* out);
+
+/* Work counters of one pass over the given view, from an instrumented copy of
+ * the trace kernels: rays traced, 8-wide nodes visited, child boxes tested,
+ * triangle and sphere tests. Used for the algorithmic bytes and FLOPs. */
+typedef struct {
+    int64_t rays, primary_rays, shadow_rays;
+    int64_t nodes, box_tests, tri_tests, sphere_tests;
+} rcp_counters;
+
+/* Rays traced (primary, shadow) by the scene's most recent rcp_render*
+ * call, counted on the device during that render. Read it after the render
+ * has completed (synchronise its stream first). */
+rcp_status rcp_last_ray_counts(const rcp_scene* scene, int64_t* primary, int64_t* shadow);
+
+/* d_in: previous image (device rgbz, NULL = I_0); d_out: this pass's image
+ * (device rgbz, nullable), so that counted passes can be chained. */
+rcp_status rcp_count_pass(const rcp_scene* scene, const rcp_camera* cam, int width, int height,
+                          const rcp_params* params, const float* d_in, float* d_out, rcp_counters* out);
+
+/* Device time (ms) of each pass of the scene's most recent render, from CUDA
+ * events recorded on the render's stream between the passes (inside the
+ * captured graph). Read after the render has completed. */
+rcp_status rcp_last_pass_times(const rcp_scene* scene, float* ms, int max_passes, int* n_passes);
+
+/* Diagnostics used by the tests (all device pointers, enqueued on `stream`):
+ *  rcp_debug_trace: n rays, orig_tmin[n*4] = (origin, t_min), dir_tmax[n*4] =
+ *    (unit direction, t_max); any_hit 0 = closest hit (t_out, prim_out), 1 =
+ *    any hit (prim_out = 1 occluded / 0 free, t_out unused); brute 1 tests
+ *    every primitive instead of walking the BVH.
+ *  rcp_debug_sort_pairs: stable LSD radix sort of n (key, value) pairs on the
+ *    low `bits` bits of the keys, in place.
+ *  rcp_debug_morton: 30-bit Morton codes of n points (xyz[n*3]) in the box
+ *    lo[3]..hi[3] (host arrays). */
+rcp_status rcp_debug_trace(const rcp_scene* scene, int64_t n, const float* orig_tmin,
+                           const float* dir_tmax, int any_hit, int brute, float* t_out,
+                           int32_t* prim_out, void* stream);
+rcp_status rcp_debug_sort_pairs(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream);
+rcp_status rcp_debug_morton(const float* xyz, int64_t n, const float* lo, const float* hi,
+                            uint32_t* codes, void* stream);
+
+/* ------------------------------------------------------------ serving ---
+ * A request = one K-pass render of a resident scene. Requests are admitted
+ * while a slot is free and their device memory (two rgbz images and a ray
+ * buffer) fits the budget, then advance one pass per scheduler step together
+ * with every other in-flight request (continuous batching: one launch per pass
+ * stage covers all admitted requests, whatever their scene, size or K). A
+ * finished request's image is copied to the caller's host buffer. */
+typedef struct rcp_server rcp_server;
+
+typedef struct {
+    int64_t submitted, completed, rejected, in_flight, queued;
+    int64_t steps;        /* scheduler steps (one pass of every in-flight request) */
+    double p50_ms, p99_ms; /* submit-to-complete latency of completed requests */
+    double frames_per_s;  /* completed requests per second since the first submit */
+    double mrays_per_s;   /* primary + shadow rays per second over the same span */
+    int64_t device_bytes_in_use, device_bytes_peak;
+} rcp_server_stats;
+
+rcp_status rcp_server_create(int64_t mem_budget_bytes, int max_slots, rcp_server** out);
+/* out_rgb: host, width*height*3 floats, caller-owned until the request is done. */
+rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_camera* cam,
+                             int width, int height, int K, const rcp_params* params, float* out_rgb,
+                             int64_t* ticket);
+/* done = 1 finished, 0 pending; the request's own status is returned. */
+rcp_status rcp_server_poll(rcp_server* srv, int64_t ticket, int* done);
+rcp_status rcp_server_wait(rcp_server* srv, int64_t ticket, double timeout_s);
+rcp_status rcp_server_stats_get(rcp_server* srv, rcp_server_stats* out);
+/* Drop queued requests and stop after the in-flight ones finish. */
+void rcp_server_destroy(rcp_server* srv);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* rcp_last_error(void);
+/* Library version string. */
+const char* rcp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,903 @@
+// abi.cu -- the C ABI of include/rcp.h: scenes, renders, tuning, diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "scene.h"
+
+namespace rcp {
+
+namespace {
+thread_local std::string g_error;
+}
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+rcp_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return RCP_ERR_OOM;
+    return RCP_ERR_CUDA;
+}
+
+RenderCtx::~RenderCtx() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (auto* p : img)
+        if (p) cudaFree(p);
+    if (rays) cudaFree(rays);
+    if (d_views) cudaFree(d_views);
+    if (h_views) cudaFreeHost(h_views);
+    if (d_work) cudaFree(d_work);
+    if (d_status) cudaFree(d_status);
+    if (d_rgb) cudaFree(d_rgb);
+    if (d_rays) cudaFree(d_rays);
+    if (io) cudaFree(io);
+    if (io_prim) cudaFree(io_prim);
+    if (staged) cudaEventDestroy(staged);
+    for (auto e : pass_ev)
+        if (e) cudaEventDestroy(e);
+}
+
+Scene::~Scene() {
+    ctx.clear();
+    for (void* p : {(void*)d_tri, (void*)d_sph, (void*)d_albedo, d_nodes, (void*)d_nbox, (void*)d_prims})
+        if (p) cudaFree(p);
+}
+
+SceneDev Scene::dev() const {
+    SceneDev s;
+    s.nodes = (const uint4*)d_nodes;
+    s.prims = d_prims;
+    s.albedo = d_albedo;
+    s.n_prims = T + S;
+    s.n_nodes = n_nodes;
+    s.light = light;
+    s.tmin = 1e-6f * diam;
+    s.eps = 1e-4f * diam;
+    return s;
+}
+
+int64_t Scene::device_bytes() const {
+    const int64_t N = T + S;
+    return T * 36 + S * 16 + N * 16 + n_nodes * (80 + 32) + N * 48;
+}
+
+void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params& p) {
+    double E[3], F[3], R[3], U[3];
+    for (int a = 0; a < 3; ++a) {
+        E[a] = cam.eye[a];
+        F[a] = (double)cam.look_at[a] - cam.eye[a];
+    }
+    double l = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    for (double& x : F) x /= l;
+    const double up[3] = {cam.up[0], cam.up[1], cam.up[2]};
+    R[0] = F[1] * up[2] - F[2] * up[1];
+    R[1] = F[2] * up[0] - F[0] * up[2];
+    R[2] = F[0] * up[1] - F[1] * up[0];
+    l = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    for (double& x : R) x /= l;
+    U[0] = R[1] * F[2] - R[2] * F[1];
+    U[1] = R[2] * F[0] - R[0] * F[2];
+    U[2] = R[0] * F[1] - R[1] * F[0];
+    const double tn = tan((double)cam.fov_y_deg * M_PI / 360.0);
+    const double hx = tn * ((double)W / H) / W, hy = tn / H;
+    const double f = p.focal_dist, k = p.k;
+    for (int a = 0; a < 3; ++a) {
+        v.E[a] = (float)E[a];
+        v.fF[a] = (float)(f * F[a]);
+        v.fR[a] = (float)(f * hx * R[a]);
+        v.fU[a] = (float)(f * hy * U[a]);
+        v.kR[a] = (float)(k * R[a]);
+        v.kU[a] = (float)(k * U[a]);
+        v.kF[a] = (float)(k * F[a]);
+    }
+    v.W = W;
+    v.H = H;
+    v.mapping = p.mapping;
+    v.z0 = p.z0;
+    v.in = nullptr;
+    v.out = nullptr;
+    v.prim = nullptr;
+    v.tiles_x = (W + 7) / 8;
+    v.pix_begin = 0;
+    v.chunk_begin = 0;
+    v.pad_ = 0;
+}
+
+}  // namespace rcp
+
+using namespace rcp;
+
+
+namespace {
+
+cudaStream_t lib_stream() {
+    static cudaStream_t s = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] { cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking); });
+    return s;
+}
+
+cudaStream_t capture_stream() {
+    thread_local cudaStream_t s = nullptr;
+    if (!s) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    return s;
+}
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+rcp_status check_view(const rcp_camera* cam, int W, int H, const rcp_params* p) {
+    if (!cam || !p) {
+        set_error("camera or params is NULL");
+        return RCP_ERR_ARG;
+    }
+    if (W < 1 || H < 1 || W > 8192 || H > 8192) {
+        set_error("width and height must be in [1, 8192]");
+        return RCP_ERR_ARG;
+    }
+    if (!(p->k >= 0.f) || !std::isfinite(p->k) || !(p->focal_dist > 0.f) || !std::isfinite(p->focal_dist) ||
+        !std::isfinite(p->z0)) {
+        set_error("k must be >= 0 and focal_dist > 0, all finite");
+        return RCP_ERR_ARG;
+    }
+    if (p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_DEPTH) {
+        set_error("unknown mapping");
+        return RCP_ERR_ARG;
+    }
+    if (!finite3(cam->eye) || !finite3(cam->look_at) || !finite3(cam->up) || !(cam->fov_y_deg > 0.f) ||
+        !(cam->fov_y_deg < 180.f)) {
+        set_error("camera must be finite with 0 < fov < 180");
+        return RCP_ERR_ARG;
+    }
+    double F[3], up[3] = {cam->up[0], cam->up[1], cam->up[2]};
+    for (int a = 0; a < 3; ++a) F[a] = (double)cam->look_at[a] - cam->eye[a];
+    const double c0 = F[1] * up[2] - F[2] * up[1], c1 = F[2] * up[0] - F[0] * up[2], c2 = F[0] * up[1] - F[1] * up[0];
+    if (F[0] == 0 && F[1] == 0 && F[2] == 0) {
+        set_error("look_at equals eye");
+        return RCP_ERR_ARG;
+    }
+    if (c0 == 0 && c1 == 0 && c2 == 0) {
+        set_error("up is parallel to the view direction");
+        return RCP_ERR_ARG;
+    }
+    return RCP_OK;
+}
+
+LaunchCfg cfg_of(const Scene& sc) {
+    LaunchCfg c;
+    c.block = sc.tuning.block;
+    c.blocks_per_sm = sc.tuning.blocks_per_sm;
+    c.chunk = sc.tuning.chunk >= 64 ? 64 : 32;
+    c.fused = sc.tuning.fused_camera != 0;
+    int st = std::max(sc.depth, 4);
+    st = (st + 3) & ~3;
+    c.stack = std::min(st, MAX_STACK);
+    return c;
+}
+
+std::string cfg_key(const LaunchCfg& c) {
+    std::ostringstream o;
+    o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/" << c.count;
+    return o.str();
+}
+
+// Lay views out for one pass: global pixel and tile offsets.
+void layout_views(std::vector<ViewDev>& v, int64_t& total_pix, int64_t& total_chunks) {
+    total_pix = 0;
+    total_chunks = 0;
+    for (auto& x : v) {
+        x.pix_begin = total_pix;
+        x.chunk_begin = total_chunks;
+        x.tiles_x = (x.W + 7) / 8;
+        total_pix += (int64_t)x.W * x.H;
+        total_chunks += (int64_t)x.tiles_x * ((x.H + 3) / 4);
+    }
+}
+
+rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t total_chunks, RenderCtx** out) {
+    std::ostringstream key;
+    key << n_views << ":" << K << ":" << total_pix << ":" << total_chunks;
+    auto it = sc.ctx.find(key.str());
+    if (it != sc.ctx.end()) {
+        *out = it->second.get();
+        return RCP_OK;
+    }
+    if (sc.ctx.size() >= 16) {  // bounded cache: drop all and rebuild
+        cudaDeviceSynchronize();
+        sc.ctx.clear();
+        sc.last = nullptr;
+    }
+    auto c = std::make_unique<RenderCtx>();
+    c->n_views = n_views;
+    c->K = K;
+    c->total_pix = total_pix;
+    c->total_chunks = total_chunks;
+    RCP_CUDA(cudaMalloc((void**)&c->img[0], sizeof(float4) * total_pix));
+    RCP_CUDA(cudaMalloc((void**)&c->img[1], sizeof(float4) * total_pix));
+    RCP_CUDA(cudaMalloc((void**)&c->rays, sizeof(float4) * 2 * total_pix));
+    RCP_CUDA(cudaMalloc((void**)&c->d_views, sizeof(ViewDev) * (size_t)K * n_views));
+    RCP_CUDA(cudaMallocHost((void**)&c->h_views, sizeof(ViewDev) * (size_t)K * n_views));
+    RCP_CUDA(cudaMalloc((void**)&c->d_work, sizeof(unsigned) * (K + 1)));
+    RCP_CUDA(cudaMalloc((void**)&c->d_status, sizeof(int) * 4));
+    RCP_CUDA(cudaMemset(c->d_status, 0, sizeof(int) * 4));
+    RCP_CUDA(cudaMalloc((void**)&c->d_rays, sizeof(unsigned long long) * 2));
+    RCP_CUDA(cudaMemset(c->d_rays, 0, sizeof(unsigned long long) * 2));
+    RCP_CUDA(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
+    for (int n = 0; n <= K; ++n) RCP_CUDA(cudaEventCreate(&c->pass_ev[n]));
+    *out = c.get();
+    sc.ctx[key.str()] = std::move(c);
+    return RCP_OK;
+}
+
+// Enqueue the K passes of ctx (views already staged in ctx->d_views).
+rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, unsigned long long* counters,
+                          cudaStream_t st) {
+    RCP_CUDA(cudaMemsetAsync(ctx.d_work, 0, sizeof(unsigned) * (ctx.K + 1), st));
+    RCP_CUDA(cudaMemsetAsync(ctx.d_rays, 0, sizeof(unsigned long long) * 2, st));
+    const SceneDev S = sc.dev();
+    RCP_CUDA(cudaEventRecord(ctx.pass_ev[0], st));
+    for (int n = 0; n < ctx.K; ++n) {
+        rcp_status r = launch_pass(S, cfg, ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix,
+                                   ctx.total_chunks, ctx.rays, ctx.d_work + n, ctx.d_status, ctx.d_rays, counters,
+                                   st);
+        if (r != RCP_OK) return r;
+        RCP_CUDA(cudaEventRecord(ctx.pass_ev[n + 1], st));
+    }
+    return RCP_OK;
+}
+
+// Run the K passes through the context's CUDA graph (captured on first use or
+// when the launch configuration changes).
+rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cudaStream_t st) {
+    const std::string key = cfg_key(cfg);
+    if (!ctx.graph || ctx.graph_key != key) {
+        if (ctx.graph) {
+            cudaGraphExecDestroy(ctx.graph);
+            ctx.graph = nullptr;
+        }
+        cudaStream_t cs = capture_stream();
+        RCP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        rcp_status r = enqueue_passes(sc, ctx, cfg, nullptr, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (r != RCP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ctx.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        ctx.graph_key = key;
+    }
+    RCP_CUDA(cudaGraphLaunch(ctx.graph, st));
+    return RCP_OK;
+}
+
+// Stage the per-pass view descriptors of one render (n_views views, K passes).
+rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const float4* const* ins,
+                       float4* const* outs, int32_t* const* prims, cudaStream_t st) {
+    RCP_CUDA(cudaEventSynchronize(ctx.staged));  // previous copy out of the staging buffer is done
+    const int K = ctx.K, nv = ctx.n_views;
+    for (int n = 0; n < K; ++n) {
+        for (int i = 0; i < nv; ++i) {
+            ViewDev v = base[i];
+            const float4* prev = (n == 0) ? (ins ? ins[i] : nullptr) : ctx.img[(n - 1) & 1] + base[i].pix_begin;
+            float4* cur = (n == K - 1) ? outs[i] : ctx.img[n & 1] + base[i].pix_begin;
+            v.in = prev;
+            v.out = cur;
+            v.prim = (n == K - 1 && prims) ? prims[i] : nullptr;
+            ctx.h_views[(size_t)n * nv + i] = v;
+        }
+    }
+    RCP_CUDA(cudaMemcpyAsync(ctx.d_views, ctx.h_views, sizeof(ViewDev) * (size_t)K * nv, cudaMemcpyHostToDevice, st));
+    RCP_CUDA(cudaEventRecord(ctx.staged, st));
+    return RCP_OK;
+}
+
+rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const int* Ws, const int* Hs, int K,
+                        const rcp_params* p, const float4* const* ins, float4* const* outs, int32_t* const* prims,
+                        cudaStream_t st, RenderCtx** ctx_out = nullptr, const LaunchCfg* cfg_override = nullptr) {
+    if (K < 1 || K > 16) {
+        set_error("K must be in [1, 16]");
+        return RCP_ERR_ARG;
+    }
+    if (n_views < 1) {
+        set_error("n_views must be >= 1");
+        return RCP_ERR_ARG;
+    }
+    std::vector<ViewDev> base(n_views);
+    for (int i = 0; i < n_views; ++i) {
+        rcp_status r = check_view(&cams[i], Ws[i], Hs[i], p);
+        if (r != RCP_OK) return r;
+        if (!outs[i]) {
+            set_error("output image is NULL");
+            return RCP_ERR_ARG;
+        }
+        make_view(base[i], cams[i], Ws[i], Hs[i], *p);
+    }
+    if (sc.depth > MAX_STACK) {
+        set_error("BVH deeper than the traversal stack");
+        return RCP_ERR_STACK;
+    }
+    int64_t total_pix, total_chunks;
+    layout_views(base, total_pix, total_chunks);
+    RenderCtx* ctx = nullptr;
+    rcp_status r = get_ctx(sc, n_views, K, total_pix, total_chunks, &ctx);
+    if (r != RCP_OK) return r;
+    r = stage_views(*ctx, base, ins, outs, prims, st);
+    if (r != RCP_OK) return r;
+    const LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
+    r = run_graph(sc, *ctx, cfg, st);
+    sc.last = ctx;
+    if (ctx_out) *ctx_out = ctx;
+    return r;
+}
+
+rcp_status check_status(RenderCtx& ctx, cudaStream_t st) {
+    int h = 0;
+    RCP_CUDA(cudaMemcpyAsync(&h, ctx.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCP_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        RCP_CUDA(cudaMemsetAsync(ctx.d_status, 0, sizeof(int), st));
+        set_error("traversal stack overflow");
+        return RCP_ERR_STACK;
+    }
+    return RCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rcp_last_error(void) { return g_error.c_str(); }
+const char* rcp_version(void) { return "rcp-gb300 0.1 (sm_103a)"; }
+
+rcp_status rcp_scene_create(const float* tri, int64_t T, const float* sph, int64_t S, const float* albedo,
+                            const rcp_light* light, rcp_scene** out) {
+    if (!out || !light || T < 0 || S < 0 || (T > 0 && !tri) || (S > 0 && !sph) || (T + S > 0 && !albedo)) {
+        set_error("rcp_scene_create: NULL array with a nonzero count, or negative count");
+        return RCP_ERR_ARG;
+    }
+    if (T + S >= (int64_t)1 << 30) {
+        set_error("rcp_scene_create: at most 2^30 - 1 primitives");
+        return RCP_ERR_ARG;
+    }
+    if (light->type != RCP_LIGHT_POINT && light->type != RCP_LIGHT_DIRECTIONAL) {
+        set_error("rcp_scene_create: unknown light type");
+        return RCP_ERR_ARG;
+    }
+    for (int64_t i = 0; i < T * 9; ++i)
+        if (!std::isfinite(tri[i])) {
+            set_error("rcp_scene_create: non-finite vertex");
+            return RCP_ERR_ARG;
+        }
+    for (int64_t i = 0; i < S * 4; ++i)
+        if (!std::isfinite(sph[i])) {
+            set_error("rcp_scene_create: non-finite sphere");
+            return RCP_ERR_ARG;
+        }
+    *out = nullptr;
+    auto sc = std::make_unique<rcp_scene>();
+    sc->T = T;
+    sc->S = S;
+    const int64_t N = T + S;
+    double lv[3] = {light->v[0], light->v[1], light->v[2]};
+    if (light->type == RCP_LIGHT_DIRECTIONAL) {
+        const double l = sqrt(lv[0] * lv[0] + lv[1] * lv[1] + lv[2] * lv[2]);
+        if (!(l > 0) || !std::isfinite(l)) {
+            set_error("rcp_scene_create: zero light direction");
+            return RCP_ERR_ARG;
+        }
+        for (double& x : lv) x /= l;
+    }
+    sc->light.type = light->type;
+    sc->light.x = (float)lv[0];
+    sc->light.y = (float)lv[1];
+    sc->light.z = (float)lv[2];
+    sc->light.ambient = light->ambient;
+    cudaStream_t st = lib_stream();
+    RCP_CUDA(cudaMalloc((void**)&sc->d_tri, sizeof(float) * 9 * (T ? T : 1)));
+    RCP_CUDA(cudaMalloc((void**)&sc->d_sph, sizeof(float) * 4 * (S ? S : 1)));
+    RCP_CUDA(cudaMalloc((void**)&sc->d_albedo, sizeof(float4) * (N ? N : 1)));
+    if (T) RCP_CUDA(cudaMemcpyAsync(sc->d_tri, tri, sizeof(float) * 9 * T, cudaMemcpyHostToDevice, st));
+    if (S) RCP_CUDA(cudaMemcpyAsync(sc->d_sph, sph, sizeof(float) * 4 * S, cudaMemcpyHostToDevice, st));
+    if (N) {
+        std::vector<float4> a(N);
+        for (int64_t i = 0; i < N; ++i) a[i] = make_float4(albedo[3 * i], albedo[3 * i + 1], albedo[3 * i + 2], 0.f);
+        RCP_CUDA(cudaMemcpyAsync(sc->d_albedo, a.data(), sizeof(float4) * N, cudaMemcpyHostToDevice, st));
+        RCP_CUDA(cudaStreamSynchronize(st));
+    }
+    rcp_status r = build_bvh(*sc, st);
+    if (r != RCP_OK) return r;
+    *out = sc.release();
+    return RCP_OK;
+}
+
+rcp_status rcp_scene_update_vertices_device(rcp_scene* sc, const float* d_tri, void* stream) {
+    if (!sc || (!d_tri && sc->T > 0)) {
+        set_error("rcp_scene_update_vertices: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(sc->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (sc->T) RCP_CUDA(cudaMemcpyAsync(sc->d_tri, d_tri, sizeof(float) * 9 * sc->T, cudaMemcpyDeviceToDevice, st));
+    return refit_bvh(*sc, st);
+}
+
+rcp_status rcp_scene_update_vertices(rcp_scene* sc, const float* tri) {
+    if (!sc || (!tri && sc->T > 0)) {
+        set_error("rcp_scene_update_vertices: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    for (int64_t i = 0; i < sc->T * 9; ++i)
+        if (!std::isfinite(tri[i])) {
+            set_error("rcp_scene_update_vertices: non-finite vertex");
+            return RCP_ERR_ARG;
+        }
+    std::lock_guard<std::mutex> lk(sc->mu);
+    cudaStream_t st = lib_stream();
+    if (sc->T) RCP_CUDA(cudaMemcpyAsync(sc->d_tri, tri, sizeof(float) * 9 * sc->T, cudaMemcpyHostToDevice, st));
+    rcp_status r = refit_bvh(*sc, st);
+    if (r != RCP_OK) return r;
+    RCP_CUDA(cudaStreamSynchronize(st));
+    return RCP_OK;
+}
+
+rcp_status rcp_scene_get_info(const rcp_scene* sc, rcp_scene_info* info) {
+    if (!sc || !info) {
+        set_error("rcp_scene_get_info: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    info->n_tris = sc->T;
+    info->n_spheres = sc->S;
+    info->n_nodes = sc->n_nodes;
+    info->depth = sc->depth;
+    info->max_leaf = sc->max_leaf;
+    info->device_bytes = sc->device_bytes();
+    info->diam = sc->diam;
+    info->build_ms = sc->build_ms;
+    return RCP_OK;
+}
+
+rcp_status rcp_scene_validate(const rcp_scene* sc) {
+    if (!sc) {
+        set_error("rcp_scene_validate: NULL scene");
+        return RCP_ERR_ARG;
+    }
+    return validate_bvh(*sc, lib_stream());
+}
+
+void rcp_scene_destroy(rcp_scene* sc) {
+    if (!sc) return;
+    cudaStreamSynchronize(lib_stream());
+    delete sc;
+}
+
+rcp_status rcp_render_device(const rcp_scene* csc, const rcp_camera* cam, int W, int H, int K, const rcp_params* p,
+                             const float* d_in, float* d_out, int32_t* d_prim, void* stream) {
+    if (!csc) {
+        set_error("rcp_render_device: NULL scene");
+        return RCP_ERR_ARG;
+    }
+    rcp_scene* sc = const_cast<rcp_scene*>(csc);
+    std::lock_guard<std::mutex> lk(sc->mu);
+    const float4* ins[1] = {(const float4*)d_in};
+    float4* outs[1] = {(float4*)d_out};
+    int32_t* prims[1] = {d_prim};
+    return render_views(*sc, 1, cam, &W, &H, K, p, ins, outs, prims, (cudaStream_t)stream);
+}
+
+rcp_status rcp_render_batch_device(const rcp_scene* csc, int n_views, const rcp_camera* cams, const int* Ws,
+                                   const int* Hs, int K, const rcp_params* p, float* const* d_outs, void* stream) {
+    if (!csc || !cams || !Ws || !Hs || !d_outs || n_views < 1) {
+        set_error("rcp_render_batch_device: NULL argument or no views");
+        return RCP_ERR_ARG;
+    }
+    rcp_scene* sc = const_cast<rcp_scene*>(csc);
+    std::lock_guard<std::mutex> lk(sc->mu);
+    return render_views(*sc, n_views, cams, Ws, Hs, K, p, nullptr, (float4* const*)d_outs, nullptr,
+                        (cudaStream_t)stream);
+}
+
+static rcp_status ensure_io(RenderCtx& ctx, bool rgb, bool prim) {
+    const int64_t P = ctx.total_pix;
+    if (!ctx.io) RCP_CUDA(cudaMalloc((void**)&ctx.io, sizeof(float4) * P));
+    if (rgb && !ctx.d_rgb) RCP_CUDA(cudaMalloc((void**)&ctx.d_rgb, sizeof(float) * 3 * P));
+    if (prim && !ctx.io_prim) RCP_CUDA(cudaMalloc((void**)&ctx.io_prim, sizeof(int32_t) * P));
+    return RCP_OK;
+}
+
+rcp_status rcp_render(const rcp_scene* csc, const rcp_camera* cam, int W, int H, int K, const rcp_params* p,
+                      float* out_rgb) {
+    if (!csc || !out_rgb) {
+        set_error("rcp_render: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    rcp_scene* sc = const_cast<rcp_scene*>(csc);
+    std::lock_guard<std::mutex> lk(sc->mu);
+    rcp_status r = check_view(cam, W, H, p);
+    if (r != RCP_OK) return r;
+    if (K < 1 || K > 16) {
+        set_error("K must be in [1, 16]");
+        return RCP_ERR_ARG;
+    }
+    cudaStream_t st = lib_stream();
+    const int64_t P = (int64_t)W * H;
+    RenderCtx* ctx = nullptr;
+    r = get_ctx(*sc, 1, K, P, (int64_t)((W + 7) / 8) * ((H + 3) / 4), &ctx);
+    if (r != RCP_OK) return r;
+    r = ensure_io(*ctx, true, false);
+    if (r != RCP_OK) return r;
+    const float4* ins[1] = {nullptr};
+    float4* outs[1] = {ctx->io};
+    r = render_views(*sc, 1, cam, &W, &H, K, p, ins, outs, nullptr, st);
+    if (r != RCP_OK) return r;
+    r = launch_pack_rgb(ctx->io, ctx->d_rgb, P, st);
+    if (r != RCP_OK) return r;
+    RCP_CUDA(cudaMemcpyAsync(out_rgb, ctx->d_rgb, sizeof(float) * 3 * P, cudaMemcpyDeviceToHost, st));
+    return check_status(*ctx, st);
+}
+
+rcp_status rcp_render_pass(const rcp_scene* csc, const rcp_camera* cam, int W, int H, const rcp_params* p,
+                           const float* in_rgbz, float* out_rgbz, int32_t* out_prim) {
+    if (!csc || !out_rgbz) {
+        set_error("rcp_render_pass: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    rcp_scene* sc = const_cast<rcp_scene*>(csc);
+    std::lock_guard<std::mutex> lk(sc->mu);
+    rcp_status r = check_view(cam, W, H, p);
+    if (r != RCP_OK) return r;
+    cudaStream_t st = lib_stream();
+    const int64_t P = (int64_t)W * H;
+    RenderCtx* ctx = nullptr;
+    r = get_ctx(*sc, 1, 1, P, (int64_t)((W + 7) / 8) * ((H + 3) / 4), &ctx);
+    if (r != RCP_OK) return r;
+    r = ensure_io(*ctx, false, out_prim != nullptr);
+    if (r != RCP_OK) return r;
+    // a one-pass render reads I_{n-1} from ctx->io and writes I_n back over it
+    // (each pixel is read and then written by the same thread)
+    if (in_rgbz) RCP_CUDA(cudaMemcpyAsync(ctx->io, in_rgbz, sizeof(float4) * P, cudaMemcpyHostToDevice, st));
+    const float4* ins[1] = {in_rgbz ? ctx->io : nullptr};
+    float4* outs[1] = {ctx->io};
+    int32_t* prims[1] = {out_prim ? ctx->io_prim : nullptr};
+    r = render_views(*sc, 1, cam, &W, &H, 1, p, ins, outs, prims, st);
+    if (r != RCP_OK) return r;
+    RCP_CUDA(cudaMemcpyAsync(out_rgbz, ctx->io, sizeof(float4) * P, cudaMemcpyDeviceToHost, st));
+    if (out_prim)
+        RCP_CUDA(cudaMemcpyAsync(out_prim, ctx->io_prim, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
+    return check_status(*ctx, st);
+}
+
+rcp_status rcp_get_tuning(const rcp_scene* sc, rcp_tuning* out) {
+    if (!sc || !out) {
+        set_error("rcp_get_tuning: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    *out = sc->tuning;
+    return RCP_OK;
+}
+
+rcp_status rcp_set_tuning(rcp_scene* sc, const rcp_tuning* t) {
+    if (!sc || !t) {
+        set_error("rcp_set_tuning: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    if ((t->block != 64 && t->block != 128 && t->block != 256) || (t->chunk != 32 && t->chunk != 64) ||
+        t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || t->node_cache < 0) {
+        set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(sc->mu);
+    sc->tuning = *t;
+    return RCP_OK;
+}
+
+rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, int H, const rcp_params* p,
+                          const float* d_in, float* d_out, rcp_counters* out) {
+    if (!csc || !out) {
+        set_error("rcp_count_pass: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    rcp_scene* sc = const_cast<rcp_scene*>(csc);
+    std::lock_guard<std::mutex> lk(sc->mu);
+    rcp_status r = check_view(cam, W, H, p);
+    if (r != RCP_OK) return r;
+    cudaStream_t st = lib_stream();
+    const int64_t P = (int64_t)W * H;
+    RenderCtx* ctx = nullptr;
+    r = get_ctx(*sc, 1, 1, P, (int64_t)((W + 7) / 8) * ((H + 3) / 4), &ctx);
+    if (r != RCP_OK) return r;
+    std::vector<ViewDev> base(1);
+    make_view(base[0], *cam, W, H, *p);
+    int64_t tp, tc;
+    layout_views(base, tp, tc);
+    const float4* ins[1] = {(const float4*)d_in};
+    float4* outs[1] = {d_out ? (float4*)d_out : ctx->img[0]};
+    r = stage_views(*ctx, base, ins, outs, nullptr, st);
+    if (r != RCP_OK) return r;
+    unsigned long long* d_cnt = nullptr;
+    RCP_CUDA(cudaMalloc((void**)&d_cnt, sizeof(unsigned long long) * 8));
+    RCP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 8, st));
+    LaunchCfg cfg = cfg_of(*sc);
+    cfg.count = true;
+    r = enqueue_passes(*sc, *ctx, cfg, d_cnt, st);
+    unsigned long long h[8] = {0};
+    if (r == RCP_OK) {
+        cudaError_t e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "rcp_count_pass");
+    }
+    cudaFree(d_cnt);
+    if (r != RCP_OK) return r;
+    out->rays = (int64_t)h[0];
+    out->primary_rays = (int64_t)h[1];
+    out->shadow_rays = (int64_t)h[2];
+    out->nodes = (int64_t)h[3];
+    out->box_tests = (int64_t)h[4];
+    out->tri_tests = (int64_t)h[5];
+    out->sphere_tests = (int64_t)h[6];
+    return check_status(*ctx, st);
+}
+
+rcp_status rcp_debug_trace(const rcp_scene* sc, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
+                           int brute, float* t_out, int32_t* prim_out, void* stream) {
+    if (!sc || n < 0 || (n > 0 && (!orig_tmin || !dir_tmax || !t_out || !prim_out))) {
+        set_error("rcp_debug_trace: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    if (((uintptr_t)orig_tmin | (uintptr_t)dir_tmax) & 15) {
+        set_error("rcp_debug_trace: ray arrays must be 16-byte aligned");
+        return RCP_ERR_ARG;
+    }
+    if (sc->depth > MAX_STACK) {
+        set_error("BVH deeper than the traversal stack");
+        return RCP_ERR_STACK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d_status = nullptr;
+    RCP_CUDA(cudaMalloc((void**)&d_status, sizeof(int)));
+    RCP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+    rcp_status r = launch_debug_trace(sc->dev(), n, orig_tmin, dir_tmax, any, brute, t_out, prim_out, d_status, st);
+    int h = 0;
+    if (r == RCP_OK) {
+        cudaError_t e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "rcp_debug_trace");
+    }
+    cudaFree(d_status);
+    if (r == RCP_OK && h) {
+        set_error("traversal stack overflow");
+        r = RCP_ERR_STACK;
+    }
+    return r;
+}
+
+rcp_status rcp_last_ray_counts(const rcp_scene* sc, int64_t* primary, int64_t* shadow) {
+    if (!sc || !primary || !shadow) {
+        set_error("rcp_last_ray_counts: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    if (!sc->last) {
+        set_error("rcp_last_ray_counts: no render yet");
+        return RCP_ERR_STATE;
+    }
+    unsigned long long h[2];
+    RCP_CUDA(cudaMemcpy(h, sc->last->d_rays, sizeof(h), cudaMemcpyDeviceToHost));
+    *primary = (int64_t)h[0];
+    *shadow = (int64_t)h[1];
+    return RCP_OK;
+}
+
+rcp_status rcp_last_pass_times(const rcp_scene* sc, float* ms, int max_passes, int* n_passes) {
+    if (!sc || !ms || !n_passes || max_passes < 1) {
+        set_error("rcp_last_pass_times: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    if (!sc->last) {
+        set_error("rcp_last_pass_times: no render yet");
+        return RCP_ERR_STATE;
+    }
+    const RenderCtx& c = *sc->last;
+    const int n = std::min(c.K, max_passes);
+    for (int i = 0; i < n; ++i) RCP_CUDA(cudaEventElapsedTime(&ms[i], c.pass_ev[i], c.pass_ev[i + 1]));
+    *n_passes = n;
+    return RCP_OK;
+}
+
+rcp_status rcp_debug_sort_pairs(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream);
+rcp_status rcp_debug_morton(const float* xyz, int64_t n, const float* lo, const float* hi, uint32_t* codes,
+                            void* stream) {
+    if (n < 0 || (n > 0 && (!xyz || !lo || !hi || !codes))) {
+        set_error("rcp_debug_morton: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    rcp_status r = debug_morton(xyz, n, lo, hi, codes, (cudaStream_t)stream);
+    if (r != RCP_OK) return r;
+    RCP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return RCP_OK;
+}
+
+}  // extern "C"
+
+namespace rcp {
+size_t radix_sort_scratch_bytes(int64_t n);
+rcp_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* alt_keys, uint32_t* alt_vals, int64_t n,
+                            int bits, void* scratch, int* d_error, cudaStream_t stream);
+}
+
+extern "C" rcp_status rcp_debug_sort_pairs(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream) {
+    if (n < 0 || bits < 1 || bits > 32 || (n > 0 && (!keys || !values))) {
+        set_error("rcp_debug_sort_pairs: bad argument");
+        return RCP_ERR_ARG;
+    }
+    if (n <= 1) return RCP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *ak = nullptr, *av = nullptr;
+    void* scratch = nullptr;
+    int* d_err = nullptr;
+    rcp_status r = RCP_OK;
+    cudaError_t e = cudaMalloc((void**)&ak, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&av, sizeof(uint32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, radix_sort_scratch_bytes(n));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e != cudaSuccess) r = cuda_fail(e, "rcp_debug_sort_pairs alloc");
+    if (r == RCP_OK) r = radix_sort_pairs(keys, values, ak, av, n, bits, scratch, d_err, st);
+    int h = 0;
+    if (r == RCP_OK) {
+        e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "rcp_debug_sort_pairs");
+    }
+    cudaFree(ak);
+    cudaFree(av);
+    cudaFree(scratch);
+    cudaFree(d_err);
+    if (r == RCP_OK && h) {
+        set_error("radix sort: look-back wait ran out");
+        r = RCP_ERR_TIMEOUT;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+std::string gpu_name() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    return prop.name;
+}
+
+// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, node_cache, us], ...}
+std::map<std::string, std::vector<double>> read_cache(const char* path) {
+    std::map<std::string, std::vector<double>> m;
+    if (!path) return m;
+    std::ifstream f(path);
+    if (!f) return m;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    size_t i = 0;
+    while ((i = s.find('"', i)) != std::string::npos) {
+        const size_t j = s.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const std::string key = s.substr(i + 1, j - i - 1);
+        const size_t a = s.find('[', j), b = s.find(']', j);
+        if (a == std::string::npos || b == std::string::npos || b < a) break;
+        std::vector<double> v;
+        std::stringstream vs(s.substr(a + 1, b - a - 1));
+        std::string tok;
+        while (std::getline(vs, tok, ',')) v.push_back(atof(tok.c_str()));
+        if (v.size() >= 6) m[key] = v;
+        i = b + 1;
+    }
+    return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, std::vector<double>>& m) {
+    if (!path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    {
+        std::ofstream f(tmp);
+        if (!f) return;
+        f << "{\n";
+        size_t n = 0;
+        for (auto& kv : m) {
+            f << "  \"" << kv.first << "\": [";
+            for (size_t q = 0; q < kv.second.size(); ++q) f << (q ? ", " : "") << kv.second[q];
+            f << "]" << (++n < m.size() ? "," : "") << "\n";
+        }
+        f << "}\n";
+    }
+    rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, int H, const rcp_params* p,
+                                   const char* cache_path, rcp_tuning* out) {
+    if (!sc) {
+        set_error("rcp_autotune: NULL scene");
+        return RCP_ERR_ARG;
+    }
+    rcp_status r = check_view(cam, W, H, p);
+    if (r != RCP_OK) return r;
+    int cls = 0;
+    for (int64_t n = sc->T + sc->S; n > 1; n >>= 1) ++cls;
+    std::ostringstream key;
+    key << gpu_name() << "|prims2^" << cls << "|" << W << "x" << H << "|map" << p->mapping;
+    auto cache = read_cache(cache_path);
+    auto it = cache.find(key.str());
+    if (it != cache.end()) {
+        rcp_tuning t{(int)it->second[0], (int)it->second[1], (int)it->second[2], (int)it->second[3],
+                     (int)it->second[4]};
+        r = rcp_set_tuning(sc, &t);
+        if (r == RCP_OK && out) *out = t;
+        if (r == RCP_OK) return RCP_OK;
+    }
+    std::lock_guard<std::mutex> lk(sc->mu);
+    cudaStream_t st = lib_stream();
+    const int64_t P = (int64_t)W * H;
+    float4* d_img = nullptr;
+    RCP_CUDA(cudaMalloc((void**)&d_img, sizeof(float4) * P));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_us = 1e30;
+    rcp_tuning best = sc->tuning;
+    const int blocks[3] = {64, 128, 256};
+    const int sms_opts[2] = {0, 0};
+    (void)sms_opts;
+    for (int b : blocks)
+        for (int fused = 0; fused < 2; ++fused)
+            for (int chunk : {32, 64}) {
+                rcp_tuning t{b, 0, chunk, fused, 0};
+                sc->tuning = t;
+                const float4* ins[1] = {nullptr};
+                float4* outs[1] = {d_img};
+                double us = 1e30;
+                // K = 2 so the second pass reads a real image; best of 3
+                for (int rep = 0; rep < 4 && r == RCP_OK; ++rep) {
+                    cudaEventRecord(e0, st);
+                    r = render_views(*sc, 1, cam, &W, &H, 2, p, ins, outs, nullptr, st);
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) r = RCP_ERR_CUDA;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) us = std::min(us, 1000.0 * ms);
+                }
+                if (r != RCP_OK) break;
+                if (us < best_us) {
+                    best_us = us;
+                    best = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_img);
+    sc->tuning = best;
+    if (r != RCP_OK) return r;
+    cache[key.str()] = {(double)best.block, (double)best.blocks_per_sm, (double)best.chunk, (double)best.fused_camera,
+                        (double)best.node_cache, best_us};
+    write_cache(cache_path, cache);
+    if (out) *out = best;
+    return RCP_OK;
+}

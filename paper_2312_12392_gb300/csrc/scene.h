@@ -1,0 +1,96 @@
+// scene.h -- host-side scene object and the render launch interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rcp_internal.cuh"
+
+namespace rcp {
+
+// Cached resources of one launch shape: ping-pong images, ray buffer, view
+// descriptors (device + pinned staging), work counters and the CUDA graph of
+// the K-pass sequence.
+struct RenderCtx {
+    int n_views = 0;
+    int K = 0;
+    int64_t total_pix = 0;
+    int64_t total_chunks = 0;
+    float4* img[2] = {nullptr, nullptr};
+    float4* rays = nullptr;
+    ViewDev* d_views = nullptr;  // K * n_views
+    ViewDev* h_views = nullptr;  // pinned staging
+    unsigned* d_work = nullptr;  // one work counter per launch
+    int* d_status = nullptr;     // [0] stack overflow
+    unsigned long long* d_rays = nullptr;  // rays traced by the last render: primary, shadow
+    float* d_rgb = nullptr;      // packed RGB for host output
+    float4* io = nullptr;        // host-API input / final image
+    int32_t* io_prim = nullptr;  // host-API hit ids
+    cudaEvent_t staged = nullptr;
+    cudaEvent_t pass_ev[17] = {};  // timing events around every pass (recorded inside the graph)
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_key;
+    ~RenderCtx();
+};
+
+struct Scene {
+    int64_t T = 0, S = 0;
+    float* d_tri = nullptr;
+    float* d_sph = nullptr;
+    float4* d_albedo = nullptr;
+    void* d_nodes = nullptr;  // WNode[n_nodes]
+    float4* d_nbox = nullptr;  // 2 per node: union box of the node's children
+    float4* d_prims = nullptr;  // 3 per primitive
+    int64_t n_nodes = 0;
+    int depth = 0;
+    int max_leaf = 0;
+    std::vector<int64_t> level_begin;
+    float diam = 0.f;
+    float build_ms = 0.f;
+    LightDev light{};
+    rcp_tuning tuning{128, 0, 32, 1, 0};
+    std::mutex mu;
+    std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
+    RenderCtx* last = nullptr;  // context of the most recent render
+    ~Scene();
+    SceneDev dev() const;
+    int64_t device_bytes() const;
+};
+
+rcp_status build_bvh(Scene& sc, cudaStream_t st);
+rcp_status refit_bvh(Scene& sc, cudaStream_t st);
+rcp_status validate_bvh(const Scene& sc, cudaStream_t st);
+rcp_status debug_morton(const float* xyz, int64_t n, const float* lo, const float* hi, uint32_t* codes,
+                        cudaStream_t st);
+
+// Fill a view descriptor (camera terms in double, rounded once).
+void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params& p);
+
+// Launch configuration of the pass kernels.
+struct LaunchCfg {
+    int block = 128;
+    int blocks_per_sm = 0;
+    int chunk = 32;
+    bool fused = true;
+    int stack = 32;  // entries per thread
+    bool count = false;
+};
+
+// One pass over n_views views whose descriptors are at d_views (device).
+rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
+                       int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work, int* d_status,
+                       unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st);
+rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
+                              int brute, float* t_out, int32_t* prim_out, int* d_status, cudaStream_t st);
+rcp_status launch_pack_rgb(const float4* img, float* rgb, int64_t n, cudaStream_t st);
+
+}  // namespace rcp
+
+// The opaque handle of the C ABI is the scene object itself.
+struct rcp_scene : public rcp::Scene {};

@@ -1,0 +1,461 @@
+// serve.cu -- continuous-batching render server (rcp_server_* in rcp.h).
+//
+// A scheduler thread owns the device work. Each step it
+//  1. admits queued requests (FIFO) while a slot is free and the request's
+//     device memory -- two rgbz images and an RGB staging buffer, allocated
+//     stream-ordered from the device's memory pool -- fits the budget;
+//  2. runs ONE pass of every admitted request: the requests are grouped by
+//     scene and each group is one launch of the pass kernels (one work queue
+//     over all of the group's views, whatever their size), groups on their
+//     own streams so they overlap on the device;
+//  3. retires requests whose K passes are done: packs RGB, copies it to the
+//     caller's buffer and frees the request's memory.
+// New requests join at the next step boundary while others are mid-recursion,
+// so short and long requests share every launch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "scene.h"
+
+
+namespace rcp {
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+LaunchCfg server_cfg(const Scene& sc) {
+    LaunchCfg c;
+    c.block = sc.tuning.block;
+    c.blocks_per_sm = sc.tuning.blocks_per_sm;
+    c.chunk = sc.tuning.chunk >= 64 ? 64 : 32;
+    c.fused = true;  // no ray buffer per request
+    int st = std::max(sc.depth, 4);
+    c.stack = std::min((st + 3) & ~3, MAX_STACK);
+    return c;
+}
+
+}  // namespace
+
+struct Request {
+    int64_t ticket = 0;
+    const rcp_scene* scene = nullptr;
+    rcp_camera cam{};
+    int W = 0, H = 0, K = 0;
+    rcp_params p{};
+    float* out_rgb = nullptr;
+    int passes_done = 0;
+    float4* img[2] = {nullptr, nullptr};
+    float* rgb = nullptr;
+    int64_t bytes = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    rcp_status status = RCP_OK;
+    bool done = false;
+};
+
+// Per-scene launch resources of a step.
+struct GroupRes {
+    cudaStream_t st = nullptr;
+    ViewDev* d_views = nullptr;
+    ViewDev* h_views = nullptr;
+    int cap = 0;
+    unsigned* d_work = nullptr;
+    int* d_status = nullptr;
+    cudaEvent_t staged = nullptr;
+};
+
+}  // namespace rcp
+
+using namespace rcp;
+
+struct rcp_server {
+    int64_t budget = 0;
+    int max_slots = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> inflight;
+    std::map<int64_t, std::unique_ptr<Request>> all;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    int64_t bytes_in_use = 0, bytes_peak = 0;
+    int64_t submitted = 0, completed = 0, rejected = 0, steps = 0;
+    double t_first = 0, t_last = 0;
+    std::vector<double> latencies_ms;
+    unsigned long long rays_total = 0;
+    unsigned long long* d_rays = nullptr;
+    cudaStream_t st_main = nullptr;
+    std::vector<GroupRes> groups;
+    cudaMemPool_t pool = nullptr;
+
+    void run();
+    rcp_status step(std::vector<Request*>& batch);
+};
+
+namespace {
+
+int64_t request_bytes(int W, int H) {
+    const int64_t P = (int64_t)W * H;
+    return P * (2 * 16 + 12) + 3 * 256;
+}
+
+rcp_status alloc_request(Request& r, cudaStream_t st) {
+    const int64_t P = (int64_t)r.W * r.H;
+    RCP_CUDA(cudaMallocAsync((void**)&r.img[0], sizeof(float4) * P, st));
+    RCP_CUDA(cudaMallocAsync((void**)&r.img[1], sizeof(float4) * P, st));
+    RCP_CUDA(cudaMallocAsync((void**)&r.rgb, sizeof(float) * 3 * P, st));
+    return RCP_OK;
+}
+
+void free_request(Request& r, cudaStream_t st) {
+    for (auto*& p : r.img)
+        if (p) {
+            cudaFreeAsync(p, st);
+            p = nullptr;
+        }
+    if (r.rgb) {
+        cudaFreeAsync(r.rgb, st);
+        r.rgb = nullptr;
+    }
+}
+
+rcp_status ensure_group(GroupRes& g, int n) {
+    if (!g.st) {
+        RCP_CUDA(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+        RCP_CUDA(cudaMalloc((void**)&g.d_work, sizeof(unsigned) * 2));
+        RCP_CUDA(cudaMalloc((void**)&g.d_status, sizeof(int) * 2));
+        RCP_CUDA(cudaMemset(g.d_status, 0, sizeof(int) * 2));
+        RCP_CUDA(cudaEventCreateWithFlags(&g.staged, cudaEventDisableTiming));
+    }
+    if (g.cap < n) {
+        if (g.d_views) cudaFree(g.d_views);
+        if (g.h_views) cudaFreeHost(g.h_views);
+        g.cap = std::max(n, 16);
+        RCP_CUDA(cudaMalloc((void**)&g.d_views, sizeof(ViewDev) * g.cap));
+        RCP_CUDA(cudaMallocHost((void**)&g.h_views, sizeof(ViewDev) * g.cap));
+    }
+    return RCP_OK;
+}
+
+double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (v.size() - 1);
+    const size_t i = (size_t)pos;
+    const double f = pos - i;
+    return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+// One pass of every request in the batch.
+rcp_status rcp_server::step(std::vector<Request*>& batch) {
+    std::map<const rcp_scene*, std::vector<Request*>> by_scene;
+    for (Request* r : batch) by_scene[r->scene].push_back(r);
+    if ((int)groups.size() < (int)by_scene.size()) groups.resize(by_scene.size());
+    RCP_CUDA(cudaMemsetAsync(d_rays, 0, sizeof(unsigned long long) * 2, st_main));
+    cudaEvent_t ready;
+    RCP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    RCP_CUDA(cudaEventRecord(ready, st_main));
+    int gi = 0;
+    rcp_status res = RCP_OK;
+    std::vector<cudaEvent_t> ends;
+    for (auto& kv : by_scene) {
+        const rcp_scene* sc = kv.first;
+        auto& reqs = kv.second;
+        GroupRes& g = groups[gi++];
+        rcp_status r = ensure_group(g, (int)reqs.size());
+        if (r != RCP_OK) {
+            res = r;
+            break;
+        }
+        RCP_CUDA(cudaEventSynchronize(g.staged));
+        std::vector<ViewDev> views(reqs.size());
+        int64_t total_pix = 0, total_chunks = 0;
+        for (size_t i = 0; i < reqs.size(); ++i) {
+            Request* q = reqs[i];
+            ViewDev& v = views[i];
+            make_view(v, q->cam, q->W, q->H, q->p);
+            v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
+            v.out = q->img[q->passes_done & 1];
+            v.pix_begin = total_pix;
+            v.chunk_begin = total_chunks;
+            total_pix += (int64_t)q->W * q->H;
+            total_chunks += (int64_t)v.tiles_x * ((q->H + 3) / 4);
+            g.h_views[i] = v;
+        }
+        RCP_CUDA(cudaStreamWaitEvent(g.st, ready, 0));
+        RCP_CUDA(cudaMemcpyAsync(g.d_views, g.h_views, sizeof(ViewDev) * reqs.size(), cudaMemcpyHostToDevice, g.st));
+        RCP_CUDA(cudaEventRecord(g.staged, g.st));
+        RCP_CUDA(cudaMemsetAsync(g.d_work, 0, sizeof(unsigned), g.st));
+        LaunchCfg cfg = server_cfg(*sc);
+        if (sc->depth > MAX_STACK) {
+            for (Request* q : reqs) q->status = RCP_ERR_STACK;
+            continue;
+        }
+        r = launch_pass(sc->dev(), cfg, g.d_views, (int)reqs.size(), total_pix, total_chunks, nullptr, g.d_work,
+                        g.d_status, d_rays, nullptr, g.st);
+        if (r != RCP_OK) {
+            res = r;
+            break;
+        }
+        for (Request* q : reqs) {
+            q->passes_done++;
+            if (q->passes_done == q->K) {
+                const int64_t P = (int64_t)q->W * q->H;
+                r = launch_pack_rgb(q->img[(q->K - 1) & 1], q->rgb, P, g.st);
+                if (r != RCP_OK) {
+                    res = r;
+                    break;
+                }
+                RCP_CUDA(cudaMemcpyAsync(q->out_rgb, q->rgb, sizeof(float) * 3 * P, cudaMemcpyDeviceToHost, g.st));
+            }
+        }
+        cudaEvent_t e;
+        RCP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        RCP_CUDA(cudaEventRecord(e, g.st));
+        RCP_CUDA(cudaStreamWaitEvent(st_main, e, 0));
+        ends.push_back(e);
+    }
+    unsigned long long h[2] = {0, 0};
+    RCP_CUDA(cudaMemcpyAsync(h, d_rays, sizeof(h), cudaMemcpyDeviceToHost, st_main));
+    cudaError_t e = cudaStreamSynchronize(st_main);
+    for (cudaEvent_t x : ends) cudaEventDestroy(x);
+    cudaEventDestroy(ready);
+    if (e != cudaSuccess) return cuda_fail(e, "server step");
+    rays_total += h[0] + h[1];
+    return res;
+}
+
+void rcp_server::run() {
+    for (;;) {
+        std::vector<Request*> batch;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                             [&] { return stop || !queue.empty() || !inflight.empty(); });
+            if (stop && inflight.empty()) {
+                for (Request* q : queue) {
+                    q->status = RCP_ERR_STATE;
+                    q->done = true;
+                }
+                queue.clear();
+                cv_done.notify_all();
+                return;
+            }
+            // admission: FIFO while a slot is free and the memory fits
+            while (!stop && !queue.empty() && (int)inflight.size() < max_slots) {
+                Request* q = queue.front();
+                if (q->bytes > budget) {  // can never fit
+                    queue.pop_front();
+                    q->status = RCP_ERR_OOM;
+                    q->done = true;
+                    ++rejected;
+                    cv_done.notify_all();
+                    continue;
+                }
+                if (bytes_in_use + q->bytes > budget) break;
+                queue.pop_front();
+                bytes_in_use += q->bytes;
+                bytes_peak = std::max(bytes_peak, bytes_in_use);
+                q->t_admit = now_s();
+                inflight.push_back(q);
+            }
+            batch = inflight;
+        }
+        if (batch.empty()) continue;
+        for (Request* q : batch)
+            if (!q->img[0]) {
+                rcp_status r = alloc_request(*q, st_main);
+                if (r != RCP_OK) q->status = r;
+            }
+        std::vector<Request*> ok;
+        for (Request* q : batch)
+            if (q->status == RCP_OK) ok.push_back(q);
+        rcp_status r = ok.empty() ? RCP_OK : step(ok);
+        const double t = now_s();
+        std::lock_guard<std::mutex> lk(mu);
+        ++steps;
+        std::vector<Request*> still;
+        for (Request* q : inflight) {
+            if (r != RCP_OK && q->status == RCP_OK) q->status = r;
+            if (q->status != RCP_OK || q->passes_done >= q->K) {
+                free_request(*q, st_main);
+                bytes_in_use -= q->bytes;
+                q->t_done = t;
+                q->done = true;
+                if (q->status == RCP_OK) {
+                    ++completed;
+                    latencies_ms.push_back(1000.0 * (q->t_done - q->t_submit));
+                    t_last = t;
+                }
+            } else {
+                still.push_back(q);
+            }
+        }
+        inflight.swap(still);
+        cv_done.notify_all();
+    }
+}
+
+extern "C" {
+
+rcp_status rcp_server_create(int64_t budget, int max_slots, rcp_server** out) {
+    if (!out || budget <= 0 || max_slots < 1 || max_slots > 4096) {
+        set_error("rcp_server_create: budget > 0 and 1 <= max_slots <= 4096");
+        return RCP_ERR_ARG;
+    }
+    auto s = std::make_unique<rcp_server>();
+    s->budget = budget;
+    s->max_slots = max_slots;
+    RCP_CUDA(cudaStreamCreateWithFlags(&s->st_main, cudaStreamNonBlocking));
+    RCP_CUDA(cudaMalloc((void**)&s->d_rays, sizeof(unsigned long long) * 2));
+    int dev = 0;
+    RCP_CUDA(cudaGetDevice(&dev));
+    RCP_CUDA(cudaDeviceGetDefaultMemPool(&s->pool, dev));
+    uint64_t thr = (uint64_t)budget;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    rcp_server* raw = s.release();
+    raw->worker = std::thread([raw] {
+        int d = 0;
+        cudaGetDevice(&d);
+        raw->run();
+    });
+    *out = raw;
+    return RCP_OK;
+}
+
+rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_camera* cam, int W, int H, int K,
+                             const rcp_params* p, float* out_rgb, int64_t* ticket) {
+    if (!srv || !scene || !cam || !p || !out_rgb || !ticket) {
+        set_error("rcp_server_submit: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    if (W < 1 || H < 1 || W > 8192 || H > 8192 || K < 1 || K > 16 || !(p->k >= 0.f) || !(p->focal_dist > 0.f) ||
+        p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_DEPTH || !(cam->fov_y_deg > 0.f) ||
+        !(cam->fov_y_deg < 180.f)) {
+        set_error("rcp_server_submit: argument out of range");
+        return RCP_ERR_ARG;
+    }
+    auto q = std::make_unique<Request>();
+    q->scene = scene;
+    q->cam = *cam;
+    q->W = W;
+    q->H = H;
+    q->K = K;
+    q->p = *p;
+    q->out_rgb = out_rgb;
+    q->bytes = request_bytes(W, H);
+    q->t_submit = now_s();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stop) {
+        set_error("rcp_server_submit: server is stopping");
+        return RCP_ERR_STATE;
+    }
+    q->ticket = srv->next_ticket++;
+    *ticket = q->ticket;
+    if (srv->submitted == 0) srv->t_first = q->t_submit;
+    ++srv->submitted;
+    srv->queue.push_back(q.get());
+    srv->all[q->ticket] = std::move(q);
+    srv->cv_work.notify_one();
+    return RCP_OK;
+}
+
+rcp_status rcp_server_poll(rcp_server* srv, int64_t ticket, int* done) {
+    if (!srv || !done) {
+        set_error("rcp_server_poll: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(ticket);
+    if (it == srv->all.end()) {
+        set_error("rcp_server_poll: unknown ticket");
+        return RCP_ERR_ARG;
+    }
+    *done = it->second->done ? 1 : 0;
+    return it->second->done ? it->second->status : RCP_OK;
+}
+
+rcp_status rcp_server_wait(rcp_server* srv, int64_t ticket, double timeout_s) {
+    if (!srv) {
+        set_error("rcp_server_wait: NULL server");
+        return RCP_ERR_ARG;
+    }
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(ticket);
+    if (it == srv->all.end()) {
+        set_error("rcp_server_wait: unknown ticket");
+        return RCP_ERR_ARG;
+    }
+    Request* q = it->second.get();
+    const bool ok = srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] { return q->done; });
+    if (!ok) {
+        set_error("rcp_server_wait: timed out");
+        return RCP_ERR_TIMEOUT;
+    }
+    if (q->status != RCP_OK) set_error("rcp_server_wait: request failed");
+    return q->status;
+}
+
+rcp_status rcp_server_stats_get(rcp_server* srv, rcp_server_stats* out) {
+    if (!srv || !out) {
+        set_error("rcp_server_stats_get: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    out->submitted = srv->submitted;
+    out->completed = srv->completed;
+    out->rejected = srv->rejected;
+    out->in_flight = (int64_t)srv->inflight.size();
+    out->queued = (int64_t)srv->queue.size();
+    out->steps = srv->steps;
+    out->p50_ms = percentile(srv->latencies_ms, 0.50);
+    out->p99_ms = percentile(srv->latencies_ms, 0.99);
+    const double span = srv->t_last - srv->t_first;
+    out->frames_per_s = span > 0 ? srv->completed / span : 0.0;
+    out->mrays_per_s = span > 0 ? srv->rays_total / span / 1e6 : 0.0;
+    out->device_bytes_in_use = srv->bytes_in_use;
+    out->device_bytes_peak = srv->bytes_peak;
+    return RCP_OK;
+}
+
+void rcp_server_destroy(rcp_server* srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+    }
+    if (srv->worker.joinable()) srv->worker.join();
+    cudaStreamSynchronize(srv->st_main);
+    for (auto& g : srv->groups) {
+        if (g.st) {
+            cudaStreamSynchronize(g.st);
+            cudaStreamDestroy(g.st);
+        }
+        if (g.d_views) cudaFree(g.d_views);
+        if (g.h_views) cudaFreeHost(g.h_views);
+        if (g.d_work) cudaFree(g.d_work);
+        if (g.d_status) cudaFree(g.d_status);
+        if (g.staged) cudaEventDestroy(g.staged);
+    }
+    if (srv->d_rays) cudaFree(srv->d_rays);
+    if (srv->st_main) cudaStreamDestroy(srv->st_main);
+    delete srv;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// trace.cu -- the pass kernels: per-pixel camera, primary + shadow trace, shade.
+//
+// Work is split into 8x4-pixel tiles (one warp each, 32 rays). A persistent
+// grid of blocks claims tiles from a global counter, a warp at a time, across
+// every view of the pass, so views of uneven size share one launch (§2: every
+// (u,v) of every image gets its own camera in the same pass).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "scene.h"
+#include "trace.cuh"
+
+namespace rcp {
+
+namespace {
+
+__device__ __forceinline__ int find_view_by_chunk(const ViewDev* __restrict__ views, int n, int64_t chunk) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].chunk_begin <= chunk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_view_by_pix(const ViewDev* __restrict__ views, int n, int64_t pix) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].pix_begin <= pix) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Camera kernel: one thread per pixel, coalesced float4 reads of I_{n-1} and
+// float4 writes of the ray (origin, t_min) + (direction, t_max).
+__global__ void __launch_bounds__(256) k_camera(const ViewDev* __restrict__ views, int n_views, int64_t total_pix,
+                                                float tmin, float4* __restrict__ rays) {
+    for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < total_pix;
+         gp += (int64_t)gridDim.x * blockDim.x) {
+        const ViewDev& v = views[find_view_by_pix(views, n_views, gp)];
+        const int64_t p = gp - v.pix_begin;
+        const int x = (int)(p % v.W), y = (int)(p / v.W);
+        const float4 c = v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
+        const RayF r = camera_ray(v, x, y, c, tmin);
+        rays[2 * gp] = make_float4(r.ox, r.oy, r.oz, r.tmin);
+        rays[2 * gp + 1] = make_float4(r.dx, r.dy, r.dz, r.tmax);
+    }
+}
+
+// Primary + shadow trace and shading of one pass. FUSED: rays are made here
+// from I_{n-1}; otherwise they are read from the camera kernel's buffer.
+template <int BLOCK, bool FUSED, bool COUNT>
+__global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __restrict__ views, int n_views,
+                                                 int64_t total_chunks, int chunk_tiles,
+                                                 const float4* __restrict__ rays, unsigned* work, int stack_entries,
+                                                 int* status, unsigned long long* ray_counts,
+                                                 unsigned long long* counters) {
+    extern __shared__ uint2 s_stack[];
+    uint2* stack = s_stack + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool overflow = false;
+    WorkCount wc{0, 0, 0, 0};
+    uint32_t n_primary = 0, n_shadow = 0;
+    for (;;) {
+        unsigned c0 = 0;
+        if (lane == 0) c0 = atomicAdd(work, (unsigned)chunk_tiles);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if ((int64_t)c0 >= total_chunks) break;
+        for (int sub = 0; sub < chunk_tiles; ++sub) {
+            const int64_t chunk = (int64_t)c0 + sub;
+            if (chunk >= total_chunks) break;
+            const ViewDev& v = views[find_view_by_chunk(views, n_views, chunk)];
+            const int64_t tile = chunk - v.chunk_begin;
+            const int tx = (int)(tile % v.tiles_x), ty = (int)(tile / v.tiles_x);
+            const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
+            if (x >= v.W || y >= v.H) continue;
+            const int64_t p = (int64_t)y * v.W + x;
+            RayF r;
+            if (FUSED) {
+                const float4 c = v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
+                r = camera_ray(v, x, y, c, S.tmin);
+            } else {
+                const float4 a = __ldg(rays + 2 * (v.pix_begin + p)), b = __ldg(rays + 2 * (v.pix_begin + p) + 1);
+                r.ox = a.x;
+                r.oy = a.y;
+                r.oz = a.z;
+                r.tmin = a.w;
+                r.dx = b.x;
+                r.dy = b.y;
+                r.dz = b.z;
+                r.tmax = b.w;
+            }
+            const Hit h = traverse<false, COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc);
+            const ShadeInfo si = shade_primary(S, r, h);
+            float4 out = si.c_shadow;
+            ++n_primary;
+            if (si.need_shadow) {
+                ++n_shadow;
+                const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, BLOCK, stack_entries, overflow, wc);
+                if (hs.rec < 0) out = si.c_lit;
+            }
+            v.out[p] = out;
+            if (v.prim) v.prim[p] = h.rec < 0 ? -1 : (int32_t)h.id;
+        }
+    }
+    if (overflow) atomicExch(&status[0], 1);
+    {
+        const unsigned np = __reduce_add_sync(0xffffffffu, n_primary);
+        const unsigned ns = __reduce_add_sync(0xffffffffu, n_shadow);
+        if (lane == 0 && ray_counts) {
+            atomicAdd(&ray_counts[0], (unsigned long long)np);
+            atomicAdd(&ray_counts[1], (unsigned long long)ns);
+        }
+    }
+    if (COUNT) {
+        atomicAdd(&counters[0], (unsigned long long)(n_primary + n_shadow));
+        atomicAdd(&counters[1], (unsigned long long)n_primary);
+        atomicAdd(&counters[2], (unsigned long long)n_shadow);
+        atomicAdd(&counters[3], (unsigned long long)wc.nodes);
+        atomicAdd(&counters[4], (unsigned long long)wc.boxes);
+        atomicAdd(&counters[5], (unsigned long long)wc.tris);
+        atomicAdd(&counters[6], (unsigned long long)wc.spheres);
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_debug_trace(SceneDev S, int64_t n, const float4* __restrict__ ot,
+                                                       const float4* __restrict__ dt, int any, int brute,
+                                                       float* __restrict__ t_out, int32_t* __restrict__ prim_out,
+                                                       int* status) {
+    extern __shared__ uint2 s_stack[];
+    uint2* stack = s_stack + threadIdx.x;
+    bool overflow = false;
+    WorkCount wc{0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = ot[i], b = dt[i];
+        RayF r{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
+        Hit h;
+        if (brute) h = any ? traverse_brute<true>(S, r) : traverse_brute<false>(S, r);
+        else h = any ? traverse<true, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc)
+                     : traverse<false, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc);
+        if (any) {
+            prim_out[i] = h.rec >= 0 ? 1 : 0;
+            t_out[i] = 0.f;
+        } else {
+            prim_out[i] = h.rec < 0 ? -1 : (int32_t)h.id;
+            t_out[i] = h.rec < 0 ? __int_as_float(0x7f800000) : h.t;
+        }
+    }
+    if (overflow) atomicExch(&status[0], 1);
+}
+
+__global__ void k_pack_rgb(const float4* __restrict__ img, float* __restrict__ rgb, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 c = img[i];
+        rgb[3 * i] = c.x;
+        rgb[3 * i + 1] = c.y;
+        rgb[3 * i + 2] = c.z;
+    }
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <int BLOCK, bool FUSED, bool COUNT>
+rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
+                          int64_t total_chunks, const float4* rays, unsigned* d_work, int* d_status,
+                          unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
+    auto kern = k_trace<BLOCK, FUSED, COUNT>;
+    const size_t smem = sizeof(uint2) * (size_t)cfg.stack * BLOCK;
+    if (smem > 48 * 1024) RCP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = cfg.blocks_per_sm;
+    if (per_sm <= 0) {
+        RCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem));
+        if (per_sm <= 0) per_sm = 1;
+    }
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    const int64_t need = (total_chunks * 32 + BLOCK - 1) / BLOCK;
+    if (grid > need) grid = need > 0 ? need : 1;
+    kern<<<(int)grid, BLOCK, smem, st>>>(S, d_views, n_views, total_chunks, cfg.chunk / 32, rays, d_work, cfg.stack,
+                                         d_status, d_rays, d_counters);
+    RCP_CUDA(cudaGetLastError());
+    return RCP_OK;
+}
+
+template <bool FUSED, bool COUNT>
+rcp_status launch_trace_b(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
+                          int64_t total_chunks, const float4* rays, unsigned* d_work, int* d_status,
+                          unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
+    switch (cfg.block) {
+        case 64:
+            return launch_trace_t<64, FUSED, COUNT>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+                                                    d_rays, d_counters, st);
+        case 256:
+            return launch_trace_t<256, FUSED, COUNT>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+                                                     d_rays, d_counters, st);
+        default:
+            return launch_trace_t<128, FUSED, COUNT>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+                                                     d_rays, d_counters, st);
+    }
+}
+
+}  // namespace
+
+rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
+                       int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work, int* d_status,
+                       unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
+    if (!cfg.fused) {
+        int64_t g = (total_pix + 255) / 256;
+        if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
+        if (g < 1) g = 1;
+        k_camera<<<(int)g, 256, 0, st>>>(d_views, n_views, total_pix, S.tmin, rays);
+        RCP_CUDA(cudaGetLastError());
+    }
+    if (cfg.count)
+        return cfg.fused ? launch_trace_b<true, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+                                                      d_rays, d_counters, st)
+                         : launch_trace_b<false, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                       d_status, d_rays, d_counters, st);
+    return cfg.fused ? launch_trace_b<true, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+                                                   d_rays, d_counters, st)
+                     : launch_trace_b<false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+                                                    d_rays, d_counters, st);
+}
+
+rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
+                              int brute, float* t_out, int32_t* prim_out, int* d_status, cudaStream_t st) {
+    if (n <= 0) return RCP_OK;
+    const size_t smem = sizeof(uint2) * MAX_STACK * 128;
+    RCP_CUDA(cudaFuncSetAttribute(k_debug_trace<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t g = (n + 127) / 128;
+    if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+    k_debug_trace<128><<<(int)g, 128, smem, st>>>(S, n, (const float4*)orig_tmin, (const float4*)dir_tmax, any, brute,
+                                                 t_out, prim_out, d_status);
+    RCP_CUDA(cudaGetLastError());
+    return RCP_OK;
+}
+
+rcp_status launch_pack_rgb(const float4* img, float* rgb, int64_t n, cudaStream_t st) {
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
+    if (g < 1) g = 1;
+    k_pack_rgb<<<(int)g, 256, 0, st>>>(img, rgb, n);
+    RCP_CUDA(cudaGetLastError());
+    return RCP_OK;
+}
+
+}  // namespace rcp

@@ -1,0 +1,397 @@
+// trace.cuh -- device functions of one recursive-camera-painting pass.
+//
+//  * camera_ray: the per-pixel camera of §2 (Eq. 2-4) and §3 (Eq. 5);
+//  * traverse<ANY>: closest-hit (ANY = false) or any-hit (ANY = true) walk of
+//    the compressed 8-wide BVH with a per-thread stack in shared memory;
+//  * hit_triangle / hit_sphere: Moller-Trumbore and the analytic sphere test;
+//  * shade_*: Lambert + ambient with a shadow ray, sky on a miss.
+// All arithmetic is float32 with explicit fused multiply-adds, so every kernel
+// that calls these functions computes bit-identical results for the same ray.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rcp_internal.cuh"
+
+namespace rcp {
+
+struct RayF {
+    float ox, oy, oz;
+    float dx, dy, dz;
+    float tmin, tmax;
+};
+
+struct Hit {
+    float t;
+    uint32_t id;   // caller's primitive id (SPHERE_BIT cleared), 0xffffffff = miss
+    int32_t rec;   // record index of the hit, -1 = miss
+};
+
+struct WorkCount {
+    uint32_t nodes, boxes, tris, spheres;
+};
+
+__device__ __forceinline__ float fdot(float ax, float ay, float az, float bx, float by, float bz) {
+    return __fmaf_rn(ax, bx, __fmaf_rn(ay, by, __fmul_rn(az, bz)));
+}
+
+// Camera of pixel (x, y) from its previous value c = (r, g, b, z).
+//   g   = eye -> focal-plane point P_p - P_e (precomputed terms, see ViewDev)
+//   V   = k ((2r-1) right + (2g-1) up + (2b-1) forward)             (Eq. 5)
+//   EYE:    origin P_e + V, direction normalize(g - V)   (P'_e = P_e + V_e)
+//   TARGET: origin P_e,     direction normalize(g + V)   (P'_p = P_p + V_p)
+//   DEPTH:  origin P_e,     direction normalize(g + |z - z0| V)       (Eq. 7)
+// The direction is P'_p - P'_e (Eq. 2) formed from the offsets, not from the
+// absolute positions, which avoids cancellation in float32.
+__device__ __forceinline__ RayF camera_ray(const ViewDev& v, int x, int y, float4 c, float tmin) {
+    const float ix = (float)(2 * x + 1 - v.W);
+    const float iy = (float)(v.H - 2 * y - 1);
+    float gx = __fmaf_rn(ix, v.fR[0], __fmaf_rn(iy, v.fU[0], v.fF[0]));
+    float gy = __fmaf_rn(ix, v.fR[1], __fmaf_rn(iy, v.fU[1], v.fF[1]));
+    float gz = __fmaf_rn(ix, v.fR[2], __fmaf_rn(iy, v.fU[2], v.fF[2]));
+    const float dr = __fmaf_rn(2.f, c.x, -1.f), dg = __fmaf_rn(2.f, c.y, -1.f), db = __fmaf_rn(2.f, c.z, -1.f);
+    const float Vx = __fmaf_rn(dr, v.kR[0], __fmaf_rn(dg, v.kU[0], __fmul_rn(db, v.kF[0])));
+    const float Vy = __fmaf_rn(dr, v.kR[1], __fmaf_rn(dg, v.kU[1], __fmul_rn(db, v.kF[1])));
+    const float Vz = __fmaf_rn(dr, v.kR[2], __fmaf_rn(dg, v.kU[2], __fmul_rn(db, v.kF[2])));
+    RayF r;
+    r.tmin = tmin;
+    r.tmax = __int_as_float(0x7f800000);
+    if (v.mapping == RCP_MAP_EYE) {
+        r.ox = __fadd_rn(v.E[0], Vx);
+        r.oy = __fadd_rn(v.E[1], Vy);
+        r.oz = __fadd_rn(v.E[2], Vz);
+        gx = __fsub_rn(gx, Vx);
+        gy = __fsub_rn(gy, Vy);
+        gz = __fsub_rn(gz, Vz);
+    } else {
+        const float m = v.mapping == RCP_MAP_DEPTH ? fabsf(__fsub_rn(c.w, v.z0)) : 1.f;
+        r.ox = v.E[0];
+        r.oy = v.E[1];
+        r.oz = v.E[2];
+        gx = __fmaf_rn(m, Vx, gx);
+        gy = __fmaf_rn(m, Vy, gy);
+        gz = __fmaf_rn(m, Vz, gz);
+    }
+    const float len2 = fdot(gx, gy, gz, gx, gy, gz);
+    if (len2 > 0.f) {
+        const float inv = __fdiv_rn(1.f, __fsqrt_rn(len2));
+        r.dx = __fmul_rn(gx, inv);
+        r.dy = __fmul_rn(gy, inv);
+        r.dz = __fmul_rn(gz, inv);
+    } else {  // P'_p == P'_e: look along the view axis
+        const float l = __fsqrt_rn(fdot(v.fF[0], v.fF[1], v.fF[2], v.fF[0], v.fF[1], v.fF[2]));
+        r.dx = __fdiv_rn(v.fF[0], l);
+        r.dy = __fdiv_rn(v.fF[1], l);
+        r.dz = __fdiv_rn(v.fF[2], l);
+    }
+    return r;
+}
+
+// Moller-Trumbore on a record (v0, e1, e2); closed bounds on u, v, u + v.
+// Returns the hit distance or +inf.
+__device__ __forceinline__ float hit_triangle(const RayF& r, float4 w0, float4 w1, float4 w2) {
+    const float e1x = w0.w, e1y = w1.x, e1z = w1.y;
+    const float e2x = w1.z, e2y = w1.w, e2z = w2.x;
+    const float px = __fmaf_rn(r.dy, e2z, -__fmul_rn(r.dz, e2y));
+    const float py = __fmaf_rn(r.dz, e2x, -__fmul_rn(r.dx, e2z));
+    const float pz = __fmaf_rn(r.dx, e2y, -__fmul_rn(r.dy, e2x));
+    const float det = fdot(e1x, e1y, e1z, px, py, pz);
+    const float tx = __fsub_rn(r.ox, w0.x), ty = __fsub_rn(r.oy, w0.y), tz = __fsub_rn(r.oz, w0.z);
+    const float un = fdot(tx, ty, tz, px, py, pz);
+    const float qx = __fmaf_rn(ty, e1z, -__fmul_rn(tz, e1y));
+    const float qy = __fmaf_rn(tz, e1x, -__fmul_rn(tx, e1z));
+    const float qz = __fmaf_rn(tx, e1y, -__fmul_rn(ty, e1x));
+    const float vn = fdot(r.dx, r.dy, r.dz, qx, qy, qz);
+    const float tn = fdot(e2x, e2y, e2z, qx, qy, qz);
+    const float inv = __frcp_rn(det);
+    const float u = __fmul_rn(un, inv), v = __fmul_rn(vn, inv), t = __fmul_rn(tn, inv);
+    const bool ok = (u >= 0.f) & (v >= 0.f) & (__fadd_rn(u, v) <= 1.f);
+    return ok ? t : __int_as_float(0x7f800000);
+}
+
+// Analytic sphere: roots -b -/+ sqrt(r^2 - |oc - b d|^2), oc = o - c, b = oc.d.
+// Returns the nearer root above tmin, else the farther, else +inf.
+__device__ __forceinline__ float hit_sphere(const RayF& r, float4 w0) {
+    const float ocx = __fsub_rn(r.ox, w0.x), ocy = __fsub_rn(r.oy, w0.y), ocz = __fsub_rn(r.oz, w0.z);
+    const float b = fdot(ocx, ocy, ocz, r.dx, r.dy, r.dz);
+    const float qx = __fmaf_rn(-b, r.dx, ocx), qy = __fmaf_rn(-b, r.dy, ocy), qz = __fmaf_rn(-b, r.dz, ocz);
+    const float disc = __fmaf_rn(w0.w, w0.w, -fdot(qx, qy, qz, qx, qy, qz));
+    if (!(disc >= 0.f)) return __int_as_float(0x7f800000);
+    const float s = __fsqrt_rn(disc);
+    const float t0 = __fsub_rn(-b, s), t1 = __fadd_rn(-b, s);
+    if (t0 > r.tmin) return t0;
+    if (t1 > r.tmin) return t1;
+    return __int_as_float(0x7f800000);
+}
+
+// byte `b` of a word as the float 1 + b/256 (exact)
+__device__ __forceinline__ float qbyte(uint32_t w, int sh) {
+    return __uint_as_float(0x3f800000u | (((w >> sh) & 0xffu) << 15));
+}
+
+// Map an 8-bit slot mask to traversal order: bit i <- bit (i ^ oct).
+__device__ __forceinline__ uint32_t to_order(uint32_t m, uint32_t oct) {
+    if (oct & 1u) m = ((m & 0x55u) << 1) | ((m >> 1) & 0x55u);
+    if (oct & 2u) m = ((m & 0x33u) << 2) | ((m >> 2) & 0x33u);
+    if (oct & 4u) m = ((m & 0x0fu) << 4) | ((m >> 4) & 0x0fu);
+    return m;
+}
+
+// 1 + 2^-17: relative slack on the far end of a box interval. Boxes are padded
+// at build time by 2^-18 of the node extent; together these cover float32
+// rounding of the slab test, so the box test never misses a primitive hit.
+#define RCP_BOX_SLACK 1.0000076f
+
+template <bool ANY, bool COUNT>
+__device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2* stack, int stride, int stack_limit,
+                                        bool& overflow, WorkCount& wc) {
+    Hit h;
+    h.t = r.tmax;
+    h.id = 0xffffffffu;
+    h.rec = -1;
+    if (S.n_nodes == 0) return h;
+    const float tiny = 1e-20f;
+    const float dx = fabsf(r.dx) > tiny ? r.dx : copysignf(tiny, r.dx);
+    const float dy = fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy);
+    const float dz = fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz);
+    const float idx = __frcp_rn(dx), idy = __frcp_rn(dy), idz = __frcp_rn(dz);
+    const uint32_t oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
+    float tfar_lim = __fmul_rn(h.t, RCP_BOX_SLACK);
+
+    // node group: x = first child node index, y = imask | (hits in traversal order) << 8
+    uint2 group = make_uint2(0u, 1u | ((1u << oct) << 8));
+    uint32_t prim_base = 0, prim_mask = 0;
+    int sp = 0;
+    // a valid BVH is a tree whose child indices grow, so every node is entered
+    // at most once; the cap only turns a corrupted structure into an error
+    for (uint32_t iter = 0;; ++iter) {
+        if (iter > (1u << 24)) {
+            overflow = true;
+            break;
+        }
+        if (group.y > 0xffu) {
+            const uint32_t hits = group.y >> 8;
+            const uint32_t i = __ffs(hits) - 1;
+            group.y &= ~(1u << (i + 8));
+            const uint32_t slot = i ^ oct;
+            const uint32_t node = group.x + __popc(group.y & 0xffu & ((1u << slot) - 1u));
+            if (group.y > 0xffu) {
+                if (sp < stack_limit) {
+                    stack[sp * stride] = group;
+                    ++sp;
+                } else {
+                    overflow = true;
+                }
+            }
+            const uint4* np = S.nodes + 5 * (size_t)node;
+            const uint4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2), d = __ldg(np + 3), e = __ldg(np + 4);
+            if (COUNT) wc.nodes++;
+            // slab terms: t(q) = (1 + q/256) * Sa + Oa = (p + q 2^e - o) / d
+            const float sx = __uint_as_float(((a.w & 0xffu) + 8u) << 23);  // 2^(ex-127) * 256
+            const float sy = __uint_as_float((((a.w >> 8) & 0xffu) + 8u) << 23);
+            const float sz = __uint_as_float((((a.w >> 16) & 0xffu) + 8u) << 23);
+            const float Sx = __fmul_rn(sx, idx), Sy = __fmul_rn(sy, idy), Sz = __fmul_rn(sz, idz);
+            const float Ox = __fsub_rn(__fmul_rn(__fsub_rn(__uint_as_float(a.x), r.ox), idx), Sx);
+            const float Oy = __fsub_rn(__fmul_rn(__fsub_rn(__uint_as_float(a.y), r.oy), idy), Sy);
+            const float Oz = __fsub_rn(__fmul_rn(__fsub_rn(__uint_as_float(a.z), r.oz), idz), Sz);
+            // near/far byte words per axis from the ray's direction signs
+            const uint32_t nx0 = (oct & 1u) ? d.z : c.x, nx1 = (oct & 1u) ? d.w : c.y;
+            const uint32_t fx0 = (oct & 1u) ? c.x : d.z, fx1 = (oct & 1u) ? c.y : d.w;
+            const uint32_t ny0 = (oct & 2u) ? e.x : c.z, ny1 = (oct & 2u) ? e.y : c.w;
+            const uint32_t fy0 = (oct & 2u) ? c.z : e.x, fy1 = (oct & 2u) ? c.w : e.y;
+            const uint32_t nz0 = (oct & 4u) ? e.z : d.x, nz1 = (oct & 4u) ? e.w : d.y;
+            const uint32_t fz0 = (oct & 4u) ? d.x : e.z, fz1 = (oct & 4u) ? d.y : e.w;
+            uint32_t hitmask = 0;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int sh = 8 * (s & 3);
+                const uint32_t wnx = s < 4 ? nx0 : nx1, wfx = s < 4 ? fx0 : fx1;
+                const uint32_t wny = s < 4 ? ny0 : ny1, wfy = s < 4 ? fy0 : fy1;
+                const uint32_t wnz = s < 4 ? nz0 : nz1, wfz = s < 4 ? fz0 : fz1;
+                const float t0x = __fmaf_rn(qbyte(wnx, sh), Sx, Ox);
+                const float t1x = __fmaf_rn(qbyte(wfx, sh), Sx, Ox);
+                const float t0y = __fmaf_rn(qbyte(wny, sh), Sy, Oy);
+                const float t1y = __fmaf_rn(qbyte(wfy, sh), Sy, Oy);
+                const float t0z = __fmaf_rn(qbyte(wnz, sh), Sz, Oz);
+                const float t1z = __fmaf_rn(qbyte(wfz, sh), Sz, Oz);
+                const float tn = fmaxf(fmaxf(t0x, t0y), fmaxf(t0z, r.tmin));
+                const float tf = fminf(fminf(t1x, t1y), t1z);
+                const bool hit = tn <= fminf(__fmul_rn(tf, RCP_BOX_SLACK), tfar_lim);
+                hitmask |= (hit ? 1u : 0u) << s;
+            }
+            const uint32_t ml = b.z, mh = b.w;
+            // non-empty slots: bytes of meta that are not zero
+            uint32_t nonempty = 0;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) nonempty |= ((((s < 4 ? ml : mh) >> (8 * (s & 3))) & 0xffu) != 0u ? 1u : 0u) << s;
+            hitmask &= nonempty;
+            if (COUNT) wc.boxes += __popc(nonempty);
+            const uint32_t imask = a.w >> 24;
+            const uint32_t hint = hitmask & imask;
+            uint32_t hleaf = hitmask & ~imask;
+            group = make_uint2(b.x, imask | (to_order(hint, oct) << 8));
+            prim_base = b.y;
+            prim_mask = 0;
+            while (hleaf) {
+                const uint32_t s = __ffs(hleaf) - 1;
+                hleaf &= hleaf - 1;
+                const uint32_t mb = ((s < 4 ? ml : mh) >> (8 * (s & 3))) & 0xffu;
+                prim_mask |= ((1u << (mb >> 5)) - 1u) << (mb & 31u);
+            }
+        } else if (prim_mask == 0) {
+            if (sp == 0) break;
+            --sp;
+            group = stack[sp * stride];
+            continue;
+        }
+        while (prim_mask) {
+            const uint32_t j = __ffs(prim_mask) - 1;
+            prim_mask &= prim_mask - 1;
+            const int32_t rec = (int32_t)(prim_base + j);
+            const float4* pp = S.prims + 3 * (size_t)rec;
+            const float4 w0 = __ldg(pp), w1 = __ldg(pp + 1), w2 = __ldg(pp + 2);
+            const uint32_t idb = __float_as_uint(w2.y);
+            float t;
+            if (idb & SPHERE_BIT) {
+                t = hit_sphere(r, w0);
+                if (COUNT) wc.spheres++;
+            } else {
+                t = hit_triangle(r, w0, w1, w2);
+                if (COUNT) wc.tris++;
+            }
+            const uint32_t id = idb & ~SPHERE_BIT;
+            if (t > r.tmin && (t < h.t || (t == h.t && id < h.id))) {
+                h.t = t;
+                h.id = id;
+                h.rec = rec;
+                if (ANY) return h;
+                tfar_lim = __fmul_rn(h.t, RCP_BOX_SLACK);
+            }
+        }
+    }
+    return h;
+}
+
+// Brute force over every record (correctness reference for the BVH walk).
+template <bool ANY>
+__device__ __forceinline__ Hit traverse_brute(const SceneDev& S, const RayF& r) {
+    Hit h;
+    h.t = r.tmax;
+    h.id = 0xffffffffu;
+    h.rec = -1;
+    for (int64_t rec = 0; rec < S.n_prims; ++rec) {
+        const float4* pp = S.prims + 3 * rec;
+        const float4 w0 = __ldg(pp), w1 = __ldg(pp + 1), w2 = __ldg(pp + 2);
+        const uint32_t idb = __float_as_uint(w2.y);
+        const float t = (idb & SPHERE_BIT) ? hit_sphere(r, w0) : hit_triangle(r, w0, w1, w2);
+        const uint32_t id = idb & ~SPHERE_BIT;
+        if (t > r.tmin && (t < h.t || (t == h.t && id < h.id))) {
+            h.t = t;
+            h.id = id;
+            h.rec = (int32_t)rec;
+            if (ANY) return h;
+        }
+    }
+    return h;
+}
+
+// What a primary hit needs for its final colour.
+struct ShadeInfo {
+    float4 c_shadow;  // colour if the shadow ray is blocked (or not cast), depth in w
+    float4 c_lit;     // colour if the light is visible
+    RayF shadow;      // the shadow ray (valid when need_shadow)
+    bool need_shadow;
+};
+
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
+
+// Shading of §2 stage 2 (reading: the paper gives no shading model):
+// hit -> albedo * (a + (1 - a) V max(0, N.L)), N facing the ray; miss -> sky
+// (1 - s)(1,1,1) + s (0.5, 0.7, 1), s = (d_y + 1)/2; clamped to [0, 1].
+__device__ __forceinline__ ShadeInfo shade_primary(const SceneDev& S, const RayF& r, const Hit& h) {
+    ShadeInfo si;
+    si.need_shadow = false;
+    if (h.rec < 0) {
+        const float s = __fmul_rn(0.5f, __fadd_rn(r.dy, 1.f));
+        const float one_s = __fsub_rn(1.f, s);
+        si.c_shadow = make_float4(clamp01(__fmaf_rn(s, 0.5f, one_s)), clamp01(__fmaf_rn(s, 0.7f, one_s)),
+                                  clamp01(__fadd_rn(one_s, s)), 0.f);
+        si.c_lit = si.c_shadow;
+        return si;
+    }
+    const float4* pp = S.prims + 3 * (size_t)h.rec;
+    const float4 w0 = __ldg(pp), w1 = __ldg(pp + 1), w2 = __ldg(pp + 2);
+    const float px = __fmaf_rn(h.t, r.dx, r.ox), py = __fmaf_rn(h.t, r.dy, r.oy), pz = __fmaf_rn(h.t, r.dz, r.oz);
+    float nx, ny, nz;
+    if (__float_as_uint(w2.y) & SPHERE_BIT) {
+        const float ir = __frcp_rn(w0.w);
+        nx = __fmul_rn(__fsub_rn(px, w0.x), ir);
+        ny = __fmul_rn(__fsub_rn(py, w0.y), ir);
+        nz = __fmul_rn(__fsub_rn(pz, w0.z), ir);
+    } else {
+        const float e1x = w0.w, e1y = w1.x, e1z = w1.y, e2x = w1.z, e2y = w1.w, e2z = w2.x;
+        nx = __fmaf_rn(e1y, e2z, -__fmul_rn(e1z, e2y));
+        ny = __fmaf_rn(e1z, e2x, -__fmul_rn(e1x, e2z));
+        nz = __fmaf_rn(e1x, e2y, -__fmul_rn(e1y, e2x));
+        const float il = __fdiv_rn(1.f, __fsqrt_rn(fdot(nx, ny, nz, nx, ny, nz)));
+        nx = __fmul_rn(nx, il);
+        ny = __fmul_rn(ny, il);
+        nz = __fmul_rn(nz, il);
+    }
+    if (fdot(nx, ny, nz, r.dx, r.dy, r.dz) > 0.f) {
+        nx = -nx;
+        ny = -ny;
+        nz = -nz;
+    }
+    float lx, ly, lz;
+    if (S.light.type == RCP_LIGHT_POINT) {
+        lx = __fsub_rn(S.light.x, px);
+        ly = __fsub_rn(S.light.y, py);
+        lz = __fsub_rn(S.light.z, pz);
+        const float il = __fdiv_rn(1.f, __fsqrt_rn(fdot(lx, ly, lz, lx, ly, lz)));
+        lx = __fmul_rn(lx, il);
+        ly = __fmul_rn(ly, il);
+        lz = __fmul_rn(lz, il);
+    } else {
+        lx = S.light.x;
+        ly = S.light.y;
+        lz = S.light.z;
+    }
+    const float ndl = fdot(nx, ny, nz, lx, ly, lz);
+    const float a = S.light.ambient;
+    const float4 alb = __ldg(S.albedo + h.id);
+    si.c_shadow = make_float4(clamp01(__fmul_rn(alb.x, a)), clamp01(__fmul_rn(alb.y, a)),
+                              clamp01(__fmul_rn(alb.z, a)), h.t);
+    if (ndl > 0.f) {
+        const float lit = __fmaf_rn(__fsub_rn(1.f, a), ndl, a);
+        si.c_lit = make_float4(clamp01(__fmul_rn(alb.x, lit)), clamp01(__fmul_rn(alb.y, lit)),
+                               clamp01(__fmul_rn(alb.z, lit)), h.t);
+        si.need_shadow = true;
+        RayF s;
+        s.ox = __fmaf_rn(S.eps, nx, px);
+        s.oy = __fmaf_rn(S.eps, ny, py);
+        s.oz = __fmaf_rn(S.eps, nz, pz);
+        s.tmin = 0.f;
+        if (S.light.type == RCP_LIGHT_POINT) {
+            float sx = __fsub_rn(S.light.x, s.ox), sy = __fsub_rn(S.light.y, s.oy), sz = __fsub_rn(S.light.z, s.oz);
+            const float dist = __fsqrt_rn(fdot(sx, sy, sz, sx, sy, sz));
+            const float il = __fdiv_rn(1.f, dist);
+            s.dx = __fmul_rn(sx, il);
+            s.dy = __fmul_rn(sy, il);
+            s.dz = __fmul_rn(sz, il);
+            s.tmax = dist;
+        } else {
+            s.dx = lx;
+            s.dy = ly;
+            s.dz = lz;
+            s.tmax = __int_as_float(0x7f800000);
+        }
+        si.shadow = s;
+    } else {
+        si.c_lit = si.c_shadow;
+    }
+    return si;
+}
+
+}  // namespace rcp

@@ -1,0 +1,158 @@
+"""GPU tests of the BVH builder's parts: radix sort, Morton codes, tree
+validity, and BVH traversal against brute force over every primitive."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2312_12392_gb300 import rcp, scenes  # noqa: E402
+import gpu_util as U  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3839, 3840, 3841, 100_003, 1_000_000])
+@pytest.mark.parametrize("bits", [30, 32])
+def test_radix_sort_matches_stable_sort(n, bits):
+    rng = np.random.default_rng(n + bits)
+    hi = 1 << bits
+    keys = rng.integers(0, hi, size=n, dtype=np.uint64).astype(np.uint32)
+    if n > 10:
+        keys[: n // 3] = keys[0]  # many duplicates: stability matters
+        rng.shuffle(keys)
+    vals = np.arange(n, dtype=np.uint32)
+    dk, dv = _dev(keys.view(np.int32)), _dev(vals.view(np.int32))
+    rcp.rcp_debug_sort_pairs(dk, dv, n, bits)
+    torch.cuda.synchronize()
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(dk.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(dv.cpu().numpy().view(np.uint32), vals[order])
+
+
+def _morton_ref(p, lo, hi):
+    q = np.clip(((p - lo) / (hi - lo) * 1024.0).astype(np.int64), 0, 1023)
+    code = np.zeros(len(p), np.int64)
+    for b in range(10):
+        for a in range(3):
+            code |= ((q[:, a] >> b) & 1) << (3 * b + (2 - a))
+    return code.astype(np.uint32)
+
+
+def test_morton_codes():
+    rng = np.random.default_rng(3)
+    p = rng.uniform(-5, 7, size=(50_000, 3)).astype(np.float32)
+    lo = np.array([-5, -5, -5], np.float32)
+    hi = np.array([7, 7, 7], np.float32)
+    codes = torch.empty(len(p), dtype=torch.int32, device="cuda")
+    rcp.rcp_debug_morton(_dev(p), len(p), lo, hi, codes)
+    got = codes.cpu().numpy().view(np.uint32)
+    want = _morton_ref(p.astype(np.float32), lo, hi)
+    # the kernel normalises in float32; allow codes to differ only where a
+    # coordinate sits on a cell boundary
+    diff = got != want
+    assert diff.mean() < 1e-3
+    # corners
+    corners = np.array([[-5, -5, -5], [7 - 1e-4, 7 - 1e-4, 7 - 1e-4]], np.float32)
+    codes2 = torch.empty(2, dtype=torch.int32, device="cuda")
+    rcp.rcp_debug_morton(_dev(corners), 2, lo, hi, codes2)
+    c = codes2.cpu().numpy().view(np.uint32)
+    assert c[0] == 0 and c[1] == (1 << 30) - 1
+
+
+SCENES = {
+    "one_tri": lambda: scenes.random_soup(1, 0, seed=1),
+    "two_tris": lambda: scenes.random_soup(2, 0, seed=2),
+    "three_prims": lambda: scenes.random_soup(2, 1, seed=3),
+    "sphere_only": lambda: scenes.random_soup(0, 5, seed=4),
+    "tiny": lambda: scenes.tiny_scene(),
+    "soup_10k": lambda: scenes.random_soup(10_000, 50, seed=5),
+    "soup_dupes": lambda: _dupes(),
+    "mid": lambda: scenes.mid_scene(),
+}
+
+
+def _dupes():
+    sc = scenes.random_soup(3000, 0, seed=9, extent=1.0, tri_size=0.01)
+    sc.tris[1000:2000] = sc.tris[0]  # identical centroids -> identical Morton codes
+    return sc
+
+
+@pytest.mark.parametrize("name", sorted(SCENES))
+def test_bvh_valid(name):
+    sc = SCENES[name]()
+    g = U.gpu_scene(sc)
+    try:
+        rcp.rcp_scene_validate(g)
+        info = rcp.rcp_scene_get_info(g)
+        assert info.n_tris == sc.n_tris and info.n_spheres == sc.n_spheres
+        assert 1 <= info.max_leaf <= 3
+        assert info.depth >= 1 and info.n_nodes >= 1
+        assert abs(info.diam - sc.diameter()) <= 1e-5 * sc.diameter() + 1e-6
+    finally:
+        rcp.rcp_scene_destroy(g)
+
+
+@pytest.mark.parametrize("name", ["tiny", "soup_10k", "soup_dupes", "three_prims", "sphere_only", "mid"])
+@pytest.mark.parametrize("any_hit", [0, 1])
+def test_bvh_equals_brute_force(name, any_hit):
+    """The BVH walk returns exactly what testing every primitive returns:
+    same primitive ids, bit-identical distances (the box test is conservative
+    and ties go to the lower id in both)."""
+    sc = SCENES[name]()
+    g = U.gpu_scene(sc)
+    try:
+        ext = max(sc.diameter() / 4, 1.0)
+        n = 20_000 if name != "mid" else 4_000
+        ot, dt = U.random_rays(n, seed=17, extent=ext, towards=(0, 0, 0))
+        if any_hit:
+            dt[:, 3] = np.random.default_rng(1).uniform(0.1, 4 * ext, n).astype(np.float32)
+        res = []
+        for brute in (0, 1):
+            t = torch.empty(n, dtype=torch.float32, device="cuda")
+            p = torch.empty(n, dtype=torch.int32, device="cuda")
+            rcp.rcp_debug_trace(g, n, _dev(ot), _dev(dt), any_hit, brute, t, p)
+            res.append((t.cpu().numpy(), p.cpu().numpy()))
+        assert np.array_equal(res[0][1], res[1][1])
+        assert np.array_equal(res[0][0], res[1][0])
+        if not any_hit:
+            assert (res[0][1] >= 0).mean() > 0.05
+    finally:
+        rcp.rcp_scene_destroy(g)
+
+
+def test_refit_after_vertex_update():
+    """Moving vertices and refitting keeps the BVH valid and its walk equal to
+    brute force on the moved geometry, and equal to a fresh build."""
+    sc = scenes.random_soup(20_000, 0, seed=21)
+    g = U.gpu_scene(sc)
+    try:
+        rng = np.random.default_rng(4)
+        moved = sc.tris + rng.normal(0, 0.3, size=sc.tris.shape).astype(np.float32)
+        rcp.rcp_scene_update_vertices(g, moved)
+        rcp.rcp_scene_validate(g)
+        fresh_sc = scenes.Scene("moved", moved, sc.spheres, sc.albedo, sc.light, sc.poses)
+        f = U.gpu_scene(fresh_sc)
+        try:
+            n = 20_000
+            ot, dt = U.random_rays(n, seed=5, extent=10.0, towards=(0, 0, 0))
+            out = []
+            for scene, brute in ((g, 0), (g, 1), (f, 0)):
+                t = torch.empty(n, dtype=torch.float32, device="cuda")
+                p = torch.empty(n, dtype=torch.int32, device="cuda")
+                rcp.rcp_debug_trace(scene, n, _dev(ot), _dev(dt), 0, brute, t, p)
+                out.append((t.cpu().numpy(), p.cpu().numpy()))
+            assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][0], out[1][0])
+            assert np.array_equal(out[0][1], out[2][1]) and np.array_equal(out[0][0], out[2][0])
+            # device-array variant
+            d = torch.from_numpy(sc.tris.copy()).cuda()
+            rcp.rcp_scene_update_vertices_device(g, d)
+            torch.cuda.synchronize()
+            rcp.rcp_scene_validate(g)
+        finally:
+            rcp.rcp_scene_destroy(f)
+    finally:
+        rcp.rcp_scene_destroy(g)

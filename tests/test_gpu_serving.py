@@ -1,0 +1,102 @@
+"""The continuous-batching server: every request's image is identical alone
+and in a mix of scenes, sizes and K (each pixel's chain is deterministic and
+independent of the other work in the launch), memory admission holds, and the
+statistics add up."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2312_12392_gb300 import rcp, scenes
+import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def two_scenes():
+    a = scenes.tiny_scene()
+    b = scenes.terrain_scene(64, seed=4, n_boxes=20)
+    ga, gb = U.gpu_scene(a), U.gpu_scene(b)
+    yield (a, ga), (b, gb)
+    rcp.rcp_scene_destroy(ga)
+    rcp.rcp_scene_destroy(gb)
+
+
+def _requests(two_scenes, n=24, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        sc, g = two_scenes[int(rng.integers(0, 2))]
+        W = int(rng.integers(8, 300))
+        H = int(rng.integers(8, 200))
+        K = int(rng.integers(1, 9))
+        cam = sc.poses[int(rng.integers(0, len(sc.poses)))]
+        d = sc.diameter()
+        f = 6.0 if sc.name == "tiny" else 0.1 * d
+        p = rcp.make_params(rcp.RCP_MAP_EYE, float(rng.uniform(0, 0.05)) * d, f)
+        out.append((g, rcp.camera_from(cam), W, H, K, p))
+    return out
+
+
+def test_alone_equals_in_mix(two_scenes):
+    reqs = _requests(two_scenes)
+    alone = [rcp.rcp_render(g, c, W, H, K, p) for g, c, W, H, K, p in reqs]
+    srv = rcp.rcp_server_create(4 << 30, 8)
+    try:
+        outs, tickets = [], []
+        for i, (g, c, W, H, K, p) in enumerate(reqs):
+            o = np.full((H, W, 3), -1.0, np.float32)
+            outs.append(o)
+            tickets.append(rcp.rcp_server_submit(srv, g, c, W, H, K, p, o))
+            if i % 5 == 4:
+                time.sleep(0.002)  # arrivals while others are in flight
+        for t in tickets:
+            rcp.rcp_server_wait(srv, t, 60.0)
+            assert rcp.rcp_server_poll(srv, t)
+        for a, o in zip(alone, outs):
+            assert np.array_equal(a, o)
+        st = rcp.rcp_server_stats_get(srv)
+        assert st.completed == len(reqs) and st.rejected == 0 and st.in_flight == 0 and st.queued == 0
+        assert st.p99_ms >= st.p50_ms > 0 and st.frames_per_s > 0 and st.mrays_per_s > 0
+        assert st.steps >= max(K for *_, K, _ in reqs)
+        assert st.device_bytes_in_use == 0 and st.device_bytes_peak > 0
+    finally:
+        rcp.rcp_server_destroy(srv)
+
+
+def test_memory_admission(two_scenes):
+    (sc, g), _ = two_scenes
+    cam = rcp.camera_from(sc.poses[0])
+    p = rcp.make_params(rcp.RCP_MAP_EYE, 1.0, 6.0)
+    W, H = 256, 256
+    per_req = W * H * 44 + 768
+    srv = rcp.rcp_server_create(2 * per_req + 100, 16)  # room for two at a time
+    try:
+        outs = [np.empty((H, W, 3), np.float32) for _ in range(6)]
+        ts = [rcp.rcp_server_submit(srv, g, cam, W, H, 3, p, o) for o in outs]
+        big = np.empty((1024, 1024, 3), np.float32)
+        tb = rcp.rcp_server_submit(srv, g, cam, 1024, 1024, 1, p, big)  # never fits
+        for t in ts:
+            rcp.rcp_server_wait(srv, t, 60.0)
+        with pytest.raises(rcp.RcpError) as e:
+            rcp.rcp_server_wait(srv, tb, 60.0)
+        assert e.value.status == rcp.RCP_ERR_OOM
+        st = rcp.rcp_server_stats_get(srv)
+        assert st.device_bytes_peak <= 2 * per_req + 100
+        assert st.completed == 6 and st.rejected == 1
+        ref = rcp.rcp_render(g, cam, W, H, 3, p)
+        for o in outs:
+            assert np.array_equal(o, ref)
+    finally:
+        rcp.rcp_server_destroy(srv)
+
+
+def test_wait_timeout_and_unknown_ticket(two_scenes):
+    srv = rcp.rcp_server_create(1 << 30, 4)
+    try:
+        with pytest.raises(rcp.RcpError) as e:
+            rcp.rcp_server_wait(srv, 12345, 0.01)
+        assert e.value.status == rcp.RCP_ERR_ARG
+    finally:
+        rcp.rcp_server_destroy(srv)
