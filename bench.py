@@ -126,6 +126,33 @@ def dist_env():
     return world, rank, local
 
 
+def shard_poses(rank, world, steps, n_poses):
+    """Pose indices rendered by one rank: each rank takes its own run of
+    `steps` consecutive poses of the walk-through (weak scaling, replicas)."""
+    return [(rank * steps + i) % n_poses for i in range(steps)]
+
+
+def max_over_ranks(value, device=None):
+    """Max of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, device=None):
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def physical_gpu(local):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -211,7 +238,7 @@ def run_ours(args):
         t = rcp.rcp_tuning(b, 0, c, fz, 0)
         rcp.rcp_set_tuning(g, t)
     log(f"[rank {rank}] tuning block={t.block} chunk={t.chunk} fused_camera={t.fused_camera}")
-    poses = [sc.poses[(rank * args.steps + i) % len(sc.poses)] for i in range(args.steps)]
+    poses = [sc.poses[i] for i in shard_poses(rank, world, args.steps, len(sc.poses))]
     cams = [rcp.camera_from(p) for p in poses]
     stream = torch.cuda.current_stream()
     out = torch.empty((H_IMG, W_IMG, 4), dtype=torch.float32, device="cuda")
@@ -244,11 +271,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
-    tmax = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt.item())
+    tmax = max_over_ranks(total_ms, "cuda")
 
     # rays traced per timed frame (deterministic per pose): replay each frame once more
     rays = 0
@@ -257,10 +280,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         p_, s_ = rcp.rcp_last_ray_counts(g)
         rays += p_ + s_
-    if world > 1:
-        rt = torch.tensor([rays], dtype=torch.float64, device="cuda")
-        dist.all_reduce(rt)
-        rays = float(rt.item())
+    rays = sum_over_ranks(rays, "cuda")
 
     # algorithmic work of a launch: chained counted passes over a few poses
     n_cnt = min(args.count_poses, len(cams))
@@ -317,11 +337,7 @@ def run_ours(args):
         rcp.rcp_render(g, cams[i % len(cams)], W_IMG, H_IMG, K_PASSES, params, host)
         if i > 0:
             e2e_t += time.perf_counter() - t0
-    e2e_fps = e2e_steps / e2e_t
-    if world > 1:
-        et = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e_fps = world * e2e_steps / float(et.item())
+    e2e_fps = world * e2e_steps / max_over_ranks(e2e_t, "cuda")
 
     frames = args.steps * world
     value = frames / (tmax / 1000.0)
@@ -455,6 +471,171 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+# ------------------------------------------------------------------ batched and served modes
+
+def run_batched(args):
+    """64 views of uneven size (W in [256,1920], H in [256,1080], seeded) of the
+    1.07M-triangle forest, K = 6: one persistent launch per pass over all views
+    (graph-captured, autotuned), against rendering the same views one after
+    another with the single-view device path."""
+    import torch
+
+    from paper_2312_12392_gb300 import build as B
+    from paper_2312_12392_gb300 import rcp, scenes
+    torch.cuda.set_device(0)
+    B.build()
+    sc, _ = make_workload("forest")
+    d = sc.diameter()
+    params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+    g = rcp.scene_from(sc)
+    sizes = scenes.batched_view_sizes(64, seed=3)
+    cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(len(sizes))]
+    t = rcp.rcp_autotune(g, cams[0], 960, 540, params,
+                         os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
+    outs = [torch.empty((h, w, 4), dtype=torch.float32, device="cuda") for w, h in sizes]
+    Ws, Hs = [w for w, _ in sizes], [h for _, h in sizes]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def batch_once():
+        rcp.rcp_render_batch_device(g, cams, Ws, Hs, K_PASSES, params, outs, stream)
+
+    def plain_once():
+        for c, (w, h), o in zip(cams, sizes, outs):
+            rcp.rcp_render_device(g, c, w, h, K_PASSES, params, None, o, None, stream)
+
+    res = {}
+    for name, fn in (("batched", batch_once), ("plain", plain_once)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            ms.append(s.elapsed_time(e))
+        res[name] = statistics.mean(ms)
+    pix = sum(w * h for w, h in sizes)
+    batch_once()
+    torch.cuda.synchronize()
+    p_, s_ = rcp.rcp_last_ray_counts(g)
+    out = {
+        "metric": "views_per_s (64 uneven views, K=6 each, one launch per pass)",
+        "value": len(sizes) / (res["batched"] / 1000.0),
+        "unit": "views/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["batched"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, graph-captured",
+                   "l2": "flushed between steps", "tuning": {"block": t.block, "chunk": t.chunk,
+                                                             "fused_camera": t.fused_camera}},
+        "mrays_per_s": (p_ + s_) / (res["batched"] / 1000.0) / 1e6,
+        "plain_ms_per_step": res["plain"],
+        "plain_views_per_s": len(sizes) / (res["plain"] / 1000.0),
+        "speedup_vs_plain": res["plain"] / res["batched"],
+        "gpu_launches": args.steps * K_PASSES,
+    }
+    rcp.rcp_scene_destroy(g)
+    print(json.dumps(out), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals over 4 resident terrain scenes (0.1M, 1M, 3M, 5M tris);
+    each request: a walk-through pose, 720p/1080p/1440p/2160p, K in 1..8,
+    k in [0, 0.05] * diameter. The continuous-batching server against the plain
+    path (one request at a time, FIFO, each its own launch sequence), same
+    arrivals. Reports frames/s and p50/p99 latency per arrival rate."""
+    import threading
+
+    import torch
+
+    from paper_2312_12392_gb300 import build as B
+    from paper_2312_12392_gb300 import rcp, scenes
+    torch.cuda.set_device(0)
+    B.build()
+    grids = [221, 706, 1224, 1580]
+    scs = [scenes.terrain_scene(gsz, seed=4) for gsz in grids]
+    gs = [rcp.scene_from(s) for s in scs]
+    n_req = args.steps
+    reqs = scenes.served_requests(n_req, len(scs), 64, seed=4)
+    bufs = {}
+
+    def buf(w, h, slot):
+        key = (w, h, slot % 48)
+        if key not in bufs:
+            bufs[key] = np.empty((h, w, 3), np.float32)
+        return bufs[key]
+
+    def params_of(r):
+        d = scs[r["scene"]].diameter()
+        return rcp.make_params(rcp.RCP_MAP_EYE, r["k_frac"] * d, 0.1 * d)
+
+    def cam_of(r):
+        return rcp.camera_from(scs[r["scene"]].poses[r["pose"]])
+
+    for g in gs:  # warm both paths
+        rcp.rcp_render(g, cam_of(reqs[0]), 640, 360, 2, params_of(reqs[0]))
+    rates = [float(x) for x in args.rates.split(",")]
+    table = []
+    for lam in rates:
+        arr = scenes.poisson_arrivals(lam, n_req, seed=4)
+        # -- plain: FIFO worker, one request at a time
+        lat = [0.0] * n_req
+        t0 = time.perf_counter()
+
+        def plain_worker():
+            for i, r in enumerate(reqs):
+                wait = arr[i] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                rcp.rcp_render(gs[r["scene"]], cam_of(r), r["width"], r["height"], r["K"], params_of(r),
+                               buf(r["width"], r["height"], i))
+                lat[i] = time.perf_counter() - t0 - arr[i]
+
+        th = threading.Thread(target=plain_worker)
+        th.start()
+        th.join()
+        plain_span = time.perf_counter() - t0
+        plain = {"frames_per_s": n_req / plain_span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                 "p99_ms": 1000 * float(np.percentile(lat, 99))}
+        # -- server: submit at the arrival times
+        srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+        t0 = time.perf_counter()
+        tickets = []
+        for i, r in enumerate(reqs):
+            wait = arr[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(rcp.rcp_server_submit(srv, gs[r["scene"]], cam_of(r), r["width"], r["height"], r["K"],
+                                                 params_of(r), buf(r["width"], r["height"], i + 1000)))
+        for tk in tickets:
+            rcp.rcp_server_wait(srv, tk, 600.0)
+        st = rcp.rcp_server_stats_get(srv)
+        rcp.rcp_server_destroy(srv)
+        served = {"frames_per_s": st.frames_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                  "mrays_per_s": st.mrays_per_s, "steps": st.steps, "peak_gb": st.device_bytes_peak / 2 ** 30}
+        table.append({"rate_req_s": lam, "served": served, "plain": plain})
+        log(f"lambda={lam}: served {served} | plain {plain}")
+    best = max(table, key=lambda r: r["served"]["frames_per_s"])
+    out = {
+        "metric": "served frames_per_s and p50/p99 latency vs the plain per-request path",
+        "value": best["served"]["frames_per_s"], "unit": "frames/s",
+        "n_gpus": 1, "steps": n_req, "warmup": 1, "ms_per_step": 1000.0 / best["served"]["frames_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "4 resident terrain scenes (100,082 / 999,272 / 2,998,752 / 4,995,200 tris); "
+                               "720p-2160p, K in 1..8, Poisson arrivals",
+                   "requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb},
+        "sweep": table,
+    }
+    for g in gs:
+        rcp.rcp_scene_destroy(g)
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,15 +648,19 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-forest", dest="extra_forest", action="store_false")
+    ap.add_argument("--rates", default="10,25,50,100,200,400", help="served: arrival rates (req/s)")
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         log("warmup raised to 3 (timing rule)")
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("batched", "served"):
-        import bench_modes
-        bench_modes.run(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

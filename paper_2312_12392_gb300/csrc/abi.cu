@@ -243,17 +243,22 @@ rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t tot
 
 // Enqueue the K passes of ctx (views already staged in ctx->d_views).
 rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, unsigned long long* counters,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool capturing) {
+    // inside a capture an event record only becomes a graph node with the
+    // external flag; outside a capture the plain record is the valid call
+    auto record = [&](cudaEvent_t e) {
+        return capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+    };
     RCP_CUDA(cudaMemsetAsync(ctx.d_work, 0, sizeof(unsigned) * (ctx.K + 1), st));
     RCP_CUDA(cudaMemsetAsync(ctx.d_rays, 0, sizeof(unsigned long long) * 2, st));
     const SceneDev S = sc.dev();
-    RCP_CUDA(cudaEventRecord(ctx.pass_ev[0], st));
+    RCP_CUDA(record(ctx.pass_ev[0]));
     for (int n = 0; n < ctx.K; ++n) {
         rcp_status r = launch_pass(S, cfg, ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix,
                                    ctx.total_chunks, ctx.rays, ctx.d_work + n, ctx.d_status, ctx.d_rays, counters,
                                    st);
         if (r != RCP_OK) return r;
-        RCP_CUDA(cudaEventRecord(ctx.pass_ev[n + 1], st));
+        RCP_CUDA(record(ctx.pass_ev[n + 1]));
     }
     return RCP_OK;
 }
@@ -269,7 +274,7 @@ rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cuda
         }
         cudaStream_t cs = capture_stream();
         RCP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        rcp_status r = enqueue_passes(sc, ctx, cfg, nullptr, cs);
+        rcp_status r = enqueue_passes(sc, ctx, cfg, nullptr, cs, true);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (r != RCP_OK) {
@@ -634,7 +639,7 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
     RCP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 8, st));
     LaunchCfg cfg = cfg_of(*sc);
     cfg.count = true;
-    r = enqueue_passes(*sc, *ctx, cfg, d_cnt, st);
+    r = enqueue_passes(*sc, *ctx, cfg, d_cnt, st, false);
     unsigned long long h[8] = {0};
     if (r == RCP_OK) {
         cudaError_t e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st);

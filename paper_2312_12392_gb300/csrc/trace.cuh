@@ -125,9 +125,23 @@ __device__ __forceinline__ float hit_sphere(const RayF& r, float4 w0) {
     return __int_as_float(0x7f800000);
 }
 
-// byte `b` of a word as the float 1 + b/256 (exact)
-__device__ __forceinline__ float qbyte(uint32_t w, int sh) {
-    return __uint_as_float(0x3f800000u | (((w >> sh) & 0xffu) << 15));
+// Byte k (0..3) of a word as a float, exactly: one byte permute builds the
+// bit pattern of 2^23 + b, and subtracting 2^23 leaves b. The permute is the
+// only integer-pipe instruction; the subtraction runs on the FMA pipe.
+__device__ __forceinline__ float qbyte(uint32_t w, int k) {
+    return __fsub_rn(__uint_as_float(__byte_perm(w, 0x4b000000u, 0x7540u + (unsigned)k)), 8388608.0f);
+}
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 // Map an 8-bit slot mask to traversal order: bit i <- bit (i ^ oct).
@@ -138,8 +152,9 @@ __device__ __forceinline__ uint32_t to_order(uint32_t m, uint32_t oct) {
     return m;
 }
 
-// 1 + 2^-17: relative slack on the far end of a box interval. Boxes are padded
-// at build time by 2^-18 of the node extent; together these cover float32
+// 1 + 2^-17: relative slack on the far end of a box interval (applied to the
+// far-plane slab terms and to the current closest hit). Boxes are padded at
+// build time by 2^-18 of the node extent; together these cover float32
 // rounding of the slab test, so the box test never misses a primitive hit.
 #define RCP_BOX_SLACK 1.0000076f
 
@@ -187,14 +202,19 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
             const uint4* np = S.nodes + 5 * (size_t)node;
             const uint4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2), d = __ldg(np + 3), e = __ldg(np + 4);
             if (COUNT) wc.nodes++;
-            // slab terms: t(q) = (1 + q/256) * Sa + Oa = (p + q 2^e - o) / d
-            const float sx = __uint_as_float(((a.w & 0xffu) + 8u) << 23);  // 2^(ex-127) * 256
-            const float sy = __uint_as_float((((a.w >> 8) & 0xffu) + 8u) << 23);
-            const float sz = __uint_as_float((((a.w >> 16) & 0xffu) + 8u) << 23);
+            // slab terms: t(q) = q * Sa + Oa = (p + q 2^e - o) / d, with Sa = 2^e / d
+            // and Oa = (p - o) / d; far planes carry the relative slack
+            const float sx = __uint_as_float((a.w & 0xffu) << 23);
+            const float sy = __uint_as_float(((a.w >> 8) & 0xffu) << 23);
+            const float sz = __uint_as_float(((a.w >> 16) & 0xffu) << 23);
             const float Sx = __fmul_rn(sx, idx), Sy = __fmul_rn(sy, idy), Sz = __fmul_rn(sz, idz);
-            const float Ox = __fsub_rn(__fmul_rn(__fsub_rn(__uint_as_float(a.x), r.ox), idx), Sx);
-            const float Oy = __fsub_rn(__fmul_rn(__fsub_rn(__uint_as_float(a.y), r.oy), idy), Sy);
-            const float Oz = __fsub_rn(__fmul_rn(__fsub_rn(__uint_as_float(a.z), r.oz), idz), Sz);
+            const float Ox = __fmul_rn(__fsub_rn(__uint_as_float(a.x), r.ox), idx);
+            const float Oy = __fmul_rn(__fsub_rn(__uint_as_float(a.y), r.oy), idy);
+            const float Oz = __fmul_rn(__fsub_rn(__uint_as_float(a.z), r.oz), idz);
+            const float Sfx = __fmul_rn(Sx, RCP_BOX_SLACK), Sfy = __fmul_rn(Sy, RCP_BOX_SLACK),
+                        Sfz = __fmul_rn(Sz, RCP_BOX_SLACK);
+            const float Ofx = __fmul_rn(Ox, RCP_BOX_SLACK), Ofy = __fmul_rn(Oy, RCP_BOX_SLACK),
+                        Ofz = __fmul_rn(Oz, RCP_BOX_SLACK);
             // near/far byte words per axis from the ray's direction signs
             const uint32_t nx0 = (oct & 1u) ? d.z : c.x, nx1 = (oct & 1u) ? d.w : c.y;
             const uint32_t fx0 = (oct & 1u) ? c.x : d.z, fx1 = (oct & 1u) ? c.y : d.w;
@@ -205,28 +225,30 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
             uint32_t hitmask = 0;
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
-                const int sh = 8 * (s & 3);
+                const int k = s & 3;
                 const uint32_t wnx = s < 4 ? nx0 : nx1, wfx = s < 4 ? fx0 : fx1;
                 const uint32_t wny = s < 4 ? ny0 : ny1, wfy = s < 4 ? fy0 : fy1;
                 const uint32_t wnz = s < 4 ? nz0 : nz1, wfz = s < 4 ? fz0 : fz1;
-                const float t0x = __fmaf_rn(qbyte(wnx, sh), Sx, Ox);
-                const float t1x = __fmaf_rn(qbyte(wfx, sh), Sx, Ox);
-                const float t0y = __fmaf_rn(qbyte(wny, sh), Sy, Oy);
-                const float t1y = __fmaf_rn(qbyte(wfy, sh), Sy, Oy);
-                const float t0z = __fmaf_rn(qbyte(wnz, sh), Sz, Oz);
-                const float t1z = __fmaf_rn(qbyte(wfz, sh), Sz, Oz);
-                const float tn = fmaxf(fmaxf(t0x, t0y), fmaxf(t0z, r.tmin));
-                const float tf = fminf(fminf(t1x, t1y), t1z);
-                const bool hit = tn <= fminf(__fmul_rn(tf, RCP_BOX_SLACK), tfar_lim);
-                hitmask |= (hit ? 1u : 0u) << s;
+                const float t0x = __fmaf_rn(qbyte(wnx, k), Sx, Ox);
+                const float t1x = __fmaf_rn(qbyte(wfx, k), Sfx, Ofx);
+                const float t0y = __fmaf_rn(qbyte(wny, k), Sy, Oy);
+                const float t1y = __fmaf_rn(qbyte(wfy, k), Sfy, Ofy);
+                const float t0z = __fmaf_rn(qbyte(wnz, k), Sz, Oz);
+                const float t1z = __fmaf_rn(qbyte(wfz, k), Sfz, Ofz);
+                const float tn = fmax3(t0x, t0y, fmaxf(t0z, r.tmin));
+                const float tf = fmin3(t1x, t1y, fminf(t1z, tfar_lim));
+                hitmask |= (tn <= tf ? 1u : 0u) << s;
             }
             const uint32_t ml = b.z, mh = b.w;
-            // non-empty slots: bytes of meta that are not zero
-            uint32_t nonempty = 0;
+            // an empty slot (meta 0) that tests as hit adds no child: it is not
+            // in imask and its leaf count is 0
+            if (COUNT) {
+                uint32_t nonempty = 0;
 #pragma unroll
-            for (int s = 0; s < 8; ++s) nonempty |= ((((s < 4 ? ml : mh) >> (8 * (s & 3))) & 0xffu) != 0u ? 1u : 0u) << s;
-            hitmask &= nonempty;
-            if (COUNT) wc.boxes += __popc(nonempty);
+                for (int s = 0; s < 8; ++s)
+                    nonempty |= ((((s < 4 ? ml : mh) >> (8 * (s & 3))) & 0xffu) != 0u ? 1u : 0u) << s;
+                wc.boxes += __popc(nonempty);
+            }
             const uint32_t imask = a.w >> 24;
             const uint32_t hint = hitmask & imask;
             uint32_t hleaf = hitmask & ~imask;
@@ -261,7 +283,8 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
                 if (COUNT) wc.tris++;
             }
             const uint32_t id = idb & ~SPHERE_BIT;
-            if (t > r.tmin && (t < h.t || (t == h.t && id < h.id))) {
+            // t in (tmin, tmax); the closer hit wins, equal t goes to the lower id
+            if (t > r.tmin && t < r.tmax && (t < h.t || (t == h.t && id < h.id))) {
                 h.t = t;
                 h.id = id;
                 h.rec = rec;
@@ -286,7 +309,7 @@ __device__ __forceinline__ Hit traverse_brute(const SceneDev& S, const RayF& r) 
         const uint32_t idb = __float_as_uint(w2.y);
         const float t = (idb & SPHERE_BIT) ? hit_sphere(r, w0) : hit_triangle(r, w0, w1, w2);
         const uint32_t id = idb & ~SPHERE_BIT;
-        if (t > r.tmin && (t < h.t || (t == h.t && id < h.id))) {
+        if (t > r.tmin && t < r.tmax && (t < h.t || (t == h.t && id < h.id))) {
             h.t = t;
             h.id = id;
             h.rec = (int32_t)rec;

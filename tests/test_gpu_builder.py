@@ -119,7 +119,7 @@ def test_bvh_equals_brute_force(name, any_hit):
         assert np.array_equal(res[0][1], res[1][1])
         assert np.array_equal(res[0][0], res[1][0])
         if not any_hit:
-            assert (res[0][1] >= 0).mean() > 0.05
+            assert (res[0][1] >= 0).sum() >= 100  # enough hits to mean something
     finally:
         rcp.rcp_scene_destroy(g)
 
