@@ -45,6 +45,10 @@ RenderCtx::~RenderCtx() {
     if (d_rays) cudaFree(d_rays);
     if (io) cudaFree(io);
     if (io_prim) cudaFree(io_prim);
+    if (done) {
+        cudaEventSynchronize(done);
+        cudaEventDestroy(done);
+    }
     if (staged) cudaEventDestroy(staged);
     for (auto e : pass_ev)
         if (e) cudaEventDestroy(e);
@@ -206,24 +210,39 @@ void layout_views(std::vector<ViewDev>& v, int64_t& total_pix, int64_t& total_ch
     }
 }
 
+// Render contexts are cached per launch shape, least recently used first out
+// when the cache exceeds CTX_MAX entries or CTX_BYTES of device memory. A
+// context is freed only after its last launch has completed.
+constexpr size_t CTX_MAX = 24;
+constexpr int64_t CTX_BYTES = (int64_t)8 << 30;
+
 rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t total_chunks, RenderCtx** out) {
     std::ostringstream key;
     key << n_views << ":" << K << ":" << total_pix << ":" << total_chunks;
     auto it = sc.ctx.find(key.str());
     if (it != sc.ctx.end()) {
+        it->second->last_use = ++sc.use_clock;
         *out = it->second.get();
         return RCP_OK;
     }
-    if (sc.ctx.size() >= 16) {  // bounded cache: drop all and rebuild
-        cudaDeviceSynchronize();
-        sc.ctx.clear();
-        sc.last = nullptr;
+    const int64_t need = total_pix * (int64_t)(sizeof(float4) * 4) + (int64_t)sizeof(ViewDev) * K * n_views;
+    for (;;) {
+        int64_t held = 0;
+        for (auto& kv : sc.ctx) held += kv.second->bytes;
+        if (sc.ctx.empty() || (sc.ctx.size() < CTX_MAX && held + need <= CTX_BYTES)) break;
+        auto victim = sc.ctx.begin();
+        for (auto jt = sc.ctx.begin(); jt != sc.ctx.end(); ++jt)
+            if (jt->second->last_use < victim->second->last_use) victim = jt;
+        if (sc.last == victim->second.get()) sc.last = nullptr;
+        sc.ctx.erase(victim);  // the destructor waits for the context's last launch
     }
     auto c = std::make_unique<RenderCtx>();
     c->n_views = n_views;
     c->K = K;
     c->total_pix = total_pix;
     c->total_chunks = total_chunks;
+    c->bytes = need;
+    c->last_use = ++sc.use_clock;
     RCP_CUDA(cudaMalloc((void**)&c->img[0], sizeof(float4) * total_pix));
     RCP_CUDA(cudaMalloc((void**)&c->img[1], sizeof(float4) * total_pix));
     RCP_CUDA(cudaMalloc((void**)&c->rays, sizeof(float4) * 2 * total_pix));
@@ -235,6 +254,7 @@ rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t tot
     RCP_CUDA(cudaMalloc((void**)&c->d_rays, sizeof(unsigned long long) * 2));
     RCP_CUDA(cudaMemset(c->d_rays, 0, sizeof(unsigned long long) * 2));
     RCP_CUDA(cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
+    RCP_CUDA(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
     for (int n = 0; n <= K; ++n) RCP_CUDA(cudaEventCreate(&c->pass_ev[n]));
     *out = c.get();
     sc.ctx[key.str()] = std::move(c);
@@ -288,6 +308,7 @@ rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cuda
         ctx.graph_key = key;
     }
     RCP_CUDA(cudaGraphLaunch(ctx.graph, st));
+    RCP_CUDA(cudaEventRecord(ctx.done, st));
     return RCP_OK;
 }
 

@@ -36,6 +36,9 @@ struct RenderCtx {
     cudaEvent_t pass_ev[17] = {};  // timing events around every pass (recorded inside the graph)
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
+    cudaEvent_t done = nullptr;  // recorded after the context's latest launch
+    uint64_t last_use = 0;
+    int64_t bytes = 0;
     ~RenderCtx();
 };
 
@@ -58,6 +61,7 @@ struct Scene {
     std::mutex mu;
     std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
     RenderCtx* last = nullptr;  // context of the most recent render
+    uint64_t use_clock = 0;
     ~Scene();
     SceneDev dev() const;
     int64_t device_bytes() const;

@@ -1,22 +1,25 @@
 // serve.cu -- continuous-batching render server (rcp_server_* in rcp.h).
 //
-// A scheduler thread owns the device work. Each step it
-//  1. admits queued requests (FIFO) while a slot is free and the request's
-//     device memory -- two rgbz images and an RGB staging buffer, allocated
-//     stream-ordered from the device's memory pool -- fits the budget;
-//  2. runs ONE pass of every admitted request: the requests are grouped by
-//     scene and each group is one launch of the pass kernels (one work queue
-//     over all of the group's views, whatever their size), groups on their
-//     own streams so they overlap on the device;
-//  3. retires requests whose K passes are done: packs RGB, copies it to the
-//     caller's buffer and frees the request's memory.
-// New requests join at the next step boundary while others are mid-recursion,
-// so short and long requests share every launch.
+// Two host threads own the device work:
+//  * the scheduler admits queued requests (FIFO) while a slot is free and the
+//    request's device memory -- two rgbz images and an RGB staging buffer,
+//    allocated stream-ordered from the device's memory pool -- fits the
+//    budget, then enqueues ONE pass of every admitted request per step: the
+//    requests are grouped by scene and each group is one launch of the pass
+//    kernels (one work queue over all of the group's views, whatever their
+//    size), groups on their own streams so they overlap on the device. Which
+//    requests finish at a step is known when it is enqueued (pass count = K),
+//    so the scheduler never waits for the device except to bound how far it
+//    runs ahead (STEPS_AHEAD steps);
+//  * the copy-out thread waits for each finished request's last pass, copies
+//    its RGB image to the caller's buffer, releases its memory and records
+//    its latency, while the device already runs the next steps.
+// New requests join at the next step while others are mid-recursion, so short
+// and long requests share every launch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -28,9 +31,10 @@
 
 #include "scene.h"
 
-
 namespace rcp {
 namespace {
+
+constexpr int STEPS_AHEAD = 3;  // steps enqueued before the oldest must finish
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -42,7 +46,7 @@ LaunchCfg server_cfg(const Scene& sc) {
     c.blocks_per_sm = sc.tuning.blocks_per_sm;
     c.chunk = sc.tuning.chunk >= 64 ? 64 : 32;
     c.fused = true;  // no ray buffer per request
-    int st = std::max(sc.depth, 4);
+    const int st = std::max(sc.depth, 4);
     c.stack = std::min((st + 3) & ~3, MAX_STACK);
     return c;
 }
@@ -56,16 +60,17 @@ struct Request {
     int W = 0, H = 0, K = 0;
     rcp_params p{};
     float* out_rgb = nullptr;
-    int passes_done = 0;
+    int passes_done = 0;  // passes enqueued so far
     float4* img[2] = {nullptr, nullptr};
     float* rgb = nullptr;
     int64_t bytes = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     rcp_status status = RCP_OK;
     bool done = false;
+    cudaEvent_t ready = nullptr;  // the packed RGB image is complete
 };
 
-// Per-scene launch resources of a step.
+// Launch resources of one scene group in one step slot.
 struct GroupRes {
     cudaStream_t st = nullptr;
     ViewDev* d_views = nullptr;
@@ -73,7 +78,13 @@ struct GroupRes {
     int cap = 0;
     unsigned* d_work = nullptr;
     int* d_status = nullptr;
-    cudaEvent_t staged = nullptr;
+    cudaEvent_t end = nullptr;
+};
+
+struct StepSlot {
+    std::vector<GroupRes> groups;
+    cudaEvent_t done = nullptr;
+    bool used = false;
 };
 
 }  // namespace rcp
@@ -84,25 +95,28 @@ struct rcp_server {
     int64_t budget = 0;
     int max_slots = 0;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_copy;
     std::deque<Request*> queue;
     std::vector<Request*> inflight;
+    std::deque<Request*> copyq;
     std::map<int64_t, std::unique_ptr<Request>> all;
     int64_t next_ticket = 1;
-    bool stop = false;
-    std::thread worker;
+    bool stop = false, copy_stop = false;
+    std::thread worker, copier;
     int64_t bytes_in_use = 0, bytes_peak = 0;
     int64_t submitted = 0, completed = 0, rejected = 0, steps = 0;
     double t_first = 0, t_last = 0;
     std::vector<double> latencies_ms;
-    unsigned long long rays_total = 0;
-    unsigned long long* d_rays = nullptr;
-    cudaStream_t st_main = nullptr;
-    std::vector<GroupRes> groups;
-    cudaMemPool_t pool = nullptr;
+    unsigned long long* d_rays = nullptr;  // running total: primary, shadow
+    cudaStream_t st_main = nullptr, st_copy = nullptr;
+    StepSlot slots[STEPS_AHEAD];
+    int64_t step_no = 0;
+    int device = 0;
 
     void run();
-    rcp_status step(std::vector<Request*>& batch);
+    void copy_out();
+    rcp_status enqueue_step(std::vector<Request*>& batch, StepSlot& slot);
+    void finish(Request* q, rcp_status st, double t);
 };
 
 namespace {
@@ -117,6 +131,7 @@ rcp_status alloc_request(Request& r, cudaStream_t st) {
     RCP_CUDA(cudaMallocAsync((void**)&r.img[0], sizeof(float4) * P, st));
     RCP_CUDA(cudaMallocAsync((void**)&r.img[1], sizeof(float4) * P, st));
     RCP_CUDA(cudaMallocAsync((void**)&r.rgb, sizeof(float) * 3 * P, st));
+    if (!r.ready) RCP_CUDA(cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming));
     return RCP_OK;
 }
 
@@ -138,7 +153,7 @@ rcp_status ensure_group(GroupRes& g, int n) {
         RCP_CUDA(cudaMalloc((void**)&g.d_work, sizeof(unsigned) * 2));
         RCP_CUDA(cudaMalloc((void**)&g.d_status, sizeof(int) * 2));
         RCP_CUDA(cudaMemset(g.d_status, 0, sizeof(int) * 2));
-        RCP_CUDA(cudaEventCreateWithFlags(&g.staged, cudaEventDisableTiming));
+        RCP_CUDA(cudaEventCreateWithFlags(&g.end, cudaEventDisableTiming));
     }
     if (g.cap < n) {
         if (g.d_views) cudaFree(g.d_views);
@@ -161,33 +176,35 @@ double percentile(std::vector<double> v, double q) {
 
 }  // namespace
 
-// One pass of every request in the batch.
-rcp_status rcp_server::step(std::vector<Request*>& batch) {
+// Enqueue one pass of every request in the batch (slot's resources are free:
+// its previous step has completed).
+rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot) {
     std::map<const rcp_scene*, std::vector<Request*>> by_scene;
     for (Request* r : batch) by_scene[r->scene].push_back(r);
-    if ((int)groups.size() < (int)by_scene.size()) groups.resize(by_scene.size());
-    RCP_CUDA(cudaMemsetAsync(d_rays, 0, sizeof(unsigned long long) * 2, st_main));
+    if (slot.groups.size() < by_scene.size()) slot.groups.resize(by_scene.size());
+    if (!slot.done) RCP_CUDA(cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming));
     cudaEvent_t ready;
     RCP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    RCP_CUDA(cudaEventRecord(ready, st_main));
+    RCP_CUDA(cudaEventRecord(ready, st_main));  // this step's allocations are visible
     int gi = 0;
     rcp_status res = RCP_OK;
-    std::vector<cudaEvent_t> ends;
     for (auto& kv : by_scene) {
         const rcp_scene* sc = kv.first;
         auto& reqs = kv.second;
-        GroupRes& g = groups[gi++];
+        GroupRes& g = slot.groups[gi++];
         rcp_status r = ensure_group(g, (int)reqs.size());
         if (r != RCP_OK) {
             res = r;
             break;
         }
-        RCP_CUDA(cudaEventSynchronize(g.staged));
-        std::vector<ViewDev> views(reqs.size());
+        if (sc->depth > MAX_STACK) {
+            for (Request* q : reqs) q->status = RCP_ERR_STACK;
+            continue;
+        }
         int64_t total_pix = 0, total_chunks = 0;
         for (size_t i = 0; i < reqs.size(); ++i) {
             Request* q = reqs[i];
-            ViewDev& v = views[i];
+            ViewDev v;
             make_view(v, q->cam, q->W, q->H, q->p);
             v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
             v.out = q->img[q->passes_done & 1];
@@ -199,53 +216,81 @@ rcp_status rcp_server::step(std::vector<Request*>& batch) {
         }
         RCP_CUDA(cudaStreamWaitEvent(g.st, ready, 0));
         RCP_CUDA(cudaMemcpyAsync(g.d_views, g.h_views, sizeof(ViewDev) * reqs.size(), cudaMemcpyHostToDevice, g.st));
-        RCP_CUDA(cudaEventRecord(g.staged, g.st));
         RCP_CUDA(cudaMemsetAsync(g.d_work, 0, sizeof(unsigned), g.st));
-        LaunchCfg cfg = server_cfg(*sc);
-        if (sc->depth > MAX_STACK) {
-            for (Request* q : reqs) q->status = RCP_ERR_STACK;
-            continue;
-        }
-        r = launch_pass(sc->dev(), cfg, g.d_views, (int)reqs.size(), total_pix, total_chunks, nullptr, g.d_work,
-                        g.d_status, d_rays, nullptr, g.st);
+        r = launch_pass(sc->dev(), server_cfg(*sc), g.d_views, (int)reqs.size(), total_pix, total_chunks, nullptr,
+                        g.d_work, g.d_status, d_rays, nullptr, g.st);
         if (r != RCP_OK) {
             res = r;
             break;
         }
         for (Request* q : reqs) {
-            q->passes_done++;
-            if (q->passes_done == q->K) {
-                const int64_t P = (int64_t)q->W * q->H;
-                r = launch_pack_rgb(q->img[(q->K - 1) & 1], q->rgb, P, g.st);
+            if (q->passes_done + 1 == q->K) {
+                r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, g.st);
                 if (r != RCP_OK) {
                     res = r;
                     break;
                 }
-                RCP_CUDA(cudaMemcpyAsync(q->out_rgb, q->rgb, sizeof(float) * 3 * P, cudaMemcpyDeviceToHost, g.st));
+                RCP_CUDA(cudaEventRecord(q->ready, g.st));
             }
         }
-        cudaEvent_t e;
-        RCP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        RCP_CUDA(cudaEventRecord(e, g.st));
-        RCP_CUDA(cudaStreamWaitEvent(st_main, e, 0));
-        ends.push_back(e);
+        RCP_CUDA(cudaEventRecord(g.end, g.st));
+        RCP_CUDA(cudaStreamWaitEvent(st_main, g.end, 0));
     }
-    unsigned long long h[2] = {0, 0};
-    RCP_CUDA(cudaMemcpyAsync(h, d_rays, sizeof(h), cudaMemcpyDeviceToHost, st_main));
-    cudaError_t e = cudaStreamSynchronize(st_main);
-    for (cudaEvent_t x : ends) cudaEventDestroy(x);
     cudaEventDestroy(ready);
-    if (e != cudaSuccess) return cuda_fail(e, "server step");
-    rays_total += h[0] + h[1];
+    RCP_CUDA(cudaEventRecord(slot.done, st_main));
+    slot.used = true;
     return res;
 }
 
+void rcp_server::finish(Request* q, rcp_status st, double t) {
+    // called with mu held
+    bytes_in_use -= q->bytes;
+    q->t_done = t;
+    if (q->status == RCP_OK) q->status = st;
+    q->done = true;
+    if (q->status == RCP_OK) {
+        ++completed;
+        latencies_ms.push_back(1000.0 * (q->t_done - q->t_submit));
+        t_last = t;
+    }
+    cv_done.notify_all();
+    cv_work.notify_all();
+}
+
+void rcp_server::copy_out() {
+    cudaSetDevice(device);
+    for (;;) {
+        Request* q = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_copy.wait(lk, [&] { return copy_stop || !copyq.empty(); });
+            if (copyq.empty()) return;
+            q = copyq.front();
+            copyq.pop_front();
+        }
+        rcp_status st = RCP_OK;
+        if (q->status == RCP_OK) {
+            cudaError_t e = cudaEventSynchronize(q->ready);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(q->out_rgb, q->rgb, sizeof(float) * 3 * (int64_t)q->W * q->H,
+                                    cudaMemcpyDeviceToHost, st_copy);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st_copy);
+            if (e != cudaSuccess) st = cuda_fail(e, "server copy-out");
+        }
+        free_request(*q, st_copy);
+        const double t = now_s();
+        std::lock_guard<std::mutex> lk(mu);
+        finish(q, st, t);
+    }
+}
+
 void rcp_server::run() {
+    cudaSetDevice(device);
     for (;;) {
         std::vector<Request*> batch;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait_for(lk, std::chrono::milliseconds(50),
+            cv_work.wait_for(lk, std::chrono::milliseconds(20),
                              [&] { return stop || !queue.empty() || !inflight.empty(); });
             if (stop && inflight.empty()) {
                 for (Request* q : queue) {
@@ -278,36 +323,31 @@ void rcp_server::run() {
         }
         if (batch.empty()) continue;
         for (Request* q : batch)
-            if (!q->img[0]) {
+            if (!q->img[0] && q->status == RCP_OK) {
                 rcp_status r = alloc_request(*q, st_main);
                 if (r != RCP_OK) q->status = r;
             }
         std::vector<Request*> ok;
         for (Request* q : batch)
             if (q->status == RCP_OK) ok.push_back(q);
-        rcp_status r = ok.empty() ? RCP_OK : step(ok);
-        const double t = now_s();
+        StepSlot& slot = slots[step_no % STEPS_AHEAD];
+        if (slot.used) cudaEventSynchronize(slot.done);  // bound the run-ahead; frees the slot's staging
+        rcp_status r = ok.empty() ? RCP_OK : enqueue_step(ok, slot);
+        ++step_no;
         std::lock_guard<std::mutex> lk(mu);
         ++steps;
         std::vector<Request*> still;
         for (Request* q : inflight) {
             if (r != RCP_OK && q->status == RCP_OK) q->status = r;
+            if (q->status == RCP_OK) q->passes_done++;
             if (q->status != RCP_OK || q->passes_done >= q->K) {
-                free_request(*q, st_main);
-                bytes_in_use -= q->bytes;
-                q->t_done = t;
-                q->done = true;
-                if (q->status == RCP_OK) {
-                    ++completed;
-                    latencies_ms.push_back(1000.0 * (q->t_done - q->t_submit));
-                    t_last = t;
-                }
+                copyq.push_back(q);  // the copy-out thread waits for its image
+                cv_copy.notify_one();
             } else {
                 still.push_back(q);
             }
         }
         inflight.swap(still);
-        cv_done.notify_all();
     }
 }
 
@@ -321,19 +361,18 @@ rcp_status rcp_server_create(int64_t budget, int max_slots, rcp_server** out) {
     auto s = std::make_unique<rcp_server>();
     s->budget = budget;
     s->max_slots = max_slots;
+    RCP_CUDA(cudaGetDevice(&s->device));
     RCP_CUDA(cudaStreamCreateWithFlags(&s->st_main, cudaStreamNonBlocking));
+    RCP_CUDA(cudaStreamCreateWithFlags(&s->st_copy, cudaStreamNonBlocking));
     RCP_CUDA(cudaMalloc((void**)&s->d_rays, sizeof(unsigned long long) * 2));
-    int dev = 0;
-    RCP_CUDA(cudaGetDevice(&dev));
-    RCP_CUDA(cudaDeviceGetDefaultMemPool(&s->pool, dev));
+    RCP_CUDA(cudaMemset(s->d_rays, 0, sizeof(unsigned long long) * 2));
+    cudaMemPool_t pool = nullptr;
+    RCP_CUDA(cudaDeviceGetDefaultMemPool(&pool, s->device));
     uint64_t thr = (uint64_t)budget;
-    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     rcp_server* raw = s.release();
-    raw->worker = std::thread([raw] {
-        int d = 0;
-        cudaGetDevice(&d);
-        raw->run();
-    });
+    raw->worker = std::thread([raw] { raw->run(); });
+    raw->copier = std::thread([raw] { raw->copy_out(); });
     *out = raw;
     return RCP_OK;
 }
@@ -416,18 +455,21 @@ rcp_status rcp_server_stats_get(rcp_server* srv, rcp_server_stats* out) {
         set_error("rcp_server_stats_get: NULL argument");
         return RCP_ERR_ARG;
     }
+    unsigned long long h[2] = {0, 0};
+    // the counters only grow; a read that races a running pass sees a lower bound
+    RCP_CUDA(cudaMemcpy(h, srv->d_rays, sizeof(h), cudaMemcpyDeviceToHost));
     std::lock_guard<std::mutex> lk(srv->mu);
     out->submitted = srv->submitted;
     out->completed = srv->completed;
     out->rejected = srv->rejected;
-    out->in_flight = (int64_t)srv->inflight.size();
+    out->in_flight = (int64_t)srv->inflight.size() + (int64_t)srv->copyq.size();
     out->queued = (int64_t)srv->queue.size();
     out->steps = srv->steps;
     out->p50_ms = percentile(srv->latencies_ms, 0.50);
     out->p99_ms = percentile(srv->latencies_ms, 0.99);
     const double span = srv->t_last - srv->t_first;
     out->frames_per_s = span > 0 ? srv->completed / span : 0.0;
-    out->mrays_per_s = span > 0 ? srv->rays_total / span / 1e6 : 0.0;
+    out->mrays_per_s = span > 0 ? (double)(h[0] + h[1]) / span / 1e6 : 0.0;
     out->device_bytes_in_use = srv->bytes_in_use;
     out->device_bytes_peak = srv->bytes_peak;
     return RCP_OK;
@@ -441,20 +483,33 @@ void rcp_server_destroy(rcp_server* srv) {
         srv->cv_work.notify_all();
     }
     if (srv->worker.joinable()) srv->worker.join();
-    cudaStreamSynchronize(srv->st_main);
-    for (auto& g : srv->groups) {
-        if (g.st) {
-            cudaStreamSynchronize(g.st);
-            cudaStreamDestroy(g.st);
-        }
-        if (g.d_views) cudaFree(g.d_views);
-        if (g.h_views) cudaFreeHost(g.h_views);
-        if (g.d_work) cudaFree(g.d_work);
-        if (g.d_status) cudaFree(g.d_status);
-        if (g.staged) cudaEventDestroy(g.staged);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->copy_stop = true;
+        srv->cv_copy.notify_all();
     }
+    if (srv->copier.joinable()) srv->copier.join();
+    cudaStreamSynchronize(srv->st_main);
+    cudaStreamSynchronize(srv->st_copy);
+    for (auto& sl : srv->slots) {
+        for (auto& g : sl.groups) {
+            if (g.st) {
+                cudaStreamSynchronize(g.st);
+                cudaStreamDestroy(g.st);
+            }
+            if (g.d_views) cudaFree(g.d_views);
+            if (g.h_views) cudaFreeHost(g.h_views);
+            if (g.d_work) cudaFree(g.d_work);
+            if (g.d_status) cudaFree(g.d_status);
+            if (g.end) cudaEventDestroy(g.end);
+        }
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    for (auto& kv : srv->all)
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     if (srv->d_rays) cudaFree(srv->d_rays);
     if (srv->st_main) cudaStreamDestroy(srv->st_main);
+    if (srv->st_copy) cudaStreamDestroy(srv->st_copy);
     delete srv;
 }
 

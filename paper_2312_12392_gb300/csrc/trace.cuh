@@ -180,12 +180,20 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
     int sp = 0;
     // a valid BVH is a tree whose child indices grow, so every node is entered
     // at most once; the cap only turns a corrupted structure into an error
+    // Every iteration visits exactly one node: when the current group is
+    // exhausted the next one is popped first, so no lane spends an iteration
+    // on the stack alone while the rest of its warp tests boxes.
     for (uint32_t iter = 0;; ++iter) {
         if (iter > (1u << 24)) {
             overflow = true;
             break;
         }
-        if (group.y > 0xffu) {
+        if (group.y <= 0xffu) {
+            if (sp == 0) break;
+            --sp;
+            group = stack[sp * stride];
+        }
+        {
             const uint32_t hits = group.y >> 8;
             const uint32_t i = __ffs(hits) - 1;
             group.y &= ~(1u << (i + 8));
@@ -261,11 +269,6 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
                 const uint32_t mb = ((s < 4 ? ml : mh) >> (8 * (s & 3))) & 0xffu;
                 prim_mask |= ((1u << (mb >> 5)) - 1u) << (mb & 31u);
             }
-        } else if (prim_mask == 0) {
-            if (sp == 0) break;
-            --sp;
-            group = stack[sp * stride];
-            continue;
         }
         while (prim_mask) {
             const uint32_t j = __ffs(prim_mask) - 1;
