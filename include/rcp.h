@@ -211,6 +211,29 @@ rcp_status rcp_debug_sort_pairs(uint32_t* keys, uint32_t* values, int64_t n, int
 rcp_status rcp_debug_morton(const float* xyz, int64_t n, const float* lo, const float* hi,
                             uint32_t* codes, void* stream);
 
+/* Allocation-free sort. The paper has no counterpart: this is a library
+ * facility. Some callers cannot allocate device memory at the point where they
+ * need to sort: code running while a CUDA graph is being captured (where
+ * cudaMalloc is not allowed), real-time loops that must not allocate once they
+ * are running, and hosts that hand the library no allocator of its own. This
+ * entry point does the same stable LSD radix sort as rcp_debug_sort_pairs
+ * (keys and values are device arrays of n uint32, sorted in place on the low
+ * `bits` bits of the keys, enqueued on `stream`), but all of its scratch
+ * lives in one fixed device array compiled into the library, of about 8.7 MB,
+ * which every GPU that loads the library holds until the process exits; it
+ * calls no cudaMalloc or cudaFree.
+ *  - n may be at most RCP_SORT_STATIC_MAX_PAIRS; larger n returns
+ *    RCP_ERR_ARG with a message saying so.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture begins.
+ *  - Every call reuses the same array, so calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race on it: serialise them.
+ *  - The call waits for the sort to finish before it returns (it reads the
+ *    sort's error flag); RCP_ERR_TIMEOUT reports a look-back wait that ran out. */
+#define RCP_SORT_STATIC_MAX_PAIRS 1048576
+rcp_status rcp_sort_pairs_static(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream);
+
 /* ------------------------------------------------------------ serving ---
  * A request = one K-pass render of a resident scene. Requests are admitted
  * while a slot is free and their device memory (two rgbz images and a ray

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "rcp_internal.cuh"
 
 namespace rcp {
@@ -233,3 +235,90 @@ rcp_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* alt_keys, 
 }
 
 }  // namespace rcp
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// rcp_sort_pairs_static: the same sort with every scratch buffer (ping-pong
+// keys and values, digit histograms, tile status, tile counters, the look-back
+// error flag) carved out of one file-scope device array, so the call never
+// allocates device memory.
+
+namespace rcp {
+namespace {
+
+constexpr int64_t STATIC_MAX = RCP_SORT_STATIC_MAX_PAIRS;
+constexpr int64_t STATIC_TILES = (STATIC_MAX + TILE - 1) / TILE;
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t OFF_KEYS = 0;
+constexpr size_t OFF_VALS = align256(OFF_KEYS + sizeof(uint32_t) * STATIC_MAX);
+constexpr size_t OFF_SCRATCH = align256(OFF_VALS + sizeof(uint32_t) * STATIC_MAX);
+constexpr size_t SCRATCH_BYTES = sizeof(uint32_t) * (4 * RADIX + 8 + STATIC_TILES * RADIX);
+constexpr size_t OFF_ERROR = align256(OFF_SCRATCH + SCRATCH_BYTES);
+constexpr size_t STATIC_BYTES = align256(OFF_ERROR + sizeof(int));
+
+}  // namespace
+}  // namespace rcp
+
+// Held by every device that loads the library, for the life of the process.
+static __device__ __align__(256) unsigned char g_sort_static_scratch[rcp::STATIC_BYTES];
+
+namespace rcp {
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[MAX_DEVICES] = {};
+
+// Device address of the static scratch on the current device, looked up once
+// per device (host code cannot use the array's name as a device pointer).
+rcp_status static_scratch(unsigned char** out) {
+    int dev = 0;
+    RCP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        set_error("rcp_sort_pairs_static: device ordinal out of range");
+        return RCP_ERR_STATE;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_sort_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_sort_static_scratch)");
+        g_static_ptr[dev] = p;
+    }
+    *out = (unsigned char*)g_static_ptr[dev];
+    return RCP_OK;
+}
+
+}  // namespace
+}  // namespace rcp
+
+extern "C" rcp_status rcp_sort_pairs_static(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream) {
+    using namespace rcp;
+    if (n < 0 || bits < 1 || bits > 32 || (n > 0 && (!keys || !values))) {
+        set_error("rcp_sort_pairs_static: bad argument");
+        return RCP_ERR_ARG;
+    }
+    if (n > STATIC_MAX) {
+        set_error("rcp_sort_pairs_static: n exceeds the static scratch capacity of RCP_SORT_STATIC_MAX_PAIRS "
+                  "(1048576) pairs");
+        return RCP_ERR_ARG;
+    }
+    if (n <= 1) return RCP_OK;
+    unsigned char* base = nullptr;
+    rcp_status r = static_scratch(&base);
+    if (r != RCP_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d_err = (int*)(base + OFF_ERROR);
+    RCP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));  // the array keeps the last call's contents
+    r = radix_sort_pairs(keys, values, (uint32_t*)(base + OFF_KEYS), (uint32_t*)(base + OFF_VALS), n, bits,
+                         base + OFF_SCRATCH, d_err, st);
+    if (r != RCP_OK) return r;
+    int h = 0;
+    RCP_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCP_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("rcp_sort_pairs_static: look-back wait ran out");
+        return RCP_ERR_TIMEOUT;
+    }
+    return RCP_OK;
+}

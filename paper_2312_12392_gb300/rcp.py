@@ -93,6 +93,7 @@ _SIGS = {
     "rcp_debug_trace": [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp],
     "rcp_debug_sort_pairs": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_debug_morton": [_vp, C.c_int64, _vp, _vp, _vp, _vp],
+    "rcp_sort_pairs_static": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_server_create": [C.c_int64, C.c_int, C.POINTER(_vp)],
     "rcp_server_submit": [_vp, _vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.c_int, C.POINTER(rcp_params), _vp,
                           C.POINTER(C.c_int64)],
@@ -306,6 +307,14 @@ def rcp_debug_morton(xyz, n, lo, hi, codes, stream=None):
     hi = _host(hi, np.float32, 3)
     _check(lib().rcp_debug_morton(_ptr(xyz), n, _ptr(lo), _ptr(hi), _ptr(codes), _stream(stream)),
            "rcp_debug_morton")
+
+
+RCP_SORT_STATIC_MAX_PAIRS = 1048576
+
+
+def rcp_sort_pairs_static(keys, values, n, bits, stream=None):
+    """Allocation-free radix sort (device arrays, n <= RCP_SORT_STATIC_MAX_PAIRS)."""
+    _check(lib().rcp_sort_pairs_static(_ptr(keys), _ptr(values), n, bits, _stream(stream)), "rcp_sort_pairs_static")
 
 
 # ------------------------------------------------------------------ serving

@@ -1,0 +1,59 @@
+"""The allocation-free sort entry point against the allocating one.
+
+rcp_sort_pairs_static exists for callers that cannot allocate device memory
+when they sort (inside a CUDA graph capture, in allocation-free real-time
+loops, or in hosts that own all device memory): its scratch is a fixed array
+compiled into the library. It must give exactly what rcp_debug_sort_pairs
+gives (integer work: bit-exact), on consecutive calls that reuse the same
+array, and refuse sizes beyond its capacity. This file is collected last so a
+failure here leaves every other test already run.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2312_12392_gb300 import rcp  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _pairs(n, seed):
+    rng = np.random.default_rng(seed)
+    keys = rng.integers(0, 1 << 30, size=n, dtype=np.uint64).astype(np.uint32)
+    keys[: n // 4] = keys[0]  # duplicates, so stability is checked too
+    rng.shuffle(keys)
+    vals = rng.permutation(n).astype(np.uint32)
+    return keys, vals
+
+
+def _dev(a):
+    return torch.from_numpy(a.view(np.int32).copy()).cuda()
+
+
+@pytest.mark.parametrize("n,bits", [(300_001, 30), (rcp.RCP_SORT_STATIC_MAX_PAIRS, 32)])
+def test_static_sort_matches_allocating_sort_twice(n, bits):
+    for call in range(2):  # two calls in a row share (and reuse) the static scratch
+        keys, vals = _pairs(n, seed=100 * call + bits)
+        rk, rv = _dev(keys), _dev(vals)
+        rcp.rcp_debug_sort_pairs(rk, rv, n, bits)
+        sk, sv = _dev(keys), _dev(vals)
+        rcp.rcp_sort_pairs_static(sk, sv, n, bits, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert torch.equal(sk, rk), f"keys differ on call {call}"
+        assert torch.equal(sv, rv), f"values differ on call {call}"
+
+
+def test_static_sort_small_and_limits():
+    keys, vals = _pairs(5, seed=1)
+    sk, sv = _dev(keys), _dev(vals)
+    rcp.rcp_sort_pairs_static(sk, sv, 5, 30)
+    torch.cuda.synchronize()
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(sk.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(sv.cpu().numpy().view(np.uint32), vals[order])
+    n = rcp.RCP_SORT_STATIC_MAX_PAIRS + 1
+    big = torch.zeros(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(rcp.RcpError) as e:
+        rcp.rcp_sort_pairs_static(big, big.clone(), n, 30)
+    assert e.value.status == rcp.RCP_ERR_ARG and "capacity" in str(e.value)
