@@ -9,7 +9,7 @@ replayed from the library's captured CUDA graph with the scene resident in HBM.
 L2 is flushed (a 256 MB write) between steps, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload mid|forest|batched|served]
+                    [--workload mid|forest|batched|served|stress]
 
 With N > 1 (torchrun) every rank renders its own poses (replicas, no
 collective on the data path); the time is the max over ranks.
@@ -649,13 +649,83 @@ def run_served(args):
     print(json.dumps(out), flush=True)
 
 
+def run_stress(args):
+    """25,000-tree forest (12.57M triangles), 3840x2160, K=8: every frame the
+    wind sways the trees (input generated on the device with torch), the BVH is
+    refitted (rcp_scene_update_vertices_device) and the frame is rendered."""
+    import torch
+
+    from paper_2312_12392_gb300 import build as B
+    from paper_2312_12392_gb300 import rcp, scenes
+    torch.cuda.set_device(0)
+    B.build()
+    t0 = time.perf_counter()
+    sc = scenes.forest_scene(25_000, seed=5)
+    gen_s = time.perf_counter() - t0
+    W, H, K = 3840, 2160, 8
+    d = sc.diameter()
+    params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+    g = rcp.scene_from(sc)
+    info = rcp.rcp_scene_get_info(g)
+    base = torch.from_numpy(sc.tris).cuda().reshape(-1, 3, 3)
+    amp = torch.from_numpy(sc.sway_amp).cuda()
+    phase = torch.from_numpy(sc.sway_phase).cuda()
+    moved = torch.empty_like(base)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(args.steps + args.warmup)]
+
+    def sway(frame):
+        ang = 2.0 * np.pi * 0.5 * (frame / 60.0) + phase
+        moved.copy_(base)
+        moved[:, :, 0] += amp * torch.sin(ang)[:, None]
+        moved[:, :, 2] += amp * torch.cos(ang)[:, None]
+
+    for i in range(args.warmup):
+        sway(i)
+        rcp.rcp_scene_update_vertices_device(g, moved, stream)
+        rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
+    torch.cuda.synchronize()
+    refit_ms, render_ms, frame_ms, rays = [], [], [], 0
+    for i in range(args.warmup, args.warmup + args.steps):
+        sway(i)  # input generation, outside the timed events
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        rcp.rcp_scene_update_vertices_device(g, moved, stream)
+        e1.record(stream)
+        rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
+        e2.record(stream)
+        e2.synchronize()
+        refit_ms.append(e0.elapsed_time(e1))
+        render_ms.append(e1.elapsed_time(e2))
+        frame_ms.append(e0.elapsed_time(e2))
+        p_, s_ = rcp.rcp_last_ray_counts(g)
+        rays += p_ + s_
+    rcp.rcp_scene_validate(g)
+    tot = sum(frame_ms) / 1000.0
+    res = {
+        "metric": "frames_per_s (3840x2160, K=8, per-frame refit)",
+        "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"stress: {info.n_tris:,} tris (25,000 swaying cone trees), 3840x2160, K=8, "
+                               "wind sway A=0.02*h_tree at 0.5 Hz, refit every frame",
+                   "scene_generation_s": gen_s, "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
+                   "depth": info.depth},
+        "refit_ms": statistics.mean(refit_ms), "render_ms": statistics.mean(render_ms),
+        "mrays_per_s": rays / tot / 1e6, "gpu_launches_per_step": K + 2 + info.depth,
+    }
+    rcp.rcp_scene_destroy(g)
+    print(json.dumps(res), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress"])
     ap.add_argument("--tuning", default="128,32,1", help="'auto' or block,chunk,fused_camera")
     ap.add_argument("--count-poses", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -674,6 +744,8 @@ def main(argv=None):
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "stress":
+        run_stress(args)
     else:
         run_ours(args)
 

@@ -62,6 +62,8 @@ class Scene:
     albedo: np.ndarray  # (T+S, 3) float32
     light: Light
     poses: list = field(default_factory=list)  # list[Camera]
+    sway_amp: np.ndarray | None = None  # (T, 3) per triangle-vertex sway amplitude (forest)
+    sway_phase: np.ndarray | None = None  # (T,) per triangle sway phase (forest)
 
     @property
     def n_tris(self) -> int:
@@ -354,8 +356,27 @@ def forest_scene(n_trees: int = 2000, seed: int = 3, extent: float | None = None
     d = np.array([0.4, 0.8, 0.3])
     d /= np.linalg.norm(d)
     poses = _walkthrough(rng, height, span=0.75 * half, n_poses=n_poses, eye_height=1.0, pitch_deg=-5.0)
-    return Scene(f"forest{n_trees}", _f32(tris), np.zeros((0, 4), np.float32), _f32(albedo),
-                 Light(LIGHT_DIRECTIONAL, tuple(d.tolist()), 0.1), poses)
+    sc = Scene(f"forest{n_trees}", _f32(tris), np.zeros((0, 4), np.float32), _f32(albedo),
+               Light(LIGHT_DIRECTIONAL, tuple(d.tolist()), 0.1), poses)
+    # wind sway inputs: per triangle-vertex amplitude A * h_v / h_tree = 0.02 * h_v
+    # (h_v = height above the tree's base; the ground does not move) and a
+    # seeded phase per tree
+    vert_h = (verts[..., 1] - base_y.reshape(-1, 1, 1)).reshape(n_trees * 500, 3)
+    phase = rng.uniform(0.0, 2.0 * np.pi, n_trees)
+    sc.sway_amp = _f32(np.concatenate([np.zeros((ground.shape[0], 3)), 0.02 * vert_h], axis=0))
+    sc.sway_phase = _f32(np.concatenate([np.zeros(ground.shape[0]), np.repeat(phase, 500)]))
+    return sc
+
+
+def sway_vertices(base_tris, sway_amp, sway_phase, frame, fps=60.0, freq=0.5):
+    """Wind sway of frame `frame` (numpy reference of the stress workload):
+    x += a sin(2 pi f t + phi), z += a cos(2 pi f t + phi), t = frame / fps."""
+    t = frame / fps
+    ang = 2.0 * np.pi * freq * t + sway_phase.astype(np.float64)
+    v = base_tris.reshape(-1, 3, 3).astype(np.float64).copy()
+    v[:, :, 0] += sway_amp * np.sin(ang)[:, None]
+    v[:, :, 2] += sway_amp * np.cos(ang)[:, None]
+    return _f32(v.reshape(-1, 9))
 
 
 def random_soup(n_tris: int, n_spheres: int = 0, seed: int = 0, extent: float = 10.0,
