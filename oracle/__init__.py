@@ -66,6 +66,10 @@ def _bind(lib):
     lib.orc_shade_ray.argtypes = [C.c_void_p, dp, dp, dp, lp, C.POINTER(C.c_int)]
     lib.orc_render_pass.restype = i32
     lib.orc_render_pass.argtypes = [C.c_void_p, dp, i32, i32, i32, d, d, d, fp, lp, i64, dp, ip, up, i32]
+    lib.orc_imagespace_pass.restype = i32
+    lib.orc_imagespace_pass.argtypes = [fp, fp, i32, i32, C.c_float, lp, i64, fp]
+    lib.orc_mirror_index.restype = i64
+    lib.orc_mirror_index.argtypes = [i64, i64]
     lib.orc_render.restype = i32
     lib.orc_render.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, lp, i64, dp, ip, up, i32]
     return lib
@@ -198,3 +202,25 @@ def hit_sphere(c, r, o, d, tmin=0.0, tmax=np.inf, libpath=None):
     t = C.c_double()
     ok = lib(libpath).orc_hit_sphere(_dp(_vec(c)), r, _dp(_vec(o)), _dp(_vec(d)), tmin, tmax, C.byref(t))
     return (t.value if ok else None)
+
+
+def mirror_index(i, n, libpath=None):
+    return lib(libpath).orc_mirror_index(int(i), int(n))
+
+
+def imagespace_pass(base, prev, W, H, k_px, pix=None, libpath=None):
+    """One image-space pass: returns (n, 4) float32 (n = W*H or len(pix))."""
+    b = np.ascontiguousarray(base, dtype=np.float32).reshape(-1)
+    p = np.ascontiguousarray(prev, dtype=np.float32).reshape(-1)
+    if b.size != W * H * 4 or p.size != W * H * 4:
+        raise ValueError("base and prev must be H*W*4 floats")
+    n = W * H if pix is None else len(pix)
+    out = np.zeros((n, 4), np.float32)
+    pp = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
+    fptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    rc = lib(libpath).orc_imagespace_pass(fptr(b), fptr(p), W, H, float(np.float32(k_px)),
+                                          None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n,
+                                          fptr(out))
+    if rc != 0:
+        raise ValueError("orc_imagespace_pass rejected its arguments")
+    return out

@@ -126,11 +126,11 @@ double orc_scene_diam(const orc_scene* s) { return s ? s->diam : 0.0; }
  * Per-pixel camera: §2 (Eq. 2-4) and §3 (Eq. 5).
  *
  * Base pinhole frame (reading: right-handed, +R screen-right, +U screen-up, so
- * that "R=1 moves right, G=1 moves up" in §3 holds): F = normalize(look_at -
+ * that red moves a pixel right and green moves it up, as §3 states): F = normalize(look_at -
  * eye), R = normalize(F x up), U = R x F. Pixel (x, y) is sampled at its centre
  * (u, v) = ((x+.5)/W, (y+.5)/H), row 0 at the top. P_p is the pixel's point on
- * the focal plane at distance f along F (reading of "the 3D position of the
- * texture coordinate (u,v)"):
+ * the focal plane at distance f along F (reading of §2's 3D point of the
+ * texture coordinate (u,v)):
  *     P_p = P_e + f * (F + (2u-1) tan(fov/2) (W/H) R + (1-2v) tan(fov/2) U).
  * The colour mapping of Eq. 5, with (R, G, B) along (right, up, forward):
  *     V = k * ((2r-1) R + (2g-1) U + (2b-1) F).
@@ -332,7 +332,7 @@ static double hit_cos(const orc_scene* s, int64_t id, const double o[3], const d
 /* ---------------------------------------------------------------- tracing */
 
 /*
- * Closest hit (the paper's "shooting rays", §3): every primitive is tested and
+ * Closest hit (the rays of §3's second stage): every primitive is tested and
  * the smallest t in (tmin, tmax) wins; equal t goes to the lower id (reading:
  * the paper has no tie rule). Triangles have ids 0..T-1, spheres T..T+S-1.
  */
@@ -454,7 +454,7 @@ int orc_trace_any(const orc_scene* s, const double o[3], const double d[3], doub
 /* ---------------------------------------------------------------- shading */
 
 /*
- * Render one primary ray (§2 stage 2, "compute the new image"). The paper does
+ * Render one primary ray (§2 stage 2, the new image of the pass). The paper does
  * not state a shading model; the reading used here:
  *  - hit: c = albedo * (a + (1 - a) * V * max(0, N . L)), with ambient a, a
  *    white light of intensity 1 and no distance falloff; V = 1 unless the
@@ -628,4 +628,49 @@ int orc_render(const orc_scene* s, const double cam[10], int W, int H, int K, in
     J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = K; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
     J.in = NULL; J.pix = pix; J.npix = npix; J.out = out_rgbz; J.prim = out_prim; J.flag = out_flag;
     return run_job(&J, nthreads);
+}
+
+/* ---------------------------------------------------------------- image space */
+
+/*
+ * Mirror ("reflect") edge rule of §6.1: an index past an edge is reflected
+ * back into the image about that edge, the edge pixel itself not repeated
+ * (-1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2), again and again for offsets of more
+ * than one image width. Reading: the paper names mirroring but not its exact
+ * form; this is the reflection that keeps the sample nearest to its original.
+ */
+int64_t orc_mirror_index(int64_t i, int64_t n) {
+    if (n <= 1) return 0;
+    const int64_t period = 2 * n;
+    int64_t m = i % period;
+    if (m < 0) m += period;
+    return m < n ? m : period - 1 - m;
+}
+
+/*
+ * One image-space pass (§6, §6.1). Reading: the displacement is Eq. 5's
+ * k (2c - 1) restricted to the screen plane (B moves along the view axis and
+ * does not move a pixel), k_px being k in pixels; the sample is the nearest
+ * pixel. float32 arithmetic with no fused multiply-add (built with
+ * -ffp-contract=off) decides the pixel, in the order written here.
+ */
+int orc_imagespace_pass(const float* base, const float* prev, int W, int H, float k_px, const int64_t* pix,
+                        int64_t npix, float* out) {
+    if (!base || !prev || !out || W < 1 || H < 1 || !(k_px >= 0.0f)) return -1;
+    if (!pix) npix = (int64_t)W * H;
+    for (int64_t i = 0; i < npix; ++i) {
+        const int64_t p = pix ? pix[i] : i;
+        if (p < 0 || p >= (int64_t)W * H) return -1;
+        const int x = (int)(p % W), y = (int)(p / W);
+        const float* c = prev + 4 * p;
+        const float dr = 2.0f * c[0] - 1.0f;
+        const float dg = 2.0f * c[1] - 1.0f;
+        const float sx = (float)x + k_px * dr;
+        const float sy = (float)y - k_px * dg;
+        const int64_t ix = orc_mirror_index((int64_t)floorf(sx + 0.5f), W);
+        const int64_t iy = orc_mirror_index((int64_t)floorf(sy + 0.5f), H);
+        if (ix < 0 || ix >= W || iy < 0 || iy >= H) return -1;
+        memcpy(out + 4 * i, base + 4 * (iy * W + ix), 4 * sizeof(float));
+    }
+    return 0;
 }

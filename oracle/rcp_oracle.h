@@ -110,6 +110,21 @@ int orc_render(const orc_scene* s, const double cam[10], int W, int H, int K, in
                double k, double f, double z0, const int64_t* pix, int64_t npix,
                double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads);
 
+/* Image-space pass (§6: with V_e = 0 a pass reduces to re-sampling the
+ * rendered image at a displaced pixel; §6.1: mirrored screen edges). base = the frame's
+ * rendered image (H*W*4), prev = I_{n-1} (H*W*4), both float32. For pixel
+ * (x, y) with previous colour c, the displacement in pixels is
+ *   dx = k_px * (2 c.r - 1),  dy = -k_px * (2 c.g - 1)   (R right, G up: Eq. 5)
+ * the sample is the nearest pixel to (x + dx, y + dy), reflected into the
+ * image without repeating the edge pixel (-1 -> 0, W -> W-1, repeatedly), and
+ * I_n(x, y) = base at that pixel (all four lanes). The displacement and the
+ * rounding are done in float32, the precision of the pixel grid decision.
+ * Writes npix*4 floats to out (pix = NULL: every pixel). */
+int orc_imagespace_pass(const float* base, const float* prev, int W, int H, float k_px, const int64_t* pix,
+                        int64_t npix, float* out);
+/* The reflection of an integer pixel index into [0, n). */
+int64_t orc_mirror_index(int64_t i, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -445,4 +445,75 @@ def check_ground_plane_image(lp=None):
         assert abs(rgbz[p, 3] - 4.0 / -d[1]) < 1e-12
 
 
+# --------------------------------------------------------------------------- image space (§6, §6.1)
+
+def check_mirror_rule(lp=None):
+    """Reflection without repeating the edge pixel, repeated for big offsets."""
+    n = 5
+    got = [O.mirror_index(i, n, libpath=lp) for i in range(-12, 17)]
+    want = []
+    for i in range(-12, 17):
+        j = i
+        while j < 0 or j >= n:
+            j = -j - 1 if j < 0 else 2 * n - 1 - j
+        want.append(j)
+    assert got == want
+    assert [O.mirror_index(i, 5, libpath=lp) for i in (-1, -2, 5, 6, 10)] == [0, 1, 4, 3, 0]
+    assert O.mirror_index(7, 1, libpath=lp) == 0
+
+
+def _ramp(W, H):
+    # every pixel carries its own coordinates, so a gather is readable
+    b = np.zeros((H, W, 4), np.float32)
+    b[..., 0] = np.arange(W)[None, :]
+    b[..., 1] = np.arange(H)[:, None]
+    b[..., 2] = 7.0
+    b[..., 3] = np.arange(W * H).reshape(H, W)
+    return b
+
+
+def check_imagespace_shifts(lp=None):
+    """Grey and pure blue do not move; R=1 samples k pixels to the right, R=0
+    to the left, G=1 k rows up (towards row 0), G=0 down; edges mirror."""
+    W, H, k = 11, 7, 3.0
+    base = _ramp(W, H)
+
+    def run(c, kk=k):
+        prev = np.empty((H, W, 4), np.float32)
+        prev[...] = c
+        return O.imagespace_pass(base, prev, W, H, kk, libpath=lp).reshape(H, W, 4)
+
+    for c in [(0.5, 0.5, 0.5, 0.0), (0.5, 0.5, 1.0, 2.0), (0.5, 0.5, 0.0, 9.0)]:
+        assert np.array_equal(run(c), base)
+    mx = lambda i: O.mirror_index(i, W, libpath=lp)
+    my = lambda i: O.mirror_index(i, H, libpath=lp)
+    for (c, fx, fy) in [((1.0, 0.5, 0.5, 0), lambda x: mx(x + 3), lambda y: y),
+                        ((0.0, 0.5, 0.5, 0), lambda x: mx(x - 3), lambda y: y),
+                        ((0.5, 1.0, 0.5, 0), lambda x: x, lambda y: my(y - 3)),
+                        ((0.5, 0.0, 0.5, 0), lambda x: x, lambda y: my(y + 3)),
+                        ((1.0, 1.0, 0.5, 0), lambda x: mx(x + 3), lambda y: my(y - 3))]:
+        out = run(c)
+        for y in range(H):
+            for x in range(W):
+                assert out[y, x, 0] == fx(x) and out[y, x, 1] == fy(y), (c, x, y)
+                assert out[y, x, 2] == 7.0 and out[y, x, 3] == fy(y) * W + fx(x)
+
+
+def check_imagespace_rounding(lp=None):
+    """The nearest pixel is taken; halves round up (towards +x / +y)."""
+    W, H = 9, 5
+    base = _ramp(W, H)
+    prev = np.full((H, W, 4), 0.5, np.float32)
+    prev[..., 0] = 1.0
+    for kk, shift in [(1.4, 1), (1.6, 2), (0.5, 1), (0.49, 0), (2.5, 3)]:
+        out = O.imagespace_pass(base, prev, W, H, kk, libpath=lp).reshape(H, W, 4)
+        assert out[2, 3, 0] == 3 + shift, (kk, out[2, 3, 0])
+    prev[..., 0] = 0.0
+    out = O.imagespace_pass(base, prev, W, H, 0.5, libpath=lp).reshape(H, W, 4)
+    assert out[2, 3, 0] == 3  # x - 0.5 rounds half up to x
+    sub = O.imagespace_pass(base, prev, W, H, 2.0, pix=np.array([0, 13, 44]), libpath=lp)
+    full = O.imagespace_pass(base, prev, W, H, 2.0, libpath=lp)
+    assert np.array_equal(sub, full[[0, 13, 44]])
+
+
 ALL_CHECKS = [v for k, v in sorted(globals().items()) if k.startswith("check_")]

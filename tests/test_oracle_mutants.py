@@ -43,6 +43,11 @@ MUTANTS = {
     "no_recursion": ("memcpy(c, rgbz, sizeof(double) * 4);", "(void)rgbz;"),
     "sphere_id_offset": ("best_id = s->T + j;", "best_id = j;"),
     "flag_dropped": ("    *flag = amb;\n    return 0;\n}\n\n/*\n * Any hit", "    *flag = 0;\n    return 0;\n}\n\n/*\n * Any hit"),
+    "image_green_sign": ("const float sy = (float)y - k_px * dg;", "const float sy = (float)y + k_px * dg;"),
+    "image_uses_blue": ("const float dg = 2.0f * c[1] - 1.0f;", "const float dg = 2.0f * c[2] - 1.0f;"),
+    "image_round_down": ("(int64_t)floorf(sx + 0.5f)", "(int64_t)floorf(sx)"),
+    "mirror_repeats_edge": ("return m < n ? m : period - 1 - m;", "return m < n ? m : period - m;"),
+    "image_no_centering": ("const float dr = 2.0f * c[0] - 1.0f;", "const float dr = c[0];"),
     "tmin_ignored": ("if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > tmin && t < best)",
                      "if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > 0.0 && t < best)"),
 }
