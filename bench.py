@@ -9,7 +9,7 @@ replayed from the library's captured CUDA graph with the scene resident in HBM.
 L2 is flushed (a 256 MB write) between steps, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload mid|forest|batched|served|stress]
+                    [--workload mid|forest|batched|served|stress|imagespace]
 
 With N > 1 (torchrun) every rank renders its own poses (replicas, no
 collective on the data path); the time is the max over ranks.
@@ -719,13 +719,70 @@ def run_stress(args):
     print(json.dumps(res), flush=True)
 
 
+def run_imagespace(args):
+    """The image-space reduction (§6): mid terrain at 3840x2160, K=6; pass 1 is
+    traced, passes 2..6 gather from it (k = 8 pixels, mirrored edges). The
+    gather kernel's roofline is HBM: 48 bytes per pixel (read I_{n-1} and the
+    traced image, write I_n), 398 MB per pass at 4K (above the 129 MB L2)."""
+    import torch
+
+    from paper_2312_12392_gb300 import build as B
+    from paper_2312_12392_gb300 import rcp
+    torch.cuda.set_device(0)
+    B.build()
+    sc, _ = make_workload("mid")
+    W, H, K, kpx = 3840, 2160, 6, 8.0
+    d = sc.diameter()
+    params = rcp.make_params(rcp.RCP_MAP_IMAGE, kpx, 0.1 * d)
+    g = rcp.scene_from(sc)
+    stream = torch.cuda.current_stream()
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(args.steps + args.warmup)]
+    for i in range(args.warmup):
+        rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
+    torch.cuda.synchronize()
+    frame_ms, trace_ms, gather_ms = [], [], []
+    for i in range(args.warmup, args.warmup + args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
+        e.record(stream)
+        e.synchronize()
+        frame_ms.append(s.elapsed_time(e))
+        pt = rcp.rcp_last_pass_times(g)
+        trace_ms.append(pt[0])
+        gather_ms.extend(pt[1:])
+    hbm_gbs, _, peak_src = measured_peaks()
+    g_s = statistics.mean(gather_ms) / 1000.0
+    bytes_launch = 48.0 * W * H
+    tot = sum(frame_ms) / 1000.0
+    res = {
+        "metric": "frames_per_s (image-space reduction, 3840x2160, K=6)",
+        "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "mid terrain 133k tris, 3840x2160, K=6, RCP_MAP_IMAGE k=8 px: 1 traced pass + 5 "
+                               "gather passes", "l2": "flushed between steps"},
+        "trace_pass_ms": statistics.mean(trace_ms),
+        "roofline": {"bound": "hbm", "kernel": "k_imagespace (one gather pass)", "launch_ms": g_s * 1e3,
+                     "achieved": bytes_launch / g_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                     "frac": bytes_launch / g_s / 1e9 / hbm_gbs, "traffic": None,
+                     "algorithmic_bytes_per_launch": bytes_launch, "peak_source": peak_src},
+        "gpu_launches": args.steps * K,
+    }
+    rcp.rcp_scene_destroy(g)
+    print(json.dumps(res), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress", "imagespace"])
     ap.add_argument("--tuning", default="128,32,1", help="'auto' or block,chunk,fused_camera")
     ap.add_argument("--count-poses", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -746,6 +803,8 @@ def main(argv=None):
         run_served(args)
     elif args.workload == "stress":
         run_stress(args)
+    elif args.workload == "imagespace":
+        run_imagespace(args)
     else:
         run_ours(args)
 

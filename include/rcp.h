@@ -70,8 +70,14 @@ typedef struct {
  *                  P_p (at focal_dist along the view axis).
  *  RCP_MAP_TARGET: P'_e = P_e, P'_p = P_p + V (the paper's §3 example).
  *  RCP_MAP_DEPTH:  P'_e = P_e, P'_p = P_p + |z - z0| * V, z = the previous
- *                  pass's hit distance (§4, Eq. 7). */
-typedef enum { RCP_MAP_EYE = 0, RCP_MAP_TARGET = 1, RCP_MAP_DEPTH = 2 } rcp_mapping;
+ *                  pass's hit distance (§4, Eq. 7).
+ *  RCP_MAP_IMAGE:  the image-space reduction of §6 (V_e = 0): pass 1 is traced;
+ *                  every later pass re-samples pass 1's image at the pixel
+ *                  displaced by k * (2r - 1) to the right and k * (2g - 1) up
+ *                  (k in PIXELS for this mapping), nearest pixel, with the
+ *                  screen edges mirrored (§6.1). K-pass device and host renders
+ *                  only; it needs no scene work after pass 1. */
+typedef enum { RCP_MAP_EYE = 0, RCP_MAP_TARGET = 1, RCP_MAP_DEPTH = 2, RCP_MAP_IMAGE = 3 } rcp_mapping;
 
 typedef struct {
     int32_t mapping;  /* rcp_mapping */
@@ -139,6 +145,15 @@ rcp_status rcp_render_pass(const rcp_scene* scene, const rcp_camera* cam, int wi
 rcp_status rcp_render_device(const rcp_scene* scene, const rcp_camera* cam, int width, int height,
                              int K, const rcp_params* params, const float* d_in, float* d_out,
                              int32_t* d_prim, void* stream);
+
+/* One image-space pass (§6, §6.1) on device images (rgbz, width*height*4
+ * floats each): out(x,y) = base at the nearest pixel to (x + k_px (2r - 1),
+ * y - k_px (2g - 1)), (r, g) = prev(x,y), indices reflected into the image
+ * without repeating the edge pixel (-1 -> 0, width -> width-1, repeatedly).
+ * The displacement and rounding are computed in float32. out must not alias
+ * base or prev. Enqueued on `stream`. */
+rcp_status rcp_imagespace_pass_device(const float* d_base, const float* d_prev, float* d_out, int width,
+                                      int height, float k_px, void* stream);
 
 /* Many views of one scene in one persistent launch per pass (§2's per-(u,v)
  * cameras for every view at once). cams, widths, heights: host arrays of

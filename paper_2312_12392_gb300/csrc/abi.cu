@@ -45,6 +45,7 @@ RenderCtx::~RenderCtx() {
     if (d_rays) cudaFree(d_rays);
     if (io) cudaFree(io);
     if (io_prim) cudaFree(io_prim);
+    if (base_img) cudaFree(base_img);
     if (done) {
         cudaEventSynchronize(done);
         cudaEventDestroy(done);
@@ -111,6 +112,9 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.H = H;
     v.mapping = p.mapping;
     v.z0 = p.z0;
+    v.kpx = p.mapping == RCP_MAP_IMAGE ? p.k : 0.f;
+    v.pad0_ = 0;
+    v.base = nullptr;
     v.in = nullptr;
     v.out = nullptr;
     v.prim = nullptr;
@@ -156,7 +160,7 @@ rcp_status check_view(const rcp_camera* cam, int W, int H, const rcp_params* p) 
         set_error("k must be >= 0 and focal_dist > 0, all finite");
         return RCP_ERR_ARG;
     }
-    if (p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_DEPTH) {
+    if (p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_IMAGE) {
         set_error("unknown mapping");
         return RCP_ERR_ARG;
     }
@@ -274,9 +278,11 @@ rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg,
     const SceneDev S = sc.dev();
     RCP_CUDA(record(ctx.pass_ev[0]));
     for (int n = 0; n < ctx.K; ++n) {
-        rcp_status r = launch_pass(S, cfg, ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix,
-                                   ctx.total_chunks, ctx.rays, ctx.d_work + n, ctx.d_status, ctx.d_rays, counters,
-                                   st);
+        rcp_status r = (ctx.image_mode && n > 0)
+                           ? launch_imagespace(ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix, st)
+                           : launch_pass(S, cfg, ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix,
+                                         ctx.total_chunks, ctx.rays, ctx.d_work + n, ctx.d_status, ctx.d_rays,
+                                         counters, st);
         if (r != RCP_OK) return r;
         RCP_CUDA(record(ctx.pass_ev[n + 1]));
     }
@@ -286,7 +292,7 @@ rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg,
 // Run the K passes through the context's CUDA graph (captured on first use or
 // when the launch configuration changes).
 rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cudaStream_t st) {
-    const std::string key = cfg_key(cfg);
+    const std::string key = cfg_key(cfg) + (ctx.image_mode ? "/image" : "/trace");
     if (!ctx.graph || ctx.graph_key != key) {
         if (ctx.graph) {
             cudaGraphExecDestroy(ctx.graph);
@@ -317,14 +323,23 @@ rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const f
                        float4* const* outs, int32_t* const* prims, cudaStream_t st) {
     RCP_CUDA(cudaEventSynchronize(ctx.staged));  // previous copy out of the staging buffer is done
     const int K = ctx.K, nv = ctx.n_views;
+    ctx.image_mode = base[0].mapping == RCP_MAP_IMAGE && K > 1;
+    if (ctx.image_mode && !ctx.base_img) RCP_CUDA(cudaMalloc((void**)&ctx.base_img, sizeof(float4) * ctx.total_pix));
     for (int n = 0; n < K; ++n) {
         for (int i = 0; i < nv; ++i) {
             ViewDev v = base[i];
-            const float4* prev = (n == 0) ? (ins ? ins[i] : nullptr) : ctx.img[(n - 1) & 1] + base[i].pix_begin;
-            float4* cur = (n == K - 1) ? outs[i] : ctx.img[n & 1] + base[i].pix_begin;
+            const int64_t off = base[i].pix_begin;
+            float4* cur = (n == K - 1) ? outs[i] : ctx.img[n & 1] + off;
+            const float4* prev = (n == 0) ? (ins ? ins[i] : nullptr) : ctx.img[(n - 1) & 1] + off;
+            if (ctx.image_mode) {
+                // pass 1 is traced into base_img; pass n >= 2 gathers from it
+                if (n == 0) cur = ctx.base_img + off;
+                if (n == 1) prev = ctx.base_img + off;
+                v.base = ctx.base_img + off;
+            }
             v.in = prev;
             v.out = cur;
-            v.prim = (n == K - 1 && prims) ? prims[i] : nullptr;
+            v.prim = (n == K - 1 && prims && !ctx.image_mode) ? prims[i] : nullptr;
             ctx.h_views[(size_t)n * nv + i] = v;
         }
     }
@@ -353,6 +368,10 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
             return RCP_ERR_ARG;
         }
         make_view(base[i], cams[i], Ws[i], Hs[i], *p);
+        if (p->mapping == RCP_MAP_IMAGE && ins && ins[i]) {
+            set_error("RCP_MAP_IMAGE renders start from I_0 (d_in must be NULL); use rcp_imagespace_pass_device");
+            return RCP_ERR_ARG;
+        }
     }
     if (sc.depth > MAX_STACK) {
         set_error("BVH deeper than the traversal stack");
@@ -587,6 +606,11 @@ rcp_status rcp_render_pass(const rcp_scene* csc, const rcp_camera* cam, int W, i
     std::lock_guard<std::mutex> lk(sc->mu);
     rcp_status r = check_view(cam, W, H, p);
     if (r != RCP_OK) return r;
+    if (p->mapping == RCP_MAP_IMAGE) {
+        set_error("rcp_render_pass: an image-space pass needs the frame's traced image; use "
+                  "rcp_imagespace_pass_device");
+        return RCP_ERR_ARG;
+    }
     cudaStream_t st = lib_stream();
     const int64_t P = (int64_t)W * H;
     RenderCtx* ctx = nullptr;
@@ -606,6 +630,25 @@ rcp_status rcp_render_pass(const rcp_scene* csc, const rcp_camera* cam, int W, i
     if (out_prim)
         RCP_CUDA(cudaMemcpyAsync(out_prim, ctx->io_prim, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
     return check_status(*ctx, st);
+}
+
+rcp_status rcp_imagespace_pass_device(const float* d_base, const float* d_prev, float* d_out, int W, int H,
+                                      float k_px, void* stream) {
+    if (!d_base || !d_prev || !d_out || W < 1 || H < 1 || W > 8192 || H > 8192 || !(k_px >= 0.f) ||
+        !std::isfinite(k_px)) {
+        set_error("rcp_imagespace_pass_device: NULL image, size outside [1, 8192] or k_px not finite >= 0");
+        return RCP_ERR_ARG;
+    }
+    if (((uintptr_t)d_base | (uintptr_t)d_prev | (uintptr_t)d_out) & 15) {
+        set_error("rcp_imagespace_pass_device: images must be 16-byte aligned");
+        return RCP_ERR_ARG;
+    }
+    if (d_out == d_base || d_out == d_prev) {
+        set_error("rcp_imagespace_pass_device: out must not alias base or prev");
+        return RCP_ERR_ARG;
+    }
+    return launch_imagespace_single((const float4*)d_base, (const float4*)d_prev, (float4*)d_out, W, H, k_px,
+                                    (cudaStream_t)stream);
 }
 
 rcp_status rcp_get_tuning(const rcp_scene* sc, rcp_tuning* out) {

@@ -67,8 +67,11 @@ struct ViewDev {
     int W, H;
     int mapping;
     float z0;
-    const float4* in;  // previous image, nullptr = I_0
-    float4* out;       // this pass's image
+    float kpx;  // image-space displacement strength (pixels)
+    int pad0_;
+    const float4* in;    // previous image, nullptr = I_0
+    const float4* base;  // image-space passes: the frame's traced image
+    float4* out;         // this pass's image
     int32_t* prim;     // nullable hit ids
     int64_t pix_begin;  // first global pixel index of this view
     int64_t chunk_begin;  // first work chunk (8x4 tile) of this view

@@ -31,6 +31,8 @@ struct RenderCtx {
     unsigned long long* d_rays = nullptr;  // rays traced by the last render: primary, shadow
     float* d_rgb = nullptr;      // packed RGB for host output
     float4* io = nullptr;        // host-API input / final image
+    float4* base_img = nullptr;  // image-space mapping: the traced pass-1 image
+    bool image_mode = false;     // passes 2..K are image-space gathers
     int32_t* io_prim = nullptr;  // host-API hit ids
     cudaEvent_t staged = nullptr;
     cudaEvent_t pass_ev[17] = {};  // timing events around every pass (recorded inside the graph)
@@ -93,6 +95,10 @@ rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
                               int brute, float* t_out, int32_t* prim_out, int* d_status, cudaStream_t st);
 rcp_status launch_pack_rgb(const float4* img, float* rgb, int64_t n, cudaStream_t st);
+// Image-space pass over every view (views' base/in/out set).
+rcp_status launch_imagespace(const ViewDev* d_views, int n_views, int64_t total_pix, cudaStream_t st);
+rcp_status launch_imagespace_single(const float4* base, const float4* prev, float4* out, int W, int H, float kpx,
+                                    cudaStream_t st);
 
 }  // namespace rcp
 

@@ -162,6 +162,51 @@ __global__ void k_pack_rgb(const float4* __restrict__ img, float* __restrict__ r
     }
 }
 
+// ---------------------------------------------------------------- image space (§6, §6.1)
+
+// Reflect a pixel index into [0, n) about the image edges, the edge pixel not
+// repeated (-1 -> 0, n -> n-1), as often as needed.
+__device__ __forceinline__ int64_t mirror_px(int64_t i, int64_t n) {
+    if (i >= 0 && i < n) return i;
+    if (n <= 1) return 0;
+    const int64_t period = 2 * n;
+    int64_t m = i % period;
+    if (m < 0) m += period;
+    return m < n ? m : period - 1 - m;
+}
+
+// I_n(x, y) = base at the nearest pixel to (x + kpx (2r - 1), y - kpx (2g - 1)),
+// (r, g) = I_{n-1}(x, y); float32 without fused multiply-add decides the pixel.
+__device__ __forceinline__ float4 gather_pixel(const float4* __restrict__ base, const float4* __restrict__ prev,
+                                               int W, int H, int x, int y, float kpx) {
+    const float4 c = __ldg(prev + (int64_t)y * W + x);
+    const float dr = __fsub_rn(__fmul_rn(2.f, c.x), 1.f);
+    const float dg = __fsub_rn(__fmul_rn(2.f, c.y), 1.f);
+    const float sx = __fadd_rn((float)x, __fmul_rn(kpx, dr));
+    const float sy = __fsub_rn((float)y, __fmul_rn(kpx, dg));
+    const int64_t ix = mirror_px((int64_t)floorf(__fadd_rn(sx, 0.5f)), W);
+    const int64_t iy = mirror_px((int64_t)floorf(__fadd_rn(sy, 0.5f)), H);
+    return __ldg(base + iy * W + ix);
+}
+
+__global__ void __launch_bounds__(256) k_imagespace(const ViewDev* __restrict__ views, int n_views, int64_t total_pix) {
+    for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp < total_pix;
+         gp += (int64_t)gridDim.x * blockDim.x) {
+        const ViewDev& v = views[find_view_by_pix(views, n_views, gp)];
+        const int64_t p = gp - v.pix_begin;
+        const int x = (int)(p % v.W), y = (int)(p / v.W);
+        v.out[p] = gather_pixel(v.base, v.in, v.W, v.H, x, y, v.kpx);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_imagespace_single(const float4* __restrict__ base,
+                                                          const float4* __restrict__ prev, float4* __restrict__ out,
+                                                          int W, int H, float kpx) {
+    const int64_t P = (int64_t)W * H;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = gather_pixel(base, prev, W, H, (int)(p % W), (int)(p / W), kpx);
+}
+
 int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -243,6 +288,26 @@ rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tm
     if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
     k_debug_trace<128><<<(int)g, 128, smem, st>>>(S, n, (const float4*)orig_tmin, (const float4*)dir_tmax, any, brute,
                                                  t_out, prim_out, d_status);
+    RCP_CUDA(cudaGetLastError());
+    return RCP_OK;
+}
+
+rcp_status launch_imagespace(const ViewDev* d_views, int n_views, int64_t total_pix, cudaStream_t st) {
+    int64_t g = (total_pix + 255) / 256;
+    if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+    if (g < 1) g = 1;
+    k_imagespace<<<(int)g, 256, 0, st>>>(d_views, n_views, total_pix);
+    RCP_CUDA(cudaGetLastError());
+    return RCP_OK;
+}
+
+rcp_status launch_imagespace_single(const float4* base, const float4* prev, float4* out, int W, int H, float kpx,
+                                    cudaStream_t st) {
+    const int64_t P = (int64_t)W * H;
+    int64_t g = (P + 255) / 256;
+    if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+    if (g < 1) g = 1;
+    k_imagespace_single<<<(int)g, 256, 0, st>>>(base, prev, out, W, H, kpx);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }

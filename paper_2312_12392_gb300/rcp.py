@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "librcp.so")
 
 RCP_OK, RCP_ERR_ARG, RCP_ERR_OOM, RCP_ERR_CUDA, RCP_ERR_STACK, RCP_ERR_TIMEOUT, RCP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 RCP_LIGHT_POINT, RCP_LIGHT_DIRECTIONAL = 0, 1
-RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH = 0, 1, 2
+RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH, RCP_MAP_IMAGE = 0, 1, 2, 3
 
 
 class RcpError(RuntimeError):
@@ -93,6 +93,7 @@ _SIGS = {
     "rcp_debug_trace": [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp],
     "rcp_debug_sort_pairs": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_debug_morton": [_vp, C.c_int64, _vp, _vp, _vp, _vp],
+    "rcp_imagespace_pass_device": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp],
     "rcp_sort_pairs_static": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_server_create": [C.c_int64, C.c_int, C.POINTER(_vp)],
     "rcp_server_submit": [_vp, _vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.c_int, C.POINTER(rcp_params), _vp,
@@ -253,6 +254,11 @@ def rcp_render_batch_device(scene, cams, widths, heights, K, params: rcp_params,
     oa = (C.c_void_p * n)(*[_ptr(o) for o in d_outs])
     _check(lib().rcp_render_batch_device(scene, n, ca, wa, ha, K, C.byref(params), oa, _stream(stream)),
            "rcp_render_batch_device")
+
+
+def rcp_imagespace_pass_device(d_base, d_prev, d_out, width, height, k_px, stream=None):
+    _check(lib().rcp_imagespace_pass_device(_ptr(d_base), _ptr(d_prev), _ptr(d_out), width, height, float(k_px),
+                                            _stream(stream)), "rcp_imagespace_pass_device")
 
 
 def rcp_get_tuning(scene) -> rcp_tuning:
