@@ -25,7 +25,7 @@ _LIB = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-MAP_EYE, MAP_TARGET, MAP_DEPTH = 0, 1, 2
+MAP_EYE, MAP_TARGET, MAP_DEPTH, MAP_NORMAL = 0, 1, 2, 4
 LIGHT_POINT, LIGHT_DIRECTIONAL = 0, 1
 TOL = 1e-5
 
@@ -70,6 +70,10 @@ def _bind(lib):
     lib.orc_imagespace_pass.argtypes = [fp, fp, i32, i32, C.c_float, lp, i64, fp]
     lib.orc_mirror_index.restype = i64
     lib.orc_mirror_index.argtypes = [i64, i64]
+    lib.orc_normal_encode.restype = C.c_uint32
+    lib.orc_normal_encode.argtypes = [dp]
+    lib.orc_normal_decode.restype = i32
+    lib.orc_normal_decode.argtypes = [C.c_uint32, dp]
     lib.orc_render.restype = i32
     lib.orc_render.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, lp, i64, dp, ip, up, i32]
     return lib
@@ -223,4 +227,23 @@ def imagespace_pass(base, prev, W, H, k_px, pix=None, libpath=None):
                                           fptr(out))
     if rc != 0:
         raise ValueError("orc_imagespace_pass rejected its arguments")
+    return out
+
+
+def normal_encode(n, libpath=None):
+    return int(lib(libpath).orc_normal_encode(_dp(_vec(n))))
+
+
+def normal_decode(code, libpath=None):
+    out = np.zeros(3)
+    ok = lib(libpath).orc_normal_decode(int(code) & 0xffffffff, _dp(out))
+    return out, bool(ok)
+
+
+def rgbz_to_image(rgbz, mapping):
+    """Oracle pass output (n, 4) float64 -> float32 image rows; for the normal
+    mapping the fourth lane's value is the 32-bit normal code, stored as bits."""
+    out = np.asarray(rgbz, dtype=np.float32).copy()
+    if mapping == MAP_NORMAL:
+        out[:, 3] = np.asarray(rgbz[:, 3], dtype=np.uint64).astype(np.uint32).view(np.float32)
     return out

@@ -160,9 +160,18 @@ int orc_camera_ray(const double cam[10], int W, int H, int x, int y, int mapping
     for (int a = 0; a < 3; ++a) Pp[a] = Pe[a] + f * (F[a] + sx * R[a] + sy * U[a]);
     const double dr = 2.0 * c[0] - 1.0, dg = 2.0 * c[1] - 1.0, db = 2.0 * c[2] - 1.0;
     for (int a = 0; a < 3; ++a) V[a] = k * (dr * R[a] + dg * U[a] + db * F[a]);
+    if (mapping == ORC_MAP_NORMAL) {
+        /* §5, Eq. 8: V_p = k (C x N); z carries the previous pass's normal code */
+        double N[3], C[3], X[3];
+        sub3(Pp, Pe, C);
+        normalize3(C);
+        orc_normal_decode((uint32_t)z, N);
+        cross3(C, N, X);
+        for (int a = 0; a < 3; ++a) V[a] = k * X[a];
+    }
     if (mapping == ORC_MAP_EYE) {
         for (int a = 0; a < 3; ++a) { Pe2[a] = Pe[a] + V[a]; Pp2[a] = Pp[a]; }
-    } else if (mapping == ORC_MAP_TARGET) {
+    } else if (mapping == ORC_MAP_TARGET || mapping == ORC_MAP_NORMAL) {
         for (int a = 0; a < 3; ++a) { Pe2[a] = Pe[a]; Pp2[a] = Pp[a] + V[a]; }
     } else {
         const double m = fabs(z - z0);
@@ -535,6 +544,54 @@ typedef struct {
     pthread_mutex_t mu;
 } job_t;
 
+/* ---------------------------------------------------------------- normals */
+
+/* Octahedral map of a unit vector (the sphere folded onto the octahedron
+ * |x|+|y|+|z| = 1 and unfolded into the square [-1,1]^2), then 16 bits per
+ * coordinate. Reading: §5 stores normals with the image; the code packs one
+ * into the image's fourth float lane. */
+uint32_t orc_normal_encode(const double n[3]) {
+    const double s = fabs(n[0]) + fabs(n[1]) + fabs(n[2]);
+    if (!(s > 0.0)) return 0;
+    double px = n[0] / s, py = n[1] / s;
+    if (n[2] < 0.0) {
+        const double ox = px, oy = py;
+        px = (1.0 - fabs(oy)) * (ox >= 0.0 ? 1.0 : -1.0);
+        py = (1.0 - fabs(ox)) * (oy >= 0.0 ? 1.0 : -1.0);
+    }
+    const long qx = lround(px * 32767.0), qy = lround(py * 32767.0);
+    return (uint32_t)(qx + 32768) | ((uint32_t)(qy + 32768) << 16);
+}
+
+int orc_normal_decode(uint32_t code, double n[3]) {
+    if (code == 0) {
+        n[0] = n[1] = n[2] = 0.0;
+        return 0;
+    }
+    const double px = ((double)(code & 0xffffu) - 32768.0) / 32767.0;
+    const double py = ((double)(code >> 16) - 32768.0) / 32767.0;
+    double x = px, y = py;
+    const double zz = 1.0 - fabs(px) - fabs(py);
+    if (zz < 0.0) {
+        x = (1.0 - fabs(py)) * (px >= 0.0 ? 1.0 : -1.0);
+        y = (1.0 - fabs(px)) * (py >= 0.0 ? 1.0 : -1.0);
+    }
+    n[0] = x;
+    n[1] = y;
+    n[2] = zz;
+    normalize3(n);
+    return 1;
+}
+
+/* The facing geometric normal of the primary hit of ray (o, d), 0 on a miss. */
+static uint32_t hit_normal_code(const orc_scene* s, const double o[3], const double d[3], int64_t id, double t) {
+    if (id < 0) return 0;
+    double p[3], N[3];
+    for (int a = 0; a < 3; ++a) p[a] = o[a] + t * d[a];
+    hit_normal(s, id, p, d, N);
+    return orc_normal_encode(N);
+}
+
 /* One pixel's chain of `passes` passes starting from colour c (I_{n-1}). */
 static void run_pixel(const job_t* J, int64_t i, double c[4], int passes) {
     const int64_t p = J->pix ? J->pix[i] : i;
@@ -548,7 +605,10 @@ static void run_pixel(const job_t* J, int64_t i, double c[4], int passes) {
         orc_shade_ray(J->s, o, d, rgbz, &id, &amb);
         fl |= (uint8_t)amb;
         memcpy(c, rgbz, sizeof(double) * 4);
-        if (c[3] < 0.0) c[3] = 0.0; /* a miss carries depth 0 into the next pass */
+        if (J->mapping == ORC_MAP_NORMAL)
+            c[3] = (double)hit_normal_code(J->s, o, d, id, rgbz[3]); /* the lane carries the normal code */
+        else if (c[3] < 0.0)
+            c[3] = 0.0; /* a miss carries depth 0 into the next pass */
     }
     J->out[4 * i + 0] = c[0];
     J->out[4 * i + 1] = c[1];
@@ -572,6 +632,11 @@ static void* worker(void* arg) {
             if (J->in) {
                 const int64_t p = J->pix ? J->pix[i] : i;
                 for (int a = 0; a < 4; ++a) c[a] = (double)J->in[4 * p + a];
+                if (J->mapping == ORC_MAP_NORMAL) {
+                    uint32_t bits;
+                    memcpy(&bits, J->in + 4 * p + 3, 4);
+                    c[3] = (double)bits;
+                }
             }
             run_pixel(J, i, c, J->K);
         }
@@ -597,7 +662,8 @@ static int run_job(job_t* J, int nthreads) {
 
 static int check_common(const orc_scene* s, const double* cam, int W, int H, int mapping, double k, double f) {
     if (!s || !cam || W < 1 || H < 1 || k < 0.0 || !(f > 0.0)) return -1;
-    if (mapping < ORC_MAP_EYE || mapping > ORC_MAP_DEPTH) return -1;
+    if (mapping != ORC_MAP_EYE && mapping != ORC_MAP_TARGET && mapping != ORC_MAP_DEPTH && mapping != ORC_MAP_NORMAL)
+        return -1;
     return 0;
 }
 

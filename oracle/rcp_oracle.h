@@ -40,8 +40,19 @@ extern "C" {
  * ORC_MAP_TARGET: V_e = 0, V_p = k*(2c-1) in (right, up, forward): the paper's
  *                 own example in §3.
  * ORC_MAP_DEPTH:  V_e = 0, V_p = k*|z - z0|*(2c-1) (§4, Eq. 7); z is the
- *                 previous pass's hit distance, stored beside the colour. */
-enum { ORC_MAP_EYE = 0, ORC_MAP_TARGET = 1, ORC_MAP_DEPTH = 2 };
+ *                 previous pass's hit distance, stored beside the colour.
+ * ORC_MAP_NORMAL: V_e = 0, V_p = k*(C x N) (§5, Eq. 8); C = the pixel's
+ *                 undisplaced pinhole direction, N = the previous pass's hit
+ *                 normal (facing its ray), carried in the image's fourth lane
+ *                 as a 32-bit octahedral code (0 = no normal: I_0 and misses). */
+enum { ORC_MAP_EYE = 0, ORC_MAP_TARGET = 1, ORC_MAP_DEPTH = 2, ORC_MAP_NORMAL = 4 };
+
+/* Octahedral unit-vector code (two 16-bit fields, each q + 32768 with
+ * q = round(32767 p) in [-32767, 32767], p the octahedral coordinates), so a
+ * real normal never has code 0. */
+uint32_t orc_normal_encode(const double n[3]);
+/* Returns 0 and zeroes n for code 0, else writes the unit vector and returns 1. */
+int orc_normal_decode(uint32_t code, double n[3]);
 enum { ORC_LIGHT_POINT = 0, ORC_LIGHT_DIRECTIONAL = 1 };
 
 /* Relative distance under which a ray counts as ambiguous (near an edge, a

@@ -516,4 +516,61 @@ def check_imagespace_rounding(lp=None):
     assert np.array_equal(sub, full[[0, 13, 44]])
 
 
+# --------------------------------------------------------------------------- normal mapping (§5, Eq. 8)
+
+def check_normal_codes(lp=None):
+    """Octahedral codes: round trip within 1e-4, never 0 for a real normal,
+    0 decodes to 'no normal'; the six axes come back exactly."""
+    rng = np.random.default_rng(8)
+    for _ in range(500):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        c = O.normal_encode(n, libpath=lp)
+        m, ok = O.normal_decode(c, libpath=lp)
+        assert c != 0 and ok and np.linalg.norm(m - n) < 1e-4
+    for ax in np.vstack([np.eye(3), -np.eye(3)]):
+        m, ok = O.normal_decode(O.normal_encode(ax, libpath=lp), libpath=lp)
+        assert ok and np.allclose(m, ax, atol=1e-12)
+    m, ok = O.normal_decode(0, libpath=lp)
+    assert not ok and not m.any()
+
+
+def check_normal_mapping_camera(lp=None):
+    """V_p = k (C x N): for the centre ray C = (0,0,-1) and N = +y the target
+    moves by +k along x (right); N along C does not move it; no normal (code
+    0, as in I_0) gives the pinhole ray."""
+    W, H, k, f = 21, 21, 0.7, 4.0
+    x, y = W // 2, H // 2
+    _, d0 = _ray(CAM_Z, W, H, x, y, O.MAP_TARGET, 0.0, f, lp=lp)
+    code_up = O.normal_encode([0.0, 1.0, 0.0], libpath=lp)
+    o, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, z=float(code_up), lp=lp)
+    P = o + d * (f / -d[2])  # where the ray meets the focal plane z = -f
+    assert np.allclose(P, [k, 0.0, -f], atol=1e-4 * k)
+    code_back = O.normal_encode([0.0, 0.0, 1.0], libpath=lp)
+    _, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, z=float(code_back), lp=lp)
+    assert np.allclose(d, d0, atol=1e-12)
+    _, d = _ray(CAM_Z, W, H, 3, 5, O.MAP_NORMAL, k, f, z=0.0, lp=lp)
+    _, e = _ray(CAM_Z, W, H, 3, 5, O.MAP_TARGET, 0.0, f, lp=lp)
+    assert np.array_equal(d, e)
+
+
+def check_normal_mapping_render(lp=None):
+    """Pass 1 is pinhole (I_0 has no normal); a ground plane seen straight on
+    from above has N parallel to C at the centre, so the centre pixel keeps its
+    colour; the fourth lane carries the hit normal's code (0 on a miss)."""
+    L = np.array([0.3, 0.8, 0.2])
+    sc = _scene(tris=GROUND, albedo=[[0.6, 0.4, 0.2]] * 2, light=L, lp=lp)
+    cam = np.array([0.3, 4.0, 0.2, 0.3, 0.0, 0.2, 0.0, 0.0, -1.0, 40.0])
+    W, H = 9, 7
+    a, pa, _ = sc.render_pass(cam, W, H, O.MAP_NORMAL, 0.5, 1.0)
+    b, pb, _ = sc.render_pass(cam, W, H, O.MAP_TARGET, 0.0, 1.0)
+    assert np.array_equal(a[:, :3], b[:, :3]) and np.array_equal(pa, pb)
+    up = O.normal_encode([0.0, 1.0, 0.0], libpath=lp)
+    assert np.all(a[:, 3] == up)
+    img = O.rgbz_to_image(a, O.MAP_NORMAL).reshape(H, W, 4)
+    c2, _, _ = sc.render_pass(cam, W, H, O.MAP_NORMAL, 0.5, 1.0, in_rgbz=img)
+    centre = (H // 2) * W + W // 2
+    assert np.allclose(c2[centre, :3], a[centre, :3], atol=1e-12)
+
+
 ALL_CHECKS = [v for k, v in sorted(globals().items()) if k.startswith("check_")]

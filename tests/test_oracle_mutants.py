@@ -48,6 +48,10 @@ MUTANTS = {
     "image_round_down": ("(int64_t)floorf(sx + 0.5f)", "(int64_t)floorf(sx)"),
     "mirror_repeats_edge": ("return m < n ? m : period - 1 - m;", "return m < n ? m : period - m;"),
     "image_no_centering": ("const float dr = 2.0f * c[0] - 1.0f;", "const float dr = c[0];"),
+    "normal_cross_swapped": ("cross3(C, N, X);", "cross3(N, C, X);"),
+    "normal_no_fold": ("    if (zz < 0.0) {\n        x = (1.0 - fabs(py))", "    if (0) {\n        x = (1.0 - fabs(py))"),
+    "normal_code_no_offset": ("return (uint32_t)(qx + 32768) | ((uint32_t)(qy + 32768) << 16);",
+                              "return (uint32_t)(qx & 0xffff) | ((uint32_t)(qy & 0xffff) << 16);"),
     "tmin_ignored": ("if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > tmin && t < best)",
                      "if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > 0.0 && t < best)"),
 }
