@@ -76,8 +76,20 @@ typedef struct {
  *                  displaced by k * (2r - 1) to the right and k * (2g - 1) up
  *                  (k in PIXELS for this mapping), nearest pixel, with the
  *                  screen edges mirrored (§6.1). K-pass device and host renders
- *                  only; it needs no scene work after pass 1. */
-typedef enum { RCP_MAP_EYE = 0, RCP_MAP_TARGET = 1, RCP_MAP_DEPTH = 2, RCP_MAP_IMAGE = 3 } rcp_mapping;
+ *                  only; it needs no scene work after pass 1.
+ *  RCP_MAP_NORMAL: P'_e = P_e, P'_p = P_p + k * (C x N) (§5, Eq. 8): C = the
+ *                  pixel's undisplaced pinhole direction, N = the previous
+ *                  pass's hit normal (facing its ray). For this mapping the
+ *                  fourth float of every rgbz pixel holds, as raw bits, a 32-bit
+ *                  octahedral code of that normal (two 16-bit fields q + 32768,
+ *                  q = round(32767 p)); code 0 = no normal (I_0, misses). */
+typedef enum {
+    RCP_MAP_EYE = 0,
+    RCP_MAP_TARGET = 1,
+    RCP_MAP_DEPTH = 2,
+    RCP_MAP_IMAGE = 3,
+    RCP_MAP_NORMAL = 4
+} rcp_mapping;
 
 typedef struct {
     int32_t mapping;  /* rcp_mapping */

@@ -112,7 +112,7 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.H = H;
     v.mapping = p.mapping;
     v.z0 = p.z0;
-    v.kpx = p.mapping == RCP_MAP_IMAGE ? p.k : 0.f;
+    v.kpx = (p.mapping == RCP_MAP_IMAGE || p.mapping == RCP_MAP_NORMAL) ? p.k : 0.f;
     v.pad0_ = 0;
     v.base = nullptr;
     v.in = nullptr;
@@ -160,7 +160,7 @@ rcp_status check_view(const rcp_camera* cam, int W, int H, const rcp_params* p) 
         set_error("k must be >= 0 and focal_dist > 0, all finite");
         return RCP_ERR_ARG;
     }
-    if (p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_IMAGE) {
+    if (p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_NORMAL) {
         set_error("unknown mapping");
         return RCP_ERR_ARG;
     }

@@ -67,7 +67,7 @@ struct ViewDev {
     int W, H;
     int mapping;
     float z0;
-    float kpx;  // image-space displacement strength (pixels)
+    float kpx;  // IMAGE: displacement in pixels; NORMAL: k in world units
     int pad0_;
     const float4* in;    // previous image, nullptr = I_0
     const float4* base;  // image-space passes: the frame's traced image

@@ -384,7 +384,7 @@ rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_
         return RCP_ERR_ARG;
     }
     if (W < 1 || H < 1 || W > 8192 || H > 8192 || K < 1 || K > 16 || !(p->k >= 0.f) || !(p->focal_dist > 0.f) ||
-        p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_DEPTH /* no image-space requests */ ||
+        p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_NORMAL || p->mapping == RCP_MAP_IMAGE ||
         !(cam->fov_y_deg > 0.f) ||
         !(cam->fov_y_deg < 180.f)) {
         set_error("rcp_server_submit: argument out of range");

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                 const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, BLOCK, stack_entries, overflow, wc);
                 if (hs.rec < 0) out = si.c_lit;
             }
+            if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(si.normal_code);
             v.out[p] = out;
             if (v.prim) v.prim[p] = h.rec < 0 ? -1 : (int32_t)h.id;
         }

@@ -36,6 +36,42 @@ __device__ __forceinline__ float fdot(float ax, float ay, float az, float bx, fl
     return __fmaf_rn(ax, bx, __fmaf_rn(ay, by, __fmul_rn(az, bz)));
 }
 
+// Octahedral code of a unit vector (16 bits per folded coordinate, offset so
+// that no real normal has code 0) and its inverse; code 0 = no normal.
+__device__ __forceinline__ uint32_t normal_encode(float nx, float ny, float nz) {
+    const float s = __fadd_rn(__fadd_rn(fabsf(nx), fabsf(ny)), fabsf(nz));
+    if (!(s > 0.f)) return 0u;
+    float px = __fdiv_rn(nx, s), py = __fdiv_rn(ny, s);
+    if (nz < 0.f) {
+        const float ox = px, oy = py;
+        px = copysignf(__fsub_rn(1.f, fabsf(oy)), ox >= 0.f ? 1.f : -1.f);
+        py = copysignf(__fsub_rn(1.f, fabsf(ox)), oy >= 0.f ? 1.f : -1.f);
+    }
+    const int qx = (int)roundf(__fmul_rn(px, 32767.f)), qy = (int)roundf(__fmul_rn(py, 32767.f));
+    return (uint32_t)(qx + 32768) | ((uint32_t)(qy + 32768) << 16);
+}
+
+__device__ __forceinline__ bool normal_decode(uint32_t code, float& x, float& y, float& z) {
+    if (code == 0u) {
+        x = y = z = 0.f;
+        return false;
+    }
+    const float px = __fdiv_rn((float)(int)(code & 0xffffu) - 32768.f, 32767.f);
+    const float py = __fdiv_rn((float)(int)(code >> 16) - 32768.f, 32767.f);
+    z = __fsub_rn(__fsub_rn(1.f, fabsf(px)), fabsf(py));
+    x = px;
+    y = py;
+    if (z < 0.f) {
+        x = copysignf(__fsub_rn(1.f, fabsf(py)), px >= 0.f ? 1.f : -1.f);
+        y = copysignf(__fsub_rn(1.f, fabsf(px)), py >= 0.f ? 1.f : -1.f);
+    }
+    const float il = __fdiv_rn(1.f, __fsqrt_rn(__fmaf_rn(x, x, __fmaf_rn(y, y, __fmul_rn(z, z)))));
+    x = __fmul_rn(x, il);
+    y = __fmul_rn(y, il);
+    z = __fmul_rn(z, il);
+    return true;
+}
+
 // Camera of pixel (x, y) from its previous value c = (r, g, b, z).
 //   g   = eye -> focal-plane point P_p - P_e (precomputed terms, see ViewDev)
 //   V   = k ((2r-1) right + (2g-1) up + (2b-1) forward)             (Eq. 5)
@@ -57,7 +93,20 @@ __device__ __forceinline__ RayF camera_ray(const ViewDev& v, int x, int y, float
     RayF r;
     r.tmin = tmin;
     r.tmax = __int_as_float(0x7f800000);
-    if (v.mapping == RCP_MAP_EYE) {
+    if (v.mapping == RCP_MAP_NORMAL) {
+        // §5, Eq. 8: V_p = k (C x N), C = normalize(g), N from the previous pass
+        float nx, ny, nz;
+        normal_decode(__float_as_uint(c.w), nx, ny, nz);
+        const float il = __fdiv_rn(1.f, __fsqrt_rn(fdot(gx, gy, gz, gx, gy, gz)));
+        const float cx = __fmul_rn(gx, il), cy = __fmul_rn(gy, il), cz = __fmul_rn(gz, il);
+        const float k = v.kpx;
+        gx = __fmaf_rn(k, __fmaf_rn(cy, nz, -__fmul_rn(cz, ny)), gx);
+        gy = __fmaf_rn(k, __fmaf_rn(cz, nx, -__fmul_rn(cx, nz)), gy);
+        gz = __fmaf_rn(k, __fmaf_rn(cx, ny, -__fmul_rn(cy, nx)), gz);
+        r.ox = v.E[0];
+        r.oy = v.E[1];
+        r.oz = v.E[2];
+    } else if (v.mapping == RCP_MAP_EYE) {
         r.ox = __fadd_rn(v.E[0], Vx);
         r.oy = __fadd_rn(v.E[1], Vy);
         r.oz = __fadd_rn(v.E[2], Vz);
@@ -328,6 +377,7 @@ struct ShadeInfo {
     float4 c_lit;     // colour if the light is visible
     RayF shadow;      // the shadow ray (valid when need_shadow)
     bool need_shadow;
+    uint32_t normal_code;  // octahedral code of the facing hit normal, 0 on a miss
 };
 
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
@@ -338,6 +388,7 @@ __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 
 __device__ __forceinline__ ShadeInfo shade_primary(const SceneDev& S, const RayF& r, const Hit& h) {
     ShadeInfo si;
     si.need_shadow = false;
+    si.normal_code = 0u;
     if (h.rec < 0) {
         const float s = __fmul_rn(0.5f, __fadd_rn(r.dy, 1.f));
         const float one_s = __fsub_rn(1.f, s);
@@ -384,6 +435,7 @@ __device__ __forceinline__ ShadeInfo shade_primary(const SceneDev& S, const RayF
         ly = S.light.y;
         lz = S.light.z;
     }
+    si.normal_code = normal_encode(nx, ny, nz);
     const float ndl = fdot(nx, ny, nz, lx, ly, lz);
     const float a = S.light.ambient;
     const float4 alb = __ldg(S.albedo + h.id);

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "librcp.so")
 
 RCP_OK, RCP_ERR_ARG, RCP_ERR_OOM, RCP_ERR_CUDA, RCP_ERR_STACK, RCP_ERR_TIMEOUT, RCP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 RCP_LIGHT_POINT, RCP_LIGHT_DIRECTIONAL = 0, 1
-RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH, RCP_MAP_IMAGE = 0, 1, 2, 3
+RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH, RCP_MAP_IMAGE, RCP_MAP_NORMAL = 0, 1, 2, 3, 4
 
 
 class RcpError(RuntimeError):

@@ -100,8 +100,9 @@ def per_pass_parity(sc, cam, W, H, K, mapping, k, f, pix=None, z0=0.0, g=None, o
             g_rgbz = out.reshape(-1, 4)[idx]
             rep.add(g_rgbz, prim[idx], o_rgbz, o_prim, o_flag)
             nxt = out.reshape(-1, 4).copy()
-            nxt[idx] = o_rgbz.astype(np.float32)
+            nxt[idx] = O.rgbz_to_image(o_rgbz, mapping)
             img = nxt.reshape(H, W, 4)
+            rep.last = (g_rgbz.copy(), o_rgbz, o_flag, prim[idx].copy(), o_prim)
     finally:
         if own_g:
             rcp.rcp_scene_destroy(g)

@@ -91,3 +91,33 @@ def test_forest_per_pass_and_psnr():
         assert p >= U.PSNR_MIN
     finally:
         rcp.rcp_scene_destroy(g)
+
+
+@pytest.mark.parametrize("scene_name", ["tiny", "mid"])
+def test_normal_mapping(scene_name, tiny, mid):
+    """§5, Eq. 8 (V_p = k C x N): per-pass parity, and the normal codes the GPU
+    writes decode to the oracle's normals within the code's resolution."""
+    import oracle as O
+    sc = tiny if scene_name == "tiny" else mid
+    d = sc.diameter()
+    if scene_name == "tiny":
+        W, H, pix, f = 128, 96, None, 6.0
+    else:
+        W, H, f = 1920, 1080, 0.1 * d
+        pix = scenes.pixel_subset(W, H, 2048, seed=77)
+    rep = U.per_pass_parity(sc, sc.poses[0], W, H, 4, rcp.RCP_MAP_NORMAL, 0.03 * d, f, pix=pix)
+    print(rep.assert_ok(f"{scene_name} NORMAL"))
+    g_rgbz, o_rgbz, o_flag, g_prim, o_prim = rep.last
+    ok = (o_flag == 0) & (o_prim >= 0) & (g_prim == o_prim)
+    codes_g = g_rgbz[:, 3].view(np.uint32)
+    worst = 0.0
+    for cg, co in zip(codes_g[ok], o_rgbz[ok, 3].astype(np.uint64)):
+        ng, okg = O.normal_decode(int(cg))
+        no, oko = O.normal_decode(int(co))
+        assert okg and oko
+        worst = max(worst, float(np.linalg.norm(ng - no)))
+    assert worst < 2e-4, worst
+    assert np.all(codes_g[o_prim < 0] == 0) or not (o_prim < 0).any()
+    p, _ = U.end_to_end_psnr(sc, sc.poses[0], W, H, 4, rcp.RCP_MAP_NORMAL, 0.03 * d, f, pix=pix)
+    print(f"{scene_name} NORMAL K=4 PSNR {p:.1f} dB")
+    assert p >= U.PSNR_MIN
