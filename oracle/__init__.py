@@ -74,6 +74,14 @@ def _bind(lib):
     lib.orc_normal_encode.argtypes = [dp]
     lib.orc_normal_decode.restype = i32
     lib.orc_normal_decode.argtypes = [C.c_uint32, dp]
+    lib.orc_render_pass_ms.restype = i32
+    lib.orc_render_pass_ms.argtypes = [C.c_void_p, dp, i32, i32, i32, d, d, d, i32, fp, fp, lp, i64, dp, ip, up, i32]
+    lib.orc_render_ms.restype = i32
+    lib.orc_render_ms.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, i32, fp, dp, up, i32]
+    lib.orc_sample_image.restype = i32
+    lib.orc_sample_image.argtypes = [fp, i32, i32, d, d, i32, dp]
+    lib.orc_camera_ray_at.restype = i32
+    lib.orc_camera_ray_at.argtypes = [dp, i32, i32, d, d, i32, d, d, d, dp, d, dp, dp]
     lib.orc_render.restype = i32
     lib.orc_render.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, lp, i64, dp, ip, up, i32]
     return lib
@@ -169,6 +177,38 @@ class OracleScene:
             raise ValueError("orc_render_pass rejected its arguments")
         return out, prim, flag
 
+    def render_pass_ms(self, cam, W, H, mapping, k, f, jitter, in_rgbz=None, pix=None, z0=0.0, nthreads=0):
+        """Multi-sample pass; jitter (spp, 2) offsets in [0,1). Returns (rgbz, prim of sample 0, flag)."""
+        cam = _vec(cam)
+        jit = np.ascontiguousarray(jitter, dtype=np.float32).reshape(-1)
+        n = W * H if pix is None else len(pix)
+        out = np.zeros((n, 4))
+        prim = np.zeros(n, np.int32)
+        flag = np.zeros(n, np.uint8)
+        inp = None if in_rgbz is None else np.ascontiguousarray(in_rgbz, dtype=np.float32).reshape(-1)
+        pp = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
+        fptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+        rc = self._lib.orc_render_pass_ms(
+            self.h, _dp(cam), W, H, mapping, k, f, z0, jit.size // 2, fptr(jit), None if inp is None else fptr(inp),
+            None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n, _dp(out),
+            prim.ctypes.data_as(C.POINTER(C.c_int32)), flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
+        if rc != 0:
+            raise ValueError("orc_render_pass_ms rejected its arguments")
+        return out, prim, flag
+
+    def render_ms(self, cam, W, H, K, mapping, k, f, jitter, z0=0.0, nthreads=0):
+        """K multi-sample passes over the whole image: (rgbz (W*H, 4), OR of flags)."""
+        cam = _vec(cam)
+        jit = np.ascontiguousarray(jitter, dtype=np.float32).reshape(-1)
+        out = np.zeros((W * H, 4))
+        flag = np.zeros(W * H, np.uint8)
+        rc = self._lib.orc_render_ms(self.h, _dp(cam), W, H, K, mapping, k, f, z0, jit.size // 2,
+                                     jit.ctypes.data_as(C.POINTER(C.c_float)), _dp(out),
+                                     flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
+        if rc != 0:
+            raise ValueError("orc_render_ms rejected its arguments")
+        return out, flag
+
     def render(self, cam, W, H, K, mapping, k, f, pix=None, z0=0.0, nthreads=0):
         """K passes from I_0; returns (rgbz of the last pass, prim of the last pass, OR of flags)."""
         cam = _vec(cam)
@@ -247,3 +287,21 @@ def rgbz_to_image(rgbz, mapping):
     if mapping == MAP_NORMAL:
         out[:, 3] = np.asarray(rgbz[:, 3], dtype=np.uint64).astype(np.uint32).view(np.float32)
     return out
+
+
+def sample_image(img, W, H, px, py, mapping=MAP_EYE, libpath=None):
+    a = np.ascontiguousarray(img, dtype=np.float32).reshape(-1)
+    out = np.zeros(4)
+    rc = lib(libpath).orc_sample_image(a.ctypes.data_as(C.POINTER(C.c_float)), W, H, float(px), float(py), mapping,
+                                       _dp(out))
+    if rc != 0:
+        raise ValueError("orc_sample_image rejected its arguments")
+    return out
+
+
+def camera_ray_at(cam, W, H, px, py, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, libpath=None):
+    o = np.zeros(3)
+    d = np.zeros(3)
+    rc = lib(libpath).orc_camera_ray_at(_dp(_vec(cam)), W, H, float(px), float(py), mapping, k, f, z0, _dp(_vec(c)),
+                                        z, _dp(o), _dp(d))
+    return o, d, rc

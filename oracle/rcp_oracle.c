@@ -143,6 +143,15 @@ double orc_scene_diam(const orc_scene* s) { return s ? s->diam : 0.0; }
 int orc_camera_ray(const double cam[10], int W, int H, int x, int y, int mapping,
                    double k, double f, double z0, const double c[3], double z,
                    double o[3], double d[3]) {
+    return orc_camera_ray_at(cam, W, H, (double)x + 0.5, (double)y + 0.5, mapping, k, f, z0, c, z, o, d);
+}
+
+/* The same camera for a sample at pixel coordinates (px, py): (u, v) =
+ * (px/W, py/H); the pixel centre is (x + 0.5, y + 0.5) (§2 allows any number
+ * of jittered samples per pixel). */
+int orc_camera_ray_at(const double cam[10], int W, int H, double px, double py, int mapping,
+                      double k, double f, double z0, const double c[3], double z,
+                      double o[3], double d[3]) {
     const double* Pe = cam;
     double F[3], R[3], U[3];
     sub3(cam + 3, cam, F);
@@ -152,8 +161,8 @@ int orc_camera_ray(const double cam[10], int W, int H, int x, int y, int mapping
     cross3(R, F, U);
     const double tn = tan(cam[9] * M_PI / 360.0);
     const double aspect = (double)W / (double)H;
-    const double u = ((double)x + 0.5) / (double)W;
-    const double v = ((double)y + 0.5) / (double)H;
+    const double u = px / (double)W;
+    const double v = py / (double)H;
     const double sx = (2.0 * u - 1.0) * tn * aspect;
     const double sy = (1.0 - 2.0 * v) * tn;
     double Pp[3], V[3], Pe2[3], Pp2[3];
@@ -535,6 +544,9 @@ typedef struct {
     int W, H, K, mapping;
     double k, f, z0;
     const float* in;
+    const double* in_d;  /* previous image in double (multi-sample chains) */
+    int spp;             /* samples per pixel, 0 = one at the centre */
+    const float* jitter; /* spp (dx, dy) offsets inside the pixel */
     const int64_t* pix;
     int64_t npix;
     double* out;
@@ -592,6 +604,92 @@ static uint32_t hit_normal_code(const orc_scene* s, const double o[3], const dou
     return orc_normal_encode(N);
 }
 
+/*
+ * The previous image seen by a sample at pixel coordinates (px, py): bilinear
+ * between the four nearest pixel centres, indices clamped at the edges (§2's
+ * (u,v) need not sit on a pixel centre). For the normal mapping the fourth
+ * lane is a code, so it comes from the nearest pixel instead. in_f or in_d
+ * (float or double H*W*4 image); both NULL = I_0.
+ */
+static void sample_prev(const float* in_f, const double* in_d, int W, int H, double px, double py, int mapping,
+                        double c[4]) {
+    if (!in_f && !in_d) {
+        c[0] = c[1] = c[2] = 0.5;
+        c[3] = 0.0;
+        return;
+    }
+    const double qx = px - 0.5, qy = py - 0.5;
+    const double fx0 = floor(qx), fy0 = floor(qy);
+    const double wx = qx - fx0, wy = qy - fy0;
+    int64_t xs[2] = {(int64_t)fx0, (int64_t)fx0 + 1}, ys[2] = {(int64_t)fy0, (int64_t)fy0 + 1};
+    for (int j = 0; j < 2; ++j) {
+        xs[j] = xs[j] < 0 ? 0 : (xs[j] >= W ? W - 1 : xs[j]);
+        ys[j] = ys[j] < 0 ? 0 : (ys[j] >= H ? H - 1 : ys[j]);
+    }
+    const double w[2][2] = {{(1.0 - wx) * (1.0 - wy), wx * (1.0 - wy)}, {(1.0 - wx) * wy, wx * wy}};
+    for (int a = 0; a < 4; ++a) {
+        double acc = 0.0;
+        for (int r = 0; r < 2; ++r)
+            for (int q = 0; q < 2; ++q) {
+                const int64_t idx = 4 * (ys[r] * W + xs[q]) + a;
+                acc += w[r][q] * (in_f ? (double)in_f[idx] : in_d[idx]);
+            }
+        c[a] = acc;
+    }
+    if (mapping == ORC_MAP_NORMAL) {
+        int64_t nx = (int64_t)floor(qx + 0.5), ny = (int64_t)floor(qy + 0.5);
+        nx = nx < 0 ? 0 : (nx >= W ? W - 1 : nx);
+        ny = ny < 0 ? 0 : (ny >= H ? H - 1 : ny);
+        const int64_t idx = 4 * (ny * W + nx) + 3;
+        if (in_f) {
+            uint32_t bits;
+            memcpy(&bits, in_f + idx, 4);
+            c[3] = (double)bits;
+        } else {
+            c[3] = in_d[idx];
+        }
+    }
+}
+
+int orc_sample_image(const float* in, int W, int H, double px, double py, int mapping, double c[4]) {
+    if (!in || W < 1 || H < 1) return -1;
+    sample_prev(in, NULL, W, H, px, py, mapping, c);
+    return 0;
+}
+
+/* One pass of one pixel with J->spp jittered samples: each sample reads I_{n-1}
+ * at its own (u,v), gets its own camera and is traced and shaded; the pixel is
+ * the mean of its samples (colour and depth; the normal mapping keeps sample
+ * 0's normal code). Reading: §2's anti-aliasing samples are averaged. */
+static void run_pixel_ms(const job_t* J, int64_t i) {
+    const int64_t p = J->pix ? J->pix[i] : i;
+    const int x = (int)(p % J->W), y = (int)(p / J->W);
+    double acc[4] = {0, 0, 0, 0};
+    uint8_t fl = 0;
+    int64_t id0 = -1;
+    double code0 = 0.0;
+    for (int s = 0; s < J->spp; ++s) {
+        const double px = (double)x + (double)J->jitter[2 * s], py = (double)y + (double)J->jitter[2 * s + 1];
+        double c[4], o[3], d[3], rgbz[4];
+        sample_prev(J->in, J->in_d, J->W, J->H, px, py, J->mapping, c);
+        int amb = 0;
+        int64_t id = -1;
+        if (orc_camera_ray_at(J->cam, J->W, J->H, px, py, J->mapping, J->k, J->f, J->z0, c, c[3], o, d)) fl = 1;
+        orc_shade_ray(J->s, o, d, rgbz, &id, &amb);
+        fl |= (uint8_t)amb;
+        if (rgbz[3] < 0.0) rgbz[3] = 0.0;
+        for (int a = 0; a < 4; ++a) acc[a] += rgbz[a];
+        if (s == 0) {
+            id0 = id;
+            if (J->mapping == ORC_MAP_NORMAL) code0 = (double)hit_normal_code(J->s, o, d, id, rgbz[3]);
+        }
+    }
+    for (int a = 0; a < 4; ++a) J->out[4 * i + a] = acc[a] / (double)J->spp;
+    if (J->mapping == ORC_MAP_NORMAL) J->out[4 * i + 3] = code0;
+    if (J->prim) J->prim[i] = (int32_t)id0;
+    if (J->flag) J->flag[i] = fl;
+}
+
 /* One pixel's chain of `passes` passes starting from colour c (I_{n-1}). */
 static void run_pixel(const job_t* J, int64_t i, double c[4], int passes) {
     const int64_t p = J->pix ? J->pix[i] : i;
@@ -627,6 +725,10 @@ static void* worker(void* arg) {
         pthread_mutex_unlock(&J->mu);
         if (i0 >= J->npix) break;
         int64_t i1 = i0 + 64 < J->npix ? i0 + 64 : J->npix;
+        if (J->spp > 0) {
+            for (int64_t i = i0; i < i1; ++i) run_pixel_ms(J, i);
+            continue;
+        }
         for (int64_t i = i0; i < i1; ++i) {
             double c[4] = {0.5, 0.5, 0.5, 0.0};
             if (J->in) {
@@ -694,6 +796,58 @@ int orc_render(const orc_scene* s, const double cam[10], int W, int H, int K, in
     J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = K; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
     J.in = NULL; J.pix = pix; J.npix = npix; J.out = out_rgbz; J.prim = out_prim; J.flag = out_flag;
     return run_job(&J, nthreads);
+}
+
+static int check_jitter(int spp, const float* jitter) {
+    if (spp < 1 || spp > 16 || !jitter) return -1;
+    for (int i = 0; i < 2 * spp; ++i)
+        if (!(jitter[i] >= 0.0f && jitter[i] < 1.0f)) return -1;
+    return 0;
+}
+
+int orc_render_pass_ms(const orc_scene* s, const double cam[10], int W, int H, int mapping, double k, double f,
+                       double z0, int spp, const float* jitter, const float* in_rgbz, const int64_t* pix,
+                       int64_t npix, double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads) {
+    if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz || check_jitter(spp, jitter)) return -1;
+    if (!pix) npix = (int64_t)W * H;
+    for (int64_t i = 0; pix && i < npix; ++i)
+        if (pix[i] < 0 || pix[i] >= (int64_t)W * H) return -1;
+    job_t J;
+    memset(&J, 0, sizeof(J));
+    J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = 1; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
+    J.in = in_rgbz; J.spp = spp; J.jitter = jitter;
+    J.pix = pix; J.npix = npix; J.out = out_rgbz; J.prim = out_prim; J.flag = out_flag;
+    return run_job(&J, nthreads);
+}
+
+/* K multi-sample passes from I_0 over the whole image (a sample reads its
+ * neighbours' previous values, so chains are no longer per pixel); the image
+ * is carried in double between passes. out_flag = OR over the passes. */
+int orc_render_ms(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping, double k, double f,
+                  double z0, int spp, const float* jitter, double* out_rgbz, uint8_t* out_flag, int nthreads) {
+    if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz || K < 1 || check_jitter(spp, jitter)) return -1;
+    const int64_t P = (int64_t)W * H;
+    double* prev = (double*)malloc(sizeof(double) * 4 * P);
+    uint8_t* fl = (uint8_t*)calloc((size_t)P, 1);
+    if (!prev || !fl) {
+        free(prev);
+        free(fl);
+        return -1;
+    }
+    if (out_flag) memset(out_flag, 0, (size_t)P);
+    for (int n = 0; n < K; ++n) {
+        job_t J;
+        memset(&J, 0, sizeof(J));
+        J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = 1; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
+        J.in_d = n == 0 ? NULL : prev; J.spp = spp; J.jitter = jitter;
+        J.npix = P; J.out = out_rgbz; J.flag = fl;
+        run_job(&J, nthreads);
+        memcpy(prev, out_rgbz, sizeof(double) * 4 * P);
+        for (int64_t i = 0; out_flag && i < P; ++i) out_flag[i] |= fl[i];
+    }
+    free(prev);
+    free(fl);
+    return 0;
 }
 
 /* ---------------------------------------------------------------- image space */

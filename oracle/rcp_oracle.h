@@ -81,6 +81,17 @@ int orc_camera_ray(const double cam[10], int W, int H, int x, int y, int mapping
                    double k, double f, double z0, const double c[3], double z,
                    double o[3], double d[3]);
 
+/* The same camera for a sample at pixel coordinates (px, py) (pixel centre =
+ * (x + 0.5, y + 0.5)). */
+int orc_camera_ray_at(const double cam[10], int W, int H, double px, double py, int mapping,
+                      double k, double f, double z0, const double c[3], double z,
+                      double o[3], double d[3]);
+
+/* I_{n-1} as seen by a sample at pixel coordinates (px, py): bilinear between
+ * the nearest pixel centres with edge clamping (the normal mapping's code lane
+ * from the nearest pixel). */
+int orc_sample_image(const float* in, int W, int H, double px, double py, int mapping, double c[4]);
+
 /* Single-primitive tests (exposed for closed-form pins). Return 1 on a hit with
  * t in (tmin, tmax) and write t. */
 int orc_hit_triangle(const double v0[3], const double v1[3], const double v2[3],
@@ -120,6 +131,18 @@ int orc_render_pass(const orc_scene* s, const double cam[10], int W, int H, int 
 int orc_render(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping,
                double k, double f, double z0, const int64_t* pix, int64_t npix,
                double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads);
+
+/* Multi-sample pass: spp (1..16) samples per pixel at pixel offsets jitter
+ * (2*spp floats in [0,1)); each sample reads in_rgbz (full H*W*4 image or NULL
+ * = I_0) at its own position, is traced and shaded; the pixel is the mean
+ * (normal mapping: sample 0's code). Outputs per listed pixel as
+ * orc_render_pass; out_prim = sample 0's hit. */
+int orc_render_pass_ms(const orc_scene* s, const double cam[10], int W, int H, int mapping, double k, double f,
+                       double z0, int spp, const float* jitter, const float* in_rgbz, const int64_t* pix,
+                       int64_t npix, double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads);
+/* K multi-sample passes from I_0 over the whole image (W*H*4 doubles out). */
+int orc_render_ms(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping, double k, double f,
+                  double z0, int spp, const float* jitter, double* out_rgbz, uint8_t* out_flag, int nthreads);
 
 /* Image-space pass (§6: with V_e = 0 a pass reduces to re-sampling the
  * rendered image at a displaced pixel; §6.1: mirrored screen edges). base = the frame's

@@ -573,4 +573,74 @@ def check_normal_mapping_render(lp=None):
     assert np.allclose(c2[centre, :3], a[centre, :3], atol=1e-12)
 
 
+# --------------------------------------------------------------------------- multi-sample passes (§2 jitter)
+
+def check_ms_centre_is_single(lp=None):
+    """One sample at the pixel centre, or several identical ones, is the
+    single-sample pass bit for bit (with I_0 and with a previous image)."""
+    sc = _tiny(lp)
+    W, H, k = 20, 14, 1.4
+    ref, pref, _ = sc.render_pass(TINY_CAM, W, H, O.MAP_EYE, k, 6.0)
+    img = O.rgbz_to_image(ref, O.MAP_EYE).reshape(H, W, 4)
+    for jit in ([[0.5, 0.5]], [[0.5, 0.5]] * 4):
+        a, pa, _ = sc.render_pass_ms(TINY_CAM, W, H, O.MAP_EYE, k, 6.0, jit)
+        assert np.array_equal(a, ref) and np.array_equal(pa, pref)
+        b, _, _ = sc.render_pass_ms(TINY_CAM, W, H, O.MAP_EYE, k, 6.0, jit, in_rgbz=img)
+        c, _, _ = sc.render_pass(TINY_CAM, W, H, O.MAP_EYE, k, 6.0, in_rgbz=img)
+        assert np.array_equal(b, c)
+    full, _ = sc.render_ms(TINY_CAM, W, H, 3, O.MAP_EYE, k, 6.0, [[0.5, 0.5]])
+    chain, _, _ = sc.render(TINY_CAM, W, H, 3, O.MAP_EYE, k, 6.0)
+    assert np.array_equal(full, chain)
+
+
+def check_bilinear_reads(lp=None):
+    """Bilinear reads reproduce a linear ramp exactly inside the image and
+    clamp to the edge pixels outside; the normal code lane is the nearest
+    pixel's."""
+    W, H = 8, 6
+    img = np.zeros((H, W, 4), np.float32)
+    img[..., 0] = 0.1 * np.arange(W)[None, :]
+    img[..., 1] = 0.05 * np.arange(H)[:, None]
+    img[..., 3] = (np.arange(W * H).reshape(H, W) + 1).astype(np.uint32).view(np.float32)
+    for px, py in [(1.5, 1.5), (3.25, 2.75), (6.9, 4.1), (4.0, 3.0)]:
+        c = O.sample_image(img, W, H, px, py, libpath=lp)
+        assert abs(c[0] - 0.1 * (px - 0.5)) < 1e-7 and abs(c[1] - 0.05 * (py - 0.5)) < 1e-7
+    c = O.sample_image(img, W, H, 0.1, 0.2, libpath=lp)
+    assert np.allclose(c[:2], img[0, 0, :2])
+    c = O.sample_image(img, W, H, W + 3.0, H + 0.4, libpath=lp)
+    assert np.allclose(c[:2], img[H - 1, W - 1, :2])
+    c = O.sample_image(img, W, H, 3.9, 2.2, O.MAP_NORMAL, libpath=lp)
+    assert int(c[3]) == 2 * W + 3 + 1
+
+
+def check_ms_sphere_coverage(lp=None):
+    """A unit sphere at distance 10, lit from behind (ambient only): each pixel
+    is the mean over its samples of the sphere's ambient colour (sample inside
+    the silhouette angle asin(1/10)) or the sky seen along that sample."""
+    alb = np.array([0.6, 0.3, 0.9])
+    sc = _scene(spheres=[[0, 0, -10, 1]], albedo=[alb], light=(0.0, 0.0, -1.0), lp=lp)
+    W, H = 31, 23
+    jit = np.array([[0.125, 0.375], [0.625, 0.125], [0.375, 0.875], [0.875, 0.625]], np.float32)
+    rgbz, _, flag = sc.render_pass_ms(CAM_Z, W, H, O.MAP_EYE, 0.0, 1.0, jit)
+    lim = math.asin(0.1)
+    n_mixed = 0
+    for p in range(W * H):
+        x, y = p % W, p // W
+        want = np.zeros(3)
+        hits = 0
+        for jx, jy in jit:
+            _, d, _ = O.camera_ray_at(CAM_Z, W, H, x + float(jx), y + float(jy), O.MAP_EYE, 0.0, 1.0, libpath=lp)
+            if _angle(d, np.array([0, 0, -1.0])) < lim:
+                want += 0.1 * alb
+                hits += 1
+            else:
+                sv = 0.5 * (d[1] + 1)
+                want += (1 - sv) * np.ones(3) + sv * np.array([0.5, 0.7, 1.0])
+        if flag[p]:
+            continue
+        assert np.allclose(rgbz[p, :3], want / 4, atol=1e-12), (x, y)
+        n_mixed += 0 < hits < 4
+    assert n_mixed > 4
+
+
 ALL_CHECKS = [v for k, v in sorted(globals().items()) if k.startswith("check_")]

@@ -22,7 +22,7 @@ MUTANTS = {
     "blue_axis_dropped": ("db * F[a]", "0.0 * F[a]"),
     "rows_bottom_up": ("(1.0 - 2.0 * v) * tn", "(2.0 * v - 1.0) * tn"),
     "aspect_dropped": ("* tn * aspect", "* tn"),
-    "no_half_pixel": ("((double)x + 0.5)", "((double)x)"),
+    "no_half_pixel": ("(double)x + 0.5, (double)y + 0.5", "(double)x, (double)y"),
     "eye_not_reaimed": ("Pe2[a] = Pe[a] + V[a]; Pp2[a] = Pp[a]; }", "Pe2[a] = Pe[a] + V[a]; Pp2[a] = Pp[a] + V[a]; }"),
     "target_moves_eye": ("Pe2[a] = Pe[a]; Pp2[a] = Pp[a] + V[a]; }", "Pe2[a] = Pe[a] + V[a]; Pp2[a] = Pp[a] + V[a]; }"),
     "up_axis_flipped": ("cross3(R, F, U);", "cross3(F, R, U);"),
@@ -52,6 +52,10 @@ MUTANTS = {
     "normal_no_fold": ("    if (zz < 0.0) {\n        x = (1.0 - fabs(py))", "    if (0) {\n        x = (1.0 - fabs(py))"),
     "normal_code_no_offset": ("return (uint32_t)(qx + 32768) | ((uint32_t)(qy + 32768) << 16);",
                               "return (uint32_t)(qx & 0xffff) | ((uint32_t)(qy & 0xffff) << 16);"),
+    "jitter_sign": ("const double px = (double)x + (double)J->jitter[2 * s]", "const double px = (double)x - (double)J->jitter[2 * s]"),
+    "bilinear_weights_swapped": ("{{(1.0 - wx) * (1.0 - wy), wx * (1.0 - wy)}", "{{wx * (1.0 - wy), (1.0 - wx) * (1.0 - wy)}"),
+    "ms_mean_wrong": ("J->out[4 * i + a] = acc[a] / (double)J->spp;", "J->out[4 * i + a] = acc[a] / (double)(J->spp + 1);"),
+    "bilinear_no_half_shift": ("const double qx = px - 0.5, qy = py - 0.5;", "const double qx = px, qy = py;"),
     "tmin_ignored": ("if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > tmin && t < best)",
                      "if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > 0.0 && t < best)"),
 }
