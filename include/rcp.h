@@ -91,11 +91,22 @@ typedef enum {
     RCP_MAP_NORMAL = 4
 } rcp_mapping;
 
+/* Samples per pixel (§2: any number of jittered samples per pixel). spp <= 0:
+ * one sample at the pixel centre (the default). spp in 1..16: samples at pixel
+ * offsets (jitter[2s], jitter[2s+1]) in [0,1)^2; each sample reads the previous
+ * image bilinearly at its own position (edges clamped; the normal mapping's
+ * code lane from the nearest pixel), is traced and shaded, and the pixel is the
+ * mean of its samples (the normal mapping keeps sample 0's normal code; hit ids
+ * are sample 0's). Not with RCP_MAP_IMAGE. */
+#define RCP_MAX_SPP 16
+
 typedef struct {
     int32_t mapping;  /* rcp_mapping */
     float k;          /* displacement strength lambda (world units) */
     float focal_dist; /* distance f of the focal plane along the view axis */
     float z0;         /* in-focus depth of RCP_MAP_DEPTH (ignored otherwise) */
+    int32_t spp;      /* samples per pixel, <= 0 = one at the centre */
+    float jitter[2 * RCP_MAX_SPP];
 } rcp_params;
 
 typedef struct rcp_scene rcp_scene;
@@ -149,7 +160,9 @@ rcp_status rcp_render_pass(const rcp_scene* scene, const rcp_camera* cam, int wi
                            int32_t* out_prim);
 
 /* Device variant of both: K passes starting from d_in (device rgbz image, NULL =
- * I_0), final image to d_out (device, width*height*4 floats; may equal d_in),
+ * I_0), final image to d_out (device, width*height*4 floats; may equal d_in,
+ * except for a one-pass (K = 1) render with spp > 0, whose samples read
+ * neighbouring pixels of d_in),
  * last pass's hit ids to d_prim (device, nullable). Enqueued on `stream`
  * (cudaStream_t, NULL = legacy default); the call returns once enqueued. The
  * K-pass sequence is captured once per (scene, shape, K) in a CUDA graph and

@@ -121,7 +121,8 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.tiles_x = (W + 7) / 8;
     v.pix_begin = 0;
     v.chunk_begin = 0;
-    v.pad_ = 0;
+    v.spp = p.spp > 0 ? p.spp : 0;
+    for (int i = 0; i < 2 * RCP_MAX_SPP; ++i) v.jit[i] = i < 2 * v.spp ? p.jitter[i] : 0.5f;
 }
 
 }  // namespace rcp
@@ -164,6 +165,15 @@ rcp_status check_view(const rcp_camera* cam, int W, int H, const rcp_params* p) 
         set_error("unknown mapping");
         return RCP_ERR_ARG;
     }
+    if (p->spp > RCP_MAX_SPP || (p->spp > 0 && p->mapping == RCP_MAP_IMAGE)) {
+        set_error("spp must be <= 16, and image-space renders take one sample per pixel");
+        return RCP_ERR_ARG;
+    }
+    for (int i = 0; i < 2 * (p->spp > 0 ? p->spp : 0); ++i)
+        if (!(p->jitter[i] >= 0.f && p->jitter[i] < 1.f)) {
+            set_error("jitter offsets must lie in [0, 1)");
+            return RCP_ERR_ARG;
+        }
     if (!finite3(cam->eye) || !finite3(cam->look_at) || !finite3(cam->up) || !(cam->fov_y_deg > 0.f) ||
         !(cam->fov_y_deg < 180.f)) {
         set_error("camera must be finite with 0 < fov < 180");
@@ -197,7 +207,8 @@ LaunchCfg cfg_of(const Scene& sc) {
 
 std::string cfg_key(const LaunchCfg& c) {
     std::ostringstream o;
-    o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/" << c.count;
+    o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/" << c.count
+      << "/" << c.ms;
     return o.str();
 }
 
@@ -368,6 +379,10 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
             return RCP_ERR_ARG;
         }
         make_view(base[i], cams[i], Ws[i], Hs[i], *p);
+        if (p->spp > 0 && K == 1 && ins && ins[i] == outs[i]) {
+            set_error("a one-pass multi-sample render reads neighbouring pixels of d_in: d_out must not alias it");
+            return RCP_ERR_ARG;
+        }
         if (p->mapping == RCP_MAP_IMAGE && ins && ins[i]) {
             set_error("RCP_MAP_IMAGE renders start from I_0 (d_in must be NULL); use rcp_imagespace_pass_device");
             return RCP_ERR_ARG;
@@ -384,7 +399,8 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     if (r != RCP_OK) return r;
     r = stage_views(*ctx, base, ins, outs, prims, st);
     if (r != RCP_OK) return r;
-    const LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
+    LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
+    cfg.ms = p->spp > 0;
     r = run_graph(sc, *ctx, cfg, st);
     sc.last = ctx;
     if (ctx_out) *ctx_out = ctx;
@@ -618,10 +634,10 @@ rcp_status rcp_render_pass(const rcp_scene* csc, const rcp_camera* cam, int W, i
     if (r != RCP_OK) return r;
     r = ensure_io(*ctx, false, out_prim != nullptr);
     if (r != RCP_OK) return r;
-    // a one-pass render reads I_{n-1} from ctx->io and writes I_n back over it
-    // (each pixel is read and then written by the same thread)
-    if (in_rgbz) RCP_CUDA(cudaMemcpyAsync(ctx->io, in_rgbz, sizeof(float4) * P, cudaMemcpyHostToDevice, st));
-    const float4* ins[1] = {in_rgbz ? ctx->io : nullptr};
+    // I_{n-1} goes to ctx->img[1] (unused by a one-pass render) and I_n to
+    // ctx->io: separate buffers, since jittered samples read neighbouring pixels
+    if (in_rgbz) RCP_CUDA(cudaMemcpyAsync(ctx->img[1], in_rgbz, sizeof(float4) * P, cudaMemcpyHostToDevice, st));
+    const float4* ins[1] = {in_rgbz ? ctx->img[1] : nullptr};
     float4* outs[1] = {ctx->io};
     int32_t* prims[1] = {out_prim ? ctx->io_prim : nullptr};
     r = render_views(*sc, 1, cam, &W, &H, 1, p, ins, outs, prims, st);
@@ -703,6 +719,7 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
     RCP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 8, st));
     LaunchCfg cfg = cfg_of(*sc);
     cfg.count = true;
+    cfg.ms = p->spp > 0;
     r = enqueue_passes(*sc, *ctx, cfg, d_cnt, st, false);
     unsigned long long h[8] = {0};
     if (r == RCP_OK) {

@@ -76,7 +76,8 @@ struct ViewDev {
     int64_t pix_begin;  // first global pixel index of this view
     int64_t chunk_begin;  // first work chunk (8x4 tile) of this view
     int tiles_x;
-    int pad_;
+    int spp;              // samples per pixel, 0 = one at the centre
+    float jit[2 * RCP_MAX_SPP];
 };
 
 // Host-side owner of a built scene.

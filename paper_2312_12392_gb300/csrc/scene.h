@@ -86,6 +86,7 @@ struct LaunchCfg {
     bool fused = true;
     int stack = 32;  // entries per thread
     bool count = false;
+    bool ms = false;  // jittered multi-sample kernel
 };
 
 // One pass over n_views views whose descriptors are at d_views (device).

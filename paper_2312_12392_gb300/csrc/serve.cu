@@ -217,8 +217,10 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
         RCP_CUDA(cudaStreamWaitEvent(g.st, ready, 0));
         RCP_CUDA(cudaMemcpyAsync(g.d_views, g.h_views, sizeof(ViewDev) * reqs.size(), cudaMemcpyHostToDevice, g.st));
         RCP_CUDA(cudaMemsetAsync(g.d_work, 0, sizeof(unsigned), g.st));
-        r = launch_pass(sc->dev(), server_cfg(*sc), g.d_views, (int)reqs.size(), total_pix, total_chunks, nullptr,
-                        g.d_work, g.d_status, d_rays, nullptr, g.st);
+        LaunchCfg cfg = server_cfg(*sc);
+        for (Request* q : reqs) cfg.ms = cfg.ms || q->p.spp > 0;
+        r = launch_pass(sc->dev(), cfg, g.d_views, (int)reqs.size(), total_pix, total_chunks, nullptr, g.d_work,
+                        g.d_status, d_rays, nullptr, g.st);
         if (r != RCP_OK) {
             res = r;
             break;
@@ -385,7 +387,7 @@ rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_
     }
     if (W < 1 || H < 1 || W > 8192 || H > 8192 || K < 1 || K > 16 || !(p->k >= 0.f) || !(p->focal_dist > 0.f) ||
         p->mapping < RCP_MAP_EYE || p->mapping > RCP_MAP_NORMAL || p->mapping == RCP_MAP_IMAGE ||
-        !(cam->fov_y_deg > 0.f) ||
+        !(cam->fov_y_deg > 0.f) || p->spp > RCP_MAX_SPP ||
         !(cam->fov_y_deg < 180.f)) {
         set_error("rcp_server_submit: argument out of range");
         return RCP_ERR_ARG;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_camera(const ViewDev* __restrict__ view
         const int64_t p = gp - v.pix_begin;
         const int x = (int)(p % v.W), y = (int)(p / v.W);
         const float4 c = v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
-        const RayF r = camera_ray(v, x, y, c, tmin);
+        const RayF r = camera_ray(v, (float)x + 0.5f, (float)y + 0.5f, c, tmin);
         rays[2 * gp] = make_float4(r.ox, r.oy, r.oz, r.tmin);
         rays[2 * gp + 1] = make_float4(r.dx, r.dy, r.dz, r.tmax);
     }
@@ -52,7 +52,25 @@ __global__ void __launch_bounds__(256) k_camera(const ViewDev* __restrict__ view
 
 // Primary + shadow trace and shading of one pass. FUSED: rays are made here
 // from I_{n-1}; otherwise they are read from the camera kernel's buffer.
-template <int BLOCK, bool FUSED, bool COUNT>
+// Trace, shadow and shade one camera ray; returns the pixel value.
+template <bool COUNT>
+__device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, uint2* stack, int stride,
+                                              int stack_entries, bool& overflow, WorkCount& wc, uint32_t& n_shadow,
+                                              uint32_t& code, int32_t& prim) {
+    const Hit h = traverse<false, COUNT>(S, r, stack, stride, stack_entries, overflow, wc);
+    const ShadeInfo si = shade_primary(S, r, h);
+    float4 out = si.c_shadow;
+    if (si.need_shadow) {
+        ++n_shadow;
+        const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, stride, stack_entries, overflow, wc);
+        if (hs.rec < 0) out = si.c_lit;
+    }
+    code = si.normal_code;
+    prim = h.rec < 0 ? -1 : (int32_t)h.id;
+    return out;
+}
+
+template <int BLOCK, bool FUSED, bool COUNT, bool MS>
 __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __restrict__ views, int n_views,
                                                  int64_t total_chunks, int chunk_tiles,
                                                  const float4* __restrict__ rays, unsigned* work, int stack_entries,
@@ -78,10 +96,44 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
             const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
             if (x >= v.W || y >= v.H) continue;
             const int64_t p = (int64_t)y * v.W + x;
+            if (MS) {
+                // jittered samples (§2): each reads I_{n-1} at its own position
+                const int ns = v.spp > 0 ? v.spp : 1;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t code0 = 0;
+                int32_t prim0 = -1;
+                for (int s = 0; s < ns; ++s) {
+                    const float jx = v.spp > 0 ? v.jit[2 * s] : 0.5f, jy = v.spp > 0 ? v.jit[2 * s + 1] : 0.5f;
+                    const float px = __fadd_rn((float)x, jx), py = __fadd_rn((float)y, jy);
+                    const float4 c = v.in ? sample_prev(v.in, v.W, v.H, px, py, v.mapping)
+                                          : make_float4(0.5f, 0.5f, 0.5f, 0.f);
+                    const RayF r = camera_ray(v, px, py, c, S.tmin);
+                    uint32_t code;
+                    int32_t prim;
+                    const float4 o = trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow,
+                                                        code, prim);
+                    ++n_primary;
+                    acc.x = __fadd_rn(acc.x, o.x);
+                    acc.y = __fadd_rn(acc.y, o.y);
+                    acc.z = __fadd_rn(acc.z, o.z);
+                    acc.w = __fadd_rn(acc.w, o.w);
+                    if (s == 0) {
+                        code0 = code;
+                        prim0 = prim;
+                    }
+                }
+                const float fn = (float)ns;
+                float4 out = make_float4(__fdiv_rn(acc.x, fn), __fdiv_rn(acc.y, fn), __fdiv_rn(acc.z, fn),
+                                         __fdiv_rn(acc.w, fn));
+                if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code0);
+                v.out[p] = out;
+                if (v.prim) v.prim[p] = prim0;
+                continue;
+            }
             RayF r;
             if (FUSED) {
                 const float4 c = v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
-                r = camera_ray(v, x, y, c, S.tmin);
+                r = camera_ray(v, (float)x + 0.5f, (float)y + 0.5f, c, S.tmin);
             } else {
                 const float4 a = __ldg(rays + 2 * (v.pix_begin + p)), b = __ldg(rays + 2 * (v.pix_begin + p) + 1);
                 r.ox = a.x;
@@ -93,18 +145,13 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                 r.dz = b.z;
                 r.tmax = b.w;
             }
-            const Hit h = traverse<false, COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc);
-            const ShadeInfo si = shade_primary(S, r, h);
-            float4 out = si.c_shadow;
+            uint32_t code;
+            int32_t prim;
+            float4 out = trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow, code, prim);
             ++n_primary;
-            if (si.need_shadow) {
-                ++n_shadow;
-                const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, BLOCK, stack_entries, overflow, wc);
-                if (hs.rec < 0) out = si.c_lit;
-            }
-            if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(si.normal_code);
+            if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
             v.out[p] = out;
-            if (v.prim) v.prim[p] = h.rec < 0 ? -1 : (int32_t)h.id;
+            if (v.prim) v.prim[p] = prim;
         }
     }
     if (overflow) atomicExch(&status[0], 1);
@@ -219,11 +266,11 @@ int sm_count() {
     return sms;
 }
 
-template <int BLOCK, bool FUSED, bool COUNT>
+template <int BLOCK, bool FUSED, bool COUNT, bool MS>
 rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                           int64_t total_chunks, const float4* rays, unsigned* d_work, int* d_status,
                           unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
-    auto kern = k_trace<BLOCK, FUSED, COUNT>;
+    auto kern = k_trace<BLOCK, FUSED, COUNT, MS>;
     const size_t smem = sizeof(uint2) * (size_t)cfg.stack * BLOCK;
     if (smem > 48 * 1024) RCP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = cfg.blocks_per_sm;
@@ -240,19 +287,19 @@ rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
     return RCP_OK;
 }
 
-template <bool FUSED, bool COUNT>
+template <bool FUSED, bool COUNT, bool MS>
 rcp_status launch_trace_b(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                           int64_t total_chunks, const float4* rays, unsigned* d_work, int* d_status,
                           unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
     switch (cfg.block) {
         case 64:
-            return launch_trace_t<64, FUSED, COUNT>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+            return launch_trace_t<64, FUSED, COUNT, MS>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
                                                     d_rays, d_counters, st);
         case 256:
-            return launch_trace_t<256, FUSED, COUNT>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+            return launch_trace_t<256, FUSED, COUNT, MS>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
                                                      d_rays, d_counters, st);
         default:
-            return launch_trace_t<128, FUSED, COUNT>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
+            return launch_trace_t<128, FUSED, COUNT, MS>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
                                                      d_rays, d_counters, st);
     }
 }
@@ -262,22 +309,28 @@ rcp_status launch_trace_b(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
 rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                        int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work, int* d_status,
                        unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
-    if (!cfg.fused) {
+    if (!cfg.fused && !cfg.ms) {
         int64_t g = (total_pix + 255) / 256;
         if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
         if (g < 1) g = 1;
         k_camera<<<(int)g, 256, 0, st>>>(d_views, n_views, total_pix, S.tmin, rays);
         RCP_CUDA(cudaGetLastError());
     }
+    if (cfg.ms) {  // jittered samples: camera inside the trace kernel
+        return cfg.count ? launch_trace_b<true, true, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                            d_status, d_rays, d_counters, st)
+                         : launch_trace_b<true, false, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                             d_status, d_rays, d_counters, st);
+    }
     if (cfg.count)
-        return cfg.fused ? launch_trace_b<true, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
-                                                      d_rays, d_counters, st)
-                         : launch_trace_b<false, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                       d_status, d_rays, d_counters, st);
-    return cfg.fused ? launch_trace_b<true, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
-                                                   d_rays, d_counters, st)
-                     : launch_trace_b<false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
-                                                    d_rays, d_counters, st);
+        return cfg.fused ? launch_trace_b<true, true, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                             d_status, d_rays, d_counters, st)
+                         : launch_trace_b<false, true, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                              d_status, d_rays, d_counters, st);
+    return cfg.fused ? launch_trace_b<true, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                          d_status, d_rays, d_counters, st)
+                     : launch_trace_b<false, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                           d_status, d_rays, d_counters, st);
 }
 
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,

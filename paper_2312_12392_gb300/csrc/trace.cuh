@@ -80,9 +80,10 @@ __device__ __forceinline__ bool normal_decode(uint32_t code, float& x, float& y,
 //   DEPTH:  origin P_e,     direction normalize(g + |z - z0| V)       (Eq. 7)
 // The direction is P'_p - P'_e (Eq. 2) formed from the offsets, not from the
 // absolute positions, which avoids cancellation in float32.
-__device__ __forceinline__ RayF camera_ray(const ViewDev& v, int x, int y, float4 c, float tmin) {
-    const float ix = (float)(2 * x + 1 - v.W);
-    const float iy = (float)(v.H - 2 * y - 1);
+// (px, py): the sample's pixel coordinates (pixel centre = x + 0.5, y + 0.5).
+__device__ __forceinline__ RayF camera_ray(const ViewDev& v, float px, float py, float4 c, float tmin) {
+    const float ix = __fsub_rn(__fmul_rn(2.f, px), (float)v.W);
+    const float iy = __fsub_rn((float)v.H, __fmul_rn(2.f, py));
     float gx = __fmaf_rn(ix, v.fR[0], __fmaf_rn(iy, v.fU[0], v.fF[0]));
     float gy = __fmaf_rn(ix, v.fR[1], __fmaf_rn(iy, v.fU[1], v.fF[1]));
     float gz = __fmaf_rn(ix, v.fR[2], __fmaf_rn(iy, v.fU[2], v.fF[2]));
@@ -133,6 +134,34 @@ __device__ __forceinline__ RayF camera_ray(const ViewDev& v, int x, int y, float
         r.dx = __fdiv_rn(v.fF[0], l);
         r.dy = __fdiv_rn(v.fF[1], l);
         r.dz = __fdiv_rn(v.fF[2], l);
+    }
+    return r;
+}
+
+// I_{n-1} seen by a sample at (px, py): bilinear between the four nearest
+// pixel centres, indices clamped; the normal mapping's code lane comes from the
+// nearest pixel.
+__device__ __forceinline__ float4 sample_prev(const float4* __restrict__ img, int W, int H, float px, float py,
+                                              int mapping) {
+    const float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f);
+    const float fx0 = floorf(qx), fy0 = floorf(qy);
+    const float wx = __fsub_rn(qx, fx0), wy = __fsub_rn(qy, fy0);
+    const int x0 = min(max((int)fx0, 0), W - 1), x1 = min(max((int)fx0 + 1, 0), W - 1);
+    const int y0 = min(max((int)fy0, 0), H - 1), y1 = min(max((int)fy0 + 1, 0), H - 1);
+    const float4 a = __ldg(img + (int64_t)y0 * W + x0), b = __ldg(img + (int64_t)y0 * W + x1);
+    const float4 c = __ldg(img + (int64_t)y1 * W + x0), d = __ldg(img + (int64_t)y1 * W + x1);
+    const float w00 = __fmul_rn(__fsub_rn(1.f, wx), __fsub_rn(1.f, wy)), w10 = __fmul_rn(wx, __fsub_rn(1.f, wy));
+    const float w01 = __fmul_rn(__fsub_rn(1.f, wx), wy), w11 = __fmul_rn(wx, wy);
+    float4 r;
+    r.x = __fmaf_rn(w11, d.x, __fmaf_rn(w01, c.x, __fmaf_rn(w10, b.x, __fmul_rn(w00, a.x))));
+    r.y = __fmaf_rn(w11, d.y, __fmaf_rn(w01, c.y, __fmaf_rn(w10, b.y, __fmul_rn(w00, a.y))));
+    r.z = __fmaf_rn(w11, d.z, __fmaf_rn(w01, c.z, __fmaf_rn(w10, b.z, __fmul_rn(w00, a.z))));
+    if (mapping == RCP_MAP_NORMAL) {
+        const int nx = min(max((int)floorf(__fadd_rn(qx, 0.5f)), 0), W - 1);
+        const int ny = min(max((int)floorf(__fadd_rn(qy, 0.5f)), 0), H - 1);
+        r.w = __ldg(img + (int64_t)ny * W + nx).w;
+    } else {
+        r.w = __fmaf_rn(w11, d.w, __fmaf_rn(w01, c.w, __fmaf_rn(w10, b.w, __fmul_rn(w00, a.w))));
     }
     return r;
 }

@@ -39,8 +39,12 @@ class rcp_camera(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3), ("fov_y_deg", C.c_float)]
 
 
+RCP_MAX_SPP = 16
+
+
 class rcp_params(C.Structure):
-    _fields_ = [("mapping", C.c_int32), ("k", C.c_float), ("focal_dist", C.c_float), ("z0", C.c_float)]
+    _fields_ = [("mapping", C.c_int32), ("k", C.c_float), ("focal_dist", C.c_float), ("z0", C.c_float),
+                ("spp", C.c_int32), ("jitter", C.c_float * (2 * RCP_MAX_SPP))]
 
 
 class rcp_scene_info(C.Structure):
@@ -170,8 +174,17 @@ def make_camera(eye, look_at, up=(0.0, 1.0, 0.0), fov_y_deg=60.0) -> rcp_camera:
     return rcp_camera((C.c_float * 3)(*eye), (C.c_float * 3)(*look_at), (C.c_float * 3)(*up), float(fov_y_deg))
 
 
-def make_params(mapping=RCP_MAP_EYE, k=0.0, focal_dist=1.0, z0=0.0) -> rcp_params:
-    return rcp_params(int(mapping), float(k), float(focal_dist), float(z0))
+def make_params(mapping=RCP_MAP_EYE, k=0.0, focal_dist=1.0, z0=0.0, jitter=None) -> rcp_params:
+    """jitter: None (one sample at the pixel centre) or (spp, 2) offsets in [0,1)."""
+    p = rcp_params(int(mapping), float(k), float(focal_dist), float(z0), 0)
+    if jitter is not None:
+        j = np.asarray(jitter, dtype=np.float32).reshape(-1, 2)
+        if not 1 <= len(j) <= RCP_MAX_SPP:
+            raise ValueError("1..16 samples per pixel")
+        p.spp = len(j)
+        for i, v in enumerate(j.reshape(-1)):
+            p.jitter[i] = float(v)
+    return p
 
 
 def make_light(type_, v, ambient=0.1) -> rcp_light:
