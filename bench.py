@@ -235,7 +235,7 @@ def run_ours(args):
                              os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
     else:
         b, c, fz = (int(x) for x in args.tuning.split(","))
-        t = rcp.rcp_tuning(b, 0, c, fz, 0)
+        t = rcp.rcp_tuning(b, 0, c, fz)
         rcp.rcp_set_tuning(g, t)
     log(f"[rank {rank}] tuning block={t.block} chunk={t.chunk} fused_camera={t.fused_camera}")
     poses = [sc.poses[i] for i in shard_poses(rank, world, args.steps, len(sc.poses))]

@@ -192,14 +192,12 @@ rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rc
 /* Traversal tuning. block: threads per block (64, 128, 256); blocks_per_sm:
  * resident blocks of the persistent launch (0 = occupancy maximum); chunk:
  * pixels a warp claims per fetch (32 or 64); fused_camera: 1 = rays are made
- * inside the trace kernel, 0 = a separate camera kernel writes a ray buffer;
- * node_cache: top BVH nodes kept in shared memory (0, 64, 256). */
+ * inside the trace kernel, 0 = a separate camera kernel writes a ray buffer. */
 typedef struct {
     int32_t block;
     int32_t blocks_per_sm;
     int32_t chunk;
     int32_t fused_camera;
-    int32_t node_cache;
 } rcp_tuning;
 
 rcp_status rcp_get_tuning(const rcp_scene* scene, rcp_tuning* out);

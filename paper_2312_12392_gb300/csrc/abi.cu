@@ -682,8 +682,8 @@ rcp_status rcp_set_tuning(rcp_scene* sc, const rcp_tuning* t) {
         return RCP_ERR_ARG;
     }
     if ((t->block != 64 && t->block != 128 && t->block != 256) || (t->chunk != 32 && t->chunk != 64) ||
-        t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || t->node_cache < 0) {
-        set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32");
+        t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || (t->fused_camera != 0 && t->fused_camera != 1)) {
+        set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32, fused 0/1");
         return RCP_ERR_ARG;
     }
     std::lock_guard<std::mutex> lk(sc->mu);
@@ -872,7 +872,7 @@ std::string gpu_name() {
     return prop.name;
 }
 
-// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, node_cache, us], ...}
+// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, us], ...}
 std::map<std::string, std::vector<double>> read_cache(const char* path) {
     std::map<std::string, std::vector<double>> m;
     if (!path) return m;
@@ -892,7 +892,7 @@ std::map<std::string, std::vector<double>> read_cache(const char* path) {
         std::stringstream vs(s.substr(a + 1, b - a - 1));
         std::string tok;
         while (std::getline(vs, tok, ',')) v.push_back(atof(tok.c_str()));
-        if (v.size() >= 6) m[key] = v;
+        if (v.size() >= 5) m[key] = v;
         i = b + 1;
     }
     return m;
@@ -933,8 +933,7 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     auto cache = read_cache(cache_path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-        rcp_tuning t{(int)it->second[0], (int)it->second[1], (int)it->second[2], (int)it->second[3],
-                     (int)it->second[4]};
+        rcp_tuning t{(int)it->second[0], (int)it->second[1], (int)it->second[2], (int)it->second[3]};
         r = rcp_set_tuning(sc, &t);
         if (r == RCP_OK && out) *out = t;
         if (r == RCP_OK) return RCP_OK;
@@ -955,7 +954,7 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     for (int b : blocks)
         for (int fused = 0; fused < 2; ++fused)
             for (int chunk : {32, 64}) {
-                rcp_tuning t{b, 0, chunk, fused, 0};
+                rcp_tuning t{b, 0, chunk, fused};
                 sc->tuning = t;
                 const float4* ins[1] = {nullptr};
                 float4* outs[1] = {d_img};
@@ -982,7 +981,7 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     sc->tuning = best;
     if (r != RCP_OK) return r;
     cache[key.str()] = {(double)best.block, (double)best.blocks_per_sm, (double)best.chunk, (double)best.fused_camera,
-                        (double)best.node_cache, best_us};
+                        best_us};
     write_cache(cache_path, cache);
     if (out) *out = best;
     return RCP_OK;

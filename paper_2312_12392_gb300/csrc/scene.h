@@ -59,7 +59,7 @@ struct Scene {
     float diam = 0.f;
     float build_ms = 0.f;
     LightDev light{};
-    rcp_tuning tuning{128, 0, 32, 1, 0};
+    rcp_tuning tuning{128, 0, 32, 1};
     std::mutex mu;
     std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
     RenderCtx* last = nullptr;  // context of the most recent render

@@ -54,7 +54,7 @@ class rcp_scene_info(C.Structure):
 
 class rcp_tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
-                ("fused_camera", C.c_int32), ("node_cache", C.c_int32)]
+                ("fused_camera", C.c_int32)]
 
 
 class rcp_counters(C.Structure):

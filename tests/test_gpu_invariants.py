@@ -56,7 +56,7 @@ def test_launch_shapes_identical(tiny_g):
         for block in (64, 128, 256):
             for fused in (0, 1):
                 for chunk in (32, 64):
-                    rcp.rcp_set_tuning(g, rcp.rcp_tuning(block, 0, chunk, fused, 0))
+                    rcp.rcp_set_tuning(g, rcp.rcp_tuning(block, 0, chunk, fused))
                     out = _render(g, cam, 640, 360, 3, p)
                     if ref is None:
                         ref = out
@@ -193,4 +193,4 @@ def test_autotune_cache(tmp_path, tiny_g):
     assert t.block in (64, 128, 256) and t.chunk in (32, 64)
     t2 = rcp.rcp_autotune(g, cam, 256, 256, p, path)  # from the cache
     assert (t2.block, t2.chunk, t2.fused_camera) == (t.block, t.chunk, t.fused_camera)
-    rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, 0))
+    rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1))
