@@ -552,7 +552,7 @@ typedef struct {
     double* out;
     int32_t* prim;
     uint8_t* flag;
-    int64_t next;
+    int64_t next, chunk;
     pthread_mutex_t mu;
 } job_t;
 
@@ -721,10 +721,10 @@ static void* worker(void* arg) {
     for (;;) {
         pthread_mutex_lock(&J->mu);
         int64_t i0 = J->next;
-        J->next += 64;
+        J->next += J->chunk;
         pthread_mutex_unlock(&J->mu);
         if (i0 >= J->npix) break;
-        int64_t i1 = i0 + 64 < J->npix ? i0 + 64 : J->npix;
+        int64_t i1 = i0 + J->chunk < J->npix ? i0 + J->chunk : J->npix;
         if (J->spp > 0) {
             for (int64_t i = i0; i < i1; ++i) run_pixel_ms(J, i);
             continue;
@@ -753,6 +753,11 @@ static int run_job(job_t* J, int nthreads) {
     pthread_t th[256];
     pthread_mutex_init(&J->mu, NULL);
     J->next = 0;
+    /* pixels per claim: up to 64, but small enough that every thread gets
+       several claims when the sample is small */
+    J->chunk = J->npix / (8 * (int64_t)nthreads);
+    if (J->chunk > 64) J->chunk = 64;
+    if (J->chunk < 1) J->chunk = 1;
     int started = 0;
     for (int i = 0; i < nthreads; ++i)
         if (pthread_create(&th[i], NULL, worker, J) == 0) ++started;
