@@ -37,7 +37,7 @@ W_IMG, H_IMG, K_PASSES = 1920, 1080, 6
 L2_FLUSH_BYTES = 256 << 20
 # FP32 lane-operations per unit of work ("Roofline")
 OPS_BOX, OPS_TRI, OPS_SPH, OPS_PIXEL = 14, 34, 20, 40
-BYTES_NODE, BYTES_PRIM, BYTES_PIXEL_PASS = 80, 48, 32
+BYTES_NODE, BYTES_PRIM, BYTES_PIXEL_PASS = 208, 48, 32
 
 
 def log(*a):
@@ -189,11 +189,18 @@ def cpu_oracle_sample(sc, poses, target_s, nthreads=0, min_px=64, max_px=8192):
     d = sc.diameter()
     k, f = float(np.float32(0.02 * d)), float(np.float32(0.1 * d))
     cam = poses[0].as_array().astype(np.float32).astype(np.float64)
-    pix = scenes.pixel_subset(W_IMG, H_IMG, min_px, seed=11)
-    t0 = time.perf_counter()
-    o.render(cam, W_IMG, H_IMG, K_PASSES, O.MAP_EYE, k, f, pix=pix, nthreads=nthreads)
-    t1 = time.perf_counter() - t0
-    n = int(min(max_px, max(min_px, min_px * target_s / max(t1, 1e-6))))
+    # size the sample from a probe long enough that thread start-up and load
+    # imbalance over the host cores do not dominate it
+    m = min_px
+    while True:
+        pix = scenes.pixel_subset(W_IMG, H_IMG, m, seed=11)
+        t0 = time.perf_counter()
+        o.render(cam, W_IMG, H_IMG, K_PASSES, O.MAP_EYE, k, f, pix=pix, nthreads=nthreads)
+        t1 = time.perf_counter() - t0
+        if t1 >= min(1.0, 0.1 * target_s * len(poses)) or m * 4 > max_px:
+            break
+        m *= 4
+    n = int(min(max_px, max(min_px, m * target_s / max(t1, 1e-6))))
     total_px, total_t = 0, 0.0
     for i, pose in enumerate(poses):
         pix = scenes.pixel_subset(W_IMG, H_IMG, n, seed=12 + i)

@@ -114,7 +114,7 @@ typedef struct rcp_scene rcp_scene;
 /* Scene statistics (sizes, BVH shape, build time). */
 typedef struct {
     int64_t n_tris, n_spheres;
-    int64_t n_nodes;      /* 8-wide BVH nodes (80 bytes each) */
+    int64_t n_nodes;      /* 8-wide BVH nodes (208 bytes each) */
     int32_t depth;        /* levels of the 8-wide BVH */
     int32_t max_leaf;     /* largest leaf (primitives) */
     int64_t device_bytes; /* device memory held by the scene */
@@ -125,9 +125,10 @@ typedef struct {
 /* Build a scene and its BVH on the device (the scene S(n) of Eq. 1).
  * tri_xyz: host, T*9 floats (v0 v1 v2 per triangle); spheres: host, S*4 floats
  * (centre, radius), may be NULL when S == 0; albedo: host, (T+S)*3 floats,
- * triangles first. The BVH is an LBVH (30-bit Morton codes, radix sort, Karras
- * hierarchy, bottom-up refit) collapsed to a compressed 8-wide BVH. *out
- * receives a handle owned by the library until rcp_scene_destroy. */
+ * triangles first. The BVH is built on the device (30-bit Morton codes, radix
+ * sort, PLOC clustering into a binary tree) and collapsed to an 8-wide BVH with
+ * float child boxes. *out receives a handle owned by the library until
+ * rcp_scene_destroy. */
 rcp_status rcp_scene_create(const float* tri_xyz, int64_t T, const float* spheres, int64_t S,
                             const float* albedo, const rcp_light* light, rcp_scene** out);
 
@@ -141,7 +142,7 @@ rcp_status rcp_scene_update_vertices_device(rcp_scene* scene, const float* d_tri
 rcp_status rcp_scene_get_info(const rcp_scene* scene, rcp_scene_info* info);
 
 /* Check the BVH on the device: every primitive in exactly one leaf, every
- * child box inside its quantised slot, every primitive inside its leaf box.
+ * child's box inside its slot box, every primitive inside its leaf box.
  * RCP_OK when all hold; RCP_ERR_STATE with a message otherwise. */
 rcp_status rcp_scene_validate(const rcp_scene* scene);
 
@@ -240,8 +241,8 @@ rcp_status rcp_last_pass_times(const rcp_scene* scene, float* ms, int max_passes
  *    every primitive instead of walking the BVH.
  *  rcp_debug_sort_pairs: stable LSD radix sort of n (key, value) pairs on the
  *    low `bits` bits of the keys, in place.
- *  rcp_debug_morton: 30-bit Morton codes of n points (xyz[n*3]) in the box
- *    lo[3]..hi[3] (host arrays). */
+ *  rcp_debug_morton: 30-bit Morton codes of n points (xyz[n*3]) in the cube
+ *    with corner lo[3] and side max_a(hi[a] - lo[a]) (host arrays). */
 rcp_status rcp_debug_trace(const rcp_scene* scene, int64_t n, const float* orig_tmin,
                            const float* dir_tmax, int any_hit, int brute, float* t_out,
                            int32_t* prim_out, void* stream);

@@ -63,7 +63,7 @@ Scene::~Scene() {
 
 SceneDev Scene::dev() const {
     SceneDev s;
-    s.nodes = (const uint4*)d_nodes;
+    s.nodes = (const float4*)d_nodes;
     s.prims = d_prims;
     s.albedo = d_albedo;
     s.n_prims = T + S;
@@ -76,7 +76,7 @@ SceneDev Scene::dev() const {
 
 int64_t Scene::device_bytes() const {
     const int64_t N = T + S;
-    return T * 36 + S * 16 + N * 16 + n_nodes * (80 + 32) + N * 48;
+    return T * 36 + S * 16 + N * 16 + n_nodes * ((int64_t)sizeof(WNode) + 32) + N * 48;
 }
 
 void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params& p) {

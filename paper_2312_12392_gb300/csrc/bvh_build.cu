@@ -1,23 +1,26 @@
-// bvh_build.cu -- GPU LBVH builder collapsed to a compressed 8-wide BVH.
+// bvh_build.cu -- GPU BVH builder (Morton order, PLOC clustering) collapsed to an 8-wide BVH.
 //
 // The paper (§6) traced its scenes with OptiX and says nothing about the
 // acceleration structure; this builder serves the scene S(n) of §2, Eq. 1.
 // Steps, all on the device:
 //  1. primitive boxes and centroids; scene and centroid bounds (atomic min/max
 //     on order-preserving integer images of the floats);
-//  2. 30-bit Morton codes of the centroids (10 bits per axis);
+//  2. 30-bit Morton codes of the centroids (10 bits per axis, in the cube of
+//     the largest extent);
 //  3. radix sort of (code, primitive) pairs (radix_sort.cu);
-//  4. binary radix tree over the sorted codes: Karras's construction, one
-//     thread per internal node, equal codes ordered by index;
-//  5. bottom-up box refit, one thread per leaf, the second arrival at each
-//     node continuing upwards (atomic arrival counters);
+//  4. binary tree by PLOC (Meister and Bittner 2018): the primitives in
+//     Morton order are clusters; each round every cluster finds the cluster
+//     within 16 array positions whose union box has the least surface area,
+//     mutual pairs merge (the new node gets the union box), and the array is
+//     compacted by a prefix sum, until one cluster is left;
+//  5. leaves renumbered in depth-first order, so that every subtree's
+//     primitives are contiguous;
 //  6. collapse to 8-wide nodes, one launch per level: each wide node takes a
 //     binary node's two children and repeatedly opens the child with the
 //     largest surface area that holds more than 3 primitives, until 8 children
 //     or none left to open. Subtrees of <= 3 primitives become leaves. Children
 //     are placed in slots so that slot order approximates front-to-back order
-//     per ray octant; boxes are quantised to 8 bits against a per-node origin
-//     and power-of-two scale, rounded outwards with a small pad. Leaf
+//     per ray octant; child boxes are stored as exact float32 bounds. Leaf
 //     primitives are copied into 48-byte records, contiguous per node.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -105,11 +108,15 @@ __global__ void __launch_bounds__(BUILD_BLOCK) k_prim_bounds(const float* __rest
 }
 
 // 10 bits of each axis interleaved as ...x2y2z2 x1y1z1 x0y0z0 (x highest).
+// Every axis is scaled by the box's largest extent (a cube over lo), not by
+// its own: a flat scene (terrain, a forest floor) then keeps its thin axis in
+// the low bits, so the top of the hierarchy splits the long axes and no node
+// near the root spans the whole scene along them.
 __device__ __forceinline__ uint32_t morton30(float x, float y, float z, const float* lo, const float* hi) {
     const float c[3] = {x, y, z};
+    const float ext = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
     uint32_t q[3];
     for (int a = 0; a < 3; ++a) {
-        const float ext = hi[a] - lo[a];
         float u = ext > 0.f ? (c[a] - lo[a]) / ext : 0.f;
         int v = (int)(u * 1024.f);
         q[a] = (uint32_t)min(max(v, 0), 1023);
@@ -141,80 +148,217 @@ __global__ void k_morton_points(const float* __restrict__ xyz, int64_t n, float 
         codes[i] = morton30(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, hi);
 }
 
-// Length of the common prefix of sorted keys i and j; equal keys extend the
-// comparison with the indices themselves (so every key is distinct). -1 when j
-// is out of range.
-__device__ __forceinline__ int delta(const uint32_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
-    if (j < 0 || j >= n) return -1;
-    const uint32_t a = k[i], b = k[j];
-    if (a != b) return __clz(a ^ b);
-    return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+// ---- PLOC: parallel locally-ordered clustering (Meister and Bittner, 2018) ----
+// Clusters start as the primitives in Morton order. Every iteration each
+// cluster finds, among the PLOC_R clusters on either side of it in the array,
+// the one whose union box has the smallest surface area; mutual nearest
+// neighbours merge into a new binary node, and the array is compacted (the
+// merged cluster takes the lower position). Pairs are ordered by (area, index
+// gap, parity of the lower index, lower index), a total order, so the
+// globally smallest pair is always mutual: every iteration merges at least
+// one pair, and a run of equal boxes pairs up (0,1), (2,3), ... at once.
+// Node indices count down: the last merge creates the root, node 0.
+constexpr int PLOC_R = 16;
+constexpr int PLOC_BLOCK = 256;
+
+__device__ __forceinline__ float union_area(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+    const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+    const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+    const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+    const float a = dx * dy + dy * dz + dz * dx;
+    return a == a ? a : INFINITY;
 }
 
-// Binary radix tree (Karras 2012): internal node i covers a key range that
-// starts or ends at i. Children refs: >= 0 internal node, < 0 leaf -(j+1).
-__global__ void k_karras(const uint32_t* __restrict__ k, int64_t n, int2* __restrict__ child,
-                         int2* __restrict__ range, int* __restrict__ parent_int, int* __restrict__ parent_leaf) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1; i += (int64_t)gridDim.x * blockDim.x) {
-        const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
-        const int dmin = delta(k, n, i, i - d);
-        int64_t lmax = 2;
-        while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
-        int64_t l = 0;
-        for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-            if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
-        const int64_t j = i + l * d;
-        const int dnode = delta(k, n, i, j);
-        int64_t s = 0;
-        int64_t t = l;
-        do {
-            t = (t + 1) >> 1;
-            if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
-        } while (t > 1);
-        const int64_t gamma = i + s * d + min(d, 0);
-        const int64_t lo = min(i, j), hi = max(i, j);
-        const int left = (lo == gamma) ? -(int)(gamma + 1) : (int)gamma;
-        const int right = (hi == gamma + 1) ? -(int)(gamma + 2) : (int)(gamma + 1);
-        child[i] = make_int2(left, right);
-        range[i] = make_int2((int)lo, (int)hi);
-        if (left >= 0) parent_int[left] = (int)i;
-        else parent_leaf[-left - 1] = (int)i;
-        if (right >= 0) parent_int[right] = (int)i;
-        else parent_leaf[-right - 1] = (int)i;
-    }
-}
-
-// Bottom-up refit: one thread per leaf; at each internal node the second
-// arriving thread merges both children and goes on (the first stops).
-__global__ void k_refit_binary(const uint32_t* __restrict__ sorted_ids, int64_t n, const float4* __restrict__ plo,
-                               const float4* __restrict__ phi, const int2* __restrict__ child,
-                               const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
-                               float4* blo, float4* bhi, int* arrivals) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        int node = parent_leaf[j];
-        int guard = 0;
-        while (node >= 0 && ++guard < 4096) {
-            __threadfence();
-            if (atomicAdd(&arrivals[node], 1) == 0) break;
-            __threadfence();
-            const int2 c = child[node];
-            float4 l[2], h[2];
-            const int cs[2] = {c.x, c.y};
-            for (int q = 0; q < 2; ++q) {
-                if (cs[q] >= 0) {
-                    l[q] = __ldcg(&blo[cs[q]]);
-                    h[q] = __ldcg(&bhi[cs[q]]);
-                } else {
-                    const uint32_t id = sorted_ids[-cs[q] - 1];
-                    l[q] = plo[id];
-                    h[q] = phi[id];
-                }
-            }
-            __stcg(&blo[node], make_float4(fminf(l[0].x, l[1].x), fminf(l[0].y, l[1].y), fminf(l[0].z, l[1].z), 0.f));
-            __stcg(&bhi[node], make_float4(fmaxf(h[0].x, h[1].x), fmaxf(h[0].y, h[1].y), fmaxf(h[0].z, h[1].z), 0.f));
-            node = parent_int[node];
+__global__ void __launch_bounds__(PLOC_BLOCK) k_ploc_nn(const float4* __restrict__ clo, const float4* __restrict__ chi,
+                                                        int64_t n, int* __restrict__ nn) {
+    __shared__ float4 slo[PLOC_BLOCK + 2 * PLOC_R], shi[PLOC_BLOCK + 2 * PLOC_R];
+    const int64_t first = (int64_t)blockIdx.x * PLOC_BLOCK;
+    for (int t = threadIdx.x; t < PLOC_BLOCK + 2 * PLOC_R; t += PLOC_BLOCK) {
+        const int64_t g = first - PLOC_R + t;
+        if (g >= 0 && g < n) {
+            slo[t] = clo[g];
+            shi[t] = chi[g];
         }
     }
+    __syncthreads();
+    const int64_t i = first + threadIdx.x;
+    if (i >= n) return;
+    const int li = threadIdx.x + PLOC_R;
+    const float4 alo = slo[li], ahi = shi[li];
+    float ba = 0.f;
+    int64_t bj = -1, bgap = 0, blo = 0;
+    for (int o = -PLOC_R; o <= PLOC_R; ++o) {
+        const int64_t j = i + o;
+        if (o == 0 || j < 0 || j >= n) continue;
+        const float a = union_area(alo, ahi, slo[li + o], shi[li + o]);
+        const int64_t gap = o < 0 ? -o : o, lo = o < 0 ? j : i;
+        bool better = bj < 0 || a < ba;
+        if (!better && a == ba) {
+            if (gap != bgap) better = gap < bgap;
+            else if ((lo & 1) != (blo & 1)) better = (lo & 1) < (blo & 1);
+            else better = lo < blo;
+        }
+        if (better) {
+            ba = a;
+            bj = j;
+            bgap = gap;
+            blo = lo;
+        }
+    }
+    nn[i] = (int)bj;
+}
+
+// flag word per cluster: merges here (lower end of a mutual pair) << 32 | stays
+__global__ void k_ploc_flags(const int* __restrict__ nn, int64_t n, unsigned long long* __restrict__ flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = nn[i];
+        const bool mutual = j >= 0 && nn[j] == (int)i;
+        const unsigned long long merge = (mutual && i < j) ? 1ull : 0ull;
+        const unsigned long long keep = (mutual && i > j) ? 0ull : 1ull;
+        flags[i] = (merge << 32) | keep;
+    }
+}
+
+__device__ __forceinline__ int leaf_count(const int* cnt, int ref) { return ref >= 0 ? cnt[ref] : 1; }
+
+// Merge mutual pairs into new nodes and compact the cluster array;
+// scan[i] = exclusive prefix of the flag words.
+__global__ void k_ploc_merge(const int* __restrict__ nn, int64_t n, const unsigned long long* __restrict__ scan,
+                             const int* __restrict__ ref, const float4* __restrict__ clo,
+                             const float4* __restrict__ chi, int node_base, int* __restrict__ ref_out,
+                             float4* __restrict__ lo_out, float4* __restrict__ hi_out, int2* __restrict__ child,
+                             float4* __restrict__ blo, float4* __restrict__ bhi, int* __restrict__ cnt,
+                             int* __restrict__ parent_int, int* __restrict__ parent_leaf) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = nn[i];
+        const bool mutual = j >= 0 && nn[j] == (int)i;
+        if (mutual && i > j) continue;
+        const unsigned long long s = scan[i];
+        const int64_t pos = (int64_t)(s & 0xffffffffull);
+        if (mutual) {
+            const int node = node_base + (int)(s >> 32);
+            const int ra = ref[i], rb = ref[j];
+            const float4 la = clo[i], ha = chi[i], lb = clo[j], hb = chi[j];
+            const float4 l = make_float4(fminf(la.x, lb.x), fminf(la.y, lb.y), fminf(la.z, lb.z), 0.f);
+            const float4 h = make_float4(fmaxf(ha.x, hb.x), fmaxf(ha.y, hb.y), fmaxf(ha.z, hb.z), 0.f);
+            child[node] = make_int2(ra, rb);
+            blo[node] = l;
+            bhi[node] = h;
+            cnt[node] = leaf_count(cnt, ra) + leaf_count(cnt, rb);
+            if (ra >= 0) parent_int[ra] = node;
+            else parent_leaf[-ra - 1] = node;
+            if (rb >= 0) parent_int[rb] = node;
+            else parent_leaf[-rb - 1] = node;
+            ref_out[pos] = node;
+            lo_out[pos] = l;
+            hi_out[pos] = h;
+        } else {
+            ref_out[pos] = ref[i];
+            lo_out[pos] = clo[i];
+            hi_out[pos] = chi[i];
+        }
+    }
+}
+
+__global__ void k_ploc_init(const uint32_t* __restrict__ sorted_ids, int64_t n, const float4* __restrict__ plo,
+                            const float4* __restrict__ phi, int* __restrict__ ref, float4* __restrict__ clo,
+                            float4* __restrict__ chi) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t id = sorted_ids[j];
+        ref[j] = -(int)(j + 1);
+        clo[j] = plo[id];
+        chi[j] = phi[id];
+    }
+}
+
+// Depth-first leaf order: a node's first leaf is the number of leaves left of
+// it, i.e. the sum of the left siblings' leaf counts on its path to the root.
+// Internal node i gets range (first, first + count - 1); leaf j gets pos[j].
+__global__ void k_dfs_offsets(const int2* __restrict__ child, const int* __restrict__ parent_int,
+                              const int* __restrict__ parent_leaf, const int* __restrict__ cnt, int64_t N,
+                              int2* __restrict__ range, int* __restrict__ pos, int* err) {
+    const int64_t total = 2 * N - 1;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const bool internal = k < N - 1;
+        int cur = internal ? (int)k : -(int)(k - (N - 1)) - 1;
+        int p = internal ? parent_int[k] : parent_leaf[k - (N - 1)];
+        int off = 0;
+        for (int guard = 0; p >= 0; ++guard) {
+            if (guard >= (1 << 22)) {
+                atomicAdd(err, 1);
+                break;
+            }
+            const int2 c = child[p];
+            if (c.y == cur) off += leaf_count(cnt, c.x);
+            cur = p;
+            p = parent_int[p];
+        }
+        if (internal) range[k] = make_int2(off, off + cnt[k] - 1);
+        else pos[k - (N - 1)] = off;
+    }
+}
+
+// Leaves renumbered into depth-first order: sorted ids permuted, and leaf
+// references in the children rewritten.
+__global__ void k_dfs_apply(const int* __restrict__ pos, const uint32_t* __restrict__ ids_in, int64_t N,
+                            uint32_t* __restrict__ ids_out, int2* __restrict__ child, int* err) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const int pk = pos[k];
+        if (pk < 0 || pk >= N) {
+            atomicAdd(err, 1);
+            continue;
+        }
+        ids_out[pk] = ids_in[k];
+        if (k < N - 1) {
+            int2 c = child[k];
+            if (c.x < 0) c.x = -pos[-c.x - 1] - 1;
+            if (c.y < 0) c.y = -pos[-c.y - 1] - 1;
+            child[k] = c;
+        }
+    }
+}
+
+// ---- exclusive scan of 64-bit words: tiles of 1024, tile sums scanned recursively ----
+constexpr int SCAN_BLOCK = 256;
+constexpr int SCAN_TILE = 4 * SCAN_BLOCK;
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_tiles(unsigned long long* data, int64_t n,
+                                                           unsigned long long* sums) {
+    __shared__ unsigned long long warp_tot[SCAN_BLOCK / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+    unsigned long long v[4];
+    for (int q = 0; q < 4; ++q) v[q] = base + q < n ? data[base + q] : 0ull;
+    const unsigned long long tsum = v[0] + v[1] + v[2] + v[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = lane < SCAN_BLOCK / 32 ? warp_tot[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < SCAN_BLOCK / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    unsigned long long run = (warp > 0 ? warp_tot[warp - 1] : 0ull) + x - tsum;
+    for (int q = 0; q < 4; ++q) {
+        if (base + q < n) data[base + q] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == SCAN_BLOCK - 1) sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(unsigned long long* data, int64_t n, const unsigned long long* offs) {
+    const int64_t i = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x;
+    const unsigned long long o = offs[blockIdx.x];
+    for (int q = 0; q < 4; ++q)
+        if (i + q * SCAN_BLOCK < n) data[i + q * SCAN_BLOCK] += o;
 }
 
 struct BinTree {
@@ -248,64 +392,28 @@ __device__ __forceinline__ void ref_box(const BinTree& bt, int ref, float3& lo, 
 
 }  // namespace
 
-// Quantise up to 8 child boxes against their union. Writes the node's origin,
-// exponents and q bytes (empty slots get an inverted box); returns the union.
-__device__ void quantise_node(WNode& nd, const float3* clo, const float3* chi, const int* slot_of, int m,
-                              float3& ulo, float3& uhi) {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int c = 0; c < m; ++c) {
-        const double l[3] = {clo[c].x, clo[c].y, clo[c].z}, h[3] = {chi[c].x, chi[c].y, chi[c].z};
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fmin(lo[a], l[a]);
-            hi[a] = fmax(hi[a], h[a]);
-        }
+// Child boxes of up to 8 children into their slots, exactly as computed
+// (empty slots get lo = +inf, hi = -inf, which no ray enters); returns the
+// union of the children.
+__device__ void write_child_boxes(WNode& nd, const float3* clo, const float3* chi, const int* slot_of, int m,
+                                  float3& ulo, float3& uhi) {
+    for (int s = 0; s < 8; ++s) {
+        nd.lo_x[s] = nd.lo_y[s] = nd.lo_z[s] = INFINITY;
+        nd.hi_x[s] = nd.hi_y[s] = nd.hi_z[s] = -INFINITY;
     }
-    ulo = make_float3((float)lo[0], (float)lo[1], (float)lo[2]);
-    uhi = make_float3((float)hi[0], (float)hi[1], (float)hi[2]);
-    double ext = fmax(fmax(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
-    double mag = fmax(fmax(fabs(lo[0]), fabs(hi[0])), fmax(fmax(fabs(lo[1]), fabs(hi[1])), fmax(fabs(lo[2]), fabs(hi[2]))));
-    double pad = ext > 0.0 ? ldexp(ext, -18) : ldexp(mag, -18) + 1e-30;
-    float p[3];
-    int e[3];
-    double s[3];
-    for (int a = 0; a < 3; ++a) {
-        p[a] = __double2float_rd(lo[a] - pad);
-        const double span = (hi[a] + pad) - (double)p[a];
-        int x = 0;
-        frexp(span / 255.0, &x);  // span/255 = m 2^x, m in [0.5, 1) -> 255 * 2^x >= span
-        x = max(x, -120);
-        x = min(x, 40);  // keeps 256 * 2^x / |d| finite for |d| >= 1e-20
-        e[a] = x;
-        s[a] = ldexp(1.0, x);
-    }
-    nd.px = p[0];
-    nd.py = p[1];
-    nd.pz = p[2];
-    uint32_t qlo[3][2] = {{0xffffffffu, 0xffffffffu}, {0xffffffffu, 0xffffffffu}, {0xffffffffu, 0xffffffffu}};
-    uint32_t qhi[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    ulo = make_float3(INFINITY, INFINITY, INFINITY);
+    uhi = make_float3(-INFINITY, -INFINITY, -INFINITY);
     for (int c = 0; c < m; ++c) {
         const int sl = slot_of[c];
-        const double l[3] = {clo[c].x, clo[c].y, clo[c].z}, h[3] = {chi[c].x, chi[c].y, chi[c].z};
-        for (int a = 0; a < 3; ++a) {
-            double ql = floor((l[a] - pad - (double)p[a]) / s[a]);
-            double qh = ceil((h[a] + pad - (double)p[a]) / s[a]);
-            ql = fmin(fmax(ql, 0.0), 255.0);
-            qh = fmin(fmax(qh, 0.0), 255.0);
-            const int sh = 8 * (sl & 3);
-            qlo[a][sl >> 2] = (qlo[a][sl >> 2] & ~(0xffu << sh)) | ((uint32_t)ql << sh);
-            qhi[a][sl >> 2] = (qhi[a][sl >> 2] & ~(0xffu << sh)) | ((uint32_t)qh << sh);
-        }
+        nd.lo_x[sl] = clo[c].x;
+        nd.lo_y[sl] = clo[c].y;
+        nd.lo_z[sl] = clo[c].z;
+        nd.hi_x[sl] = chi[c].x;
+        nd.hi_y[sl] = chi[c].y;
+        nd.hi_z[sl] = chi[c].z;
+        ulo = make_float3(fminf(ulo.x, clo[c].x), fminf(ulo.y, clo[c].y), fminf(ulo.z, clo[c].z));
+        uhi = make_float3(fmaxf(uhi.x, chi[c].x), fmaxf(uhi.y, chi[c].y), fmaxf(uhi.z, chi[c].z));
     }
-    for (int w = 0; w < 2; ++w) {
-        nd.qlo_x[w] = qlo[0][w];
-        nd.qlo_y[w] = qlo[1][w];
-        nd.qlo_z[w] = qlo[2][w];
-        nd.qhi_x[w] = qhi[0][w];
-        nd.qhi_y[w] = qhi[1][w];
-        nd.qhi_z[w] = qhi[2][w];
-    }
-    nd.e_imask = (nd.e_imask & 0xff000000u) | (uint32_t)(e[0] + 127) | ((uint32_t)(e[1] + 127) << 8) |
-                 ((uint32_t)(e[2] + 127) << 16);
 }
 
 __device__ __forceinline__ void write_prim_record(float4* __restrict__ rec, const float* __restrict__ tri,
@@ -422,7 +530,6 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
     const uint32_t child_base = n_int ? atomicAdd(&counters[0], (uint32_t)n_int) : 0u;
     const uint32_t prim_base = n_prim ? atomicAdd(&counters[1], (uint32_t)n_prim) : 0u;
     WNode nd;
-    nd.e_imask = 0;
     nd.child_base = child_base;
     nd.prim_base = prim_base;
     uint32_t meta[2] = {0, 0};
@@ -455,9 +562,8 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
     }
     nd.meta_lo = meta[0];
     nd.meta_hi = meta[1];
-    nd.e_imask = imask << 24;
     float3 ulo, uhi;
-    quantise_node(nd, clo, chi, slot_of, m, ulo, uhi);
+    write_child_boxes(nd, clo, chi, slot_of, m, ulo, uhi);
     nodes[w] = nd;
     nbox[2 * w] = make_float4(ulo.x, ulo.y, ulo.z, 0.f);
     nbox[2 * w + 1] = make_float4(uhi.x, uhi.y, uhi.z, 0.f);
@@ -492,7 +598,7 @@ __global__ void k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbo
     float3 clo[8], chi[8];
     int slot_of[8];
     int m = 0;
-    const uint32_t imask = nd.e_imask >> 24;
+    const uint32_t imask = internal_mask(nd.meta_lo, nd.meta_hi);
     for (int s = 0; s < 8; ++s) {
         const uint32_t mb = ((s < 4 ? nd.meta_lo : nd.meta_hi) >> (8 * (s & 3))) & 0xffu;
         if (!mb) continue;
@@ -518,7 +624,7 @@ __global__ void k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbo
         ++m;
     }
     float3 ulo, uhi;
-    quantise_node(nd, clo, chi, slot_of, m, ulo, uhi);
+    write_child_boxes(nd, clo, chi, slot_of, m, ulo, uhi);
     nodes[w] = nd;
     nbox[2 * w] = make_float4(ulo.x, ulo.y, ulo.z, 0.f);
     nbox[2 * w + 1] = make_float4(uhi.x, uhi.y, uhi.z, 0.f);
@@ -527,14 +633,12 @@ __global__ void k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbo
 // ---------------------------------------------------------------- validation
 
 __device__ __forceinline__ void slot_box(const WNode& nd, int s, double lo[3], double hi[3]) {
-    const float p[3] = {nd.px, nd.py, nd.pz};
-    const uint32_t* ql[3] = {nd.qlo_x, nd.qlo_y, nd.qlo_z};
-    const uint32_t* qh[3] = {nd.qhi_x, nd.qhi_y, nd.qhi_z};
-    for (int a = 0; a < 3; ++a) {
-        const double sc = ldexp(1.0, (int)((nd.e_imask >> (8 * a)) & 0xffu) - 127);
-        lo[a] = (double)p[a] + sc * (double)((ql[a][s >> 2] >> (8 * (s & 3))) & 0xffu);
-        hi[a] = (double)p[a] + sc * (double)((qh[a][s >> 2] >> (8 * (s & 3))) & 0xffu);
-    }
+    lo[0] = nd.lo_x[s];
+    lo[1] = nd.lo_y[s];
+    lo[2] = nd.lo_z[s];
+    hi[0] = nd.hi_x[s];
+    hi[1] = nd.hi_y[s];
+    hi[2] = nd.hi_z[s];
 }
 
 __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, const float4* __restrict__ nbox,
@@ -544,7 +648,7 @@ __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, con
     const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (w >= n_nodes) return;
     const WNode nd = nodes[w];
-    const uint32_t imask = nd.e_imask >> 24;
+    const uint32_t imask = internal_mask(nd.meta_lo, nd.meta_hi);
     for (int s = 0; s < 8; ++s) {
         const uint32_t mb = ((s < 4 ? nd.meta_lo : nd.meta_hi) >> (8 * (s & 3))) & 0xffu;
         if (!mb) {
@@ -612,6 +716,94 @@ struct DevBuf {
     cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, sizeof(T) * (n ? n : 1)); }
 };
 
+// Tile counts of each level of the recursive scan of up to n words.
+std::vector<int64_t> scan_levels(int64_t n) {
+    std::vector<int64_t> lv;
+    do {
+        n = (n + SCAN_TILE - 1) / SCAN_TILE;
+        lv.push_back(n);
+    } while (n > 1);
+    return lv;
+}
+
+// Exclusive scan of d[0..n) in place; the sum of all n words lands in *total.
+// aux holds the tile sums of this level followed by those of deeper levels.
+void scan_u64(unsigned long long* d, int64_t n, unsigned long long* aux, const std::vector<int64_t>& lv, size_t l,
+              unsigned long long* total, cudaStream_t st) {
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(d, n, aux);
+    if (tiles > 1) {
+        scan_u64(aux, tiles, aux + lv[l], lv, l + 1, total, st);
+        k_scan_add<<<(unsigned)tiles, SCAN_BLOCK, 0, st>>>(d, n, aux);
+    } else {
+        cudaMemcpyAsync(total, aux, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+    }
+}
+
+// Binary tree over the N >= 2 primitives in Morton order (ids_in) by PLOC.
+// Fills child, blo/bhi and range of internal nodes 0..N-2 (root 0), with the
+// leaves renumbered depth-first: ids_out[j] is the primitive of leaf j.
+rcp_status build_ploc(int64_t N, const uint32_t* ids_in, uint32_t* ids_out, const float4* plo, const float4* phi,
+                      int2* child, int2* range, float4* blo, float4* bhi, int* parent_int, int* parent_leaf,
+                      int* d_err, int cap, cudaStream_t st) {
+    DevBuf<int> ref_a, ref_b, nn, cnt, pos;
+    DevBuf<float4> lo_a, hi_a, lo_b, hi_b;
+    DevBuf<unsigned long long> flags, aux, total;
+    const std::vector<int64_t> lv = scan_levels(N);
+    int64_t aux_n = 0;
+    for (int64_t t : lv) aux_n += t;
+    RCP_CUDA(ref_a.alloc(N));
+    RCP_CUDA(ref_b.alloc(N));
+    RCP_CUDA(nn.alloc(N));
+    RCP_CUDA(cnt.alloc(N));
+    RCP_CUDA(pos.alloc(N));
+    RCP_CUDA(lo_a.alloc(N));
+    RCP_CUDA(hi_a.alloc(N));
+    RCP_CUDA(lo_b.alloc(N));
+    RCP_CUDA(hi_b.alloc(N));
+    RCP_CUDA(flags.alloc(N));
+    RCP_CUDA(aux.alloc(aux_n));
+    RCP_CUDA(total.alloc(1));
+    RCP_CUDA(cudaMemsetAsync(parent_int, 0xff, sizeof(int) * N, st));
+    RCP_CUDA(cudaMemsetAsync(parent_leaf, 0xff, sizeof(int) * N, st));
+    int *rin = ref_a.p, *rout = ref_b.p;
+    float4 *lin = lo_a.p, *hin = hi_a.p, *lout = lo_b.p, *hout = hi_b.p;
+    k_ploc_init<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(ids_in, N, plo, phi, rin, lin, hin);
+    int64_t n = N, created = 0;
+    while (n > 1) {
+        k_ploc_nn<<<(unsigned)((n + PLOC_BLOCK - 1) / PLOC_BLOCK), PLOC_BLOCK, 0, st>>>(lin, hin, n, nn.p);
+        k_ploc_flags<<<grid_for(n, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(nn.p, n, flags.p);
+        scan_u64(flags.p, n, aux.p, lv, 0, total.p, st);
+        unsigned long long ht = 0;
+        RCP_CUDA(cudaMemcpyAsync(&ht, total.p, sizeof(ht), cudaMemcpyDeviceToHost, st));
+        RCP_CUDA(cudaStreamSynchronize(st));
+        const int64_t merges = (int64_t)(ht >> 32), keeps = (int64_t)(ht & 0xffffffffull);
+        // the smallest pair is always mutual, so an iteration without a merge
+        // means the device state is corrupt
+        if (merges < 1 || keeps != n - merges || created + merges > N - 1) {
+            set_error("BVH build: clustering made no progress");
+            return RCP_ERR_STATE;
+        }
+        const int node_base = (int)(N - 1 - created - merges);
+        k_ploc_merge<<<grid_for(n, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(nn.p, n, flags.p, rin, lin, hin,
+                                                                             node_base, rout, lout, hout, child,
+                                                                             blo, bhi, cnt.p, parent_int,
+                                                                             parent_leaf);
+        created += merges;
+        n = keeps;
+        std::swap(rin, rout);
+        std::swap(lin, lout);
+        std::swap(hin, hout);
+    }
+    k_dfs_offsets<<<grid_for(2 * N - 1, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(child, parent_int, parent_leaf,
+                                                                                 cnt.p, N, range, pos.p, d_err);
+    k_dfs_apply<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(pos.p, ids_in, N, ids_out, child, d_err);
+    RCP_CUDA(cudaGetLastError());
+    // the scratch above is freed on return: finish using it first
+    RCP_CUDA(cudaStreamSynchronize(st));
+    return RCP_OK;
+}
+
 }  // namespace
 
 rcp_status build_bvh(Scene& sc, cudaStream_t st) {
@@ -624,7 +816,7 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     DevBuf<float4> plo, phi, blo, bhi;
     DevBuf<uint32_t> keys, vals, akeys, avals, bounds, counters;
     DevBuf<int2> child, range, fa, fb;
-    DevBuf<int> parent_int, parent_leaf, arrivals, err;
+    DevBuf<int> parent_int, parent_leaf, err;
     DevBuf<char> scratch;
     RCP_CUDA(plo.alloc(N));
     RCP_CUDA(phi.alloc(N));
@@ -634,14 +826,13 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     RCP_CUDA(avals.alloc(N));
     RCP_CUDA(bounds.alloc(12));
     RCP_CUDA(counters.alloc(4));
-    RCP_CUDA(err.alloc(1));
+    RCP_CUDA(err.alloc(2));
     RCP_CUDA(child.alloc(N));
     RCP_CUDA(range.alloc(N));
     RCP_CUDA(blo.alloc(N));
     RCP_CUDA(bhi.alloc(N));
     RCP_CUDA(parent_int.alloc(N));
     RCP_CUDA(parent_leaf.alloc(N));
-    RCP_CUDA(arrivals.alloc(N));
     RCP_CUDA(fa.alloc(n_nodes_cap));
     RCP_CUDA(fb.alloc(n_nodes_cap));
     RCP_CUDA(scratch.alloc(radix_sort_scratch_bytes(N)));
@@ -660,7 +851,7 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int cap = sms * 16;
-    RCP_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    RCP_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int), st));
     RCP_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(uint32_t) * 4, st));
     k_init_bounds<<<1, 32, 0, st>>>(bounds.p);
     k_prim_bounds<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(sc.d_tri, sc.d_sph, T, N, plo.p, phi.p,
@@ -668,15 +859,28 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     k_morton<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(plo.p, phi.p, N, bounds.p, keys.p, vals.p);
     rcp_status rs = radix_sort_pairs(keys.p, vals.p, akeys.p, avals.p, N, 30, scratch.p, err.p, st);
     if (rs != RCP_OK) return rs;
+    uint32_t* ids = vals.p;  // primitive ids in leaf order (Morton order, then depth-first)
     if (N >= 2) {
-        RCP_CUDA(cudaMemsetAsync(arrivals.p, 0, sizeof(int) * N, st));
-        k_karras<<<grid_for(N - 1, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(keys.p, N, child.p, range.p,
-                                                                             parent_int.p, parent_leaf.p);
-        // the root has no parent
-        int minus1 = -1;
-        RCP_CUDA(cudaMemcpyAsync(parent_int.p, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
-        k_refit_binary<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(
-            vals.p, N, plo.p, phi.p, child.p, parent_int.p, parent_leaf.p, blo.p, bhi.p, arrivals.p);
+        // a sort whose look-back wait ran out leaves no valid permutation to cluster
+        int sort_flag = 0;
+        RCP_CUDA(cudaMemcpyAsync(&sort_flag, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RCP_CUDA(cudaStreamSynchronize(st));
+        if (sort_flag) {
+            set_error("radix sort: look-back wait ran out");
+            cudaFree(nodes_full);
+            cudaFree(nbox_full);
+            cudaFree(prims);
+            return RCP_ERR_TIMEOUT;
+        }
+        rcp_status pr = build_ploc(N, vals.p, avals.p, plo.p, phi.p, child.p, range.p, blo.p, bhi.p, parent_int.p,
+                                   parent_leaf.p, err.p + 1, cap, st);
+        if (pr != RCP_OK) {
+            cudaFree(nodes_full);
+            cudaFree(nbox_full);
+            cudaFree(prims);
+            return pr;
+        }
+        ids = avals.p;
     }
     // scene bounds -> diameter
     uint32_t hb[12];
@@ -709,10 +913,17 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         uint32_t one = 1;
         RCP_CUDA(cudaMemcpyAsync(counters.p, &one, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
         int* d_max_leaf = err.p;  // reuse: err[0] is the sort's flag, checked below before reuse
-        int sort_err = 0;
-        RCP_CUDA(cudaMemcpyAsync(&sort_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int herr[2] = {0, 0};
+        RCP_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
         RCP_CUDA(cudaStreamSynchronize(st));
-        if (sort_err) {
+        if (herr[1]) {
+            set_error("BVH build: the clustered tree is malformed (a path to the root too long or a leaf out of range)");
+            cudaFree(nodes_full);
+            cudaFree(nbox_full);
+            cudaFree(prims);
+            return RCP_ERR_STATE;
+        }
+        if (herr[0]) {
             set_error("radix sort: look-back wait ran out");
             cudaFree(nodes_full);
             cudaFree(nbox_full);
@@ -720,7 +931,7 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
             return RCP_ERR_TIMEOUT;
         }
         RCP_CUDA(cudaMemsetAsync(d_max_leaf, 0, sizeof(int), st));
-        BinTree bt{child.p, range.p, blo.p, bhi.p, plo.p, phi.p, vals.p};
+        BinTree bt{child.p, range.p, blo.p, bhi.p, plo.p, phi.p, ids};
         int n_front = 1;
         int64_t begin = 0;
         int2* cur = fa.p;

@@ -1,7 +1,7 @@
 // rcp_internal.cuh -- shared device types of the renderer (not part of the ABI).
 //
 // Layout in device memory (all 16-byte aligned):
-//  * WNode: one compressed 8-wide BVH node, 80 bytes = 5 x uint4.
+//  * WNode: one 8-wide BVH node with float child boxes, 208 bytes = 13 x float4.
 //  * Prim records: 3 x float4 = 48 bytes per primitive, in leaf order:
 //      triangle  w0 = (v0.xyz, e1.x)  w1 = (e1.yz, e2.xy)  w2 = (e2.z, id, 0, 0)
 //      sphere    w0 = (centre, r)     w1 = 0               w2 = (0, id | SPHERE_BIT, 0, 0)
@@ -22,21 +22,29 @@ namespace rcp {
 constexpr uint32_t SPHERE_BIT = 0x80000000u;
 constexpr int MAX_STACK = 64;  // traversal stack entries (>= BVH depth)
 
-// One 8-wide node. Child slot s (0..7) has a quantised box
-//   lo = p + q_lo[s] * 2^e,  hi = p + q_hi[s] * 2^e   (per axis)
-// and meta[s]: 0 = empty, 0x80 | rank = internal child (node child_base +
-// rank, ranks counted in slot order), (count << 5) | offset = leaf of `count`
-// (1..3) primitive records at prim_base + offset.
+// One 8-wide node, 13 rows of 16 bytes. Child slot s (0..7) has the float
+// box lo_a[s]..hi_a[s] per axis a (an empty slot: lo = +inf, hi = -inf), and
+// meta[s]: 0 = empty, 0x80 | rank = internal child (node child_base + rank,
+// ranks counted in slot order), (count << 5) | offset = leaf of `count` (1..3)
+// primitive records at prim_base + offset. Rows 0-1 lo_x, 2-3 hi_x, 4-5 lo_y,
+// 6-7 hi_y, 8-9 lo_z, 10-11 hi_z, 12 the header.
 struct __align__(16) WNode {
-    float px, py, pz;
-    uint32_t e_imask;  // ex | ey << 8 | ez << 16 | imask << 24 (exponents biased by 127)
+    float lo_x[8], hi_x[8], lo_y[8], hi_y[8], lo_z[8], hi_z[8];
     uint32_t child_base;
     uint32_t prim_base;
     uint32_t meta_lo, meta_hi;  // meta[0..3], meta[4..7]
-    uint32_t qlo_x[2], qlo_y[2], qlo_z[2];
-    uint32_t qhi_x[2], qhi_y[2], qhi_z[2];
 };
-static_assert(sizeof(WNode) == 80, "WNode must be 80 bytes");
+constexpr int NODE_ROWS = 13;
+static_assert(sizeof(WNode) == 16 * NODE_ROWS, "WNode must be 13 rows of 16 bytes");
+
+// Slots holding internal children: bit s set when meta byte s has its top bit.
+// Each half gathers bits 7, 15, 23, 31 into bits 28..31 with one multiply
+// (the partial products below bit 28 never carry into it).
+__host__ __device__ __forceinline__ uint32_t internal_mask(uint32_t meta_lo, uint32_t meta_hi) {
+    const uint32_t a = ((meta_lo & 0x80808080u) * 0x00204081u) >> 28;
+    const uint32_t b = ((meta_hi & 0x80808080u) * 0x00204081u) >> 28;
+    return a | (b << 4);
+}
 
 struct LightDev {
     int type;
@@ -46,7 +54,7 @@ struct LightDev {
 
 // Device-resident scene: BVH, primitive records and shading data.
 struct SceneDev {
-    const uint4* nodes;    // n_nodes * 5
+    const float4* nodes;   // n_nodes * NODE_ROWS
     const float4* prims;   // n_prims * 3
     const float4* albedo;  // n_prims
     int64_t n_prims;

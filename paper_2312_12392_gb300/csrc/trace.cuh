@@ -2,7 +2,7 @@
 //
 //  * camera_ray: the per-pixel camera of §2 (Eq. 2-4) and §3 (Eq. 5);
 //  * traverse<ANY>: closest-hit (ANY = false) or any-hit (ANY = true) walk of
-//    the compressed 8-wide BVH with a per-thread stack in shared memory;
+//    the 8-wide BVH (float child boxes) with a per-thread stack in shared memory;
 //  * hit_triangle / hit_sphere: Moller-Trumbore and the analytic sphere test;
 //  * shade_*: Lambert + ambient with a shadow ray, sky on a miss.
 // All arithmetic is float32 with explicit fused multiply-adds, so every kernel
@@ -203,13 +203,6 @@ __device__ __forceinline__ float hit_sphere(const RayF& r, float4 w0) {
     return __int_as_float(0x7f800000);
 }
 
-// Byte k (0..3) of a word as a float, exactly: one byte permute builds the
-// bit pattern of 2^23 + b, and subtracting 2^23 leaves b. The permute is the
-// only integer-pipe instruction; the subtraction runs on the FMA pipe.
-__device__ __forceinline__ float qbyte(uint32_t w, int k) {
-    return __fsub_rn(__uint_as_float(__byte_perm(w, 0x4b000000u, 0x7540u + (unsigned)k)), 8388608.0f);
-}
-
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -230,10 +223,16 @@ __device__ __forceinline__ uint32_t to_order(uint32_t m, uint32_t oct) {
     return m;
 }
 
-// 1 + 2^-17: relative slack on the far end of a box interval (applied to the
-// far-plane slab terms and to the current closest hit). Boxes are padded at
-// build time by 2^-18 of the node extent; together these cover float32
-// rounding of the slab test, so the box test never misses a primitive hit.
+// Box test. Per axis, entry and exit are t = p * (1/d) - o * (1/d), one FMA
+// per plane, made conservative by directed rounding: near planes round
+// o * (1/d) up and the FMA down, far planes the reverse, so each computed
+// entry is <= and each exit >= the exact (p - o) * (1/d) of the rounded
+// reciprocal. The reciprocal's own relative error (<= 2^-24, different per
+// axis) is covered by scaling the far planes' reciprocal by RCP_FAR_SCALE =
+// 1 + 2^-21 away from zero. RCP_BOX_SLACK = 1 + 2^-17 widens the current
+// closest hit, so that boxes holding an equal-t hit (ties go to the lower
+// id) are still entered. The box test therefore never misses a primitive hit.
+#define RCP_FAR_SCALE 1.000000476837158203125f
 #define RCP_BOX_SLACK 1.0000076f
 
 template <bool ANY, bool COUNT>
@@ -250,6 +249,17 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
     const float dz = fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz);
     const float idx = __frcp_rn(dx), idy = __frcp_rn(dy), idz = __frcp_rn(dz);
     const uint32_t oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
+    // far-plane reciprocals, magnified away from zero
+    const float fdx = dx > 0.f ? __fmul_ru(idx, RCP_FAR_SCALE) : __fmul_rd(idx, RCP_FAR_SCALE);
+    const float fdy = dy > 0.f ? __fmul_ru(idy, RCP_FAR_SCALE) : __fmul_rd(idy, RCP_FAR_SCALE);
+    const float fdz = dz > 0.f ? __fmul_ru(idz, RCP_FAR_SCALE) : __fmul_rd(idz, RCP_FAR_SCALE);
+    // -o * (1/d): rounded down for near planes, up for far planes
+    const float nox = -__fmul_ru(r.ox, idx), noy = -__fmul_ru(r.oy, idy), noz = -__fmul_ru(r.oz, idz);
+    const float fox = -__fmul_rd(r.ox, fdx), foy = -__fmul_rd(r.oy, fdy), foz = -__fmul_rd(r.oz, fdz);
+    // node rows of the near and far planes per axis (lo rows first, then hi)
+    const int rxn = (oct & 1u) ? 2 : 0, rxf = 2 - rxn;
+    const int ryn = (oct & 2u) ? 6 : 4, ryf = 10 - ryn;
+    const int rzn = (oct & 4u) ? 10 : 8, rzf = 18 - rzn;
     float tfar_lim = __fmul_rn(h.t, RCP_BOX_SLACK);
 
     // node group: x = first child node index, y = imask | (hits in traversal order) << 8
@@ -285,47 +295,32 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
                     overflow = true;
                 }
             }
-            const uint4* np = S.nodes + 5 * (size_t)node;
-            const uint4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2), d = __ldg(np + 3), e = __ldg(np + 4);
+            const float4* np = S.nodes + NODE_ROWS * (size_t)node;
+            const uint4 hd = __ldg(reinterpret_cast<const uint4*>(np + 12));
             if (COUNT) wc.nodes++;
-            // slab terms: t(q) = q * Sa + Oa = (p + q 2^e - o) / d, with Sa = 2^e / d
-            // and Oa = (p - o) / d; far planes carry the relative slack
-            const float sx = __uint_as_float((a.w & 0xffu) << 23);
-            const float sy = __uint_as_float(((a.w >> 8) & 0xffu) << 23);
-            const float sz = __uint_as_float(((a.w >> 16) & 0xffu) << 23);
-            const float Sx = __fmul_rn(sx, idx), Sy = __fmul_rn(sy, idy), Sz = __fmul_rn(sz, idz);
-            const float Ox = __fmul_rn(__fsub_rn(__uint_as_float(a.x), r.ox), idx);
-            const float Oy = __fmul_rn(__fsub_rn(__uint_as_float(a.y), r.oy), idy);
-            const float Oz = __fmul_rn(__fsub_rn(__uint_as_float(a.z), r.oz), idz);
-            const float Sfx = __fmul_rn(Sx, RCP_BOX_SLACK), Sfy = __fmul_rn(Sy, RCP_BOX_SLACK),
-                        Sfz = __fmul_rn(Sz, RCP_BOX_SLACK);
-            const float Ofx = __fmul_rn(Ox, RCP_BOX_SLACK), Ofy = __fmul_rn(Oy, RCP_BOX_SLACK),
-                        Ofz = __fmul_rn(Oz, RCP_BOX_SLACK);
-            // near/far byte words per axis from the ray's direction signs
-            const uint32_t nx0 = (oct & 1u) ? d.z : c.x, nx1 = (oct & 1u) ? d.w : c.y;
-            const uint32_t fx0 = (oct & 1u) ? c.x : d.z, fx1 = (oct & 1u) ? c.y : d.w;
-            const uint32_t ny0 = (oct & 2u) ? e.x : c.z, ny1 = (oct & 2u) ? e.y : c.w;
-            const uint32_t fy0 = (oct & 2u) ? c.z : e.x, fy1 = (oct & 2u) ? c.w : e.y;
-            const uint32_t nz0 = (oct & 4u) ? e.z : d.x, nz1 = (oct & 4u) ? e.w : d.y;
-            const uint32_t fz0 = (oct & 4u) ? d.x : e.z, fz1 = (oct & 4u) ? d.y : e.w;
             uint32_t hitmask = 0;
+            // both halves unrolled: the second half's rows load while the
+            // first half's slots are tested (faster than the lower-register
+            // form that tests one half at a time)
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const int k = s & 3;
-                const uint32_t wnx = s < 4 ? nx0 : nx1, wfx = s < 4 ? fx0 : fx1;
-                const uint32_t wny = s < 4 ? ny0 : ny1, wfy = s < 4 ? fy0 : fy1;
-                const uint32_t wnz = s < 4 ? nz0 : nz1, wfz = s < 4 ? fz0 : fz1;
-                const float t0x = __fmaf_rn(qbyte(wnx, k), Sx, Ox);
-                const float t1x = __fmaf_rn(qbyte(wfx, k), Sfx, Ofx);
-                const float t0y = __fmaf_rn(qbyte(wny, k), Sy, Oy);
-                const float t1y = __fmaf_rn(qbyte(wfy, k), Sfy, Ofy);
-                const float t0z = __fmaf_rn(qbyte(wnz, k), Sz, Oz);
-                const float t1z = __fmaf_rn(qbyte(wfz, k), Sfz, Ofz);
-                const float tn = fmax3(t0x, t0y, fmaxf(t0z, r.tmin));
-                const float tf = fmin3(t1x, t1y, fminf(t1z, tfar_lim));
-                hitmask |= (tn <= tf ? 1u : 0u) << s;
+            for (int half = 0; half < 2; ++half) {
+                const float4 nx = __ldg(np + rxn + half), fx = __ldg(np + rxf + half);
+                const float4 ny = __ldg(np + ryn + half), fy = __ldg(np + ryf + half);
+                const float4 nz = __ldg(np + rzn + half), fz = __ldg(np + rzf + half);
+                const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+                const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+                const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float t0x = __fmaf_rd(nxs[k], idx, nox), t1x = __fmaf_ru(fxs[k], fdx, fox);
+                    const float t0y = __fmaf_rd(nys[k], idy, noy), t1y = __fmaf_ru(fys[k], fdy, foy);
+                    const float t0z = __fmaf_rd(nzs[k], idz, noz), t1z = __fmaf_ru(fzs[k], fdz, foz);
+                    const float tn = fmax3(t0x, t0y, fmaxf(t0z, r.tmin));
+                    const float tf = fmin3(t1x, t1y, fminf(t1z, tfar_lim));
+                    hitmask |= (tn <= tf ? 1u : 0u) << (4 * half + k);
+                }
             }
-            const uint32_t ml = b.z, mh = b.w;
+            const uint32_t ml = hd.z, mh = hd.w;
             // an empty slot (meta 0) that tests as hit adds no child: it is not
             // in imask and its leaf count is 0
             if (COUNT) {
@@ -335,11 +330,11 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
                     nonempty |= ((((s < 4 ? ml : mh) >> (8 * (s & 3))) & 0xffu) != 0u ? 1u : 0u) << s;
                 wc.boxes += __popc(nonempty);
             }
-            const uint32_t imask = a.w >> 24;
+            const uint32_t imask = internal_mask(ml, mh);
             const uint32_t hint = hitmask & imask;
             uint32_t hleaf = hitmask & ~imask;
-            group = make_uint2(b.x, imask | (to_order(hint, oct) << 8));
-            prim_base = b.y;
+            group = make_uint2(hd.x, imask | (to_order(hint, oct) << 8));
+            prim_base = hd.y;
             prim_mask = 0;
             while (hleaf) {
                 const uint32_t s = __ffs(hleaf) - 1;

@@ -34,7 +34,10 @@ def test_radix_sort_matches_stable_sort(n, bits):
 
 
 def _morton_ref(p, lo, hi):
-    q = np.clip(((p - lo) / (hi - lo) * 1024.0).astype(np.int64), 0, 1023)
+    """Interleaved 10-bit cells of each axis, all axes scaled by the largest
+    extent of the box (a cube with corner lo)."""
+    ext = float(np.max(hi - lo))
+    q = np.clip(((p - lo) / ext * 1024.0).astype(np.int64), 0, 1023)
     code = np.zeros(len(p), np.int64)
     for b in range(10):
         for a in range(3):
@@ -42,14 +45,18 @@ def _morton_ref(p, lo, hi):
     return code.astype(np.uint32)
 
 
+def _codes(p, lo, hi):
+    codes = torch.empty(len(p), dtype=torch.int32, device="cuda")
+    rcp.rcp_debug_morton(_dev(p), len(p), lo, hi, codes)
+    return codes.cpu().numpy().view(np.uint32)
+
+
 def test_morton_codes():
     rng = np.random.default_rng(3)
     p = rng.uniform(-5, 7, size=(50_000, 3)).astype(np.float32)
     lo = np.array([-5, -5, -5], np.float32)
     hi = np.array([7, 7, 7], np.float32)
-    codes = torch.empty(len(p), dtype=torch.int32, device="cuda")
-    rcp.rcp_debug_morton(_dev(p), len(p), lo, hi, codes)
-    got = codes.cpu().numpy().view(np.uint32)
+    got = _codes(p, lo, hi)
     want = _morton_ref(p.astype(np.float32), lo, hi)
     # the kernel normalises in float32; allow codes to differ only where a
     # coordinate sits on a cell boundary
@@ -57,10 +64,23 @@ def test_morton_codes():
     assert diff.mean() < 1e-3
     # corners
     corners = np.array([[-5, -5, -5], [7 - 1e-4, 7 - 1e-4, 7 - 1e-4]], np.float32)
-    codes2 = torch.empty(2, dtype=torch.int32, device="cuda")
-    rcp.rcp_debug_morton(_dev(corners), 2, lo, hi, codes2)
-    c = codes2.cpu().numpy().view(np.uint32)
+    c = _codes(corners, lo, hi)
     assert c[0] == 0 and c[1] == (1 << 30) - 1
+
+
+def test_morton_flat_box_keeps_thin_axis_low():
+    """A slab 256 x 8 x 256: y spans 8/256 of the cube, i.e. cells 0..31, so
+    its bits never reach the top 5 interleaved levels; x and z use all 10."""
+    rng = np.random.default_rng(4)
+    lo = np.array([-128, 0, -128], np.float32)
+    hi = np.array([128, 8, 128], np.float32)
+    p = (lo + rng.uniform(0, 1, size=(20_000, 3)) * (hi - lo)).astype(np.float32)
+    got = _codes(p, lo, hi)
+    assert (got != _morton_ref(p, lo, hi)).mean() < 1e-3
+    y_bits = sum(1 << (3 * b + 1) for b in range(10))
+    assert np.all((got & y_bits) < (1 << 14))  # y bits 5..9 (positions 16..28) are zero
+    top = np.array([[127.999, 7.999, 127.999]], np.float32)
+    assert _codes(top, lo, hi)[0] == _morton_ref(top, lo, hi)[0]
 
 
 SCENES = {
