@@ -127,7 +127,8 @@ typedef struct {
  * (centre, radius), may be NULL when S == 0; albedo: host, (T+S)*3 floats,
  * triangles first. The BVH is built on the device (30-bit Morton codes, radix
  * sort, PLOC clustering into a binary tree) and collapsed to an 8-wide BVH with
- * float child boxes. *out receives a handle owned by the library until
+ * float child boxes, and validated (as rcp_scene_validate) before it is
+ * returned. *out receives a handle owned by the library until
  * rcp_scene_destroy. */
 rcp_status rcp_scene_create(const float* tri_xyz, int64_t T, const float* spheres, int64_t S,
                             const float* albedo, const rcp_light* light, rcp_scene** out);

@@ -483,6 +483,10 @@ rcp_status rcp_scene_create(const float* tri, int64_t T, const float* sph, int64
     }
     rcp_status r = build_bvh(*sc, st);
     if (r != RCP_OK) return r;
+    // the traversal reads child and record indices without range checks: a
+    // tree is only handed out once every index in it is known to be in range
+    r = validate_bvh(*sc, st);
+    if (r != RCP_OK) return r;
     *out = sc.release();
     return RCP_OK;
 }

@@ -17,8 +17,8 @@
 //     primitives are contiguous;
 //  6. collapse to 8-wide nodes, one launch per level: each wide node takes a
 //     binary node's two children and repeatedly opens the child with the
-//     largest surface area that holds more than 3 primitives, until 8 children
-//     or none left to open. Subtrees of <= 3 primitives become leaves. Children
+//     largest surface area that holds more than LEAF_MAX (3) primitives, until 8
+//     children or none left to open. Subtrees of <= LEAF_MAX primitives become leaves. Children
 //     are placed in slots so that slot order approximates front-to-back order
 //     per ray octant; child boxes are stored as exact float32 bounds. Leaf
 //     primitives are copied into 48-byte records, contiguous per node.
@@ -44,6 +44,10 @@ rcp_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* alt_keys, 
 namespace {
 
 constexpr int BUILD_BLOCK = 256;
+// Most primitives in one leaf slot. A leaf's meta byte holds count << 5 |
+// offset with bit 7 clear (bit 7 marks an internal child), so count <= 3.
+constexpr int LEAF_MAX = 3;
+static_assert(LEAF_MAX >= 1 && LEAF_MAX <= 3, "a leaf's count must leave the meta byte's top bit clear");
 
 __device__ __forceinline__ uint32_t f2ord(float f) {
     const uint32_t u = __float_as_uint(f);
@@ -469,7 +473,7 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
         int best = -1;
         float best_area = -1.f;
         for (int c = 0; c < m; ++c) {
-            if (cref[c] < 0 || clast[c] - cfirst[c] + 1 <= 3) continue;
+            if (cref[c] < 0 || clast[c] - cfirst[c] + 1 <= LEAF_MAX) continue;
             const float dx = chi[c].x - clo[c].x, dy = chi[c].y - clo[c].y, dz = chi[c].z - clo[c].z;
             const float area = dx * dy + dy * dz + dz * dx;
             if (area > best_area) {
@@ -523,7 +527,7 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
     int is_int[8];
     int n_int = 0, n_prim = 0;
     for (int c = 0; c < m; ++c) {
-        is_int[c] = cref[c] >= 0 && clast[c] - cfirst[c] + 1 > 3;
+        is_int[c] = cref[c] >= 0 && clast[c] - cfirst[c] + 1 > LEAF_MAX;
         if (is_int[c]) ++n_int;
         else n_prim += clast[c] - cfirst[c] + 1;
     }

@@ -266,8 +266,11 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
     uint2 group = make_uint2(0u, 1u | ((1u << oct) << 8));
     uint32_t prim_base = 0, prim_mask = 0;
     int sp = 0;
-    // a valid BVH is a tree whose child indices grow, so every node is entered
-    // at most once; the cap only turns a corrupted structure into an error
+    // Every node and record index read here is in range: the builder
+    // validates each tree (child indices above the parent and below n_nodes,
+    // ranks matching the slot masks, records below n_prims) before a scene is
+    // returned, and refits keep the topology. Child indices grow, so every
+    // node is entered at most once; the cap only bounds the loop.
     // Every iteration visits exactly one node: when the current group is
     // exhausted the next one is popped first, so no lane spends an iteration
     // on the stack alone while the rest of its warp tests boxes.
