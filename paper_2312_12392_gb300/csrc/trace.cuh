@@ -243,10 +243,16 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
     h.id = 0xffffffffu;
     h.rec = -1;
     if (S.n_nodes == 0) return h;
-    const float tiny = 1e-20f;
-    const float dx = fabsf(r.dx) > tiny ? r.dx : copysignf(tiny, r.dx);
-    const float dy = fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy);
-    const float dz = fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz);
+    // A zero component stays zero (as +0, so that the octant bit and the sign
+    // of 1/d agree) and its reciprocal is +inf: the ray is parallel to that
+    // axis's planes. Its slab terms are then +-inf, or NaN where inf - inf
+    // meets a plane level with the origin; min/max drop NaN operands, and
+    // t_min and the far limit are never NaN, so a NaN term leaves the slab
+    // unbounded. Nudging d away from zero instead would tilt a ray that lies
+    // exactly in a box face out of that box.
+    const float dx = r.dx == 0.f ? 0.f : r.dx;
+    const float dy = r.dy == 0.f ? 0.f : r.dy;
+    const float dz = r.dz == 0.f ? 0.f : r.dz;
     const float idx = __frcp_rn(dx), idy = __frcp_rn(dy), idz = __frcp_rn(dz);
     const uint32_t oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
     // far-plane reciprocals, magnified away from zero

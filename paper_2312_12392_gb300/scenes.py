@@ -393,6 +393,38 @@ def random_soup(n_tris: int, n_spheres: int = 0, seed: int = 0, extent: float = 
                  _f32(alb), Light(LIGHT_POINT, (extent, 3 * extent, extent), 0.1), [cam])
 
 
+def blocks_scene(n: int = 32, n_cubes: int = 200, seed: int = 6,
+                 offset: tuple = (0.0, 0.0, 0.0)) -> Scene:
+    """Axis-aligned geometry on integer coordinates (for traversal edge cases):
+    a flat n x n grid of unit quads at y = 0, each split into two triangles
+    along the diagonal from (x, z) to (x+1, z+1), and unit cubes (12 triangles)
+    on seeded grid cells, stacked up to 3 high. Every vertex coordinate is an
+    integer plus `offset`, so boxes are flat or share faces exactly."""
+    rng = np.random.default_rng(seed)
+    tris = []
+    for x in range(n):
+        for z in range(n):
+            a, b, c, d = (x, 0, z), (x + 1, 0, z), (x + 1, 0, z + 1), (x, 0, z + 1)
+            tris += [a + c + b, a + d + c]
+    corners = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], np.float64)
+    faces = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    cells = rng.integers(0, n, size=(n_cubes, 2))
+    heights = rng.integers(1, 4, size=n_cubes)
+    for (cx, cz), h in zip(cells, heights):
+        for level in range(int(h)):
+            base = np.array([cx, level, cz], np.float64)
+            for f in faces:
+                q = [tuple(corners[i] + base) for i in f]
+                tris += [q[0] + q[1] + q[2], q[0] + q[2] + q[3]]
+    t = np.asarray(tris, np.float64) + np.tile(np.asarray(offset, np.float64), 3)
+    alb = rng.uniform(0.1, 0.9, size=(len(t), 3))
+    c = np.asarray(offset, np.float64) + np.array([n / 2, 0.0, n / 2])
+    cam = Camera(tuple(c + np.array([0.0, n / 2, 1.5 * n])), tuple(c), (0.0, 1.0, 0.0), 60.0)
+    d = np.array([0.4, 0.8, 0.3]) / np.linalg.norm([0.4, 0.8, 0.3])
+    return Scene(f"blocks{n}_{n_cubes}", _f32(t), np.zeros((0, 4), np.float32), _f32(alb),
+                 Light(LIGHT_DIRECTIONAL, tuple(d.tolist()), 0.1), [cam])
+
+
 # --------------------------------------------------------------------------
 # view sets and samples
 # --------------------------------------------------------------------------

@@ -51,3 +51,16 @@ def test_pixel_subset_and_requests():
     assert all(256 <= w <= 1920 and 256 <= h <= 1080 for w, h in sizes)
     arr = scenes.poisson_arrivals(50.0, 1000)
     assert abs(np.mean(np.diff(arr)) - 1 / 50.0) < 0.2 / 50.0
+
+
+def test_blocks_scene_integer_grid():
+    a = scenes.blocks_scene(8, n_cubes=10, seed=3)
+    b = scenes.blocks_scene(8, n_cubes=10, seed=3)
+    assert np.array_equal(a.tris, b.tris)
+    # 2 triangles per floor quad, 12 per stacked unit cube
+    assert (a.n_tris - 2 * 8 * 8) % 12 == 0 and a.n_tris > 2 * 8 * 8
+    assert np.array_equal(a.tris, np.round(a.tris))
+    floor = a.tris[: 2 * 8 * 8].reshape(-1, 3, 3)
+    assert np.all(floor[:, :, 1] == 0.0)
+    off = scenes.blocks_scene(8, n_cubes=10, seed=3, offset=(1e4, 0.0, -5e3))
+    assert np.array_equal(off.tris - np.tile(np.float32([1e4, 0.0, -5e3]), 3), a.tris)
