@@ -52,6 +52,20 @@ def measured_peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+FOREST_WORKLOADS = ("forest", "batched", "stress")
+
+
+def collapse_for(args, workload):
+    """BVH collapse policy: --collapse, or by scene kind ('auto'): the surface-
+    area dynamic program for the forests (measured +11 % frames/s there), the
+    largest-area greedy for the terrains (measured +1.2 % there)."""
+    from paper_2312_12392_gb300 import rcp
+    name = args.collapse
+    if name == "auto":
+        name = "sah" if workload in FOREST_WORKLOADS else "area"
+    return (rcp.RCP_COLLAPSE_SAH if name == "sah" else rcp.RCP_COLLAPSE_AREA), name
+
+
 def csrc_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_12392_gb300", "csrc")
@@ -231,8 +245,9 @@ def run_ours(args):
     sc, desc = make_workload(args.workload)
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+    collapse, collapse_name = collapse_for(args, args.workload)
     t0 = time.perf_counter()
-    g = rcp.scene_from(sc)
+    g = rcp.scene_from(sc, collapse)
     build_s = time.perf_counter() - t0
     info = rcp.rcp_scene_get_info(g)
     log(f"[rank {rank}] scene {sc.name}: {info.n_tris} tris, {info.n_nodes} nodes, depth {info.depth}, "
@@ -366,6 +381,7 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded procedural scene and walk-through)",
         "config": {"workload": desc, "l2": "flushed between steps (256 MB write, outside the timed events)",
+                   "bvh_collapse": collapse_name,
                    "tuning": {"block": t.block, "chunk": t.chunk, "fused_camera": t.fused_camera},
                    "parallelism": f"replicas x{world} (poses split across ranks, no collective on the data path)"},
         "mrays_per_s": rays / (tmax / 1000.0) / 1e6,
@@ -400,7 +416,8 @@ def forest_extra(args):
     sc, desc = make_workload("forest")
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
-    g = rcp.scene_from(sc)
+    collapse, collapse_name = collapse_for(args, "forest")
+    g = rcp.scene_from(sc, collapse)
     try:
         cams = [rcp.camera_from(sc.poses[i]) for i in range(16)]
         stream = torch.cuda.current_stream()
@@ -424,7 +441,7 @@ def forest_extra(args):
         info = rcp.rcp_scene_get_info(g)
         return {"workload": desc, "frames_per_s": len(cams) / tot, "mrays_per_s": rays / tot / 1e6,
                 "ms_per_frame": 1000 * tot / len(cams), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
-                "depth": info.depth}
+                "depth": info.depth, "bvh_collapse": collapse_name}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -498,7 +515,8 @@ def run_batched(args):
     sc, _ = make_workload("forest")
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
-    g = rcp.scene_from(sc)
+    collapse, collapse_name = collapse_for(args, "batched")
+    g = rcp.scene_from(sc, collapse)
     sizes = scenes.batched_view_sizes(64, seed=3)
     cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(len(sizes))]
     t = rcp.rcp_autotune(g, cams[0], 960, 540, params,
@@ -542,6 +560,7 @@ def run_batched(args):
         "ms_per_step": res["batched"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, graph-captured",
+                   "bvh_collapse": collapse_name,
                    "l2": "flushed between steps", "tuning": {"block": t.block, "chunk": t.chunk,
                                                              "fused_camera": t.fused_camera}},
         "mrays_per_s": (p_ + s_) / (res["batched"] / 1000.0) / 1e6,
@@ -570,7 +589,8 @@ def run_served(args):
     B.build()
     grids = [221, 706, 1224, 1580]
     scs = [scenes.terrain_scene(gsz, seed=4) for gsz in grids]
-    gs = [rcp.scene_from(s) for s in scs]
+    collapse, collapse_name = collapse_for(args, "served")
+    gs = [rcp.scene_from(s, collapse) for s in scs]
     n_req = args.steps
     reqs = scenes.served_requests(n_req, len(scs), 64, seed=4)
     diams = [s.diameter() for s in scs]
@@ -646,7 +666,8 @@ def run_served(args):
         "value": best["served"]["frames_per_s"], "unit": "frames/s",
         "n_gpus": 1, "steps": n_req, "warmup": 1, "ms_per_step": 1000.0 / best["served"]["frames_per_s"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "4 resident terrain scenes (100,082 / 999,272 / 2,998,752 / 4,995,200 tris); "
+        "config": {"bvh_collapse": collapse_name,
+                   "workload": "4 resident terrain scenes (100,082 / 999,272 / 2,998,752 / 4,995,200 tris); "
                                "720p-2160p, K in 1..8, Poisson arrivals",
                    "requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb},
         "sweep": table,
@@ -672,7 +693,8 @@ def run_stress(args):
     W, H, K = 3840, 2160, 8
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
-    g = rcp.scene_from(sc)
+    collapse, collapse_name = collapse_for(args, "stress")
+    g = rcp.scene_from(sc, collapse)
     info = rcp.rcp_scene_get_info(g)
     base = torch.from_numpy(sc.tris).cuda().reshape(-1, 3, 3)
     amp = torch.from_numpy(sc.sway_amp).cuda()
@@ -715,7 +737,8 @@ def run_stress(args):
         "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"stress: {info.n_tris:,} tris (25,000 swaying cone trees), 3840x2160, K=8, "
+        "config": {"bvh_collapse": collapse_name,
+                   "workload": f"stress: {info.n_tris:,} tris (25,000 swaying cone trees), 3840x2160, K=8, "
                                "wind sway A=0.02*h_tree at 0.5 Hz, refit every frame",
                    "scene_generation_s": gen_s, "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
                    "depth": info.depth},
@@ -741,7 +764,8 @@ def run_imagespace(args):
     W, H, K, kpx = 3840, 2160, 6, 8.0
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_IMAGE, kpx, 0.1 * d)
-    g = rcp.scene_from(sc)
+    collapse, collapse_name = collapse_for(args, "imagespace")
+    g = rcp.scene_from(sc, collapse)
     stream = torch.cuda.current_stream()
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -770,7 +794,8 @@ def run_imagespace(args):
         "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "mid terrain 133k tris, 3840x2160, K=6, RCP_MAP_IMAGE k=8 px: 1 traced pass + 5 "
+        "config": {"bvh_collapse": collapse_name,
+                   "workload": "mid terrain 133k tris, 3840x2160, K=6, RCP_MAP_IMAGE k=8 px: 1 traced pass + 5 "
                                "gather passes", "l2": "flushed between steps"},
         "trace_pass_ms": statistics.mean(trace_ms),
         "roofline": {"bound": "hbm", "kernel": "k_imagespace (one gather pass)", "launch_ms": g_s * 1e3,
@@ -791,6 +816,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress", "imagespace"])
     ap.add_argument("--tuning", default="128,32,1", help="'auto' or block,chunk,fused_camera")
+    ap.add_argument("--collapse", default="auto", choices=["auto", "area", "sah"],
+                    help="BVH collapse policy; auto: sah for the forest workloads, area for the terrains")
     ap.add_argument("--count-poses", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -428,6 +428,15 @@ const char* rcp_version(void) { return "rcp-gb300 0.1 (sm_103a)"; }
 
 rcp_status rcp_scene_create(const float* tri, int64_t T, const float* sph, int64_t S, const float* albedo,
                             const rcp_light* light, rcp_scene** out) {
+    return rcp_scene_create_ex(tri, T, sph, S, albedo, light, nullptr, out);
+}
+
+rcp_status rcp_scene_create_ex(const float* tri, int64_t T, const float* sph, int64_t S, const float* albedo,
+                               const rcp_light* light, const rcp_build_options* options, rcp_scene** out) {
+    if (options && options->collapse != RCP_COLLAPSE_AREA && options->collapse != RCP_COLLAPSE_SAH) {
+        set_error("rcp_scene_create_ex: unknown collapse policy");
+        return RCP_ERR_ARG;
+    }
     if (!out || !light || T < 0 || S < 0 || (T > 0 && !tri) || (S > 0 && !sph) || (T + S > 0 && !albedo)) {
         set_error("rcp_scene_create: NULL array with a nonzero count, or negative count");
         return RCP_ERR_ARG;
@@ -452,6 +461,7 @@ rcp_status rcp_scene_create(const float* tri, int64_t T, const float* sph, int64
         }
     *out = nullptr;
     auto sc = std::make_unique<rcp_scene>();
+    sc->collapse = options ? options->collapse : RCP_COLLAPSE_AREA;
     sc->T = T;
     sc->S = S;
     const int64_t N = T + S;
@@ -534,6 +544,8 @@ rcp_status rcp_scene_get_info(const rcp_scene* sc, rcp_scene_info* info) {
     info->device_bytes = sc->device_bytes();
     info->diam = sc->diam;
     info->build_ms = sc->build_ms;
+    info->collapse = sc->collapse;
+    info->reserved_ = 0;
     return RCP_OK;
 }
 

@@ -15,10 +15,12 @@
 //     compacted by a prefix sum, until one cluster is left;
 //  5. leaves renumbered in depth-first order, so that every subtree's
 //     primitives are contiguous;
-//  6. collapse to 8-wide nodes, one launch per level: each wide node takes a
-//     binary node's two children and repeatedly opens the child with the
-//     largest surface area that holds more than LEAF_MAX (3) primitives, until 8
-//     children or none left to open. Subtrees of <= LEAF_MAX primitives become leaves. Children
+//  6. collapse to 8-wide nodes, one launch per level. Subtrees of <= LEAF_MAX
+//     (3) primitives become leaves. Which binary nodes are opened into a wide
+//     node's 8 slots follows the scene's policy: RCP_COLLAPSE_AREA repeatedly
+//     opens the child of largest surface area that holds more than LEAF_MAX
+//     primitives; RCP_COLLAPSE_SAH shares the slots out by a bottom-up dynamic
+//     program over the binary tree that minimises the surface-area cost. Children
 //     are placed in slots so that slot order approximates front-to-back order
 //     per ray octant; child boxes are stored as exact float32 bounds. Leaf
 //     primitives are copied into 48-byte records, contiguous per node.
@@ -322,6 +324,97 @@ __global__ void k_dfs_apply(const int* __restrict__ pos, const uint32_t* __restr
     }
 }
 
+// ---- slot assignment of the 8-wide collapse by surface-area cost ----
+// Cost model (SAH, up to the common factor 1 / area(root)): visiting a wide
+// node costs SAH_NODE primitive tests, in proportion to the node's area; a
+// leaf costs one test per primitive, in proportion to its area. For binary
+// node n and k = 1..8, dp[n][k-1] is the least cost of the subtree of n when
+// it may take up to k slots of its parent's wide node: one slot (a leaf if it
+// holds <= LEAF_MAX primitives, else a wide node of its own), or its two
+// children sharing the k slots (a subtree of <= LEAF_MAX primitives always
+// takes one slot, a leaf). split[n] byte k-1 (k >= 2) is the left
+// child's share of the best split, 0 when one slot is best; byte 0 is the
+// left share of the best split of all 8 slots, used when n is a wide node.
+// A node visit in the trace kernel is about 3.8 times a triangle test.
+constexpr float SAH_NODE = 3.8f;
+
+__device__ __forceinline__ float box_area(float4 lo, float4 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ void slot_costs(int ref, const float4* dp, const float4* plo, const float4* phi,
+                                           const uint32_t* ids, float d[8]) {
+    if (ref < 0) {  // one primitive: a leaf of one, whatever the slots
+        const uint32_t id = ids[-ref - 1];
+        const float a = box_area(plo[id], phi[id]);
+        for (int k = 0; k < 8; ++k) d[k] = a;
+    } else {
+        const float4 u = __ldcg(&dp[2 * ref]), v = __ldcg(&dp[2 * ref + 1]);
+        d[0] = u.x, d[1] = u.y, d[2] = u.z, d[3] = u.w, d[4] = v.x, d[5] = v.y, d[6] = v.z, d[7] = v.w;
+    }
+}
+
+// Bottom up, one thread per leaf: at each node the second arriving thread
+// computes it from both children (the first stops).
+__global__ void k_sah_dp(const int2* __restrict__ child, const int2* __restrict__ range,
+                         const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
+                         const float4* __restrict__ blo, const float4* __restrict__ bhi,
+                         const float4* __restrict__ plo, const float4* __restrict__ phi,
+                         const uint32_t* __restrict__ ids, int64_t N, float4* dp, uint2* split, int* arrivals,
+                         int* err) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        int node = parent_leaf[j];
+        for (int guard = 0; node >= 0; ++guard) {
+            if (guard >= (1 << 22)) {
+                atomicAdd(err, 1);
+                break;
+            }
+            __threadfence();
+            if (atomicAdd(&arrivals[node], 1) == 0) break;
+            __threadfence();
+            const int2 c = child[node];
+            float dl[8], dr[8];
+            slot_costs(c.x, dp, plo, phi, ids, dl);
+            slot_costs(c.y, dp, plo, phi, ids, dr);
+            float dsplit[9];
+            int arg[9];
+            for (int k = 2; k <= 8; ++k) {
+                float best = INFINITY;
+                int ba = 1;
+                for (int a = 1; a < k; ++a) {
+                    const float v = dl[a - 1] + dr[k - a - 1];
+                    if (v < best) {
+                        best = v;
+                        ba = a;
+                    }
+                }
+                dsplit[k] = best;
+                arg[k] = ba;
+            }
+            const float area = box_area(blo[node], bhi[node]);
+            const int2 r = range[node];
+            const int cnt = r.y - r.x + 1;
+            const float c_node = area * SAH_NODE + dsplit[8];
+            const float c_one = cnt <= LEAF_MAX ? fminf(area * (float)cnt, c_node) : c_node;
+            float d[8];
+            uint32_t bytes[8];
+            d[0] = c_one;
+            bytes[0] = (uint32_t)arg[8];
+            for (int k = 2; k <= 8; ++k) {
+                const bool sp = cnt > LEAF_MAX && dsplit[k] < c_one;  // small subtrees stay one leaf
+                d[k - 1] = sp ? dsplit[k] : c_one;
+                bytes[k - 1] = sp ? (uint32_t)arg[k] : 0u;
+            }
+            __stcg(&dp[2 * node], make_float4(d[0], d[1], d[2], d[3]));
+            __stcg(&dp[2 * node + 1], make_float4(d[4], d[5], d[6], d[7]));
+            split[node] = make_uint2(bytes[0] | bytes[1] << 8 | bytes[2] << 16 | bytes[3] << 24,
+                                     bytes[4] | bytes[5] << 8 | bytes[6] << 16 | bytes[7] << 24);
+            node = parent_int[node];
+        }
+    }
+}
+
 // ---- exclusive scan of 64-bit words: tiles of 1024, tile sums scanned recursively ----
 constexpr int SCAN_BLOCK = 256;
 constexpr int SCAN_TILE = 4 * SCAN_BLOCK;
@@ -373,7 +466,13 @@ struct BinTree {
     const float4* plo;
     const float4* phi;
     const uint32_t* sorted_ids;
+    const uint2* split;  // slot splits of the surface-area policy (k_sah_dp); nullptr: area policy
 };
+
+__device__ __forceinline__ int split_share(const uint2 s, int k) {  // k = 1..8 slots; byte 0: wide-node split
+    const uint32_t w = k <= 4 ? s.x : s.y;
+    return (int)((w >> (8 * ((k - 1) & 3))) & 0xffu);
+}
 
 __device__ __forceinline__ void ref_box(const BinTree& bt, int ref, float3& lo, float3& hi, int& first, int& last) {
     float4 l, h;
@@ -462,32 +561,59 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
     if (ref < 0) {
         m = 1;
         cref[0] = ref;
+        ref_box(bt, ref, clo[0], chi[0], cfirst[0], clast[0]);
+    } else if (bt.split) {
+        // surface-area policy: the 8 slots of this wide node are shared out by
+        // the stored splits; a subtree given k slots is one slot (k == 1, a
+        // primitive, or share 0) or passes shares a and k - a to its children
+        int sref[8], sk[8];
+        int sp = 0;
+        m = 0;
+        const int2 c = bt.child[ref];
+        const int a = split_share(bt.split[ref], 1);
+        sref[sp] = c.y, sk[sp++] = 8 - a;
+        sref[sp] = c.x, sk[sp++] = a;
+        while (sp > 0) {
+            --sp;
+            const int x = sref[sp], k = sk[sp];
+            const int share = (x < 0 || k == 1) ? 0 : split_share(bt.split[x], k);
+            if (share <= 0 || share >= k) {
+                cref[m++] = x;
+                continue;
+            }
+            const int2 cc = bt.child[x];
+            sref[sp] = cc.y, sk[sp++] = k - share;
+            sref[sp] = cc.x, sk[sp++] = share;
+        }
+        for (int q = 0; q < m; ++q) ref_box(bt, cref[q], clo[q], chi[q], cfirst[q], clast[q]);
     } else {
+        // area policy: start from the two children and repeatedly open the
+        // child of largest surface area that holds more than LEAF_MAX primitives
         const int2 c = bt.child[ref];
         cref[0] = c.x;
         cref[1] = c.y;
         m = 2;
-    }
-    for (int c = 0; c < m; ++c) ref_box(bt, cref[c], clo[c], chi[c], cfirst[c], clast[c]);
-    while (m < 8) {
-        int best = -1;
-        float best_area = -1.f;
-        for (int c = 0; c < m; ++c) {
-            if (cref[c] < 0 || clast[c] - cfirst[c] + 1 <= LEAF_MAX) continue;
-            const float dx = chi[c].x - clo[c].x, dy = chi[c].y - clo[c].y, dz = chi[c].z - clo[c].z;
-            const float area = dx * dy + dy * dz + dz * dx;
-            if (area > best_area) {
-                best_area = area;
-                best = c;
+        for (int q = 0; q < m; ++q) ref_box(bt, cref[q], clo[q], chi[q], cfirst[q], clast[q]);
+        while (m < 8) {
+            int best = -1;
+            float best_area = -1.f;
+            for (int q = 0; q < m; ++q) {
+                if (cref[q] < 0 || clast[q] - cfirst[q] + 1 <= LEAF_MAX) continue;
+                const float dx = chi[q].x - clo[q].x, dy = chi[q].y - clo[q].y, dz = chi[q].z - clo[q].z;
+                const float area = dx * dy + dy * dz + dz * dx;
+                if (area > best_area) {
+                    best_area = area;
+                    best = q;
+                }
             }
+            if (best < 0) break;
+            const int2 ch = bt.child[cref[best]];
+            cref[best] = ch.x;
+            ref_box(bt, ch.x, clo[best], chi[best], cfirst[best], clast[best]);
+            cref[m] = ch.y;
+            ref_box(bt, ch.y, clo[m], chi[m], cfirst[m], clast[m]);
+            ++m;
         }
-        if (best < 0) break;
-        const int2 ch = bt.child[cref[best]];
-        cref[best] = ch.x;
-        ref_box(bt, ch.x, clo[best], chi[best], cfirst[best], clast[best]);
-        cref[m] = ch.y;
-        ref_box(bt, ch.y, clo[m], chi[m], cfirst[m], clast[m]);
-        ++m;
     }
     // slots: greedy assignment of children to octant directions
     float3 cen;
@@ -864,6 +990,9 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     rcp_status rs = radix_sort_pairs(keys.p, vals.p, akeys.p, avals.p, N, 30, scratch.p, err.p, st);
     if (rs != RCP_OK) return rs;
     uint32_t* ids = vals.p;  // primitive ids in leaf order (Morton order, then depth-first)
+    DevBuf<float4> dp;
+    DevBuf<uint2> split;
+    DevBuf<int> arrivals;
     if (N >= 2) {
         // a sort whose look-back wait ran out leaves no valid permutation to cluster
         int sort_flag = 0;
@@ -885,6 +1014,16 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
             return pr;
         }
         ids = avals.p;
+    }
+    if (N >= 2 && sc.collapse == RCP_COLLAPSE_SAH) {
+        RCP_CUDA(dp.alloc(2 * (N - 1)));
+        RCP_CUDA(split.alloc(N - 1));
+        RCP_CUDA(arrivals.alloc(N - 1));
+        RCP_CUDA(cudaMemsetAsync(arrivals.p, 0, sizeof(int) * (N - 1), st));
+        k_sah_dp<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(child.p, range.p, parent_int.p,
+                                                                         parent_leaf.p, blo.p, bhi.p, plo.p, phi.p,
+                                                                         ids, N, dp.p, split.p, arrivals.p,
+                                                                         err.p + 1);
     }
     // scene bounds -> diameter
     uint32_t hb[12];
@@ -935,7 +1074,8 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
             return RCP_ERR_TIMEOUT;
         }
         RCP_CUDA(cudaMemsetAsync(d_max_leaf, 0, sizeof(int), st));
-        BinTree bt{child.p, range.p, blo.p, bhi.p, plo.p, phi.p, ids};
+        BinTree bt{child.p, range.p, blo.p, bhi.p, plo.p, phi.p, ids,
+                   sc.collapse == RCP_COLLAPSE_SAH ? split.p : nullptr};
         int n_front = 1;
         int64_t begin = 0;
         int2* cur = fa.p;

@@ -55,6 +55,7 @@ struct Scene {
     int64_t n_nodes = 0;
     int depth = 0;
     int max_leaf = 0;
+    int collapse = RCP_COLLAPSE_AREA;  // rcp_collapse policy of the build
     std::vector<int64_t> level_begin;
     float diam = 0.f;
     float build_ms = 0.f;

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "librcp.so")
 RCP_OK, RCP_ERR_ARG, RCP_ERR_OOM, RCP_ERR_CUDA, RCP_ERR_STACK, RCP_ERR_TIMEOUT, RCP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 RCP_LIGHT_POINT, RCP_LIGHT_DIRECTIONAL = 0, 1
 RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH, RCP_MAP_IMAGE, RCP_MAP_NORMAL = 0, 1, 2, 3, 4
+RCP_COLLAPSE_AREA, RCP_COLLAPSE_SAH = 0, 1
 
 
 class RcpError(RuntimeError):
@@ -49,7 +50,12 @@ class rcp_params(C.Structure):
 
 class rcp_scene_info(C.Structure):
     _fields_ = [("n_tris", C.c_int64), ("n_spheres", C.c_int64), ("n_nodes", C.c_int64), ("depth", C.c_int32),
-                ("max_leaf", C.c_int32), ("device_bytes", C.c_int64), ("diam", C.c_float), ("build_ms", C.c_float)]
+                ("max_leaf", C.c_int32), ("device_bytes", C.c_int64), ("diam", C.c_float), ("build_ms", C.c_float),
+                ("collapse", C.c_int32), ("reserved_", C.c_int32)]
+
+
+class rcp_build_options(C.Structure):
+    _fields_ = [("collapse", C.c_int32)]
 
 
 class rcp_tuning(C.Structure):
@@ -75,6 +81,8 @@ _lib = None
 _vp = C.c_void_p
 _SIGS = {
     "rcp_scene_create": [_vp, C.c_int64, _vp, C.c_int64, _vp, C.POINTER(rcp_light), C.POINTER(_vp)],
+    "rcp_scene_create_ex": [_vp, C.c_int64, _vp, C.c_int64, _vp, C.POINTER(rcp_light), C.POINTER(rcp_build_options),
+                            C.POINTER(_vp)],
     "rcp_scene_update_vertices": [_vp, _vp],
     "rcp_scene_update_vertices_device": [_vp, _vp, _vp],
     "rcp_scene_get_info": [_vp, C.POINTER(rcp_scene_info)],
@@ -203,6 +211,21 @@ def rcp_scene_create(tri_xyz, spheres, albedo, light: rcp_light):
     out = C.c_void_p()
     _check(lib().rcp_scene_create(_ptr(tri) if T else None, T, _ptr(sph) if S else None, S,
                                   _ptr(alb) if T + S else None, C.byref(light), C.byref(out)), "rcp_scene_create")
+    return out.value
+
+
+def rcp_scene_create_ex(tri_xyz, spheres, albedo, light: rcp_light, collapse=RCP_COLLAPSE_AREA):
+    tri = _host(tri_xyz, np.float32).reshape(-1)
+    sph = _host(spheres if spheres is not None else np.zeros(0), np.float32).reshape(-1)
+    alb = _host(albedo, np.float32).reshape(-1)
+    T, S = tri.size // 9, sph.size // 4
+    if tri.size != 9 * T or sph.size != 4 * S or alb.size != 3 * (T + S):
+        raise ValueError("tri_xyz must be T*9, spheres S*4 and albedo (T+S)*3 floats")
+    opt = rcp_build_options(int(collapse))
+    out = C.c_void_p()
+    _check(lib().rcp_scene_create_ex(_ptr(tri) if T else None, T, _ptr(sph) if S else None, S,
+                                     _ptr(alb) if T + S else None, C.byref(light), C.byref(opt), C.byref(out)),
+           "rcp_scene_create_ex")
     return out.value
 
 
@@ -384,9 +407,13 @@ def rcp_version() -> str:
 
 # ------------------------------------------------------------------ helpers
 
-def scene_from(sc):
-    """Create a library scene from a scenes.Scene."""
-    return rcp_scene_create(sc.tris, sc.spheres, sc.albedo, make_light(sc.light.type, sc.light.v, sc.light.ambient))
+def scene_from(sc, collapse=None):
+    """Create a library scene from a scenes.Scene (collapse: an RCP_COLLAPSE_*
+    build policy, None = the library default)."""
+    light = make_light(sc.light.type, sc.light.v, sc.light.ambient)
+    if collapse is None:
+        return rcp_scene_create(sc.tris, sc.spheres, sc.albedo, light)
+    return rcp_scene_create_ex(sc.tris, sc.spheres, sc.albedo, light, collapse)
 
 
 def camera_from(cam):

@@ -79,10 +79,11 @@ def _trace(g, ot, dt, any_hit, brute):
     return t.cpu().numpy(), p.cpu().numpy()
 
 
+@pytest.mark.parametrize("collapse", [rcp.RCP_COLLAPSE_AREA, rcp.RCP_COLLAPSE_SAH])
 @pytest.mark.parametrize("offset", [(0.0, 0.0, 0.0), (1e4, 0.0, 1e4), (-3e3, 50.0, 7e3)])
-def test_closest_and_any_hit_equal_brute_force(offset):
+def test_closest_and_any_hit_equal_brute_force(offset, collapse):
     sc = scenes.blocks_scene(N_GRID, offset=offset)
-    g = U.gpu_scene(sc)
+    g = U.gpu_scene(sc, collapse)
     try:
         ot, dt = _rays(offset, seed=31)
         tb, pb = _trace(g, ot, dt, 0, 1)

@@ -101,13 +101,18 @@ def _dupes():
     return sc
 
 
+COLLAPSE = [rcp.RCP_COLLAPSE_AREA, rcp.RCP_COLLAPSE_SAH]
+
+
+@pytest.mark.parametrize("collapse", COLLAPSE)
 @pytest.mark.parametrize("name", sorted(SCENES))
-def test_bvh_valid(name):
+def test_bvh_valid(name, collapse):
     sc = SCENES[name]()
-    g = U.gpu_scene(sc)
+    g = U.gpu_scene(sc, collapse)
     try:
         rcp.rcp_scene_validate(g)
         info = rcp.rcp_scene_get_info(g)
+        assert info.collapse == collapse
         assert info.n_tris == sc.n_tris and info.n_spheres == sc.n_spheres
         assert 1 <= info.max_leaf <= 3
         assert info.depth >= 1 and info.n_nodes >= 1
@@ -116,14 +121,15 @@ def test_bvh_valid(name):
         rcp.rcp_scene_destroy(g)
 
 
+@pytest.mark.parametrize("collapse", COLLAPSE)
 @pytest.mark.parametrize("name", ["tiny", "soup_10k", "soup_dupes", "three_prims", "sphere_only", "mid"])
 @pytest.mark.parametrize("any_hit", [0, 1])
-def test_bvh_equals_brute_force(name, any_hit):
+def test_bvh_equals_brute_force(name, any_hit, collapse):
     """The BVH walk returns exactly what testing every primitive returns:
     same primitive ids, bit-identical distances (the box test is conservative
     and ties go to the lower id in both)."""
     sc = SCENES[name]()
-    g = U.gpu_scene(sc)
+    g = U.gpu_scene(sc, collapse)
     try:
         ext = max(sc.diameter() / 4, 1.0)
         n = 20_000 if name != "mid" else 4_000
@@ -176,3 +182,27 @@ def test_refit_after_vertex_update():
             rcp.rcp_scene_destroy(f)
     finally:
         rcp.rcp_scene_destroy(g)
+
+
+def test_unknown_collapse_rejected():
+    sc = scenes.tiny_scene()
+    with pytest.raises(rcp.RcpError):
+        U.gpu_scene(sc, 7)
+
+
+@pytest.mark.parametrize("name", ["mid", "forest"])
+def test_collapse_policies_render_identical_images(name):
+    """Both collapse policies walk different trees over the same primitives;
+    ties go to the lower id, so the images are bit-identical."""
+    sc = scenes.mid_scene() if name == "mid" else scenes.forest_scene()
+    d = sc.diameter()
+    p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+    imgs = []
+    for collapse in COLLAPSE:
+        g = U.gpu_scene(sc, collapse)
+        try:
+            imgs.append([rcp.rcp_render(g, rcp.camera_from(sc.poses[i]), 480, 270, 6, p) for i in (3, 40)])
+        finally:
+            rcp.rcp_scene_destroy(g)
+    for a, b in zip(*imgs):
+        assert np.array_equal(a, b)
