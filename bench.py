@@ -732,6 +732,51 @@ def run_stress(args):
         rays += p_ + s_
     rcp.rcp_scene_validate(g)
     tot = sum(frame_ms) / 1000.0
+
+    # End to end, every frame's RGB delivered to host memory, the same frames:
+    # (1) one stream: sway, refit, render, copy out, frame after frame;
+    # (2) the serving path with two copies of the scene used in turn, so that
+    #     frame f's sway and refit overlap frame f-1's render and copy-out (a
+    #     copy is refitted only once the request two frames back, its last
+    #     user, is done). Three host buffers rotate (at most two in flight).
+    n = args.steps
+    frames = [args.warmup + i for i in range(n)]
+    bufs = {k: [np.zeros((H, W, 3), np.float32) for _ in range(3)] for k in ("single", "served")}
+    t0 = time.perf_counter()
+    for i, f in enumerate(frames):
+        sway(f)
+        rcp.rcp_scene_update_vertices_device(g, moved, stream)
+        torch.cuda.synchronize()  # the render runs on the library's stream
+        rcp.rcp_render(g, cams[f], W, H, K, params, bufs["single"][i % 3])
+    single_s = time.perf_counter() - t0
+    g2 = rcp.scene_from(sc, collapse)
+    copies = [g, g2]
+    budget = int(args.serve_budget_gb * (1 << 30))
+    # warm the device memory pool with one request per copy on a server of its
+    # own, so that the timed server's latency figures hold the timed frames only
+    srv = rcp.rcp_server_create(budget, args.serve_slots)
+    for j in range(2):
+        rcp.rcp_server_wait(srv, rcp.rcp_server_submit(srv, copies[j], cams[0], W, H, K, params,
+                                                       bufs["served"][j]), 600.0)
+    rcp.rcp_server_destroy(srv)
+    srv = rcp.rcp_server_create(budget, args.serve_slots)
+    tickets = []
+    t0 = time.perf_counter()
+    for i, f in enumerate(frames):
+        if i >= 2:
+            rcp.rcp_server_wait(srv, tickets[i - 2], 600.0)
+        sway(f)
+        rcp.rcp_scene_update_vertices_device(copies[i % 2], moved, stream)
+        torch.cuda.synchronize()
+        tickets.append(rcp.rcp_server_submit(srv, copies[i % 2], cams[f], W, H, K, params, bufs["served"][i % 3]))
+    for tk in tickets[-2:]:
+        rcp.rcp_server_wait(srv, tk, 600.0)
+    served_s = time.perf_counter() - t0
+    st = rcp.rcp_server_stats_get(srv)
+    rcp.rcp_server_destroy(srv)
+    same_last = bool(np.array_equal(bufs["single"][(n - 1) % 3], bufs["served"][(n - 1) % 3]))
+    rcp.rcp_scene_destroy(g2)
+    out_bytes = H * W * 3 * 4
     res = {
         "metric": "frames_per_s (3840x2160, K=8, per-frame refit)",
         "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -744,6 +789,11 @@ def run_stress(args):
                    "depth": info.depth},
         "refit_ms": statistics.mean(refit_ms), "render_ms": statistics.mean(render_ms),
         "mrays_per_s": rays / tot / 1e6, "gpu_launches_per_step": K + 2 + info.depth,
+        "e2e": {"value": n / single_s, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": out_bytes,
+                "api": "single stream: rcp_scene_update_vertices_device + rcp_render (host RGB) per frame"},
+        "served_e2e": {"value": n / served_s, "unit": "frames/s", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                       "d2h_bytes_per_step": out_bytes, "last_frame_identical_to_single_stream": same_last,
+                       "api": "rcp_server_submit (host RGB), two scene copies refitted in turn"},
     }
     rcp.rcp_scene_destroy(g)
     print(json.dumps(res), flush=True)

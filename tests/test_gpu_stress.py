@@ -38,3 +38,37 @@ def test_swaying_forest_refit_parity():
             rep.assert_ok(f"sway frame {frame}")
     finally:
         rcp.rcp_scene_destroy(g)
+
+
+def test_served_two_copy_stream_equals_single_stream():
+    """The stress workload's serving path (two copies of a swaying scene,
+    refitted in turn while the other renders) delivers the same frames as one
+    stream that refits and renders frame after frame."""
+    sc = scenes.forest_scene(40, seed=5)
+    d = sc.diameter()
+    W, H, K = 320, 180, 3
+    p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+    frames = [0, 7, 13, 29, 30]
+    g = U.gpu_scene(sc)
+    g2 = U.gpu_scene(sc)
+    srv = rcp.rcp_server_create(1 << 30, 4)
+    try:
+        single = []
+        for f in frames:
+            rcp.rcp_scene_update_vertices(g, scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, f))
+            single.append(rcp.rcp_render(g, rcp.camera_from(sc.poses[f]), W, H, K, p))
+        copies, outs, tickets = [g, g2], [np.zeros((H, W, 3), np.float32) for _ in frames], []
+        for i, f in enumerate(frames):
+            if i >= 2:
+                rcp.rcp_server_wait(srv, tickets[i - 2], 60.0)
+            rcp.rcp_scene_update_vertices(copies[i % 2], scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, f))
+            tickets.append(rcp.rcp_server_submit(srv, copies[i % 2], rcp.camera_from(sc.poses[f]), W, H, K, p,
+                                                 outs[i]))
+        for tk in tickets:
+            rcp.rcp_server_wait(srv, tk, 60.0)
+        for a, b in zip(single, outs):
+            assert np.array_equal(a, b)
+    finally:
+        rcp.rcp_server_destroy(srv)
+        rcp.rcp_scene_destroy(g2)
+        rcp.rcp_scene_destroy(g)
