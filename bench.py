@@ -10,6 +10,16 @@ L2 is flushed (a 256 MB write) between steps, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload mid|forest|batched|served|stress|imagespace]
+                    [--collapse auto|area|sah] [--tuning auto|block,chunk,fused]
+
+The other workloads print their own line: the 1.07M-triangle forest, 64
+batched forest views in one persistent launch, Poisson-arrival serving
+against the plain per-request path, the 12.57M-triangle swaying forest at 4K
+with per-frame refit (device-only, one stream and the serving path end to
+end), and the image-space gather passes. --collapse auto builds the forests'
+BVHs with the surface-area slot assignment and the terrains' with the
+largest-area rule (the faster for each, as measured); the choice is printed in
+each line's config.
 
 With N > 1 (torchrun) every rank renders its own poses (replicas, no
 collective on the data path); the time is the max over ranks.

@@ -1,6 +1,6 @@
 // radix_sort.cu -- onesweep LSD radix sort of (uint32 key, uint32 value) pairs.
 //
-// Used by the LBVH builder to order primitives by 30-bit Morton code. One
+// Used by the BVH builder to order primitives by 30-bit Morton code. One
 // histogram kernel counts all digit passes at once; then one kernel per 8-bit
 // digit ranks a tile of keys in shared memory (warp match + per-warp counters,
 // stable), finds the tile's global offset per digit by decoupled look-back over
