@@ -77,10 +77,16 @@ def collapse_for(args, workload):
 
 
 def csrc_hash():
+    """Hash of the CUDA/C++ sources with comments and whitespace removed, so
+    that a recorded ncu figure stays tied to the code it was taken on."""
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_12392_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+        src = open(os.path.join(d, f), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(f.encode() + b"\0" + " ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
