@@ -327,6 +327,62 @@ def check_flags(lp=None):
     assert f == 0 and p == 0
 
 
+def check_any_hit(lp=None):
+    """Any-hit: occluded exactly when some primitive is hit at t in the open
+    interval (t_min, t_max); a hit at t_max itself does not occlude. On random
+    rays it agrees with 'the closest hit lies before t_max'."""
+    sc = _scene(tris=GROUND, spheres=[[0, 2, 0, 1]], albedo=[[0.5] * 3] * 3, lp=lp)
+    o, d = [0.3, 10, 0.2], [0, -1, 0]
+    t_sph, p, _ = sc.trace_closest(o, d, 0.0)  # the sphere's top, at t = 10 - (2 + sqrt(1 - 0.13))
+    assert p == 2 and abs(t_sph - (8 - math.sqrt(1 - 0.13))) < 1e-12
+    occ, _ = sc.trace_any(o, d, 0.0, np.inf)
+    assert occ == 1
+    occ, f = sc.trace_any(o, d, 0.0, t_sph)  # t_max exactly at the hit: free
+    assert occ == 0 and f == 1  # ... and flagged: the hit sits on the interval's end
+    occ, _ = sc.trace_any(o, d, 0.0, t_sph * (1 + 1e-9))
+    assert occ == 1
+    occ, _ = sc.trace_any(o, d, 9.0, 9.5)  # interval past the sphere and before the ground
+    assert occ == 0
+    occ, _ = sc.trace_any(o, d, 9.0, 10.5)  # reaches the ground at t = 10
+    assert occ == 1
+    occ, _ = sc.trace_any([5, 10, 5], [0, 1, 0], 0.0, np.inf)  # upwards: nothing
+    assert occ == 0
+    occ, f = sc.trace_any([5, 10, 5], [0, -1, 0], 0.0, 10.0)  # t_max exactly at the ground: free
+    assert occ == 0 and f == 1
+    occ, _ = sc.trace_any([5, 10, 5], [0, -1, 0], 0.0, 10.0 * (1 + 1e-9))
+    assert occ == 1
+    rng = np.random.default_rng(12)
+    soup = rng.uniform(-3, 3, size=(40, 9))
+    sph = np.concatenate([rng.uniform(-3, 3, size=(5, 3)), rng.uniform(0.2, 0.8, size=(5, 1))], 1)
+    sc = _scene(tris=soup, spheres=sph, albedo=[[0.5] * 3] * 45, lp=lp)
+    n_occ = 0
+    for _ in range(3000):
+        o = rng.uniform(-5, 5, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        tmax = rng.uniform(0.5, 8.0)
+        t, p, f1 = sc.trace_closest(o, d, 1e-6)
+        occ, f2 = sc.trace_any(o, d, 1e-6, tmax)
+        if f1 or f2:
+            continue
+        assert occ == (1 if (p >= 0 and t < tmax) else 0), (o, d, tmax, t, p)
+        n_occ += occ
+    assert 200 < n_occ < 2800
+
+
+def check_scene_diam(lp=None):
+    """The scene diameter (which sets t_min and the shadow offset) is the
+    diagonal of the box around every triangle vertex and every sphere."""
+    tri = [[1, 2, 3, 4, -1, 0, 2, 2, 7]]
+    sph = [[-2, 0, 1, 0.5], [0, 5, 0, 2]]
+    sc = _scene(tris=tri, spheres=sph, albedo=[[0.5] * 3] * 3, lp=lp)
+    # per axis: the three vertices, then each sphere's centre -/+ radius
+    lo = np.array([min(1, 4, 2, -2.5, -2), min(2, -1, 2, -0.5, 3), min(3, 0, 7, 0.5, -2)])
+    hi = np.array([max(1, 4, 2, -1.5, 2), max(2, -1, 2, 0.5, 7), max(3, 0, 7, 1.5, 2)])
+    assert abs(sc.diam - float(np.linalg.norm(hi - lo))) < 1e-12
+    assert abs(_scene(tris=GROUND, albedo=[[0.5] * 3] * 2, lp=lp).diam - math.sqrt(800)) < 1e-12
+
+
 # --------------------------------------------------------------------------- passes
 
 def _tiny(lp=None):

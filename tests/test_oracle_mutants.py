@@ -58,6 +58,9 @@ MUTANTS = {
     "bilinear_no_half_shift": ("const double qx = px - 0.5, qy = py - 0.5;", "const double qx = px, qy = py;"),
     "tmin_ignored": ("if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > tmin && t < best)",
                      "if (mt_raw(s->v + 9 * i, s->n + 3 * i, o, d, &t) && t > 0.0 && t < best)"),
+    "any_hit_closed_end": ("if (t > tmin && t < tmax) {", "if (t > tmin && t <= tmax) {"),
+    "any_hit_sphere_closed_end": ("if (ts[r] > tmin && ts[r] < tmax) {", "if (ts[r] > tmin && ts[r] <= tmax) {"),
+    "diam_ignores_radius": ("if (c[a] - c[3] < lo[a]) lo[a] = c[a] - c[3];", "if (c[a] < lo[a]) lo[a] = c[a];"),
 }
 
 
