@@ -844,6 +844,24 @@ struct DevBuf {
         if (p) cudaFree(p);
     }
     cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, sizeof(T) * (n ? n : 1)); }
+    T* release() {
+        T* q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+// Two timing events, destroyed on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    cudaError_t create() {
+        cudaError_t e = cudaEventCreate(&a);
+        return e == cudaSuccess ? cudaEventCreate(&b) : e;
+    }
 };
 
 // Tile counts of each level of the recursive scan of up to n words.
@@ -939,10 +957,9 @@ rcp_status build_ploc(int64_t N, const uint32_t* ids_in, uint32_t* ids_out, cons
 rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     const int64_t T = sc.T, N = sc.T + sc.S;
     const int64_t n_nodes_cap = N > 1 ? N : 1;
-    cudaEvent_t e0, e1;
-    RCP_CUDA(cudaEventCreate(&e0));
-    RCP_CUDA(cudaEventCreate(&e1));
-    RCP_CUDA(cudaEventRecord(e0, st));
+    EventPair ev;
+    RCP_CUDA(ev.create());
+    RCP_CUDA(cudaEventRecord(ev.a, st));
     DevBuf<float4> plo, phi, blo, bhi;
     DevBuf<uint32_t> keys, vals, akeys, avals, bounds, counters;
     DevBuf<int2> child, range, fa, fb;
@@ -967,12 +984,11 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     RCP_CUDA(fb.alloc(n_nodes_cap));
     RCP_CUDA(scratch.alloc(radix_sort_scratch_bytes(N)));
     // outputs sized for the worst case, trimmed at the end
-    WNode* nodes_full = nullptr;
-    float4* nbox_full = nullptr;
-    RCP_CUDA(cudaMalloc((void**)&nodes_full, sizeof(WNode) * n_nodes_cap));
-    RCP_CUDA(cudaMalloc((void**)&nbox_full, sizeof(float4) * 2 * n_nodes_cap));
-    float4* prims = nullptr;
-    RCP_CUDA(cudaMalloc((void**)&prims, sizeof(float4) * 3 * (N ? N : 1)));
+    DevBuf<WNode> nodes_full;
+    DevBuf<float4> nbox_full, prims;
+    RCP_CUDA(nodes_full.alloc(n_nodes_cap));
+    RCP_CUDA(nbox_full.alloc(2 * n_nodes_cap));
+    RCP_CUDA(prims.alloc(3 * N));
 
     int sms = 148;
     {
@@ -1000,17 +1016,11 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         RCP_CUDA(cudaStreamSynchronize(st));
         if (sort_flag) {
             set_error("radix sort: look-back wait ran out");
-            cudaFree(nodes_full);
-            cudaFree(nbox_full);
-            cudaFree(prims);
             return RCP_ERR_TIMEOUT;
         }
         rcp_status pr = build_ploc(N, vals.p, avals.p, plo.p, phi.p, child.p, range.p, blo.p, bhi.p, parent_int.p,
                                    parent_leaf.p, err.p + 1, cap, st);
         if (pr != RCP_OK) {
-            cudaFree(nodes_full);
-            cudaFree(nbox_full);
-            cudaFree(prims);
             return pr;
         }
         ids = avals.p;
@@ -1061,16 +1071,10 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         RCP_CUDA(cudaStreamSynchronize(st));
         if (herr[1]) {
             set_error("BVH build: the clustered tree is malformed (a path to the root too long or a leaf out of range)");
-            cudaFree(nodes_full);
-            cudaFree(nbox_full);
-            cudaFree(prims);
             return RCP_ERR_STATE;
         }
         if (herr[0]) {
             set_error("radix sort: look-back wait ran out");
-            cudaFree(nodes_full);
-            cudaFree(nbox_full);
-            cudaFree(prims);
             return RCP_ERR_TIMEOUT;
         }
         RCP_CUDA(cudaMemsetAsync(d_max_leaf, 0, sizeof(int), st));
@@ -1083,16 +1087,13 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         while (n_front > 0) {
             if (depth >= 512) {
                 set_error("BVH collapse did not terminate (corrupted binary tree)");
-                cudaFree(nodes_full);
-                cudaFree(nbox_full);
-                cudaFree(prims);
                 return RCP_ERR_STATE;
             }
             level_begin.push_back(begin);
             ++depth;
             RCP_CUDA(cudaMemsetAsync(counters.p + 2, 0, sizeof(uint32_t), st));
-            k_collapse<<<(n_front + 127) / 128, 128, 0, st>>>(bt, cur, n_front, nxt, counters.p, nodes_full,
-                                                               nbox_full, prims, sc.d_tri, sc.d_sph, T, d_max_leaf);
+            k_collapse<<<(n_front + 127) / 128, 128, 0, st>>>(bt, cur, n_front, nxt, counters.p, nodes_full.p,
+                                                               nbox_full.p, prims.p, sc.d_tri, sc.d_sph, T, d_max_leaf);
             uint32_t hc[3];
             RCP_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
             RCP_CUDA(cudaStreamSynchronize(st));
@@ -1113,22 +1114,19 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     RCP_CUDA(cudaMalloc((void**)&sc.d_nodes, sizeof(WNode) * (n_nodes ? n_nodes : 1)));
     RCP_CUDA(cudaMalloc((void**)&sc.d_nbox, sizeof(float4) * 2 * (n_nodes ? n_nodes : 1)));
     if (n_nodes) {
-        RCP_CUDA(cudaMemcpyAsync(sc.d_nodes, nodes_full, sizeof(WNode) * n_nodes, cudaMemcpyDeviceToDevice, st));
-        RCP_CUDA(cudaMemcpyAsync(sc.d_nbox, nbox_full, sizeof(float4) * 2 * n_nodes, cudaMemcpyDeviceToDevice, st));
+        RCP_CUDA(cudaMemcpyAsync(sc.d_nodes, nodes_full.p, sizeof(WNode) * n_nodes, cudaMemcpyDeviceToDevice, st));
+        RCP_CUDA(cudaMemcpyAsync(sc.d_nbox, nbox_full.p, sizeof(float4) * 2 * n_nodes, cudaMemcpyDeviceToDevice,
+                                 st));
     }
-    RCP_CUDA(cudaEventRecord(e1, st));
+    RCP_CUDA(cudaEventRecord(ev.b, st));
     RCP_CUDA(cudaStreamSynchronize(st));
-    cudaFree(nodes_full);
-    cudaFree(nbox_full);
-    sc.d_prims = prims;
+    sc.d_prims = prims.release();
     sc.n_nodes = n_nodes;
     sc.depth = depth;
     sc.level_begin = level_begin;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, ev.a, ev.b);
     sc.build_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }
@@ -1136,10 +1134,9 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
 rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
     const int64_t N = sc.T + sc.S;
     if (N == 0 || sc.n_nodes == 0) return RCP_OK;
-    cudaEvent_t e0, e1;
-    RCP_CUDA(cudaEventCreate(&e0));
-    RCP_CUDA(cudaEventCreate(&e1));
-    RCP_CUDA(cudaEventRecord(e0, st));
+    EventPair ev;
+    RCP_CUDA(ev.create());
+    RCP_CUDA(cudaEventRecord(ev.a, st));
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1151,13 +1148,11 @@ rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
         k_refit_wide<<<(int)((e - b + 127) / 128), 128, 0, st>>>((WNode*)sc.d_nodes, sc.d_nbox, b, e, sc.d_prims,
                                                                   sc.d_tri, sc.d_sph, sc.T);
     }
-    RCP_CUDA(cudaEventRecord(e1, st));
-    RCP_CUDA(cudaEventSynchronize(e1));
+    RCP_CUDA(cudaEventRecord(ev.b, st));
+    RCP_CUDA(cudaEventSynchronize(ev.b));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, ev.a, ev.b);
     sc.build_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }
