@@ -730,21 +730,17 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
     float4* outs[1] = {d_out ? (float4*)d_out : ctx->img[0]};
     r = stage_views(*ctx, base, ins, outs, nullptr, st);
     if (r != RCP_OK) return r;
-    unsigned long long* d_cnt = nullptr;
-    RCP_CUDA(cudaMalloc((void**)&d_cnt, sizeof(unsigned long long) * 8));
-    RCP_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 8, st));
+    DevBuf<unsigned long long> d_cnt;
+    RCP_CUDA(d_cnt.alloc(8));
+    RCP_CUDA(cudaMemsetAsync(d_cnt.p, 0, sizeof(unsigned long long) * 8, st));
     LaunchCfg cfg = cfg_of(*sc);
     cfg.count = true;
     cfg.ms = p->spp > 0;
-    r = enqueue_passes(*sc, *ctx, cfg, d_cnt, st, false);
-    unsigned long long h[8] = {0};
-    if (r == RCP_OK) {
-        cudaError_t e = cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) r = cuda_fail(e, "rcp_count_pass");
-    }
-    cudaFree(d_cnt);
+    r = enqueue_passes(*sc, *ctx, cfg, d_cnt.p, st, false);
     if (r != RCP_OK) return r;
+    unsigned long long h[8] = {0};
+    RCP_CUDA(cudaMemcpyAsync(h, d_cnt.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RCP_CUDA(cudaStreamSynchronize(st));
     out->rays = (int64_t)h[0];
     out->primary_rays = (int64_t)h[1];
     out->shadow_rays = (int64_t)h[2];
@@ -770,22 +766,19 @@ rcp_status rcp_debug_trace(const rcp_scene* sc, int64_t n, const float* orig_tmi
         return RCP_ERR_STACK;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    int* d_status = nullptr;
-    RCP_CUDA(cudaMalloc((void**)&d_status, sizeof(int)));
-    RCP_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
-    rcp_status r = launch_debug_trace(sc->dev(), n, orig_tmin, dir_tmax, any, brute, t_out, prim_out, d_status, st);
+    DevBuf<int> d_status;
+    RCP_CUDA(d_status.alloc(1));
+    RCP_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
+    rcp_status r = launch_debug_trace(sc->dev(), n, orig_tmin, dir_tmax, any, brute, t_out, prim_out, d_status.p, st);
+    if (r != RCP_OK) return r;
     int h = 0;
-    if (r == RCP_OK) {
-        cudaError_t e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) r = cuda_fail(e, "rcp_debug_trace");
-    }
-    cudaFree(d_status);
-    if (r == RCP_OK && h) {
+    RCP_CUDA(cudaMemcpyAsync(&h, d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCP_CUDA(cudaStreamSynchronize(st));
+    if (h) {
         set_error("traversal stack overflow");
-        r = RCP_ERR_STACK;
+        return RCP_ERR_STACK;
     }
-    return r;
+    return RCP_OK;
 }
 
 rcp_status rcp_last_ray_counts(const rcp_scene* sc, int64_t* primary, int64_t* shadow) {
@@ -957,32 +950,29 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     std::lock_guard<std::mutex> lk(sc->mu);
     cudaStream_t st = lib_stream();
     const int64_t P = (int64_t)W * H;
-    float4* d_img = nullptr;
-    RCP_CUDA(cudaMalloc((void**)&d_img, sizeof(float4) * P));
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    DevBuf<float4> d_img;
+    RCP_CUDA(d_img.alloc(P));
+    EventPair ev;
+    RCP_CUDA(ev.create());
     double best_us = 1e30;
     rcp_tuning best = sc->tuning;
     const int blocks[3] = {64, 128, 256};
-    const int sms_opts[2] = {0, 0};
-    (void)sms_opts;
     for (int b : blocks)
         for (int fused = 0; fused < 2; ++fused)
             for (int chunk : {32, 64}) {
                 rcp_tuning t{b, 0, chunk, fused};
                 sc->tuning = t;
                 const float4* ins[1] = {nullptr};
-                float4* outs[1] = {d_img};
+                float4* outs[1] = {d_img.p};
                 double us = 1e30;
                 // K = 2 so the second pass reads a real image; best of 3
                 for (int rep = 0; rep < 4 && r == RCP_OK; ++rep) {
-                    cudaEventRecord(e0, st);
+                    cudaEventRecord(ev.a, st);
                     r = render_views(*sc, 1, cam, &W, &H, 2, p, ins, outs, nullptr, st);
-                    cudaEventRecord(e1, st);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) r = RCP_ERR_CUDA;
+                    cudaEventRecord(ev.b, st);
+                    if (cudaEventSynchronize(ev.b) != cudaSuccess) r = RCP_ERR_CUDA;
                     float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
+                    cudaEventElapsedTime(&ms, ev.a, ev.b);
                     if (rep > 0) us = std::min(us, 1000.0 * ms);
                 }
                 if (r != RCP_OK) break;
@@ -991,9 +981,6 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
                     best = t;
                 }
             }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(d_img);
     sc->tuning = best;
     if (r != RCP_OK) return r;
     cache[key.str()] = {(double)best.block, (double)best.blocks_per_sm, (double)best.chunk, (double)best.fused_camera,

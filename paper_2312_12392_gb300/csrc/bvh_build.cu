@@ -837,32 +837,7 @@ int grid_for(int64_t n, int block, int cap) {
     return (int)g;
 }
 
-template <class T>
-struct DevBuf {
-    T* p = nullptr;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t alloc(size_t n) { return cudaMalloc((void**)&p, sizeof(T) * (n ? n : 1)); }
-    T* release() {
-        T* q = p;
-        p = nullptr;
-        return q;
-    }
-};
 
-// Two timing events, destroyed on every return path.
-struct EventPair {
-    cudaEvent_t a = nullptr, b = nullptr;
-    ~EventPair() {
-        if (a) cudaEventDestroy(a);
-        if (b) cudaEventDestroy(b);
-    }
-    cudaError_t create() {
-        cudaError_t e = cudaEventCreate(&a);
-        return e == cudaSuccess ? cudaEventCreate(&b) : e;
-    }
-};
 
 // Tile counts of each level of the recursive scan of up to n words.
 std::vector<int64_t> scan_levels(int64_t n) {
