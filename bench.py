@@ -76,6 +76,16 @@ def collapse_for(args, workload):
     return (rcp.RCP_COLLAPSE_SAH if name == "sah" else rcp.RCP_COLLAPSE_AREA), name
 
 
+def split_for(args, workload):
+    """References per triangle at most: --split, or by scene kind ('auto'):
+    early split clipping for the static forests (long thin cone triangles),
+    none for the terrains and for the stress scene (refitted every frame,
+    which gives splitting up)."""
+    if args.split != "auto":
+        return int(args.split)
+    return 8 if workload in ("forest", "batched") else 0
+
+
 def csrc_hash():
     """Hash of the CUDA/C++ sources with comments and whitespace removed, so
     that a recorded ncu figure stays tied to the code it was taken on."""
@@ -262,8 +272,9 @@ def run_ours(args):
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
     collapse, collapse_name = collapse_for(args, args.workload)
+    split = split_for(args, args.workload)
     t0 = time.perf_counter()
-    g = rcp.scene_from(sc, collapse)
+    g = rcp.scene_from(sc, collapse, split)
     build_s = time.perf_counter() - t0
     info = rcp.rcp_scene_get_info(g)
     log(f"[rank {rank}] scene {sc.name}: {info.n_tris} tris, {info.n_nodes} nodes, depth {info.depth}, "
@@ -397,7 +408,7 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded procedural scene and walk-through)",
         "config": {"workload": desc, "l2": "flushed between steps (256 MB write, outside the timed events)",
-                   "bvh_collapse": collapse_name,
+                   "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
                    "tuning": {"block": t.block, "chunk": t.chunk, "fused_camera": t.fused_camera},
                    "parallelism": f"replicas x{world} (poses split across ranks, no collective on the data path)"},
         "mrays_per_s": rays / (tmax / 1000.0) / 1e6,
@@ -433,7 +444,8 @@ def forest_extra(args):
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
     collapse, collapse_name = collapse_for(args, "forest")
-    g = rcp.scene_from(sc, collapse)
+    split = split_for(args, "forest")
+    g = rcp.scene_from(sc, collapse, split)
     try:
         cams = [rcp.camera_from(sc.poses[i]) for i in range(16)]
         stream = torch.cuda.current_stream()
@@ -457,7 +469,8 @@ def forest_extra(args):
         info = rcp.rcp_scene_get_info(g)
         return {"workload": desc, "frames_per_s": len(cams) / tot, "mrays_per_s": rays / tot / 1e6,
                 "ms_per_frame": 1000 * tot / len(cams), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
-                "depth": info.depth, "bvh_collapse": collapse_name}
+                "depth": info.depth, "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
+                "records": info.n_records}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -532,7 +545,8 @@ def run_batched(args):
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
     collapse, collapse_name = collapse_for(args, "batched")
-    g = rcp.scene_from(sc, collapse)
+    split = split_for(args, "batched")
+    g = rcp.scene_from(sc, collapse, split)
     sizes = scenes.batched_view_sizes(64, seed=3)
     cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(len(sizes))]
     t = rcp.rcp_autotune(g, cams[0], 960, 540, params,
@@ -576,7 +590,7 @@ def run_batched(args):
         "ms_per_step": res["batched"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, graph-captured",
-                   "bvh_collapse": collapse_name,
+                   "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
                    "l2": "flushed between steps", "tuning": {"block": t.block, "chunk": t.chunk,
                                                              "fused_camera": t.fused_camera}},
         "mrays_per_s": (p_ + s_) / (res["batched"] / 1000.0) / 1e6,
@@ -884,6 +898,9 @@ def main(argv=None):
     ap.add_argument("--tuning", default="128,32,1", help="'auto' or block,chunk,fused_camera")
     ap.add_argument("--collapse", default="auto", choices=["auto", "area", "sah"],
                     help="BVH collapse policy; auto: sah for the forest workloads, area for the terrains")
+    ap.add_argument("--split", default="auto", choices=["auto"] + [str(i) for i in range(9)],
+                    help="references per triangle at most (early split clipping); auto: 8 for the static "
+                         "forests, 0 otherwise")
     ap.add_argument("--count-poses", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

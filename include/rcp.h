@@ -121,7 +121,8 @@ typedef struct {
     float diam;           /* diagonal of the scene's bounding box */
     float build_ms;       /* last BVH build (or refit) time on the device */
     int32_t collapse;     /* rcp_collapse policy the BVH was built with */
-    int32_t reserved_;
+    int32_t split_max;    /* references per triangle at most (1: no splitting) */
+    int64_t n_records;    /* leaf records (48 bytes each): one per reference */
 } rcp_scene_info;
 
 /* How the binary tree is collapsed into 8-wide nodes. The paper is silent on
@@ -137,8 +138,22 @@ typedef struct {
  *    forest), slightly slower on a terrain. */
 typedef enum { RCP_COLLAPSE_AREA = 0, RCP_COLLAPSE_SAH = 1 } rcp_collapse;
 
+/* Early split clipping (Ernst and Greiner 2007), also a choice of this
+ * library: with split_max = m >= 2, a triangle whose box's half-area exceeds
+ * 4 times its own area enters the build as up to m references. Its box is
+ * halved at the midpoint of the longest axis, the triangle is clipped to each
+ * half, and large halves are halved again. Each reference is bounded by the
+ * box of its clipped part, so long thin triangles (a cone's sides from apex
+ * to base) no longer bloat the boxes above them. Every reference's leaf
+ * record is the whole triangle: images are the same as without splitting. A
+ * refit (rcp_scene_update_vertices*) bounds every record by its whole moved
+ * triangle, which stays correct but gives the benefit up: splitting is meant
+ * for static scenes. split_max 0 or 1: no splitting. */
+#define RCP_SPLIT_MAX 8
+
 typedef struct {
-    int32_t collapse; /* rcp_collapse */
+    int32_t collapse;  /* rcp_collapse */
+    int32_t split_max; /* 0 or 1: no splitting; 2..RCP_SPLIT_MAX: references per triangle at most */
 } rcp_build_options;
 
 /* Build a scene and its BVH on the device (the scene S(n) of Eq. 1).
@@ -152,7 +167,8 @@ typedef struct {
 rcp_status rcp_scene_create(const float* tri_xyz, int64_t T, const float* spheres, int64_t S,
                             const float* albedo, const rcp_light* light, rcp_scene** out);
 /* The same with build options (NULL = the defaults of rcp_scene_create). An
- * unknown collapse policy is RCP_ERR_ARG. */
+ * unknown collapse policy or split_max outside [0, RCP_SPLIT_MAX] is
+ * RCP_ERR_ARG. */
 rcp_status rcp_scene_create_ex(const float* tri_xyz, int64_t T, const float* spheres, int64_t S,
                                const float* albedo, const rcp_light* light, const rcp_build_options* options,
                                rcp_scene** out);

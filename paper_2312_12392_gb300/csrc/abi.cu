@@ -57,7 +57,8 @@ RenderCtx::~RenderCtx() {
 
 Scene::~Scene() {
     ctx.clear();
-    for (void* p : {(void*)d_tri, (void*)d_sph, (void*)d_albedo, d_nodes, (void*)d_nbox, (void*)d_prims})
+    for (void* p : {(void*)d_tri, (void*)d_sph, (void*)d_albedo, d_nodes, (void*)d_nbox, (void*)d_prims,
+                    (void*)d_refbox})
         if (p) cudaFree(p);
 }
 
@@ -67,6 +68,7 @@ SceneDev Scene::dev() const {
     s.prims = d_prims;
     s.albedo = d_albedo;
     s.n_prims = T + S;
+    s.n_records = n_records;
     s.n_nodes = n_nodes;
     s.light = light;
     s.tmin = 1e-6f * diam;
@@ -76,7 +78,8 @@ SceneDev Scene::dev() const {
 
 int64_t Scene::device_bytes() const {
     const int64_t N = T + S;
-    return T * 36 + S * 16 + N * 16 + n_nodes * ((int64_t)sizeof(WNode) + 32) + N * 48;
+    return T * 36 + S * 16 + N * 16 + n_nodes * ((int64_t)sizeof(WNode) + 32) + n_records * 48 +
+           (d_refbox ? n_records * 32 : 0);
 }
 
 void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params& p) {
@@ -437,6 +440,10 @@ rcp_status rcp_scene_create_ex(const float* tri, int64_t T, const float* sph, in
         set_error("rcp_scene_create_ex: unknown collapse policy");
         return RCP_ERR_ARG;
     }
+    if (options && (options->split_max < 0 || options->split_max > RCP_SPLIT_MAX)) {
+        set_error("rcp_scene_create_ex: split_max outside [0, 8]");
+        return RCP_ERR_ARG;
+    }
     if (!out || !light || T < 0 || S < 0 || (T > 0 && !tri) || (S > 0 && !sph) || (T + S > 0 && !albedo)) {
         set_error("rcp_scene_create: NULL array with a nonzero count, or negative count");
         return RCP_ERR_ARG;
@@ -462,6 +469,7 @@ rcp_status rcp_scene_create_ex(const float* tri, int64_t T, const float* sph, in
     *out = nullptr;
     auto sc = std::make_unique<rcp_scene>();
     sc->collapse = options ? options->collapse : RCP_COLLAPSE_AREA;
+    sc->split_max = options && options->split_max > 1 ? options->split_max : 1;
     sc->T = T;
     sc->S = S;
     const int64_t N = T + S;
@@ -545,7 +553,8 @@ rcp_status rcp_scene_get_info(const rcp_scene* sc, rcp_scene_info* info) {
     info->diam = sc->diam;
     info->build_ms = sc->build_ms;
     info->collapse = sc->collapse;
-    info->reserved_ = 0;
+    info->split_max = sc->split_max;
+    info->n_records = sc->n_records;
     return RCP_OK;
 }
 

@@ -22,8 +22,10 @@
 //     primitives; RCP_COLLAPSE_SAH shares the slots out by a bottom-up dynamic
 //     program over the binary tree that minimises the surface-area cost. Children
 //     are placed in slots so that slot order approximates front-to-back order
-//     per ray octant; child boxes are stored as exact float32 bounds. Leaf
-//     primitives are copied into 48-byte records, contiguous per node.
+//     per ray octant; child boxes are float32 bounds with a small outward pad
+//     (tri_pad). Leaf primitives are copied into 48-byte records, contiguous
+//     per node. Optionally (split_max > 1) long thin triangles first enter
+//     as several clipped references (early split clipping, below).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -76,6 +78,51 @@ __device__ __forceinline__ void prim_box(const float* __restrict__ tri, const fl
         const float r = fabsf(s[3]);
         lo = make_float3(__fsub_rd(s[0], r), __fsub_rd(s[1], r), __fsub_rd(s[2], r));
         hi = make_float3(__fadd_ru(s[0], r), __fadd_ru(s[1], r), __fadd_ru(s[2], r));
+    }
+}
+
+// Outward pad of a triangle's stored boxes: 2^-12 of its box's extent plus
+// 2^-18 of its coordinates' magnitude. The float ray-triangle test accepts
+// hits up to a rounding error outside the true edges and vertices; a box that
+// is exact at a vertex or an edge would let the walk skip such a hit that a
+// test of every primitive accepts. The build's decisions (Morton codes,
+// clustering, collapse) use the exact boxes; the boxes stored in the tree
+// (leaf slots, and every node's box, refitted from the padded leaves) carry
+// the pad. The scene's bounds (and its diameter) are those of the exact
+// vertices.
+__device__ __forceinline__ double tri_pad(const float3& lo, const float3& hi) {
+    const double ext = ((double)hi.x - lo.x) + ((double)hi.y - lo.y) + ((double)hi.z - lo.z);
+    const double mag = fmax(fmax(fmax(fabs((double)lo.x), fabs((double)hi.x)), fmax(fabs((double)lo.y), fabs((double)hi.y))),
+                            fmax(fabs((double)lo.z), fabs((double)hi.z)));
+    return ldexp(ext, -12) + ldexp(mag, -18);
+}
+
+__device__ __forceinline__ void pad_box(double pad, float3& lo, float3& hi) {
+    lo = make_float3(__double2float_rd(lo.x - pad), __double2float_rd(lo.y - pad), __double2float_rd(lo.z - pad));
+    hi = make_float3(__double2float_ru(hi.x + pad), __double2float_ru(hi.y + pad), __double2float_ru(hi.z + pad));
+}
+
+// A primitive's stored box: a triangle's exact box padded, a sphere's box.
+__device__ __forceinline__ void ref_box_of(const float* __restrict__ tri, const float* __restrict__ sph, int64_t T,
+                                           int64_t id, float3& lo, float3& hi) {
+    prim_box(tri, sph, T, id, lo, hi);
+    if (id < T) pad_box(tri_pad(lo, hi), lo, hi);
+}
+
+// The stored (padded) box of reference `ref`: its exact box (plo/phi),
+// padded by the pad of its primitive when that is a triangle. ref_prim maps
+// references to primitives (nullptr: references are the primitives).
+__device__ __forceinline__ void padded_ref_box(const float4* plo, const float4* phi, const uint32_t* ref_prim,
+                                               const float* tri, const float* sph, int64_t T, uint32_t ref,
+                                               float3& lo, float3& hi) {
+    const float4 l = plo[ref], h = phi[ref];
+    lo = make_float3(l.x, l.y, l.z);
+    hi = make_float3(h.x, h.y, h.z);
+    const uint32_t prim = ref_prim ? ref_prim[ref] : ref;
+    if ((int64_t)prim < T) {
+        float3 tl, th;
+        prim_box(tri, sph, T, prim, tl, th);
+        pad_box(tri_pad(tl, th), lo, hi);
     }
 }
 
@@ -152,6 +199,148 @@ __global__ void k_morton_points(const float* __restrict__ xyz, int64_t n, float 
     const float lo[3] = {l0, l1, l2}, hi[3] = {h0, h1, h2};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         codes[i] = morton30(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, hi);
+}
+
+// ---- early split clipping (Ernst and Greiner 2007) ----
+// A triangle whose box is large against its own area (long thin triangles,
+// such as a cone's sides from apex to base) enters the build as several
+// references: its box is halved at the midpoint of the longest axis, the
+// triangle is clipped to each half, and the halves whose clipped part is
+// still large are halved again, up to split_max references per triangle.
+// Each reference is bounded by the box of its clipped part, rounded outwards,
+// so the references' boxes together cover the triangle (stored with the pad
+// of the whole triangle); every reference's leaf record is the whole
+// triangle, so hits are exactly those of one record.
+constexpr float SPLIT_RATIO = 4.f;  // split while box half-area > 4 x triangle area
+constexpr int SPLIT_MAX = 8;
+
+// Box of triangle v (3 vertices) clipped to [lo, hi], in double, rounded
+// outwards to float. False when the triangle misses the box.
+__device__ bool clip_triangle_box(const double (&v)[3][3], const float lo[3], const float hi[3], float3& olo,
+                                  float3& ohi) {
+    double poly[10][3], tmp[10][3];
+    int n = 3;
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) poly[i][a] = v[i][a];
+    for (int a = 0; a < 3; ++a)
+        for (int side = 0; side < 2; ++side) {
+            const double b = side ? (double)hi[a] : (double)lo[a];
+            int m = 0;
+            for (int i = 0; i < n; ++i) {
+                const double* p = poly[i];
+                const double* q = poly[(i + 1) % n];
+                const bool pin = side ? p[a] <= b : p[a] >= b;
+                const bool qin = side ? q[a] <= b : q[a] >= b;
+                if (pin) {
+                    for (int c = 0; c < 3; ++c) tmp[m][c] = p[c];
+                    ++m;
+                }
+                if (pin != qin) {
+                    const double t = (b - p[a]) / (q[a] - p[a]);
+                    for (int c = 0; c < 3; ++c) tmp[m][c] = p[c] + t * (q[c] - p[c]);
+                    tmp[m][a] = b;  // on the plane exactly
+                    ++m;
+                }
+            }
+            n = m;
+            if (n == 0) return false;
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < 3; ++c) poly[i][c] = tmp[i][c];
+        }
+    double l[3] = {poly[0][0], poly[0][1], poly[0][2]}, h[3] = {poly[0][0], poly[0][1], poly[0][2]};
+    for (int i = 1; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            l[c] = fmin(l[c], poly[i][c]);
+            h[c] = fmax(h[c], poly[i][c]);
+        }
+    olo = make_float3(__double2float_rd(l[0]), __double2float_rd(l[1]), __double2float_rd(l[2]));
+    ohi = make_float3(__double2float_ru(h[0]), __double2float_ru(h[1]), __double2float_ru(h[2]));
+    return true;
+}
+
+// The references of triangle `id` (exact boxes, in emission order); returns
+// their number. With rlo/rhi null it only counts. Counting and writing run
+// the same steps, so they agree.
+__device__ int split_triangle(const float* __restrict__ tri, uint32_t id, int max_refs, float4* __restrict__ rlo,
+                              float4* __restrict__ rhi) {
+    const float* f = tri + 9 * (int64_t)id;
+    double v[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) v[i][a] = f[3 * i + a];
+    const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+    const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+    const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                 cz = e1[0] * e2[1] - e1[1] * e2[0];
+    const double tri_area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+    float sl[SPLIT_MAX][3], sh[SPLIT_MAX][3];
+    int sp = 0, n_out = 0;
+    for (int a = 0; a < 3; ++a) {
+        sl[0][a] = fminf(fminf(f[a], f[3 + a]), f[6 + a]);
+        sh[0][a] = fmaxf(fmaxf(f[a], f[3 + a]), f[6 + a]);
+    }
+    sp = 1;
+    while (sp > 0) {
+        --sp;
+        const float l[3] = {sl[sp][0], sl[sp][1], sl[sp][2]}, h[3] = {sh[sp][0], sh[sp][1], sh[sp][2]};
+        const double dx = (double)h[0] - l[0], dy = (double)h[1] - l[1], dz = (double)h[2] - l[2];
+        const double box_area = dx * dy + dy * dz + dz * dx;
+        // a split adds at most one box to the outstanding ones: keep <= max_refs
+        if (tri_area <= 0.0 || n_out + sp + 2 > max_refs || box_area <= SPLIT_RATIO * tri_area) {
+            if (rlo) {
+                rlo[n_out] = make_float4(l[0], l[1], l[2], 0.f);
+                rhi[n_out] = make_float4(h[0], h[1], h[2], 0.f);
+            }
+            ++n_out;
+            continue;
+        }
+        const int ax = (dx >= dy && dx >= dz) ? 0 : (dy >= dz ? 1 : 2);
+        const float mid = 0.5f * (l[ax] + h[ax]);
+        const int sp0 = sp;
+        for (int half = 1; half >= 0; --half) {
+            float cl[3] = {l[0], l[1], l[2]}, ch[3] = {h[0], h[1], h[2]};
+            if (half) cl[ax] = mid;
+            else ch[ax] = mid;
+            float3 ol, oh;
+            if (clip_triangle_box(v, cl, ch, ol, oh)) {
+                sl[sp][0] = ol.x, sl[sp][1] = ol.y, sl[sp][2] = ol.z;
+                sh[sp][0] = oh.x, sh[sp][1] = oh.y, sh[sp][2] = oh.z;
+                ++sp;
+            }
+        }
+        if (sp == sp0) {  // neither half kept a part (rounding): keep the box itself
+            if (rlo) {
+                rlo[n_out] = make_float4(l[0], l[1], l[2], 0.f);
+                rhi[n_out] = make_float4(h[0], h[1], h[2], 0.f);
+            }
+            ++n_out;
+        }
+    }
+    return n_out;
+}
+
+// References per primitive (spheres: 1).
+__global__ void k_split_count(const float* __restrict__ tri, int64_t T, int64_t N, int max_refs,
+                              unsigned long long* __restrict__ counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        counts[i] = i < T ? (unsigned long long)split_triangle(tri, (uint32_t)i, max_refs, nullptr, nullptr) : 1ull;
+}
+
+// Write the references at their offsets (exclusive prefix sum of the counts).
+__global__ void k_split_write(const float* __restrict__ tri, int64_t T, int64_t N, int max_refs,
+                              const unsigned long long* __restrict__ offsets, const float4* __restrict__ plo,
+                              const float4* __restrict__ phi, float4* __restrict__ rlo, float4* __restrict__ rhi,
+                              uint32_t* __restrict__ rprim) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (int64_t)offsets[i];
+        int n = 1;
+        if (i < T) {
+            n = split_triangle(tri, (uint32_t)i, max_refs, rlo + o, rhi + o);
+        } else {
+            rlo[o] = plo[i];
+            rhi[o] = phi[i];
+        }
+        for (int k = 0; k < n; ++k) rprim[o + k] = (uint32_t)i;
+    }
 }
 
 // ---- PLOC: parallel locally-ordered clustering (Meister and Bittner, 2018) ----
@@ -415,6 +604,46 @@ __global__ void k_sah_dp(const int2* __restrict__ child, const int2* __restrict_
     }
 }
 
+// Every binary node's box again, bottom up from the padded leaf boxes (the
+// clustering decided on exact boxes): one thread per leaf, the second thread
+// to arrive at a node computes it and goes on. Leaf j (clustering order)
+// starts at parent_leaf[j]; the children's leaf references are in depth-first
+// order, whose reference indices are ids_dfs.
+__global__ void k_refit_padded(const int2* __restrict__ child, const int* __restrict__ parent_int,
+                               const int* __restrict__ parent_leaf, const uint32_t* __restrict__ ids_dfs,
+                               const float4* __restrict__ plo, const float4* __restrict__ phi,
+                               const uint32_t* __restrict__ ref_prim, const float* __restrict__ tri,
+                               const float* __restrict__ sph, int64_t T, int64_t R, float4* blo, float4* bhi,
+                               int* arrivals, int* err) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < R; j += (int64_t)gridDim.x * blockDim.x) {
+        int node = parent_leaf[j];
+        for (int guard = 0; node >= 0; ++guard) {
+            if (guard >= (1 << 22)) {
+                atomicAdd(err, 1);
+                break;
+            }
+            __threadfence();
+            if (atomicAdd(&arrivals[node], 1) == 0) break;
+            __threadfence();
+            const int2 c = child[node];
+            float3 l[2], h[2];
+            const int cs[2] = {c.x, c.y};
+            for (int q = 0; q < 2; ++q) {
+                if (cs[q] >= 0) {
+                    const float4 a = __ldcg(&blo[cs[q]]), b = __ldcg(&bhi[cs[q]]);
+                    l[q] = make_float3(a.x, a.y, a.z);
+                    h[q] = make_float3(b.x, b.y, b.z);
+                } else {
+                    padded_ref_box(plo, phi, ref_prim, tri, sph, T, ids_dfs[-cs[q] - 1], l[q], h[q]);
+                }
+            }
+            __stcg(&blo[node], make_float4(fminf(l[0].x, l[1].x), fminf(l[0].y, l[1].y), fminf(l[0].z, l[1].z), 0.f));
+            __stcg(&bhi[node], make_float4(fmaxf(h[0].x, h[1].x), fmaxf(h[0].y, h[1].y), fmaxf(h[0].z, h[1].z), 0.f));
+            node = parent_int[node];
+        }
+    }
+}
+
 // ---- exclusive scan of 64-bit words: tiles of 1024, tile sums scanned recursively ----
 constexpr int SCAN_BLOCK = 256;
 constexpr int SCAN_TILE = 4 * SCAN_BLOCK;
@@ -467,6 +696,10 @@ struct BinTree {
     const float4* phi;
     const uint32_t* sorted_ids;
     const uint2* split;  // slot splits of the surface-area policy (k_sah_dp); nullptr: area policy
+    const uint32_t* ref_prim;  // reference -> primitive (nullptr: references are the primitives)
+    const float* tri;
+    const float* sph;
+    int64_t T;
 };
 
 __device__ __forceinline__ int split_share(const uint2 s, int k) {  // k = 1..8 slots; byte 0: wide-node split
@@ -482,15 +715,13 @@ __device__ __forceinline__ void ref_box(const BinTree& bt, int ref, float3& lo, 
         const int2 r = bt.range[ref];
         first = r.x;
         last = r.y;
+        lo = make_float3(l.x, l.y, l.z);
+        hi = make_float3(h.x, h.y, h.z);
     } else {
         const int j = -ref - 1;
-        const uint32_t id = bt.sorted_ids[j];
-        l = bt.plo[id];
-        h = bt.phi[id];
+        padded_ref_box(bt.plo, bt.phi, bt.ref_prim, bt.tri, bt.sph, bt.T, bt.sorted_ids[j], lo, hi);
         first = last = j;
     }
-    lo = make_float3(l.x, l.y, l.z);
-    hi = make_float3(h.x, h.y, h.z);
 }
 
 }  // namespace
@@ -546,10 +777,11 @@ __device__ __forceinline__ void write_prim_record(float4* __restrict__ rec, cons
 namespace {
 
 // One level of the collapse. frontier[i] = (binary ref, wide node index).
+// rec_box (nullable) receives each record's exact reference box.
 __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_front, int2* __restrict__ next_front,
                            uint32_t* counters, WNode* __restrict__ nodes, float4* __restrict__ nbox,
                            float4* __restrict__ prims, const float* __restrict__ tri, const float* __restrict__ sph,
-                           int64_t T, int* max_leaf) {
+                           int64_t T, int* max_leaf, float4* __restrict__ rec_box) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_front) return;
     const int ref = frontier[i].x;
@@ -682,9 +914,15 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
         } else {
             const int cnt = clast[c] - cfirst[c] + 1;
             mb = ((uint32_t)cnt << 5) | (uint32_t)poff;
-            for (int q = 0; q < cnt; ++q)
-                write_prim_record(prims + 3 * (int64_t)(prim_base + poff + q), tri, sph, T,
-                                  bt.sorted_ids[cfirst[c] + q]);
+            for (int q = 0; q < cnt; ++q) {
+                const uint32_t ref = bt.sorted_ids[cfirst[c] + q];
+                const int64_t rec = (int64_t)(prim_base + poff + q);
+                write_prim_record(prims + 3 * rec, tri, sph, T, bt.ref_prim ? bt.ref_prim[ref] : ref);
+                if (rec_box) {
+                    rec_box[2 * rec] = bt.plo[ref];
+                    rec_box[2 * rec + 1] = bt.phi[ref];
+                }
+            }
             poff += cnt;
             leaf_max = max(leaf_max, cnt);
         }
@@ -714,7 +952,7 @@ __global__ void k_update_records(float4* __restrict__ prims, int64_t n, const fl
 __device__ __forceinline__ void record_box(const float4* __restrict__ prims, int64_t r, const float* __restrict__ tri,
                                            const float* __restrict__ sph, int64_t T, float3& lo, float3& hi) {
     const uint32_t idb = __float_as_uint(prims[3 * r + 2].y);
-    prim_box(tri, sph, T, (int64_t)(idb & ~SPHERE_BIT), lo, hi);
+    ref_box_of(tri, sph, T, (int64_t)(idb & ~SPHERE_BIT), lo, hi);
 }
 
 // Recompute the child boxes of the nodes in [begin, end) (one level, deepest
@@ -771,8 +1009,12 @@ __device__ __forceinline__ void slot_box(const WNode& nd, int s, double lo[3], d
     hi[2] = nd.hi_z[s];
 }
 
+// n_records leaf records over n_prims primitives; rec_box (nullable): each
+// record's exact reference box, which must lie in its leaf slot (else the
+// whole primitive's exact box must).
 __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, const float4* __restrict__ nbox,
-                           const float4* __restrict__ prims, int64_t n_prims, const float* __restrict__ tri,
+                           const float4* __restrict__ prims, int64_t n_records, int64_t n_prims,
+                           const float4* __restrict__ rec_box, const float* __restrict__ tri,
                            const float* __restrict__ sph, int64_t T, unsigned* __restrict__ seen_rec,
                            unsigned* __restrict__ seen_id, unsigned* __restrict__ node_refs, int* errors) {
     const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -803,15 +1045,22 @@ __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, con
             const int cnt = mb >> 5, off = mb & 31;
             for (int q = 0; q < cnt; ++q) {
                 const int64_t r = (int64_t)nd.prim_base + off + q;
-                if (r >= n_prims) {
+                if (r >= n_records) {
                     atomicAdd(&errors[3], 1);
                     continue;
                 }
                 atomicAdd(&seen_rec[r], 1u);
                 const uint32_t id = __float_as_uint(prims[3 * r + 2].y) & ~SPHERE_BIT;
                 if (id < (uint32_t)n_prims) atomicAdd(&seen_id[id], 1u);
+                else atomicAdd(&errors[6], 1);
                 float3 pl, ph;
-                prim_box(tri, sph, T, id, pl, ph);
+                if (rec_box) {
+                    const float4 l = rec_box[2 * r], h = rec_box[2 * r + 1];
+                    pl = make_float3(l.x, l.y, l.z);
+                    ph = make_float3(h.x, h.y, h.z);
+                } else {
+                    prim_box(tri, sph, T, id, pl, ph);
+                }
                 if (pl.x < lo[0] || pl.y < lo[1] || pl.z < lo[2] || ph.x > hi[0] || ph.y > hi[1] || ph.z > hi[2])
                     atomicAdd(&errors[4], 1);
             }
@@ -819,12 +1068,15 @@ __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, con
     }
 }
 
-__global__ void k_check_counts(const unsigned* a, const unsigned* b, int64_t n, const unsigned* node_refs,
-                               int64_t n_nodes, int* errors) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// every record referenced once; every primitive in exactly one record, or in
+// at least one when triangles are split into several references
+__global__ void k_check_counts(const unsigned* a, int64_t n_records, const unsigned* b, int64_t n_prims,
+                               bool split, const unsigned* node_refs, int64_t n_nodes, int* errors) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_records;
+         i += (int64_t)gridDim.x * blockDim.x)
         if (a[i] != 1u) atomicAdd(&errors[5], 1);
-        if (b[i] != 1u) atomicAdd(&errors[6], 1);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_prims; i += (int64_t)gridDim.x * blockDim.x)
+        if (split ? b[i] < 1u : b[i] != 1u) atomicAdd(&errors[6], 1);
     for (int64_t i = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_nodes;
          i += (int64_t)gridDim.x * blockDim.x)
         if (node_refs[i] != 1u) atomicAdd(&errors[7], 1);
@@ -931,40 +1183,9 @@ rcp_status build_ploc(int64_t N, const uint32_t* ids_in, uint32_t* ids_out, cons
 
 rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     const int64_t T = sc.T, N = sc.T + sc.S;
-    const int64_t n_nodes_cap = N > 1 ? N : 1;
     EventPair ev;
     RCP_CUDA(ev.create());
     RCP_CUDA(cudaEventRecord(ev.a, st));
-    DevBuf<float4> plo, phi, blo, bhi;
-    DevBuf<uint32_t> keys, vals, akeys, avals, bounds, counters;
-    DevBuf<int2> child, range, fa, fb;
-    DevBuf<int> parent_int, parent_leaf, err;
-    DevBuf<char> scratch;
-    RCP_CUDA(plo.alloc(N));
-    RCP_CUDA(phi.alloc(N));
-    RCP_CUDA(keys.alloc(N));
-    RCP_CUDA(vals.alloc(N));
-    RCP_CUDA(akeys.alloc(N));
-    RCP_CUDA(avals.alloc(N));
-    RCP_CUDA(bounds.alloc(12));
-    RCP_CUDA(counters.alloc(4));
-    RCP_CUDA(err.alloc(2));
-    RCP_CUDA(child.alloc(N));
-    RCP_CUDA(range.alloc(N));
-    RCP_CUDA(blo.alloc(N));
-    RCP_CUDA(bhi.alloc(N));
-    RCP_CUDA(parent_int.alloc(N));
-    RCP_CUDA(parent_leaf.alloc(N));
-    RCP_CUDA(fa.alloc(n_nodes_cap));
-    RCP_CUDA(fb.alloc(n_nodes_cap));
-    RCP_CUDA(scratch.alloc(radix_sort_scratch_bytes(N)));
-    // outputs sized for the worst case, trimmed at the end
-    DevBuf<WNode> nodes_full;
-    DevBuf<float4> nbox_full, prims;
-    RCP_CUDA(nodes_full.alloc(n_nodes_cap));
-    RCP_CUDA(nbox_full.alloc(2 * n_nodes_cap));
-    RCP_CUDA(prims.alloc(3 * N));
-
     int sms = 148;
     {
         int dev = 0;
@@ -972,19 +1193,87 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int cap = sms * 16;
-    RCP_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int), st));
-    RCP_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(uint32_t) * 4, st));
+    DevBuf<float4> plo, phi;
+    DevBuf<uint32_t> bounds;
+    RCP_CUDA(plo.alloc(N));
+    RCP_CUDA(phi.alloc(N));
+    RCP_CUDA(bounds.alloc(12));
     k_init_bounds<<<1, 32, 0, st>>>(bounds.p);
     k_prim_bounds<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(sc.d_tri, sc.d_sph, T, N, plo.p, phi.p,
                                                                           bounds.p);
-    k_morton<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(plo.p, phi.p, N, bounds.p, keys.p, vals.p);
-    rcp_status rs = radix_sort_pairs(keys.p, vals.p, akeys.p, avals.p, N, 30, scratch.p, err.p, st);
+    // references: the primitives themselves, or split triangles (R >= N)
+    int64_t R = N;
+    DevBuf<float4> rlo, rhi;
+    DevBuf<uint32_t> rprim;
+    const float4* ref_lo = plo.p;
+    const float4* ref_hi = phi.p;
+    const bool split = sc.split_max > 1 && T > 0;
+    if (split) {
+        DevBuf<unsigned long long> counts, aux, total;
+        const std::vector<int64_t> lv = scan_levels(N);
+        int64_t aux_n = 0;
+        for (int64_t t : lv) aux_n += t;
+        RCP_CUDA(counts.alloc(N));
+        RCP_CUDA(aux.alloc(aux_n));
+        RCP_CUDA(total.alloc(1));
+        k_split_count<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(sc.d_tri, T, N, sc.split_max,
+                                                                              counts.p);
+        scan_u64(counts.p, N, aux.p, lv, 0, total.p, st);
+        unsigned long long hr = 0;
+        RCP_CUDA(cudaMemcpyAsync(&hr, total.p, sizeof(hr), cudaMemcpyDeviceToHost, st));
+        RCP_CUDA(cudaStreamSynchronize(st));
+        R = (int64_t)hr;
+        if (R < N || R > N * (int64_t)SPLIT_MAX || R >= ((int64_t)1 << 30)) {
+            set_error("BVH build: split references out of range (at most 2^30 - 1)");
+            return RCP_ERR_ARG;
+        }
+        RCP_CUDA(rlo.alloc(R));
+        RCP_CUDA(rhi.alloc(R));
+        RCP_CUDA(rprim.alloc(R));
+        k_split_write<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(sc.d_tri, T, N, sc.split_max, counts.p,
+                                                                              plo.p, phi.p, rlo.p, rhi.p, rprim.p);
+        RCP_CUDA(cudaStreamSynchronize(st));  // counts and aux are freed on leaving this block
+        ref_lo = rlo.p;
+        ref_hi = rhi.p;
+    }
+    const int64_t n_nodes_cap = R > 1 ? R : 1;
+    DevBuf<float4> blo, bhi;
+    DevBuf<uint32_t> keys, vals, akeys, avals, counters;
+    DevBuf<int2> child, range, fa, fb;
+    DevBuf<int> parent_int, parent_leaf, err;
+    DevBuf<char> scratch;
+    RCP_CUDA(keys.alloc(R));
+    RCP_CUDA(vals.alloc(R));
+    RCP_CUDA(akeys.alloc(R));
+    RCP_CUDA(avals.alloc(R));
+    RCP_CUDA(counters.alloc(4));
+    RCP_CUDA(err.alloc(2));
+    RCP_CUDA(child.alloc(R));
+    RCP_CUDA(range.alloc(R));
+    RCP_CUDA(blo.alloc(R));
+    RCP_CUDA(bhi.alloc(R));
+    RCP_CUDA(parent_int.alloc(R));
+    RCP_CUDA(parent_leaf.alloc(R));
+    RCP_CUDA(fa.alloc(n_nodes_cap));
+    RCP_CUDA(fb.alloc(n_nodes_cap));
+    RCP_CUDA(scratch.alloc(radix_sort_scratch_bytes(R)));
+    // outputs sized for the worst case, trimmed at the end
+    DevBuf<WNode> nodes_full;
+    DevBuf<float4> nbox_full, prims, rec_box;
+    RCP_CUDA(nodes_full.alloc(n_nodes_cap));
+    RCP_CUDA(nbox_full.alloc(2 * n_nodes_cap));
+    RCP_CUDA(prims.alloc(3 * R));
+    if (split) RCP_CUDA(rec_box.alloc(2 * R));
+    RCP_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int), st));
+    RCP_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(uint32_t) * 4, st));
+    k_morton<<<grid_for(R, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(ref_lo, ref_hi, R, bounds.p, keys.p, vals.p);
+    rcp_status rs = radix_sort_pairs(keys.p, vals.p, akeys.p, avals.p, R, 30, scratch.p, err.p, st);
     if (rs != RCP_OK) return rs;
-    uint32_t* ids = vals.p;  // primitive ids in leaf order (Morton order, then depth-first)
+    uint32_t* ids = vals.p;  // reference indices in leaf order (Morton order, then depth-first)
     DevBuf<float4> dp;
-    DevBuf<uint2> split;
+    DevBuf<uint2> slot_split;
     DevBuf<int> arrivals;
-    if (N >= 2) {
+    if (R >= 2) {
         // a sort whose look-back wait ran out leaves no valid permutation to cluster
         int sort_flag = 0;
         RCP_CUDA(cudaMemcpyAsync(&sort_flag, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -993,21 +1282,28 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
             set_error("radix sort: look-back wait ran out");
             return RCP_ERR_TIMEOUT;
         }
-        rcp_status pr = build_ploc(N, vals.p, avals.p, plo.p, phi.p, child.p, range.p, blo.p, bhi.p, parent_int.p,
+        rcp_status pr = build_ploc(R, vals.p, avals.p, ref_lo, ref_hi, child.p, range.p, blo.p, bhi.p, parent_int.p,
                                    parent_leaf.p, err.p + 1, cap, st);
         if (pr != RCP_OK) {
             return pr;
         }
         ids = avals.p;
     }
-    if (N >= 2 && sc.collapse == RCP_COLLAPSE_SAH) {
-        RCP_CUDA(dp.alloc(2 * (N - 1)));
-        RCP_CUDA(split.alloc(N - 1));
-        RCP_CUDA(arrivals.alloc(N - 1));
-        RCP_CUDA(cudaMemsetAsync(arrivals.p, 0, sizeof(int) * (N - 1), st));
-        k_sah_dp<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(child.p, range.p, parent_int.p,
-                                                                         parent_leaf.p, blo.p, bhi.p, plo.p, phi.p,
-                                                                         ids, N, dp.p, split.p, arrivals.p,
+    if (R >= 2) {
+        // node boxes from the padded leaves (the clustering used exact boxes)
+        RCP_CUDA(arrivals.alloc(R - 1));
+        RCP_CUDA(cudaMemsetAsync(arrivals.p, 0, sizeof(int) * (R - 1), st));
+        k_refit_padded<<<grid_for(R, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(
+            child.p, parent_int.p, parent_leaf.p, ids, ref_lo, ref_hi, split ? rprim.p : nullptr, sc.d_tri,
+            sc.d_sph, T, R, blo.p, bhi.p, arrivals.p, err.p + 1);
+    }
+    if (R >= 2 && sc.collapse == RCP_COLLAPSE_SAH) {
+        RCP_CUDA(dp.alloc(2 * (R - 1)));
+        RCP_CUDA(slot_split.alloc(R - 1));
+        RCP_CUDA(cudaMemsetAsync(arrivals.p, 0, sizeof(int) * (R - 1), st));
+        k_sah_dp<<<grid_for(R, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(child.p, range.p, parent_int.p,
+                                                                         parent_leaf.p, blo.p, bhi.p, ref_lo, ref_hi,
+                                                                         ids, R, dp.p, slot_split.p, arrivals.p,
                                                                          err.p + 1);
     }
     // scene bounds -> diameter
@@ -1036,7 +1332,7 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     int depth = 0;
     int64_t n_nodes = 0;
     if (N > 0) {
-        int2 root = make_int2(N >= 2 ? 0 : -1, 0);
+        int2 root = make_int2(R >= 2 ? 0 : -1, 0);
         RCP_CUDA(cudaMemcpyAsync(fa.p, &root, sizeof(int2), cudaMemcpyHostToDevice, st));
         uint32_t one = 1;
         RCP_CUDA(cudaMemcpyAsync(counters.p, &one, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
@@ -1053,8 +1349,9 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
             return RCP_ERR_TIMEOUT;
         }
         RCP_CUDA(cudaMemsetAsync(d_max_leaf, 0, sizeof(int), st));
-        BinTree bt{child.p, range.p, blo.p, bhi.p, plo.p, phi.p, ids,
-                   sc.collapse == RCP_COLLAPSE_SAH ? split.p : nullptr};
+        BinTree bt{child.p, range.p, blo.p, bhi.p, ref_lo, ref_hi, ids,
+                   sc.collapse == RCP_COLLAPSE_SAH ? slot_split.p : nullptr, split ? rprim.p : nullptr, sc.d_tri,
+                   sc.d_sph, T};
         int n_front = 1;
         int64_t begin = 0;
         int2* cur = fa.p;
@@ -1068,7 +1365,8 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
             ++depth;
             RCP_CUDA(cudaMemsetAsync(counters.p + 2, 0, sizeof(uint32_t), st));
             k_collapse<<<(n_front + 127) / 128, 128, 0, st>>>(bt, cur, n_front, nxt, counters.p, nodes_full.p,
-                                                               nbox_full.p, prims.p, sc.d_tri, sc.d_sph, T, d_max_leaf);
+                                                               nbox_full.p, prims.p, sc.d_tri, sc.d_sph, T, d_max_leaf,
+                                                               rec_box.p);
             uint32_t hc[3];
             RCP_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
             RCP_CUDA(cudaStreamSynchronize(st));
@@ -1084,8 +1382,11 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     if (sc.d_nodes) cudaFree(sc.d_nodes);
     if (sc.d_nbox) cudaFree(sc.d_nbox);
     if (sc.d_prims) cudaFree(sc.d_prims);
+    if (sc.d_refbox) cudaFree(sc.d_refbox);
     sc.d_nodes = nullptr;
     sc.d_nbox = nullptr;
+    sc.d_prims = nullptr;
+    sc.d_refbox = nullptr;
     RCP_CUDA(cudaMalloc((void**)&sc.d_nodes, sizeof(WNode) * (n_nodes ? n_nodes : 1)));
     RCP_CUDA(cudaMalloc((void**)&sc.d_nbox, sizeof(float4) * 2 * (n_nodes ? n_nodes : 1)));
     if (n_nodes) {
@@ -1096,6 +1397,8 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     RCP_CUDA(cudaEventRecord(ev.b, st));
     RCP_CUDA(cudaStreamSynchronize(st));
     sc.d_prims = prims.release();
+    sc.d_refbox = rec_box.release();
+    sc.n_records = R;
     sc.n_nodes = n_nodes;
     sc.depth = depth;
     sc.level_begin = level_begin;
@@ -1109,14 +1412,21 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
 rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
     const int64_t N = sc.T + sc.S;
     if (N == 0 || sc.n_nodes == 0) return RCP_OK;
+    // a refit bounds every record by its whole (moved) primitive, which stays
+    // conservative for split references; their clipped boxes no longer apply
+    if (sc.d_refbox) {
+        RCP_CUDA(cudaStreamSynchronize(st));
+        cudaFree(sc.d_refbox);
+        sc.d_refbox = nullptr;
+    }
     EventPair ev;
     RCP_CUDA(ev.create());
     RCP_CUDA(cudaEventRecord(ev.a, st));
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_update_records<<<grid_for(N, BUILD_BLOCK, sms * 16), BUILD_BLOCK, 0, st>>>(sc.d_prims, N, sc.d_tri, sc.d_sph,
-                                                                                 sc.T);
+    k_update_records<<<grid_for(sc.n_records, BUILD_BLOCK, sms * 16), BUILD_BLOCK, 0, st>>>(
+        sc.d_prims, sc.n_records, sc.d_tri, sc.d_sph, sc.T);
     for (int l = (int)sc.level_begin.size() - 2; l >= 0; --l) {
         const int64_t b = sc.level_begin[l], e = sc.level_begin[l + 1];
         if (e <= b) continue;
@@ -1133,29 +1443,29 @@ rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
 }
 
 rcp_status validate_bvh(const Scene& sc, cudaStream_t st) {
-    const int64_t N = sc.T + sc.S;
+    const int64_t N = sc.T + sc.S, R = sc.n_records;
     if (N == 0) return RCP_OK;
     DevBuf<unsigned> seen_rec, seen_id, node_refs;
     DevBuf<int> errors;
-    RCP_CUDA(seen_rec.alloc(N));
+    RCP_CUDA(seen_rec.alloc(R));
     RCP_CUDA(seen_id.alloc(N));
     RCP_CUDA(node_refs.alloc(sc.n_nodes));
     RCP_CUDA(errors.alloc(8));
-    RCP_CUDA(cudaMemsetAsync(seen_rec.p, 0, sizeof(unsigned) * N, st));
+    RCP_CUDA(cudaMemsetAsync(seen_rec.p, 0, sizeof(unsigned) * R, st));
     RCP_CUDA(cudaMemsetAsync(seen_id.p, 0, sizeof(unsigned) * N, st));
     RCP_CUDA(cudaMemsetAsync(node_refs.p, 0, sizeof(unsigned) * sc.n_nodes, st));
     RCP_CUDA(cudaMemsetAsync(errors.p, 0, sizeof(int) * 8, st));
     k_validate<<<(int)((sc.n_nodes + 127) / 128), 128, 0, st>>>((const WNode*)sc.d_nodes, sc.n_nodes, sc.d_nbox,
-                                                                 sc.d_prims, N, sc.d_tri, sc.d_sph, sc.T,
-                                                                 seen_rec.p, seen_id.p, node_refs.p, errors.p);
-    k_check_counts<<<grid_for(std::max<int64_t>(N, sc.n_nodes), 256, 4096), 256, 0, st>>>(
-        seen_rec.p, seen_id.p, N, node_refs.p, sc.n_nodes, errors.p);
+                                                                 sc.d_prims, R, N, sc.d_refbox, sc.d_tri, sc.d_sph,
+                                                                 sc.T, seen_rec.p, seen_id.p, node_refs.p, errors.p);
+    k_check_counts<<<grid_for(std::max<int64_t>(std::max(R, N), sc.n_nodes), 256, 4096), 256, 0, st>>>(
+        seen_rec.p, R, seen_id.p, N, sc.split_max > 1, node_refs.p, sc.n_nodes, errors.p);
     int h[8];
     RCP_CUDA(cudaMemcpyAsync(h, errors.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     RCP_CUDA(cudaStreamSynchronize(st));
     static const char* what[8] = {"slot masks",       "child index order", "child box outside slot",
                                   "leaf record range", "primitive outside leaf slot",
-                                  "record not referenced exactly once", "primitive id not exactly once",
+                                  "record not referenced exactly once", "primitive id missing or repeated",
                                   "node not referenced exactly once"};
     for (int i = 0; i < 8; ++i)
         if (h[i]) {

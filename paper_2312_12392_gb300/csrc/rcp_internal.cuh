@@ -55,9 +55,10 @@ struct LightDev {
 // Device-resident scene: BVH, primitive records and shading data.
 struct SceneDev {
     const float4* nodes;   // n_nodes * NODE_ROWS
-    const float4* prims;   // n_prims * 3
+    const float4* prims;   // n_records * 3
     const float4* albedo;  // n_prims
     int64_t n_prims;
+    int64_t n_records;     // leaf records (more than n_prims when triangles are split)
     int64_t n_nodes;
     LightDev light;
     float tmin;  // 1e-6 * diameter

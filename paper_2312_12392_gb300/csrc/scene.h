@@ -51,7 +51,10 @@ struct Scene {
     float4* d_albedo = nullptr;
     void* d_nodes = nullptr;  // WNode[n_nodes]
     float4* d_nbox = nullptr;  // 2 per node: union box of the node's children
-    float4* d_prims = nullptr;  // 3 per primitive
+    float4* d_prims = nullptr;  // 3 per leaf record (n_records)
+    float4* d_refbox = nullptr;  // 2 per record: its exact clipped box in a split build (else null)
+    int64_t n_records = 0;       // leaf records: T + S, more when triangles are split
+    int split_max = 1;           // references per triangle at most (1: no splitting)
     int64_t n_nodes = 0;
     int depth = 0;
     int max_leaf = 0;

@@ -388,7 +388,7 @@ __device__ __forceinline__ Hit traverse_brute(const SceneDev& S, const RayF& r) 
     h.t = r.tmax;
     h.id = 0xffffffffu;
     h.rec = -1;
-    for (int64_t rec = 0; rec < S.n_prims; ++rec) {
+    for (int64_t rec = 0; rec < S.n_records; ++rec) {
         const float4* pp = S.prims + 3 * rec;
         const float4 w0 = __ldg(pp), w1 = __ldg(pp + 1), w2 = __ldg(pp + 2);
         const uint32_t idb = __float_as_uint(w2.y);

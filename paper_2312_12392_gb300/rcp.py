@@ -24,6 +24,7 @@ RCP_OK, RCP_ERR_ARG, RCP_ERR_OOM, RCP_ERR_CUDA, RCP_ERR_STACK, RCP_ERR_TIMEOUT, 
 RCP_LIGHT_POINT, RCP_LIGHT_DIRECTIONAL = 0, 1
 RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH, RCP_MAP_IMAGE, RCP_MAP_NORMAL = 0, 1, 2, 3, 4
 RCP_COLLAPSE_AREA, RCP_COLLAPSE_SAH = 0, 1
+RCP_SPLIT_MAX = 8
 
 
 class RcpError(RuntimeError):
@@ -51,11 +52,11 @@ class rcp_params(C.Structure):
 class rcp_scene_info(C.Structure):
     _fields_ = [("n_tris", C.c_int64), ("n_spheres", C.c_int64), ("n_nodes", C.c_int64), ("depth", C.c_int32),
                 ("max_leaf", C.c_int32), ("device_bytes", C.c_int64), ("diam", C.c_float), ("build_ms", C.c_float),
-                ("collapse", C.c_int32), ("reserved_", C.c_int32)]
+                ("collapse", C.c_int32), ("split_max", C.c_int32), ("n_records", C.c_int64)]
 
 
 class rcp_build_options(C.Structure):
-    _fields_ = [("collapse", C.c_int32)]
+    _fields_ = [("collapse", C.c_int32), ("split_max", C.c_int32)]
 
 
 class rcp_tuning(C.Structure):
@@ -214,14 +215,14 @@ def rcp_scene_create(tri_xyz, spheres, albedo, light: rcp_light):
     return out.value
 
 
-def rcp_scene_create_ex(tri_xyz, spheres, albedo, light: rcp_light, collapse=RCP_COLLAPSE_AREA):
+def rcp_scene_create_ex(tri_xyz, spheres, albedo, light: rcp_light, collapse=RCP_COLLAPSE_AREA, split_max=0):
     tri = _host(tri_xyz, np.float32).reshape(-1)
     sph = _host(spheres if spheres is not None else np.zeros(0), np.float32).reshape(-1)
     alb = _host(albedo, np.float32).reshape(-1)
     T, S = tri.size // 9, sph.size // 4
     if tri.size != 9 * T or sph.size != 4 * S or alb.size != 3 * (T + S):
         raise ValueError("tri_xyz must be T*9, spheres S*4 and albedo (T+S)*3 floats")
-    opt = rcp_build_options(int(collapse))
+    opt = rcp_build_options(int(collapse), int(split_max))
     out = C.c_void_p()
     _check(lib().rcp_scene_create_ex(_ptr(tri) if T else None, T, _ptr(sph) if S else None, S,
                                      _ptr(alb) if T + S else None, C.byref(light), C.byref(opt), C.byref(out)),
@@ -407,13 +408,15 @@ def rcp_version() -> str:
 
 # ------------------------------------------------------------------ helpers
 
-def scene_from(sc, collapse=None):
+def scene_from(sc, collapse=None, split_max=0):
     """Create a library scene from a scenes.Scene (collapse: an RCP_COLLAPSE_*
-    build policy, None = the library default)."""
+    build policy, None = the library default; split_max: references per
+    triangle at most, 0 or 1 = no splitting)."""
     light = make_light(sc.light.type, sc.light.v, sc.light.ambient)
-    if collapse is None:
+    if collapse is None and split_max <= 1:
         return rcp_scene_create(sc.tris, sc.spheres, sc.albedo, light)
-    return rcp_scene_create_ex(sc.tris, sc.spheres, sc.albedo, light, collapse)
+    return rcp_scene_create_ex(sc.tris, sc.spheres, sc.albedo, light,
+                               RCP_COLLAPSE_AREA if collapse is None else collapse, split_max)
 
 
 def camera_from(cam):

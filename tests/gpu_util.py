@@ -38,8 +38,8 @@ def oracle_scene(sc: scenes.Scene) -> O.OracleScene:
     return O.OracleScene(sc.tris, sc.spheres, sc.albedo, sc.light.type, lv, f32(sc.light.ambient))
 
 
-def gpu_scene(sc: scenes.Scene, collapse=None):
-    return rcp.scene_from(sc, collapse)
+def gpu_scene(sc: scenes.Scene, collapse=None, split_max=0):
+    return rcp.scene_from(sc, collapse, split_max)
 
 
 def psnr(a, b):

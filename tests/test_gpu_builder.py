@@ -102,17 +102,23 @@ def _dupes():
 
 
 COLLAPSE = [rcp.RCP_COLLAPSE_AREA, rcp.RCP_COLLAPSE_SAH]
+# (collapse policy, references per triangle at most)
+BUILDS = [(rcp.RCP_COLLAPSE_AREA, 0), (rcp.RCP_COLLAPSE_SAH, 0), (rcp.RCP_COLLAPSE_SAH, 8), (rcp.RCP_COLLAPSE_AREA, 4)]
 
 
-@pytest.mark.parametrize("collapse", COLLAPSE)
+@pytest.mark.parametrize("build", BUILDS, ids=lambda b: f"c{b[0]}s{b[1]}")
 @pytest.mark.parametrize("name", sorted(SCENES))
-def test_bvh_valid(name, collapse):
+def test_bvh_valid(name, build):
+    collapse, split = build
     sc = SCENES[name]()
-    g = U.gpu_scene(sc, collapse)
+    g = U.gpu_scene(sc, collapse, split)
     try:
         rcp.rcp_scene_validate(g)
         info = rcp.rcp_scene_get_info(g)
-        assert info.collapse == collapse
+        assert info.collapse == collapse and info.split_max == max(split, 1)
+        assert sc.n_prims <= info.n_records <= sc.n_prims * max(split, 1)
+        if split <= 1:
+            assert info.n_records == sc.n_prims
         assert info.n_tris == sc.n_tris and info.n_spheres == sc.n_spheres
         assert 1 <= info.max_leaf <= 3
         assert info.depth >= 1 and info.n_nodes >= 1
@@ -121,15 +127,16 @@ def test_bvh_valid(name, collapse):
         rcp.rcp_scene_destroy(g)
 
 
-@pytest.mark.parametrize("collapse", COLLAPSE)
+@pytest.mark.parametrize("build", BUILDS, ids=lambda b: f"c{b[0]}s{b[1]}")
 @pytest.mark.parametrize("name", ["tiny", "soup_10k", "soup_dupes", "three_prims", "sphere_only", "mid"])
 @pytest.mark.parametrize("any_hit", [0, 1])
-def test_bvh_equals_brute_force(name, any_hit, collapse):
+def test_bvh_equals_brute_force(name, any_hit, build):
+    collapse, split = build
     """The BVH walk returns exactly what testing every primitive returns:
     same primitive ids, bit-identical distances (the box test is conservative
     and ties go to the lower id in both)."""
     sc = SCENES[name]()
-    g = U.gpu_scene(sc, collapse)
+    g = U.gpu_scene(sc, collapse, split)
     try:
         ext = max(sc.diameter() / 4, 1.0)
         n = 20_000 if name != "mid" else 4_000
@@ -188,21 +195,95 @@ def test_unknown_collapse_rejected():
     sc = scenes.tiny_scene()
     with pytest.raises(rcp.RcpError):
         U.gpu_scene(sc, 7)
+    for bad in (-1, rcp.RCP_SPLIT_MAX + 1):
+        with pytest.raises(rcp.RcpError):
+            U.gpu_scene(sc, rcp.RCP_COLLAPSE_AREA, bad)
+
+
+def _cone_rays(sc, n, seed):
+    """Rays aimed at the forest's triangle vertices (cone apexes included) and
+    at points on their edges, from random points around them."""
+    rng = np.random.default_rng(seed)
+    v = sc.tris.reshape(-1, 3, 3).astype(np.float64)
+    pick = rng.integers(0, len(v), n)
+    a, b = rng.integers(0, 3, n), rng.integers(0, 3, n)
+    w = rng.choice([0.0, 0.5, 0.25, 1.0], n)[:, None]
+    target = (1 - w) * v[pick, a] + w * v[pick, b]
+    src = target + rng.normal(size=(n, 3)) * 20.0
+    d = target - src
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    ot = np.zeros((n, 4), np.float32)
+    dt = np.zeros((n, 4), np.float32)
+    ot[:, :3] = src
+    dt[:, :3] = d
+    dt[:, 3] = np.inf
+    return ot, dt
+
+
+def _walk_and_brute(g, ot, dt, any_hit):
+    res = []
+    for brute in (0, 1):
+        t = torch.empty(len(ot), dtype=torch.float32, device="cuda")
+        p = torch.empty(len(ot), dtype=torch.int32, device="cuda")
+        rcp.rcp_debug_trace(g, len(ot), _dev(ot), _dev(dt), any_hit, brute, t, p)
+        res.append((t.cpu().numpy(), p.cpu().numpy()))
+    return res
+
+
+@pytest.mark.parametrize("split", [0, 4, 8])
+def test_split_references_equal_brute_force(split):
+    """Triangles split into clipped references (and unsplit trees): the walk
+    returns exactly what testing every primitive returns, also on rays aimed
+    at vertices (the cone apexes, where all split pieces meet, and where two
+    triangles tie at equal t) and at edges."""
+    sc = scenes.forest_scene(60, seed=3)
+    g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, split)
+    try:
+        info = rcp.rcp_scene_get_info(g)
+        if split > 1:
+            assert info.n_records > 1.3 * sc.n_prims  # the cones' sides are split
+        rcp.rcp_scene_validate(g)
+        ot, dt = _cone_rays(sc, 30_000, seed=4 + split)
+        for any_hit in (0, 1):
+            (tw, pw), (tb, pb) = _walk_and_brute(g, ot, dt, any_hit)
+            assert np.array_equal(pw, pb), (any_hit, int((pw != pb).sum()))
+            if not any_hit:
+                assert np.array_equal(tw.view(np.uint32), tb.view(np.uint32))
+                assert (pb >= 0).mean() > 0.5
+    finally:
+        rcp.rcp_scene_destroy(g)
+
+
+def test_split_scene_refit_stays_exact():
+    sc = scenes.forest_scene(40, seed=5)
+    g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
+    try:
+        moved = scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, 37)
+        rcp.rcp_scene_update_vertices(g, moved)
+        rcp.rcp_scene_validate(g)
+        msc = scenes.Scene("moved", moved, sc.spheres, sc.albedo, sc.light, sc.poses)
+        ot, dt = _cone_rays(msc, 20_000, seed=11)
+        (tw, pw), (tb, pb) = _walk_and_brute(g, ot, dt, 0)
+        assert np.array_equal(pw, pb) and np.array_equal(tw, tb)
+    finally:
+        rcp.rcp_scene_destroy(g)
 
 
 @pytest.mark.parametrize("name", ["mid", "forest"])
 def test_collapse_policies_render_identical_images(name):
-    """Both collapse policies walk different trees over the same primitives;
-    ties go to the lower id, so the images are bit-identical."""
+    """The collapse policies and triangle splitting walk different trees over
+    the same primitives; ties go to the lower id, so the images are
+    bit-identical."""
     sc = scenes.mid_scene() if name == "mid" else scenes.forest_scene()
     d = sc.diameter()
     p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
     imgs = []
-    for collapse in COLLAPSE:
-        g = U.gpu_scene(sc, collapse)
+    for collapse, split in [(rcp.RCP_COLLAPSE_AREA, 0), (rcp.RCP_COLLAPSE_SAH, 0), (rcp.RCP_COLLAPSE_SAH, 8)]:
+        g = U.gpu_scene(sc, collapse, split)
         try:
             imgs.append([rcp.rcp_render(g, rcp.camera_from(sc.poses[i]), 480, 270, 6, p) for i in (3, 40)])
         finally:
             rcp.rcp_scene_destroy(g)
-    for a, b in zip(*imgs):
-        assert np.array_equal(a, b)
+    for other in imgs[1:]:
+        for a, b in zip(imgs[0], other):
+            assert np.array_equal(a, b)
