@@ -78,12 +78,12 @@ def collapse_for(args, workload):
 
 def split_for(args, workload):
     """References per triangle at most: --split, or by scene kind ('auto'):
-    early split clipping for the static forests (long thin cone triangles),
-    none for the terrains and for the stress scene (refitted every frame,
-    which gives splitting up)."""
+    early split clipping for the forests (long thin cone triangles; the stress
+    forest's refits keep each reference bounded by its part of the moved
+    triangle), none for the terrains."""
     if args.split != "auto":
         return int(args.split)
-    return 8 if workload in ("forest", "batched") else 0
+    return 8 if workload in FOREST_WORKLOADS else 0
 
 
 def csrc_hash():
@@ -724,7 +724,8 @@ def run_stress(args):
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
     collapse, collapse_name = collapse_for(args, "stress")
-    g = rcp.scene_from(sc, collapse)
+    split = split_for(args, "stress")
+    g = rcp.scene_from(sc, collapse, split)
     info = rcp.rcp_scene_get_info(g)
     base = torch.from_numpy(sc.tris).cuda().reshape(-1, 3, 3)
     amp = torch.from_numpy(sc.sway_amp).cuda()
@@ -779,7 +780,7 @@ def run_stress(args):
         torch.cuda.synchronize()  # the render runs on the library's stream
         rcp.rcp_render(g, cams[f], W, H, K, params, bufs["single"][i % 3])
     single_s = time.perf_counter() - t0
-    g2 = rcp.scene_from(sc, collapse)
+    g2 = rcp.scene_from(sc, collapse, split)
     copies = [g, g2]
     budget = int(args.serve_budget_gb * (1 << 30))
     # warm the device memory pool with one request per copy on a server of its
@@ -812,7 +813,7 @@ def run_stress(args):
         "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"bvh_collapse": collapse_name,
+        "config": {"bvh_collapse": collapse_name, "bvh_split_max": split, "records": info.n_records,
                    "workload": f"stress: {info.n_tris:,} tris (25,000 swaying cone trees), 3840x2160, K=8, "
                                "wind sway A=0.02*h_tree at 0.5 Hz, refit every frame",
                    "scene_generation_s": gen_s, "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,

@@ -25,7 +25,9 @@
 //     per ray octant; child boxes are float32 bounds with a small outward pad
 //     (tri_pad). Leaf primitives are copied into 48-byte records, contiguous
 //     per node. Optionally (split_max > 1) long thin triangles first enter
-//     as several clipped references (early split clipping, below).
+//     as several clipped references (early split clipping, below); each keeps
+//     its part of the triangle, so that a refit after a vertex update bounds
+//     it by that part of the moved triangle.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -90,23 +92,19 @@ __device__ __forceinline__ void prim_box(const float* __restrict__ tri, const fl
 // (leaf slots, and every node's box, refitted from the padded leaves) carry
 // the pad. The scene's bounds (and its diameter) are those of the exact
 // vertices.
-__device__ __forceinline__ double tri_pad(const float3& lo, const float3& hi) {
-    const double ext = ((double)hi.x - lo.x) + ((double)hi.y - lo.y) + ((double)hi.z - lo.z);
-    const double mag = fmax(fmax(fmax(fabs((double)lo.x), fabs((double)hi.x)), fmax(fabs((double)lo.y), fabs((double)hi.y))),
-                            fmax(fabs((double)lo.z), fabs((double)hi.z)));
-    return ldexp(ext, -12) + ldexp(mag, -18);
+// Float arithmetic rounded upwards (the pad) and outwards (the padded box):
+// refits run it for every record of every frame, and double arithmetic is
+// slow on this GPU.
+__device__ __forceinline__ float tri_pad(const float3& lo, const float3& hi) {
+    const float ext = __fadd_ru(__fadd_ru(__fsub_ru(hi.x, lo.x), __fsub_ru(hi.y, lo.y)), __fsub_ru(hi.z, lo.z));
+    const float mag = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y))),
+                            fmaxf(fabsf(lo.z), fabsf(hi.z)));
+    return __fadd_ru(__fmul_ru(ext, 0x1p-12f), __fmul_ru(mag, 0x1p-18f));
 }
 
-__device__ __forceinline__ void pad_box(double pad, float3& lo, float3& hi) {
-    lo = make_float3(__double2float_rd(lo.x - pad), __double2float_rd(lo.y - pad), __double2float_rd(lo.z - pad));
-    hi = make_float3(__double2float_ru(hi.x + pad), __double2float_ru(hi.y + pad), __double2float_ru(hi.z + pad));
-}
-
-// A primitive's stored box: a triangle's exact box padded, a sphere's box.
-__device__ __forceinline__ void ref_box_of(const float* __restrict__ tri, const float* __restrict__ sph, int64_t T,
-                                           int64_t id, float3& lo, float3& hi) {
-    prim_box(tri, sph, T, id, lo, hi);
-    if (id < T) pad_box(tri_pad(lo, hi), lo, hi);
+__device__ __forceinline__ void pad_box(float pad, float3& lo, float3& hi) {
+    lo = make_float3(__fsub_rd(lo.x, pad), __fsub_rd(lo.y, pad), __fsub_rd(lo.z, pad));
+    hi = make_float3(__fadd_ru(hi.x, pad), __fadd_ru(hi.y, pad), __fadd_ru(hi.z, pad));
 }
 
 // The stored (padded) box of reference `ref`: its exact box (plo/phi),
@@ -340,6 +338,83 @@ __global__ void k_split_write(const float* __restrict__ tri, int64_t T, int64_t 
             rhi[o] = phi[i];
         }
         for (int k = 0; k < n; ++k) rprim[o + k] = (uint32_t)i;
+    }
+}
+
+// ---- parts of split references, for refits ----
+// A reference of a split triangle stands for the part of the triangle inside
+// its box. That part is kept as a convex polygon in the triangle's own
+// coordinates (u, v), with p = v0 + u (v1 - v0) + v (v2 - v0). Every point of
+// the triangle moves with its (u, v) when the vertices change, so a refit
+// maps the polygon through the moved vertices and bounds the reference by
+// exactly its part of the moved triangle; the parts of a triangle still cover
+// it, whatever the motion.
+constexpr int PART_MAX = 9;  // a triangle clipped by the 6 planes of a box has <= 9 vertices
+
+// The part of triangle v inside [lo, hi] (Sutherland-Hodgman in double, the
+// vertices carrying their (u, v)); returns the vertex count (0: no area left).
+__device__ int clip_triangle_uv(const double (&v)[3][3], const float lo[3], const float hi[3],
+                                float2* __restrict__ out) {
+    double poly[PART_MAX + 1][5], tmp[PART_MAX + 1][5];
+    for (int i = 0; i < 3; ++i) {
+        for (int a = 0; a < 3; ++a) poly[i][a] = v[i][a];
+        poly[i][3] = i == 1 ? 1.0 : 0.0;
+        poly[i][4] = i == 2 ? 1.0 : 0.0;
+    }
+    int n = 3;
+    for (int a = 0; a < 3; ++a)
+        for (int side = 0; side < 2; ++side) {
+            const double b = side ? (double)hi[a] : (double)lo[a];
+            int m = 0;
+            for (int i = 0; i < n; ++i) {
+                const double* p = poly[i];
+                const double* q = poly[(i + 1) % n];
+                const bool pin = side ? p[a] <= b : p[a] >= b;
+                const bool qin = side ? q[a] <= b : q[a] >= b;
+                if (pin) {
+                    for (int c = 0; c < 5; ++c) tmp[m][c] = p[c];
+                    ++m;
+                }
+                if (pin != qin) {
+                    const double t = (b - p[a]) / (q[a] - p[a]);
+                    for (int c = 0; c < 5; ++c) tmp[m][c] = p[c] + t * (q[c] - p[c]);
+                    tmp[m][a] = b;
+                    ++m;
+                }
+            }
+            n = m;
+            if (n < 3) return 0;
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < 5; ++c) poly[i][c] = tmp[i][c];
+        }
+    for (int i = 0; i < n; ++i) out[i] = make_float2((float)poly[i][3], (float)poly[i][4]);
+    return n;
+}
+
+// The part of every record of a split build: part_n[r] vertices at
+// part_uv[PART_MAX r ...]. A record whose reference box holds its whole
+// triangle, a sphere, and a part that clipping left without area (which a
+// refit then bounds by the whole moved triangle) get 0.
+__global__ void k_record_parts(const float4* __restrict__ prims, int64_t R, const float4* __restrict__ rec_box,
+                               const float* __restrict__ tri, int64_t T, float2* __restrict__ part_uv,
+                               uint8_t* __restrict__ part_n) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t idb = __float_as_uint(prims[3 * r + 2].y);
+        int n = 0;
+        if (!(idb & SPHERE_BIT) && (int64_t)idb < T) {
+            float3 tl, th;
+            prim_box(tri, nullptr, T, idb, tl, th);
+            const float4 l = rec_box[2 * r], h = rec_box[2 * r + 1];
+            if (l.x > tl.x || l.y > tl.y || l.z > tl.z || h.x < th.x || h.y < th.y || h.z < th.z) {
+                const float* f = tri + 9 * (int64_t)idb;
+                double v[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int a = 0; a < 3; ++a) v[i][a] = f[3 * i + a];
+                const float lo[3] = {l.x, l.y, l.z}, hi[3] = {h.x, h.y, h.z};
+                n = clip_triangle_uv(v, lo, hi, part_uv + PART_MAX * r);
+            }
+        }
+        part_n[r] = (uint8_t)n;
     }
 }
 
@@ -756,13 +831,25 @@ __device__ __forceinline__ void write_prim_record(float4* __restrict__ rec, cons
         const float* v = tri + 9 * (int64_t)id;
         float e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
         float e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
-        // exact double cross product of the float edges: zero only for degenerate triangles
-        const double d1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
-        const double d2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
-        const double nx = d1[1] * d2[2] - d1[2] * d2[1], ny = d1[2] * d2[0] - d1[0] * d2[2],
-                     nz = d1[0] * d2[1] - d1[1] * d2[0];
-        if (nx == 0.0 && ny == 0.0 && nz == 0.0)
-            for (int a = 0; a < 3; ++a) e1[a] = e2[a] = 0.f;  // never hit (det == 0)
+        // Degenerate (collinear) triangles are never hit (det == 0). The float
+        // cross product of the rounded edges is within 8 * 2^-24 * M1 * M2 (+
+        // 2^-24 of itself) of the exact one (M: largest edge component), so a
+        // component above 2^-19 M1 M2 proves the triangle has area; only the
+        // rest take the exact test, the double cross product of the exact
+        // edge differences.
+        const float m1 = fmaxf(fmaxf(fabsf(e1[0]), fabsf(e1[1])), fabsf(e1[2]));
+        const float m2 = fmaxf(fmaxf(fabsf(e2[0]), fabsf(e2[1])), fabsf(e2[2]));
+        const float fx = e1[1] * e2[2] - e1[2] * e2[1], fy = e1[2] * e2[0] - e1[0] * e2[2],
+                    fz = e1[0] * e2[1] - e1[1] * e2[0];
+        const float thr = 0x1p-19f * m1 * m2;
+        if (!(fmaxf(fmaxf(fabsf(fx), fabsf(fy)), fabsf(fz)) > thr && thr > 0.f)) {
+            const double d1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+            const double d2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
+            const double nx = d1[1] * d2[2] - d1[2] * d2[1], ny = d1[2] * d2[0] - d1[0] * d2[2],
+                         nz = d1[0] * d2[1] - d1[1] * d2[0];
+            if (nx == 0.0 && ny == 0.0 && nz == 0.0)
+                for (int a = 0; a < 3; ++a) e1[a] = e2[a] = 0.f;
+        }
         rec[0] = make_float4(v[0], v[1], v[2], e1[0]);
         rec[1] = make_float4(e1[1], e1[2], e2[0], e2[1]);
         rec[2] = make_float4(e2[2], __uint_as_float(id), 0.f, 0.f);
@@ -940,26 +1027,66 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
 
 // ---------------------------------------------------------------- refit after a vertex update
 
-__global__ void k_update_records(float4* __restrict__ prims, int64_t n, const float* __restrict__ tri,
-                                 const float* __restrict__ sph, int64_t T) {
+// Leaf records' parts in a split build (both null otherwise).
+struct Parts {
+    const float2* uv;
+    const uint8_t* n;
+};
+
+// Box of record r (primitive id with its sphere flag: idb) from the current
+// vertices: its part of the moved triangle when it has one (clamped to the
+// whole triangle's box, which holds the part), else its whole primitive's
+// box. Padded with the triangle's pad when `pad`.
+__device__ __forceinline__ void record_box(uint32_t idb, int64_t r, Parts parts, const float* __restrict__ tri,
+                                           const float* __restrict__ sph, int64_t T, bool pad, float3& lo,
+                                           float3& hi) {
+    const int64_t id = (int64_t)(idb & ~SPHERE_BIT);
+    float3 tl, th;
+    prim_box(tri, sph, T, id, tl, th);
+    lo = tl;
+    hi = th;
+    const int n = parts.n ? parts.n[r] : 0;
+    if (n && id < T) {
+        const float* f = tri + 9 * id;
+        const float3 a = make_float3(f[0], f[1], f[2]);
+        const float3 e1 = make_float3(f[3] - f[0], f[4] - f[1], f[5] - f[2]);
+        const float3 e2 = make_float3(f[6] - f[0], f[7] - f[1], f[8] - f[2]);
+        float3 l = make_float3(INFINITY, INFINITY, INFINITY), h = make_float3(-INFINITY, -INFINITY, -INFINITY);
+        for (int k = 0; k < n; ++k) {
+            const float2 uv = parts.uv[PART_MAX * r + k];
+            const float3 p = make_float3(fmaf(uv.y, e2.x, fmaf(uv.x, e1.x, a.x)), fmaf(uv.y, e2.y, fmaf(uv.x, e1.y, a.y)),
+                                         fmaf(uv.y, e2.z, fmaf(uv.x, e1.z, a.z)));
+            l = make_float3(fminf(l.x, p.x), fminf(l.y, p.y), fminf(l.z, p.z));
+            h = make_float3(fmaxf(h.x, p.x), fmaxf(h.y, p.y), fmaxf(h.z, p.z));
+        }
+        lo = make_float3(fmaxf(lo.x, l.x), fmaxf(lo.y, l.y), fmaxf(lo.z, l.z));
+        hi = make_float3(fminf(hi.x, h.x), fminf(hi.y, h.y), fminf(hi.z, h.z));
+    }
+    // the rounding of the stored (u, v) and of the mapping is ~2^-22 of the
+    // triangle's extent, far inside the pad of the whole triangle
+    if (pad && id < T) pad_box(tri_pad(tl, th), lo, hi);
+}
+
+// First step of a refit, one thread per record: the record rewritten from the
+// moved vertices (spheres do not move) and its padded box (rbox, 2 per
+// record), which k_refit_wide gathers into the leaf slots.
+__global__ void k_refit_records(float4* __restrict__ prims, int64_t n, Parts parts, const float* __restrict__ tri,
+                                const float* __restrict__ sph, int64_t T, float4* __restrict__ rbox) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t idb = __float_as_uint(prims[3 * r + 2].y);
-        if (idb & SPHERE_BIT) continue;
-        write_prim_record(prims + 3 * r, tri, sph, T, idb);
+        if (!(idb & SPHERE_BIT)) write_prim_record(prims + 3 * r, tri, sph, T, idb);
+        float3 lo, hi;
+        record_box(idb, r, parts, tri, sph, T, true, lo, hi);
+        rbox[2 * r] = make_float4(lo.x, lo.y, lo.z, 0.f);
+        rbox[2 * r + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
     }
 }
 
-__device__ __forceinline__ void record_box(const float4* __restrict__ prims, int64_t r, const float* __restrict__ tri,
-                                           const float* __restrict__ sph, int64_t T, float3& lo, float3& hi) {
-    const uint32_t idb = __float_as_uint(prims[3 * r + 2].y);
-    ref_box_of(tri, sph, T, (int64_t)(idb & ~SPHERE_BIT), lo, hi);
-}
-
 // Recompute the child boxes of the nodes in [begin, end) (one level, deepest
-// first) from their leaves' primitives and their internal children's boxes.
+// first) from their leaf records' boxes (rbox) and their internal children's
+// boxes.
 __global__ void k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbox, int64_t begin, int64_t end,
-                             const float4* __restrict__ prims, const float* __restrict__ tri,
-                             const float* __restrict__ sph, int64_t T) {
+                             const float4* __restrict__ rbox) {
     const int64_t w = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (w >= end) return;
     WNode nd = nodes[w];
@@ -978,10 +1105,11 @@ __global__ void k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbo
             hi = make_float3(h.x, h.y, h.z);
         } else {
             const int cnt = mb >> 5, off = mb & 31;
-            record_box(prims, nd.prim_base + off, tri, sph, T, lo, hi);
+            const float4* b = rbox + 2 * ((int64_t)nd.prim_base + off);
+            lo = make_float3(b[0].x, b[0].y, b[0].z);
+            hi = make_float3(b[1].x, b[1].y, b[1].z);
             for (int q = 1; q < cnt; ++q) {
-                float3 l2, h2;
-                record_box(prims, nd.prim_base + off + q, tri, sph, T, l2, h2);
+                const float4 l2 = b[2 * q], h2 = b[2 * q + 1];
                 lo = make_float3(fminf(lo.x, l2.x), fminf(lo.y, l2.y), fminf(lo.z, l2.z));
                 hi = make_float3(fmaxf(hi.x, h2.x), fmaxf(hi.y, h2.y), fmaxf(hi.z, h2.z));
             }
@@ -1011,10 +1139,11 @@ __device__ __forceinline__ void slot_box(const WNode& nd, int s, double lo[3], d
 
 // n_records leaf records over n_prims primitives; rec_box (nullable): each
 // record's exact reference box, which must lie in its leaf slot (else the
-// whole primitive's exact box must).
+// record's unpadded box from the current vertices must: its part of the
+// triangle after a refit of a split build, or the whole primitive's box).
 __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, const float4* __restrict__ nbox,
                            const float4* __restrict__ prims, int64_t n_records, int64_t n_prims,
-                           const float4* __restrict__ rec_box, const float* __restrict__ tri,
+                           const float4* __restrict__ rec_box, Parts parts, const float* __restrict__ tri,
                            const float* __restrict__ sph, int64_t T, unsigned* __restrict__ seen_rec,
                            unsigned* __restrict__ seen_id, unsigned* __restrict__ node_refs, int* errors) {
     const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1059,7 +1188,7 @@ __global__ void k_validate(const WNode* __restrict__ nodes, int64_t n_nodes, con
                     pl = make_float3(l.x, l.y, l.z);
                     ph = make_float3(h.x, h.y, h.z);
                 } else {
-                    prim_box(tri, sph, T, id, pl, ph);
+                    record_box(__float_as_uint(prims[3 * r + 2].y), r, parts, tri, sph, T, false, pl, ph);
                 }
                 if (pl.x < lo[0] || pl.y < lo[1] || pl.z < lo[2] || ph.x > hi[0] || ph.y > hi[1] || ph.z > hi[2])
                     atomicAdd(&errors[4], 1);
@@ -1378,11 +1507,26 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         level_begin.push_back(begin);
         RCP_CUDA(cudaMemcpyAsync(&sc.max_leaf, d_max_leaf, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
+    // the parts of split references, for refits
+    DevBuf<float2> part_uv;
+    DevBuf<uint8_t> part_n;
+    if (split) {
+        RCP_CUDA(part_uv.alloc(PART_MAX * R));
+        RCP_CUDA(part_n.alloc(R));
+        k_record_parts<<<grid_for(R, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(prims.p, R, rec_box.p, sc.d_tri, T,
+                                                                               part_uv.p, part_n.p);
+    }
     // trim the node arrays to size
     if (sc.d_nodes) cudaFree(sc.d_nodes);
     if (sc.d_nbox) cudaFree(sc.d_nbox);
     if (sc.d_prims) cudaFree(sc.d_prims);
     if (sc.d_refbox) cudaFree(sc.d_refbox);
+    if (sc.d_part_uv) cudaFree(sc.d_part_uv);
+    if (sc.d_part_n) cudaFree(sc.d_part_n);
+    if (sc.d_rbox) cudaFree(sc.d_rbox);
+    sc.d_rbox = nullptr;
+    sc.d_part_uv = nullptr;
+    sc.d_part_n = nullptr;
     sc.d_nodes = nullptr;
     sc.d_nbox = nullptr;
     sc.d_prims = nullptr;
@@ -1398,6 +1542,8 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     RCP_CUDA(cudaStreamSynchronize(st));
     sc.d_prims = prims.release();
     sc.d_refbox = rec_box.release();
+    sc.d_part_uv = part_uv.release();
+    sc.d_part_n = part_n.release();
     sc.n_records = R;
     sc.n_nodes = n_nodes;
     sc.depth = depth;
@@ -1412,26 +1558,26 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
 rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
     const int64_t N = sc.T + sc.S;
     if (N == 0 || sc.n_nodes == 0) return RCP_OK;
-    // a refit bounds every record by its whole (moved) primitive, which stays
-    // conservative for split references; their clipped boxes no longer apply
+    // a split build's references are bounded by their parts of the moved
+    // triangles; the build-time reference boxes no longer apply
     if (sc.d_refbox) {
         RCP_CUDA(cudaStreamSynchronize(st));
         cudaFree(sc.d_refbox);
         sc.d_refbox = nullptr;
     }
+    if (!sc.d_rbox) RCP_CUDA(cudaMalloc((void**)&sc.d_rbox, sizeof(float4) * 2 * sc.n_records));
     EventPair ev;
     RCP_CUDA(ev.create());
     RCP_CUDA(cudaEventRecord(ev.a, st));
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_update_records<<<grid_for(sc.n_records, BUILD_BLOCK, sms * 16), BUILD_BLOCK, 0, st>>>(
-        sc.d_prims, sc.n_records, sc.d_tri, sc.d_sph, sc.T);
+    k_refit_records<<<grid_for(sc.n_records, BUILD_BLOCK, sms * 16), BUILD_BLOCK, 0, st>>>(
+        sc.d_prims, sc.n_records, Parts{sc.d_part_uv, sc.d_part_n}, sc.d_tri, sc.d_sph, sc.T, sc.d_rbox);
     for (int l = (int)sc.level_begin.size() - 2; l >= 0; --l) {
         const int64_t b = sc.level_begin[l], e = sc.level_begin[l + 1];
         if (e <= b) continue;
-        k_refit_wide<<<(int)((e - b + 127) / 128), 128, 0, st>>>((WNode*)sc.d_nodes, sc.d_nbox, b, e, sc.d_prims,
-                                                                  sc.d_tri, sc.d_sph, sc.T);
+        k_refit_wide<<<(int)((e - b + 127) / 128), 128, 0, st>>>((WNode*)sc.d_nodes, sc.d_nbox, b, e, sc.d_rbox);
     }
     RCP_CUDA(cudaEventRecord(ev.b, st));
     RCP_CUDA(cudaEventSynchronize(ev.b));
@@ -1456,7 +1602,8 @@ rcp_status validate_bvh(const Scene& sc, cudaStream_t st) {
     RCP_CUDA(cudaMemsetAsync(node_refs.p, 0, sizeof(unsigned) * sc.n_nodes, st));
     RCP_CUDA(cudaMemsetAsync(errors.p, 0, sizeof(int) * 8, st));
     k_validate<<<(int)((sc.n_nodes + 127) / 128), 128, 0, st>>>((const WNode*)sc.d_nodes, sc.n_nodes, sc.d_nbox,
-                                                                 sc.d_prims, R, N, sc.d_refbox, sc.d_tri, sc.d_sph,
+                                                                 sc.d_prims, R, N, sc.d_refbox,
+                                                                 Parts{sc.d_part_uv, sc.d_part_n}, sc.d_tri, sc.d_sph,
                                                                  sc.T, seen_rec.p, seen_id.p, node_refs.p, errors.p);
     k_check_counts<<<grid_for(std::max<int64_t>(std::max(R, N), sc.n_nodes), 256, 4096), 256, 0, st>>>(
         seen_rec.p, R, seen_id.p, N, sc.split_max > 1, node_refs.p, sc.n_nodes, errors.p);

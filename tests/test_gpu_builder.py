@@ -254,19 +254,56 @@ def test_split_references_equal_brute_force(split):
         rcp.rcp_scene_destroy(g)
 
 
-def test_split_scene_refit_stays_exact():
+@pytest.mark.parametrize("motion", ["sway", "jitter"])
+def test_split_scene_refit_stays_exact(motion):
+    """A refit bounds each split reference by its part of the moved triangle:
+    under the stress workload's sway (a translation per triangle) and under
+    independent random moves of every vertex (which shear and scale each
+    triangle), the refitted tree validates and its walk equals brute force
+    bit for bit, twice in a row (parts are kept relative to the build)."""
     sc = scenes.forest_scene(40, seed=5)
     g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
+    rng = np.random.default_rng(19)
     try:
-        moved = scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, 37)
-        rcp.rcp_scene_update_vertices(g, moved)
-        rcp.rcp_scene_validate(g)
-        msc = scenes.Scene("moved", moved, sc.spheres, sc.albedo, sc.light, sc.poses)
-        ot, dt = _cone_rays(msc, 20_000, seed=11)
-        (tw, pw), (tb, pb) = _walk_and_brute(g, ot, dt, 0)
-        assert np.array_equal(pw, pb) and np.array_equal(tw, tb)
+        for frame in (37, 90):
+            if motion == "sway":
+                moved = scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, frame)
+            else:
+                moved = (sc.tris + rng.normal(scale=0.4, size=sc.tris.shape)).astype(np.float32)
+            rcp.rcp_scene_update_vertices(g, moved)
+            rcp.rcp_scene_validate(g)
+            msc = scenes.Scene("moved", moved, sc.spheres, sc.albedo, sc.light, sc.poses)
+            ot, dt = _cone_rays(msc, 20_000, seed=11 + frame)
+            for any_hit in (0, 1):
+                (tw, pw), (tb, pb) = _walk_and_brute(g, ot, dt, any_hit)
+                assert np.array_equal(pw, pb), (motion, frame, any_hit, int((pw != pb).sum()))
+                if not any_hit:
+                    assert np.array_equal(tw.view(np.uint32), tb.view(np.uint32))
     finally:
         rcp.rcp_scene_destroy(g)
+
+
+def test_split_refit_keeps_the_clipped_boxes():
+    """A refit with the build's own vertices leaves a split tree about as
+    tight as the build made it (the parts' boxes equal the clipped boxes up
+    to rounding and the pad), far tighter than the same tree bounded by whole
+    triangles (the unsplit tree's triangle-test count stands in for that)."""
+    sc = scenes.forest_scene(40, seed=5)
+    d = sc.diameter()
+    p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+    cam = rcp.camera_from(sc.poses[3])
+    tests = {}
+    for split in (0, 8):
+        g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, split)
+        try:
+            tests[split] = rcp.rcp_count_pass(g, cam, 320, 180, p).tri_tests
+            if split:
+                rcp.rcp_scene_update_vertices(g, sc.tris)
+                tests["refit"] = rcp.rcp_count_pass(g, cam, 320, 180, p).tri_tests
+        finally:
+            rcp.rcp_scene_destroy(g)
+    assert tests[8] < 0.6 * tests[0], tests
+    assert tests["refit"] <= 1.02 * tests[8], tests
 
 
 @pytest.mark.parametrize("name", ["mid", "forest"])
