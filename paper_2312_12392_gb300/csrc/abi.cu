@@ -58,7 +58,7 @@ RenderCtx::~RenderCtx() {
 Scene::~Scene() {
     ctx.clear();
     for (void* p : {(void*)d_tri, (void*)d_sph, (void*)d_albedo, d_nodes, (void*)d_nbox, (void*)d_prims,
-                    (void*)d_refbox, (void*)d_part_uv, (void*)d_part_n, (void*)d_rbox})
+                    (void*)d_refbox, (void*)d_part_uv, (void*)d_rec_id, (void*)d_rbox})
         if (p) cudaFree(p);
 }
 
@@ -79,7 +79,7 @@ SceneDev Scene::dev() const {
 int64_t Scene::device_bytes() const {
     const int64_t N = T + S;
     return T * 36 + S * 16 + N * 16 + n_nodes * ((int64_t)sizeof(WNode) + 32) + n_records * 48 +
-           (d_refbox ? n_records * 32 : 0) + (d_part_n ? n_records * (9 * 8 + 1) : 0) + (d_rbox ? n_records * 32 : 0);
+           (d_refbox ? n_records * 32 : 0) + (d_part_uv ? n_records * (9 * 4 + 4) : 0) + (d_rbox ? n_records * 24 : 0);
 }
 
 void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params& p) {

@@ -349,12 +349,26 @@ __global__ void k_split_write(const float* __restrict__ tri, int64_t T, int64_t 
 // maps the polygon through the moved vertices and bounds the reference by
 // exactly its part of the moved triangle; the parts of a triangle still cover
 // it, whatever the motion.
+// A vertex is stored as u and v in 16-bit fixed point (u = q / 65535), one
+// 32-bit word: u in the low half. Rounding to nearest moves a mapped vertex by
+// at most 2^-17 of each edge, 2^-16 of the triangle's extent, well inside the
+// 2^-12 extent pad of the triangle's boxes. A record's part fills PART_MAX
+// words; the word PART_END (u = v = 1, impossible in a triangle) ends a part
+// of fewer vertices, and a first word PART_END means no part (the whole
+// primitive).
 constexpr int PART_MAX = 9;  // a triangle clipped by the 6 planes of a box has <= 9 vertices
+constexpr uint32_t PART_END = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t quantize_uv(double u, double v) {
+    const double su = fmin(fmax(u, 0.0), 1.0) * 65535.0, sv = fmin(fmax(v, 0.0), 1.0) * 65535.0;
+    return (uint32_t)__double2uint_rn(su) | ((uint32_t)__double2uint_rn(sv) << 16);
+}
 
 // The part of triangle v inside [lo, hi] (Sutherland-Hodgman in double, the
-// vertices carrying their (u, v)); returns the vertex count (0: no area left).
+// vertices carrying their (u, v)), written to out[0..PART_MAX) with its end
+// marker; returns the vertex count (0: no area left, nothing written).
 __device__ int clip_triangle_uv(const double (&v)[3][3], const float lo[3], const float hi[3],
-                                float2* __restrict__ out) {
+                                uint32_t* __restrict__ out) {
     double poly[PART_MAX + 1][5], tmp[PART_MAX + 1][5];
     for (int i = 0; i < 3; ++i) {
         for (int a = 0; a < 3; ++a) poly[i][a] = v[i][a];
@@ -387,19 +401,22 @@ __device__ int clip_triangle_uv(const double (&v)[3][3], const float lo[3], cons
             for (int i = 0; i < n; ++i)
                 for (int c = 0; c < 5; ++c) poly[i][c] = tmp[i][c];
         }
-    for (int i = 0; i < n; ++i) out[i] = make_float2((float)poly[i][3], (float)poly[i][4]);
+    for (int i = 0; i < n; ++i) out[i] = quantize_uv(poly[i][3], poly[i][4]);
+    if (n < PART_MAX) out[n] = PART_END;
     return n;
 }
 
-// The part of every record of a split build: part_n[r] vertices at
-// part_uv[PART_MAX r ...]. A record whose reference box holds its whole
-// triangle, a sphere, and a part that clipping left without area (which a
-// refit then bounds by the whole moved triangle) get 0.
+// The part of every record of a split build, at part_uv[PART_MAX r ...], and
+// the record's primitive id (with its sphere flag, as in the record) at
+// rec_id[r]. A record whose reference box holds its whole triangle, a sphere,
+// and a part that clipping left without area (which a refit then bounds by
+// the whole moved triangle) get no part.
 __global__ void k_record_parts(const float4* __restrict__ prims, int64_t R, const float4* __restrict__ rec_box,
-                               const float* __restrict__ tri, int64_t T, float2* __restrict__ part_uv,
-                               uint8_t* __restrict__ part_n) {
+                               const float* __restrict__ tri, int64_t T, uint32_t* __restrict__ part_uv,
+                               uint32_t* __restrict__ rec_id) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t idb = __float_as_uint(prims[3 * r + 2].y);
+        rec_id[r] = idb;
         int n = 0;
         if (!(idb & SPHERE_BIT) && (int64_t)idb < T) {
             float3 tl, th;
@@ -414,7 +431,7 @@ __global__ void k_record_parts(const float4* __restrict__ prims, int64_t R, cons
                 n = clip_triangle_uv(v, lo, hi, part_uv + PART_MAX * r);
             }
         }
-        part_n[r] = (uint8_t)n;
+        if (n == 0) part_uv[PART_MAX * r] = PART_END;
     }
 }
 
@@ -1027,10 +1044,10 @@ __global__ void k_collapse(BinTree bt, const int2* __restrict__ frontier, int n_
 
 // ---------------------------------------------------------------- refit after a vertex update
 
-// Leaf records' parts in a split build (both null otherwise).
+// Leaf records' parts and primitive ids in a split build (both null otherwise).
 struct Parts {
-    const float2* uv;
-    const uint8_t* n;
+    const uint32_t* uv;
+    const uint32_t* id;
 };
 
 // Box of record r (primitive id with its sphere flag: idb) from the current
@@ -1045,85 +1062,103 @@ __device__ __forceinline__ void record_box(uint32_t idb, int64_t r, Parts parts,
     prim_box(tri, sph, T, id, tl, th);
     lo = tl;
     hi = th;
-    const int n = parts.n ? parts.n[r] : 0;
-    if (n && id < T) {
+    if (parts.uv && id < T && parts.uv[PART_MAX * r] != PART_END) {
         const float* f = tri + 9 * id;
         const float3 a = make_float3(f[0], f[1], f[2]);
         const float3 e1 = make_float3(f[3] - f[0], f[4] - f[1], f[5] - f[2]);
         const float3 e2 = make_float3(f[6] - f[0], f[7] - f[1], f[8] - f[2]);
         float3 l = make_float3(INFINITY, INFINITY, INFINITY), h = make_float3(-INFINITY, -INFINITY, -INFINITY);
-        for (int k = 0; k < n; ++k) {
-            const float2 uv = parts.uv[PART_MAX * r + k];
-            const float3 p = make_float3(fmaf(uv.y, e2.x, fmaf(uv.x, e1.x, a.x)), fmaf(uv.y, e2.y, fmaf(uv.x, e1.y, a.y)),
-                                         fmaf(uv.y, e2.z, fmaf(uv.x, e1.z, a.z)));
+        const uint32_t* q = parts.uv + PART_MAX * r;
+        for (int k = 0; k < PART_MAX; ++k) {
+            const uint32_t w = q[k];
+            if (w == PART_END) break;
+            const float u = (float)(w & 0xffffu) * (1.f / 65535.f), v = (float)(w >> 16) * (1.f / 65535.f);
+            const float3 p = make_float3(fmaf(v, e2.x, fmaf(u, e1.x, a.x)), fmaf(v, e2.y, fmaf(u, e1.y, a.y)),
+                                         fmaf(v, e2.z, fmaf(u, e1.z, a.z)));
             l = make_float3(fminf(l.x, p.x), fminf(l.y, p.y), fminf(l.z, p.z));
             h = make_float3(fmaxf(h.x, p.x), fmaxf(h.y, p.y), fmaxf(h.z, p.z));
         }
         lo = make_float3(fmaxf(lo.x, l.x), fmaxf(lo.y, l.y), fmaxf(lo.z, l.z));
         hi = make_float3(fminf(hi.x, h.x), fminf(hi.y, h.y), fminf(hi.z, h.z));
     }
-    // the rounding of the stored (u, v) and of the mapping is ~2^-22 of the
-    // triangle's extent, far inside the pad of the whole triangle
+    // the 16-bit (u, v) and the float mapping move a vertex by ~2^-16 of the
+    // triangle's extent, inside the pad of the whole triangle
     if (pad && id < T) pad_box(tri_pad(tl, th), lo, hi);
 }
 
 // First step of a refit, one thread per record: the record rewritten from the
-// moved vertices (spheres do not move) and its padded box (rbox, 2 per
-// record), which k_refit_wide gathers into the leaf slots.
+// moved vertices (spheres do not move) and its padded box (rbox, 6 floats per
+// record: lo, hi), which k_refit_wide gathers into the leaf slots. A split
+// build reads the records' ids from parts.id (4 bytes, not a record's sector).
 __global__ void k_refit_records(float4* __restrict__ prims, int64_t n, Parts parts, const float* __restrict__ tri,
-                                const float* __restrict__ sph, int64_t T, float4* __restrict__ rbox) {
+                                const float* __restrict__ sph, int64_t T, float2* __restrict__ rbox) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t idb = __float_as_uint(prims[3 * r + 2].y);
+        const uint32_t idb = parts.id ? parts.id[r] : __float_as_uint(prims[3 * r + 2].y);
         if (!(idb & SPHERE_BIT)) write_prim_record(prims + 3 * r, tri, sph, T, idb);
         float3 lo, hi;
         record_box(idb, r, parts, tri, sph, T, true, lo, hi);
-        rbox[2 * r] = make_float4(lo.x, lo.y, lo.z, 0.f);
-        rbox[2 * r + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+        rbox[3 * r] = make_float2(lo.x, lo.y);
+        rbox[3 * r + 1] = make_float2(lo.z, hi.x);
+        rbox[3 * r + 2] = make_float2(hi.y, hi.z);
     }
 }
 
 // Recompute the child boxes of the nodes in [begin, end) (one level, deepest
-// first) from their leaf records' boxes (rbox) and their internal children's
-// boxes.
-__global__ void k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbox, int64_t begin, int64_t end,
-                             const float4* __restrict__ rbox) {
-    const int64_t w = begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (w >= end) return;
-    WNode nd = nodes[w];
-    float3 clo[8], chi[8];
-    int slot_of[8];
-    int m = 0;
-    const uint32_t imask = internal_mask(nd.meta_lo, nd.meta_hi);
-    for (int s = 0; s < 8; ++s) {
-        const uint32_t mb = ((s < 4 ? nd.meta_lo : nd.meta_hi) >> (8 * (s & 3))) & 0xffu;
-        if (!mb) continue;
-        float3 lo, hi;
+// first). Eight lanes per node, lane s for slot s: the slot's box is the union
+// of its leaf records' boxes (rbox) or its internal child's box, and each of
+// the node's six box rows (8 floats, one 32-byte sector) is written by its
+// eight lanes together. Empty slots get the empty box (+inf, -inf) that the
+// collapse gave them. Only the node's header is read. The node's union box
+// (nbox) is reduced over its eight lanes, which share a warp.
+constexpr int REFIT_BLOCK = 128;
+static_assert(REFIT_BLOCK % 32 == 0, "a node's eight lanes must share a warp");
+
+__global__ void __launch_bounds__(REFIT_BLOCK) k_refit_wide(WNode* __restrict__ nodes, float4* __restrict__ nbox,
+                                                            int64_t begin, int64_t end,
+                                                            const float2* __restrict__ rbox) {
+    const int64_t t = blockIdx.x * (int64_t)REFIT_BLOCK + threadIdx.x;
+    const int64_t w = begin + (t >> 3);
+    const int s = (int)(t & 7);
+    const bool live = w < end;
+    float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    if (live) {
+        float* nf = reinterpret_cast<float*>(nodes + w);
+        const uint4 hd = *reinterpret_cast<const uint4*>(nf + 48);
+        const uint32_t mb = ((s < 4 ? hd.z : hd.w) >> (8 * (s & 3))) & 0xffu;
         if (mb & 0x80u) {
-            const int64_t c = nd.child_base + __popc(imask & ((1u << s) - 1u));
+            const int64_t c = hd.x + __popc(internal_mask(hd.z, hd.w) & ((1u << s) - 1u));
             const float4 l = nbox[2 * c], h = nbox[2 * c + 1];
             lo = make_float3(l.x, l.y, l.z);
             hi = make_float3(h.x, h.y, h.z);
-        } else {
+        } else if (mb) {
             const int cnt = mb >> 5, off = mb & 31;
-            const float4* b = rbox + 2 * ((int64_t)nd.prim_base + off);
-            lo = make_float3(b[0].x, b[0].y, b[0].z);
-            hi = make_float3(b[1].x, b[1].y, b[1].z);
-            for (int q = 1; q < cnt; ++q) {
-                const float4 l2 = b[2 * q], h2 = b[2 * q + 1];
-                lo = make_float3(fminf(lo.x, l2.x), fminf(lo.y, l2.y), fminf(lo.z, l2.z));
-                hi = make_float3(fmaxf(hi.x, h2.x), fmaxf(hi.y, h2.y), fmaxf(hi.z, h2.z));
+            const float2* b = rbox + 3 * ((int64_t)hd.y + off);
+            for (int q = 0; q < cnt; ++q) {
+                const float2 a = b[3 * q], m = b[3 * q + 1], z = b[3 * q + 2];
+                lo = make_float3(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, m.x));
+                hi = make_float3(fmaxf(hi.x, m.y), fmaxf(hi.y, z.x), fmaxf(hi.z, z.y));
             }
         }
-        clo[m] = lo;
-        chi[m] = hi;
-        slot_of[m] = s;
-        ++m;
+        nf[s] = lo.x;
+        nf[8 + s] = hi.x;
+        nf[16 + s] = lo.y;
+        nf[24 + s] = hi.y;
+        nf[32 + s] = lo.z;
+        nf[40 + s] = hi.z;
     }
-    float3 ulo, uhi;
-    write_child_boxes(nd, clo, chi, slot_of, m, ulo, uhi);
-    nodes[w] = nd;
-    nbox[2 * w] = make_float4(ulo.x, ulo.y, ulo.z, 0.f);
-    nbox[2 * w + 1] = make_float4(uhi.x, uhi.y, uhi.z, 0.f);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+    if (live && s == 0) {
+        nbox[2 * w] = make_float4(lo.x, lo.y, lo.z, 0.f);
+        nbox[2 * w + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    }
 }
 
 // ---------------------------------------------------------------- validation
@@ -1508,13 +1543,12 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         RCP_CUDA(cudaMemcpyAsync(&sc.max_leaf, d_max_leaf, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
     // the parts of split references, for refits
-    DevBuf<float2> part_uv;
-    DevBuf<uint8_t> part_n;
+    DevBuf<uint32_t> part_uv, rec_id;
     if (split) {
         RCP_CUDA(part_uv.alloc(PART_MAX * R));
-        RCP_CUDA(part_n.alloc(R));
+        RCP_CUDA(rec_id.alloc(R));
         k_record_parts<<<grid_for(R, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(prims.p, R, rec_box.p, sc.d_tri, T,
-                                                                               part_uv.p, part_n.p);
+                                                                               part_uv.p, rec_id.p);
     }
     // trim the node arrays to size
     if (sc.d_nodes) cudaFree(sc.d_nodes);
@@ -1522,11 +1556,11 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     if (sc.d_prims) cudaFree(sc.d_prims);
     if (sc.d_refbox) cudaFree(sc.d_refbox);
     if (sc.d_part_uv) cudaFree(sc.d_part_uv);
-    if (sc.d_part_n) cudaFree(sc.d_part_n);
+    if (sc.d_rec_id) cudaFree(sc.d_rec_id);
     if (sc.d_rbox) cudaFree(sc.d_rbox);
     sc.d_rbox = nullptr;
     sc.d_part_uv = nullptr;
-    sc.d_part_n = nullptr;
+    sc.d_rec_id = nullptr;
     sc.d_nodes = nullptr;
     sc.d_nbox = nullptr;
     sc.d_prims = nullptr;
@@ -1543,7 +1577,7 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
     sc.d_prims = prims.release();
     sc.d_refbox = rec_box.release();
     sc.d_part_uv = part_uv.release();
-    sc.d_part_n = part_n.release();
+    sc.d_rec_id = rec_id.release();
     sc.n_records = R;
     sc.n_nodes = n_nodes;
     sc.depth = depth;
@@ -1565,7 +1599,7 @@ rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
         cudaFree(sc.d_refbox);
         sc.d_refbox = nullptr;
     }
-    if (!sc.d_rbox) RCP_CUDA(cudaMalloc((void**)&sc.d_rbox, sizeof(float4) * 2 * sc.n_records));
+    if (!sc.d_rbox) RCP_CUDA(cudaMalloc((void**)&sc.d_rbox, sizeof(float2) * 3 * sc.n_records));
     EventPair ev;
     RCP_CUDA(ev.create());
     RCP_CUDA(cudaEventRecord(ev.a, st));
@@ -1573,11 +1607,12 @@ rcp_status refit_bvh(Scene& sc, cudaStream_t st) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_refit_records<<<grid_for(sc.n_records, BUILD_BLOCK, sms * 16), BUILD_BLOCK, 0, st>>>(
-        sc.d_prims, sc.n_records, Parts{sc.d_part_uv, sc.d_part_n}, sc.d_tri, sc.d_sph, sc.T, sc.d_rbox);
+        sc.d_prims, sc.n_records, Parts{sc.d_part_uv, sc.d_rec_id}, sc.d_tri, sc.d_sph, sc.T, sc.d_rbox);
     for (int l = (int)sc.level_begin.size() - 2; l >= 0; --l) {
         const int64_t b = sc.level_begin[l], e = sc.level_begin[l + 1];
         if (e <= b) continue;
-        k_refit_wide<<<(int)((e - b + 127) / 128), 128, 0, st>>>((WNode*)sc.d_nodes, sc.d_nbox, b, e, sc.d_rbox);
+        k_refit_wide<<<(int)((8 * (e - b) + REFIT_BLOCK - 1) / REFIT_BLOCK), REFIT_BLOCK, 0, st>>>(
+            (WNode*)sc.d_nodes, sc.d_nbox, b, e, sc.d_rbox);
     }
     RCP_CUDA(cudaEventRecord(ev.b, st));
     RCP_CUDA(cudaEventSynchronize(ev.b));
@@ -1603,7 +1638,7 @@ rcp_status validate_bvh(const Scene& sc, cudaStream_t st) {
     RCP_CUDA(cudaMemsetAsync(errors.p, 0, sizeof(int) * 8, st));
     k_validate<<<(int)((sc.n_nodes + 127) / 128), 128, 0, st>>>((const WNode*)sc.d_nodes, sc.n_nodes, sc.d_nbox,
                                                                  sc.d_prims, R, N, sc.d_refbox,
-                                                                 Parts{sc.d_part_uv, sc.d_part_n}, sc.d_tri, sc.d_sph,
+                                                                 Parts{sc.d_part_uv, sc.d_rec_id}, sc.d_tri, sc.d_sph,
                                                                  sc.T, seen_rec.p, seen_id.p, node_refs.p, errors.p);
     k_check_counts<<<grid_for(std::max<int64_t>(std::max(R, N), sc.n_nodes), 256, 4096), 256, 0, st>>>(
         seen_rec.p, R, seen_id.p, N, sc.split_max > 1, node_refs.p, sc.n_nodes, errors.p);

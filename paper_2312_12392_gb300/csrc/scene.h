@@ -53,9 +53,9 @@ struct Scene {
     float4* d_nbox = nullptr;  // 2 per node: union box of the node's children
     float4* d_prims = nullptr;  // 3 per leaf record (n_records)
     float4* d_refbox = nullptr;  // 2 per record: its exact clipped box in a split build (else null)
-    float2* d_part_uv = nullptr;  // split build: 9 per record, its part of its triangle as (u, v) vertices
-    uint8_t* d_part_n = nullptr;  // split build: vertices of each record's part (0: the whole primitive)
-    float4* d_rbox = nullptr;     // 2 per record: padded record boxes of the latest refit (from the first refit)
+    uint32_t* d_part_uv = nullptr;  // split build: 9 per record, its part of its triangle as 16-bit (u, v) pairs
+    uint32_t* d_rec_id = nullptr;   // split build: each record's primitive id (with the sphere flag)
+    float2* d_rbox = nullptr;       // 3 per record: padded record boxes of the latest refit (from the first refit)
     int64_t n_records = 0;       // leaf records: T + S, more when triangles are split
     int split_max = 1;           // references per triangle at most (1: no splitting)
     int64_t n_nodes = 0;
