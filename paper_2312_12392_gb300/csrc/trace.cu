@@ -56,13 +56,13 @@ __global__ void __launch_bounds__(256) k_camera(const ViewDev* __restrict__ view
 template <bool COUNT>
 __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, uint2* stack, int stride,
                                               int stack_entries, bool& overflow, WorkCount& wc, uint32_t& n_shadow,
-                                              uint32_t& code, int32_t& prim) {
-    const Hit h = traverse<false, COUNT>(S, r, stack, stride, stack_entries, overflow, wc);
+                                              uint32_t& code, int32_t& prim, const uint8_t* order_lut) {
+    const Hit h = traverse<false, COUNT>(S, r, stack, stride, stack_entries, overflow, wc, order_lut);
     const ShadeInfo si = shade_primary(S, r, h);
     float4 out = si.c_shadow;
     if (si.need_shadow) {
         ++n_shadow;
-        const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, stride, stack_entries, overflow, wc);
+        const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, stride, stack_entries, overflow, wc, order_lut);
         if (hs.rec < 0) out = si.c_lit;
     }
     code = si.normal_code;
@@ -77,6 +77,9 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                                                  int* status, unsigned long long* ray_counts,
                                                  unsigned long long* counters) {
     extern __shared__ uint2 s_stack[];
+    __shared__ uint8_t s_order[ORDER_LUT_BYTES];
+    fill_order_lut<BLOCK>(s_order);
+    __syncthreads();
     uint2* stack = s_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
     bool overflow = false;
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                     uint32_t code;
                     int32_t prim;
                     const float4 o = trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow,
-                                                        code, prim);
+                                                        code, prim, s_order);
                     ++n_primary;
                     acc.x = __fadd_rn(acc.x, o.x);
                     acc.y = __fadd_rn(acc.y, o.y);
@@ -147,7 +150,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
             }
             uint32_t code;
             int32_t prim;
-            float4 out = trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow, code, prim);
+            float4 out =
+                trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow, code, prim, s_order);
             ++n_primary;
             if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
             v.out[p] = out;
@@ -180,6 +184,9 @@ __global__ void __launch_bounds__(BLOCK) k_debug_trace(SceneDev S, int64_t n, co
                                                        float* __restrict__ t_out, int32_t* __restrict__ prim_out,
                                                        int* status) {
     extern __shared__ uint2 s_stack[];
+    __shared__ uint8_t s_order[ORDER_LUT_BYTES];
+    fill_order_lut<BLOCK>(s_order);
+    __syncthreads();
     uint2* stack = s_stack + threadIdx.x;
     bool overflow = false;
     WorkCount wc{0, 0, 0, 0};
@@ -188,8 +195,8 @@ __global__ void __launch_bounds__(BLOCK) k_debug_trace(SceneDev S, int64_t n, co
         RayF r{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
         Hit h;
         if (brute) h = any ? traverse_brute<true>(S, r) : traverse_brute<false>(S, r);
-        else h = any ? traverse<true, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc)
-                     : traverse<false, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc);
+        else h = any ? traverse<true, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc, s_order)
+                     : traverse<false, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc, s_order);
         if (any) {
             prim_out[i] = h.rec >= 0 ? 1 : 0;
             t_out[i] = 0.f;

@@ -2,7 +2,8 @@
 //
 //  * camera_ray: the per-pixel camera of §2 (Eq. 2-4) and §3 (Eq. 5);
 //  * traverse<ANY>: closest-hit (ANY = false) or any-hit (ANY = true) walk of
-//    the 8-wide BVH (float child boxes) with a per-thread stack in shared memory;
+//    the 8-wide BVH (float child boxes) with a per-thread stack and the
+//    block's traversal-order table in shared memory;
 //  * hit_triangle / hit_sphere: Moller-Trumbore and the analytic sphere test;
 //  * shade_*: Lambert + ambient with a shadow ray, sky on a miss.
 // All arithmetic is float32 with explicit fused multiply-adds, so every kernel
@@ -223,6 +224,18 @@ __device__ __forceinline__ uint32_t to_order(uint32_t m, uint32_t oct) {
     return m;
 }
 
+// The traversal-order table, lut[256 oct + m] = to_order(m, oct), filled by
+// each block into its own 2 KB of shared memory before its first walk (the
+// caller synchronises the block). One byte load per node visit replaces the
+// three conditional bit swaps: measured 3 % faster on the mid terrain.
+constexpr int ORDER_LUT_BYTES = 8 * 256;
+
+template <int BLOCK>
+__device__ __forceinline__ void fill_order_lut(uint8_t* lut) {
+    for (int i = threadIdx.x; i < ORDER_LUT_BYTES; i += BLOCK)
+        lut[i] = (uint8_t)to_order((uint32_t)(i & 255), (uint32_t)(i >> 8));
+}
+
 // Box test. Per axis, entry and exit are t = p * (1/d) - o * (1/d), one FMA
 // per plane, made conservative by directed rounding: near planes round
 // o * (1/d) up and the FMA down, far planes the reverse, so each computed
@@ -237,7 +250,7 @@ __device__ __forceinline__ uint32_t to_order(uint32_t m, uint32_t oct) {
 
 template <bool ANY, bool COUNT>
 __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2* stack, int stride, int stack_limit,
-                                        bool& overflow, WorkCount& wc) {
+                                        bool& overflow, WorkCount& wc, const uint8_t* order_lut) {
     Hit h;
     h.t = r.tmax;
     h.id = 0xffffffffu;
@@ -255,6 +268,7 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
     const float dz = r.dz == 0.f ? 0.f : r.dz;
     const float idx = __frcp_rn(dx), idy = __frcp_rn(dy), idz = __frcp_rn(dz);
     const uint32_t oct = (dx < 0.f ? 1u : 0u) | (dy < 0.f ? 2u : 0u) | (dz < 0.f ? 4u : 0u);
+    const uint8_t* ord = order_lut + (oct << 8);
     // far-plane reciprocals, magnified away from zero
     const float fdx = dx > 0.f ? __fmul_ru(idx, RCP_FAR_SCALE) : __fmul_rd(idx, RCP_FAR_SCALE);
     const float fdy = dy > 0.f ? __fmul_ru(idy, RCP_FAR_SCALE) : __fmul_rd(idy, RCP_FAR_SCALE);
@@ -342,7 +356,7 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
             const uint32_t imask = internal_mask(ml, mh);
             const uint32_t hint = hitmask & imask;
             uint32_t hleaf = hitmask & ~imask;
-            group = make_uint2(hd.x, imask | (to_order(hint, oct) << 8));
+            group = make_uint2(hd.x, imask | ((uint32_t)ord[hint] << 8));
             prim_base = hd.y;
             prim_mask = 0;
             while (hleaf) {
