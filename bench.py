@@ -418,7 +418,7 @@ def run_ours(args):
         "roofline": roof,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": K_PASSES * 160,
                 "d2h_bytes_per_step": W_IMG * H_IMG * 3 * 4,
-                "api": "rcp_render (host RGB output; view descriptors H2D, image D2H inside the timed call)"},
+                "api": "rcp_render (host RGB output; view descriptors H2D, RGB device-to-host inside the timed call: written into host memory by the last pass where the device reads pageable memory coherently, else packed and copied)"},
         "gpu_launches": args.steps * K_PASSES * (1 if t.fused_camera else 2),
         "clocks": clk,
         "wall_s": wall,

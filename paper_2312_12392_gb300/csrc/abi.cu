@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <chrono>
@@ -121,6 +122,7 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.in = nullptr;
     v.out = nullptr;
     v.prim = nullptr;
+    v.rgb = nullptr;
     v.tiles_x = (W + 7) / 8;
     v.pix_begin = 0;
     v.chunk_begin = 0;
@@ -334,7 +336,7 @@ rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cuda
 
 // Stage the per-pass view descriptors of one render (n_views views, K passes).
 rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const float4* const* ins,
-                       float4* const* outs, int32_t* const* prims, cudaStream_t st) {
+                       float4* const* outs, int32_t* const* prims, float* const* rgbs, cudaStream_t st) {
     RCP_CUDA(cudaEventSynchronize(ctx.staged));  // previous copy out of the staging buffer is done
     const int K = ctx.K, nv = ctx.n_views;
     ctx.image_mode = base[0].mapping == RCP_MAP_IMAGE && K > 1;
@@ -354,6 +356,7 @@ rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const f
             v.in = prev;
             v.out = cur;
             v.prim = (n == K - 1 && prims && !ctx.image_mode) ? prims[i] : nullptr;
+            v.rgb = (n == K - 1 && rgbs && !ctx.image_mode) ? rgbs[i] : nullptr;
             ctx.h_views[(size_t)n * nv + i] = v;
         }
     }
@@ -364,7 +367,8 @@ rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const f
 
 rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const int* Ws, const int* Hs, int K,
                         const rcp_params* p, const float4* const* ins, float4* const* outs, int32_t* const* prims,
-                        cudaStream_t st, RenderCtx** ctx_out = nullptr, const LaunchCfg* cfg_override = nullptr) {
+                        cudaStream_t st, RenderCtx** ctx_out = nullptr, const LaunchCfg* cfg_override = nullptr,
+                        float* const* rgbs = nullptr) {
     if (K < 1 || K > 16) {
         set_error("K must be in [1, 16]");
         return RCP_ERR_ARG;
@@ -400,7 +404,7 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     RenderCtx* ctx = nullptr;
     rcp_status r = get_ctx(sc, n_views, K, total_pix, total_chunks, &ctx);
     if (r != RCP_OK) return r;
-    r = stage_views(*ctx, base, ins, outs, prims, st);
+    r = stage_views(*ctx, base, ins, outs, prims, rgbs, st);
     if (r != RCP_OK) return r;
     LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
     cfg.ms = p->spp > 0;
@@ -408,6 +412,36 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     sc.last = ctx;
     if (ctx_out) *ctx_out = ctx;
     return r;
+}
+
+// Whether kernels on the current device may read and write pageable host
+// memory directly (a coherent CPU-GPU link with address translation through
+// the host's page tables, as on Grace).
+bool host_coherent() {
+    static int cached[64];
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return false;
+    std::call_once(once[dev], [dev] {
+        int a = 0, b = 0;
+        if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) a = 0;
+        if (cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) b = 0;
+        cached[dev] = a && b;
+    });
+    return cached[dev] != 0;
+}
+
+// Read and write back one byte in every page of [p, p + bytes): the pages are
+// mapped and writable before a kernel writes there.
+void touch_pages(void* p, size_t bytes) {
+    static const size_t page = [] {
+        const long s = sysconf(_SC_PAGESIZE);
+        return s > 0 ? (size_t)s : (size_t)4096;
+    }();
+    volatile unsigned char* c = (volatile unsigned char*)p;
+    for (size_t i = 0; i < bytes; i += page) c[i] = c[i];
+    if (bytes) c[bytes - 1] = c[bytes - 1];
 }
 
 rcp_status check_status(RenderCtx& ctx, cudaStream_t st) {
@@ -625,10 +659,22 @@ rcp_status rcp_render(const rcp_scene* csc, const rcp_camera* cam, int W, int H,
     RenderCtx* ctx = nullptr;
     r = get_ctx(*sc, 1, K, P, (int64_t)((W + 7) / 8) * ((H + 3) / 4), &ctx);
     if (r != RCP_OK) return r;
-    r = ensure_io(*ctx, true, false);
+    const bool direct = host_coherent() && p->mapping != RCP_MAP_IMAGE;
+    r = ensure_io(*ctx, !direct, false);
     if (r != RCP_OK) return r;
     const float4* ins[1] = {nullptr};
     float4* outs[1] = {ctx->io};
+    if (direct) {
+        // The last pass writes the caller's RGB straight into host memory over
+        // the chip-to-chip link, while it traces: no pack kernel and no copy
+        // after the frame. Each page is touched here first, so that the device
+        // never meets an unmapped page (and a bad pointer faults on the host).
+        touch_pages(out_rgb, sizeof(float) * 3 * P);
+        float* rgbs[1] = {out_rgb};
+        r = render_views(*sc, 1, cam, &W, &H, K, p, ins, outs, nullptr, st, nullptr, nullptr, rgbs);
+        if (r != RCP_OK) return r;
+        return check_status(*ctx, st);
+    }
     r = render_views(*sc, 1, cam, &W, &H, K, p, ins, outs, nullptr, st);
     if (r != RCP_OK) return r;
     r = launch_pack_rgb(ctx->io, ctx->d_rgb, P, st);
@@ -737,7 +783,7 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
     layout_views(base, tp, tc);
     const float4* ins[1] = {(const float4*)d_in};
     float4* outs[1] = {d_out ? (float4*)d_out : ctx->img[0]};
-    r = stage_views(*ctx, base, ins, outs, nullptr, st);
+    r = stage_views(*ctx, base, ins, outs, nullptr, nullptr, st);
     if (r != RCP_OK) return r;
     DevBuf<unsigned long long> d_cnt;
     RCP_CUDA(d_cnt.alloc(8));

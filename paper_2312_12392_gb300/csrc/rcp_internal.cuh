@@ -82,6 +82,8 @@ struct ViewDev {
     const float4* base;  // image-space passes: the frame's traced image
     float4* out;         // this pass's image
     int32_t* prim;     // nullable hit ids
+    float* rgb;        // nullable: this pass also writes R, G, B (3 floats per pixel, row-major) here,
+                       // host memory that the device reads and writes coherently
     int64_t pix_begin;  // first global pixel index of this view
     int64_t chunk_begin;  // first work chunk (8x4 tile) of this view
     int tiles_x;

@@ -131,6 +131,11 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                 if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code0);
                 v.out[p] = out;
                 if (v.prim) v.prim[p] = prim0;
+                if (v.rgb) {
+                    v.rgb[3 * p] = out.x;
+                    v.rgb[3 * p + 1] = out.y;
+                    v.rgb[3 * p + 2] = out.z;
+                }
                 continue;
             }
             RayF r;
@@ -156,6 +161,11 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
             if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
             v.out[p] = out;
             if (v.prim) v.prim[p] = prim;
+            if (v.rgb) {
+                v.rgb[3 * p] = out.x;
+                v.rgb[3 * p + 1] = out.y;
+                v.rgb[3 * p + 2] = out.z;
+            }
         }
     }
     if (overflow) atomicExch(&status[0], 1);
