@@ -21,6 +21,37 @@
 
 namespace rcp {
 
+// Whether kernels on the current device may read and write pageable host
+// memory directly (a coherent CPU-GPU link with address translation through
+// the host's page tables, as on Grace).
+bool host_coherent() {
+    static int cached[64];
+    static std::once_flag once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return false;
+    std::call_once(once[dev], [dev] {
+        int a = 0, b = 0;
+        if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) a = 0;
+        if (cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) b = 0;
+        cached[dev] = a && b;
+    });
+    return cached[dev] != 0;
+}
+
+// Read and write back one byte in every page of [p, p + bytes): the pages are
+// mapped and writable before a kernel writes there.
+void touch_pages(void* p, size_t bytes) {
+    static const size_t page = [] {
+        const long s = sysconf(_SC_PAGESIZE);
+        return s > 0 ? (size_t)s : (size_t)4096;
+    }();
+    volatile unsigned char* c = (volatile unsigned char*)p;
+    for (size_t i = 0; i < bytes; i += page) c[i] = c[i];
+    if (bytes) c[bytes - 1] = c[bytes - 1];
+}
+
+
 namespace {
 thread_local std::string g_error;
 }
@@ -412,36 +443,6 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     sc.last = ctx;
     if (ctx_out) *ctx_out = ctx;
     return r;
-}
-
-// Whether kernels on the current device may read and write pageable host
-// memory directly (a coherent CPU-GPU link with address translation through
-// the host's page tables, as on Grace).
-bool host_coherent() {
-    static int cached[64];
-    static std::once_flag once[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return false;
-    std::call_once(once[dev], [dev] {
-        int a = 0, b = 0;
-        if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) a = 0;
-        if (cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) b = 0;
-        cached[dev] = a && b;
-    });
-    return cached[dev] != 0;
-}
-
-// Read and write back one byte in every page of [p, p + bytes): the pages are
-// mapped and writable before a kernel writes there.
-void touch_pages(void* p, size_t bytes) {
-    static const size_t page = [] {
-        const long s = sysconf(_SC_PAGESIZE);
-        return s > 0 ? (size_t)s : (size_t)4096;
-    }();
-    volatile unsigned char* c = (volatile unsigned char*)p;
-    for (size_t i = 0; i < bytes; i += page) c[i] = c[i];
-    if (bytes) c[bytes - 1] = c[bytes - 1];
 }
 
 rcp_status check_status(RenderCtx& ctx, cudaStream_t st) {

@@ -103,6 +103,12 @@ rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
                               int brute, float* t_out, int32_t* prim_out, int* d_status, cudaStream_t st);
 rcp_status launch_pack_rgb(const float4* img, float* rgb, int64_t n, cudaStream_t st);
+
+// Whether kernels on the current device read and write pageable host memory
+// coherently (then a render's last pass can write the caller's RGB directly).
+bool host_coherent();
+// Read and write back one byte in every page of [p, p + bytes).
+void touch_pages(void* p, size_t bytes);
 // Image-space pass over every view (views' base/in/out set).
 rcp_status launch_imagespace(const ViewDev* d_views, int n_views, int64_t total_pix, cudaStream_t st);
 rcp_status launch_imagespace_single(const float4* base, const float4* prev, float4* out, int W, int H, float kpx,

@@ -13,7 +13,10 @@
 //    runs ahead (STEPS_AHEAD steps);
 //  * the copy-out thread waits for each finished request's last pass, copies
 //    its RGB image to the caller's buffer, releases its memory and records
-//    its latency, while the device already runs the next steps.
+//    its latency, while the device already runs the next steps. Where the
+//    device writes pageable host memory coherently, a request's last pass
+//    writes its RGB into the caller's buffer itself (no staging buffer, no
+//    pack kernel, no copy), and the copy-out thread only waits for it.
 // New requests join at the next step while others are mid-recursion, so short
 // and long requests share every launch.
 #include <cuda_runtime.h>
@@ -67,7 +70,7 @@ struct Request {
     double t_submit = 0, t_admit = 0, t_done = 0;
     rcp_status status = RCP_OK;
     bool done = false;
-    cudaEvent_t ready = nullptr;  // the packed RGB image is complete
+    cudaEvent_t ready = nullptr;  // the RGB image (packed, or in the caller's buffer) is complete
 };
 
 // Launch resources of one scene group in one step slot.
@@ -112,6 +115,7 @@ struct rcp_server {
     StepSlot slots[STEPS_AHEAD];
     int64_t step_no = 0;
     int device = 0;
+    bool direct = false;  // last passes write the callers' RGB buffers (host_coherent)
 
     void run();
     void copy_out();
@@ -121,16 +125,18 @@ struct rcp_server {
 
 namespace {
 
-int64_t request_bytes(int W, int H) {
+// Device memory of a request: two rgbz images, and the RGB staging buffer
+// unless its last pass writes the caller's buffer directly.
+int64_t request_bytes(int W, int H, bool direct) {
     const int64_t P = (int64_t)W * H;
-    return P * (2 * 16 + 12) + 3 * 256;
+    return P * (2 * 16 + (direct ? 0 : 12)) + 3 * 256;
 }
 
-rcp_status alloc_request(Request& r, cudaStream_t st) {
+rcp_status alloc_request(Request& r, bool direct, cudaStream_t st) {
     const int64_t P = (int64_t)r.W * r.H;
     RCP_CUDA(cudaMallocAsync((void**)&r.img[0], sizeof(float4) * P, st));
     RCP_CUDA(cudaMallocAsync((void**)&r.img[1], sizeof(float4) * P, st));
-    RCP_CUDA(cudaMallocAsync((void**)&r.rgb, sizeof(float) * 3 * P, st));
+    if (!direct) RCP_CUDA(cudaMallocAsync((void**)&r.rgb, sizeof(float) * 3 * P, st));
     if (!r.ready) RCP_CUDA(cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming));
     return RCP_OK;
 }
@@ -208,6 +214,7 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
             make_view(v, q->cam, q->W, q->H, q->p);
             v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
             v.out = q->img[q->passes_done & 1];
+            if (direct && q->passes_done + 1 == q->K) v.rgb = q->out_rgb;
             v.pix_begin = total_pix;
             v.chunk_begin = total_chunks;
             total_pix += (int64_t)q->W * q->H;
@@ -227,10 +234,12 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
         }
         for (Request* q : reqs) {
             if (q->passes_done + 1 == q->K) {
-                r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, g.st);
-                if (r != RCP_OK) {
-                    res = r;
-                    break;
+                if (!direct) {
+                    r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, g.st);
+                    if (r != RCP_OK) {
+                        res = r;
+                        break;
+                    }
                 }
                 RCP_CUDA(cudaEventRecord(q->ready, g.st));
             }
@@ -273,10 +282,10 @@ void rcp_server::copy_out() {
         rcp_status st = RCP_OK;
         if (q->status == RCP_OK) {
             cudaError_t e = cudaEventSynchronize(q->ready);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && !direct)
                 e = cudaMemcpyAsync(q->out_rgb, q->rgb, sizeof(float) * 3 * (int64_t)q->W * q->H,
                                     cudaMemcpyDeviceToHost, st_copy);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st_copy);
+            if (e == cudaSuccess && !direct) e = cudaStreamSynchronize(st_copy);
             if (e != cudaSuccess) st = cuda_fail(e, "server copy-out");
         }
         free_request(*q, st_copy);
@@ -326,7 +335,7 @@ void rcp_server::run() {
         if (batch.empty()) continue;
         for (Request* q : batch)
             if (!q->img[0] && q->status == RCP_OK) {
-                rcp_status r = alloc_request(*q, st_main);
+                rcp_status r = alloc_request(*q, direct, st_main);
                 if (r != RCP_OK) q->status = r;
             }
         std::vector<Request*> ok;
@@ -364,6 +373,7 @@ rcp_status rcp_server_create(int64_t budget, int max_slots, rcp_server** out) {
     s->budget = budget;
     s->max_slots = max_slots;
     RCP_CUDA(cudaGetDevice(&s->device));
+    s->direct = host_coherent();
     RCP_CUDA(cudaStreamCreateWithFlags(&s->st_main, cudaStreamNonBlocking));
     RCP_CUDA(cudaStreamCreateWithFlags(&s->st_copy, cudaStreamNonBlocking));
     RCP_CUDA(cudaMalloc((void**)&s->d_rays, sizeof(unsigned long long) * 2));
@@ -400,7 +410,8 @@ rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_
     q->K = K;
     q->p = *p;
     q->out_rgb = out_rgb;
-    q->bytes = request_bytes(W, H);
+    q->bytes = request_bytes(W, H, srv->direct);
+    if (srv->direct) touch_pages(out_rgb, sizeof(float) * 3 * (size_t)W * H);  // mapped before the device writes
     q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) {
