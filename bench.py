@@ -416,8 +416,8 @@ def run_ours(args):
         "mrays_per_s": rays / (tmax / 1000.0) / 1e6,
         "rays_per_frame": rays / frames,
         "roofline": roof,
-        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": K_PASSES * 160,
-                "d2h_bytes_per_step": W_IMG * H_IMG * 3 * 4,
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": rcp.rcp_render_h2d_bytes(1, K_PASSES),
+                "d2h_bytes_per_step": W_IMG * H_IMG * 3 * 4 + 4,  # the RGB image and the status word
                 "api": "rcp_render (host RGB output; view descriptors H2D, RGB device-to-host inside the timed call: written into host memory by the last pass where the device reads pageable memory coherently, else packed and copied)"},
         "gpu_launches": args.steps * K_PASSES * (1 if t.fused_camera else 2),
         "clocks": clk,

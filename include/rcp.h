@@ -275,6 +275,12 @@ rcp_status rcp_count_pass(const rcp_scene* scene, const rcp_camera* cam, int wid
  * captured graph). Read after the render has completed. */
 rcp_status rcp_last_pass_times(const rcp_scene* scene, float* ms, int max_passes, int* n_passes);
 
+/* Bytes that one rcp_render call of K passes over n_views views copies from
+ * host to device: the views' per-pass descriptors (camera terms, image
+ * pointers), uploaded once per call. The library's own bookkeeping, not part of
+ * the method. Returns -1 when K or n_views is out of range. */
+int64_t rcp_render_h2d_bytes(int n_views, int K);
+
 /* Diagnostics used by the tests (all device pointers, enqueued on `stream`):
  *  rcp_debug_trace: n rays, orig_tmin[n*4] = (origin, t_min), dir_tmax[n*4] =
  *    (unit direction, t_max); any_hit 0 = closest hit (t_out, prim_out), 1 =

@@ -853,6 +853,11 @@ rcp_status rcp_last_ray_counts(const rcp_scene* sc, int64_t* primary, int64_t* s
     return RCP_OK;
 }
 
+int64_t rcp_render_h2d_bytes(int n_views, int K) {
+    if (n_views < 1 || K < 1 || K > 16) return -1;
+    return (int64_t)sizeof(ViewDev) * n_views * K;
+}
+
 rcp_status rcp_last_pass_times(const rcp_scene* sc, float* ms, int max_passes, int* n_passes) {
     if (!sc || !ms || !n_passes || max_passes < 1) {
         set_error("rcp_last_pass_times: NULL argument");

@@ -103,6 +103,7 @@ _SIGS = {
     "rcp_count_pass": [_vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.POINTER(rcp_params), _vp, _vp,
                        C.POINTER(rcp_counters)],
     "rcp_last_pass_times": [_vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)],
+    "rcp_render_h2d_bytes": [C.c_int, C.c_int],
     "rcp_debug_trace": [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp],
     "rcp_debug_sort_pairs": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_debug_morton": [_vp, C.c_int64, _vp, _vp, _vp, _vp],
@@ -135,6 +136,7 @@ def lib():
                 f.restype = C.c_int
             L.rcp_last_error.restype = C.c_char_p
             L.rcp_version.restype = C.c_char_p
+            L.rcp_render_h2d_bytes.restype = C.c_int64
             L.rcp_scene_destroy.restype = None
             L.rcp_server_destroy.restype = None
             _lib = L
@@ -327,6 +329,11 @@ def rcp_count_pass(scene, cam: rcp_camera, width, height, params: rcp_params, d_
     _check(lib().rcp_count_pass(scene, C.byref(cam), width, height, C.byref(params), _ptr(d_in), _ptr(d_out),
                                 C.byref(c)), "rcp_count_pass")
     return c
+
+
+def rcp_render_h2d_bytes(n_views, K):
+    """Bytes one rcp_render call copies host to device (view descriptors)."""
+    return int(lib().rcp_render_h2d_bytes(int(n_views), int(K)))
 
 
 def rcp_last_pass_times(scene, max_passes=16):

@@ -70,3 +70,15 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(rcp, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         rcp.lib()
+
+
+def test_render_h2d_bytes(lib):
+    """The per-call host-to-device bytes of rcp_render (view descriptors): K
+    descriptors per view, and -1 outside the valid ranges. Host logic only."""
+    one = rcp.rcp_render_h2d_bytes(1, 1)
+    assert one > 0 and one % 8 == 0
+    assert rcp.rcp_render_h2d_bytes(1, 6) == 6 * one
+    assert rcp.rcp_render_h2d_bytes(64, 6) == 64 * 6 * one
+    assert rcp.rcp_render_h2d_bytes(0, 6) == -1
+    assert rcp.rcp_render_h2d_bytes(1, 0) == -1
+    assert rcp.rcp_render_h2d_bytes(1, 17) == -1
