@@ -77,11 +77,12 @@ def test_mid_end_to_end_psnr(mid):
 
 
 def test_forest_per_pass_and_psnr():
+    """The forest in the bench's build (surface-area collapse, split <= 8)."""
     sc = scenes.forest_scene()
     d = sc.diameter()
     W, H = 1920, 1080
     pix = scenes.pixel_subset(W, H, 1024, seed=3)
-    g = U.gpu_scene(sc)
+    g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
     o = U.oracle_scene(sc)
     try:
         rep = U.per_pass_parity(sc, sc.poses[10], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix, g=g, o=o)

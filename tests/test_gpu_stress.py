@@ -12,9 +12,12 @@ import gpu_util as U  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def test_swaying_forest_refit_parity():
+@pytest.mark.parametrize("collapse,split", [(None, 0), (rcp.RCP_COLLAPSE_SAH, 8)])
+def test_swaying_forest_refit_parity(collapse, split):
+    """Unsplit trees, and the stress workload's build (surface-area collapse,
+    split references refitted by their parts of the moved triangles)."""
     sc = scenes.forest_scene(60, seed=5)
-    g = U.gpu_scene(sc)
+    g = U.gpu_scene(sc, collapse, split)
     try:
         d = sc.diameter()
         W, H = 320, 180
@@ -71,4 +74,62 @@ def test_served_two_copy_stream_equals_single_stream():
     finally:
         rcp.rcp_server_destroy(srv)
         rcp.rcp_scene_destroy(g2)
+        rcp.rcp_scene_destroy(g)
+
+
+def _vertex_rays(tris, n, seed, dist):
+    """Rays from random points at distance ~dist aimed at triangle vertices and
+    at points on their edges (where split references meet)."""
+    rng = np.random.default_rng(seed)
+    v = tris.reshape(-1, 3, 3).astype(np.float64)
+    pick = rng.integers(0, len(v), n)
+    a, b = rng.integers(0, 3, n), rng.integers(0, 3, n)
+    w = rng.choice([0.0, 0.5, 0.25, 1.0], n)[:, None]
+    target = (1 - w) * v[pick, a] + w * v[pick, b]
+    src = target + rng.normal(size=(n, 3)) * dist
+    src[:, 1] = np.abs(src[:, 1] - target[:, 1]) + target[:, 1]  # from above
+    d = target - src
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    ot = np.zeros((n, 4), np.float32)
+    dt = np.zeros((n, 4), np.float32)
+    ot[:, :3] = src
+    dt[:, :3] = d
+    dt[:, 3] = np.inf
+    return ot, dt
+
+
+def test_full_size_stress_parity():
+    """The stress workload at full size in the bench's build: 25,000 swaying
+    cone trees (12.57M triangles), surface-area collapse with split <= 8,
+    refitted to a swayed frame. The refitted tree validates; its walk equals
+    brute force over every record on rays aimed at vertices and edges; and
+    sampled pixels of a 3840x2160, K=8 chain match the oracle pass by pass."""
+    sc = scenes.forest_scene(25_000, seed=5)
+    g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
+    try:
+        info = rcp.rcp_scene_get_info(g)
+        assert info.n_tris == 12_565_522 and info.n_records > 4 * info.n_tris
+        frame = 123
+        moved = scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, frame)
+        rcp.rcp_scene_update_vertices(g, moved)
+        rcp.rcp_scene_validate(g)
+        n = 4096
+        ot, dt = _vertex_rays(moved, n, seed=frame, dist=20.0)
+        res = []
+        for brute in (0, 1):
+            t = torch.empty(n, dtype=torch.float32, device="cuda")
+            p = torch.empty(n, dtype=torch.int32, device="cuda")
+            rcp.rcp_debug_trace(g, n, torch.from_numpy(ot).cuda(), torch.from_numpy(dt).cuda(), 0, brute, t, p)
+            res.append((t.cpu().numpy(), p.cpu().numpy()))
+        assert (res[1][1] >= 0).sum() > n // 2
+        assert np.array_equal(res[0][1], res[1][1])
+        assert np.array_equal(res[0][0].view(np.uint32), res[1][0].view(np.uint32))
+        d = sc.diameter()
+        W, H = 3840, 2160
+        msc = scenes.Scene("stress moved", moved, sc.spheres, sc.albedo, sc.light, sc.poses)
+        pix = scenes.pixel_subset(W, H, 160, seed=frame)
+        rep = U.per_pass_parity(msc, sc.poses[frame % len(sc.poses)], W, H, 8, rcp.RCP_MAP_EYE, 0.02 * d,
+                                0.1 * d, pix=pix, g=g)
+        print(rep.assert_ok(f"stress frame {frame}"))
+    finally:
         rcp.rcp_scene_destroy(g)
