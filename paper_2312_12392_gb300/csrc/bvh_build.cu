@@ -212,30 +212,38 @@ __global__ void k_morton_points(const float* __restrict__ xyz, int64_t n, float 
 constexpr float SPLIT_RATIO = 4.f;  // split while box half-area > 4 x triangle area
 constexpr int SPLIT_MAX = 8;
 
-// Box of triangle v (3 vertices) clipped to [lo, hi], in double, rounded
-// outwards to float. False when the triangle misses the box.
-__device__ bool clip_triangle_box(const double (&v)[3][3], const float lo[3], const float hi[3], float3& olo,
+// Clipping below runs in float with explicit round-to-nearest intrinsics (no
+// contraction left to the compiler), so that the counting and the writing
+// kernels, and any other caller, compute bit-identical pieces. Its rounding,
+// about 2^-23 of the coordinates and edges, sits far inside the pad that every
+// stored box carries (2^-12 of the triangle's extent plus 2^-18 of its
+// coordinates' magnitude). Double arithmetic runs at a small fraction of the
+// float rate on this GPU: the double version took 58 % of the forest's build.
+
+// Box of triangle v (3 vertices) clipped to [lo, hi] (Sutherland-Hodgman).
+// False when the triangle misses the box.
+__device__ bool clip_triangle_box(const float (&v)[3][3], const float lo[3], const float hi[3], float3& olo,
                                   float3& ohi) {
-    double poly[10][3], tmp[10][3];
+    float poly[10][3], tmp[10][3];
     int n = 3;
     for (int i = 0; i < 3; ++i)
         for (int a = 0; a < 3; ++a) poly[i][a] = v[i][a];
     for (int a = 0; a < 3; ++a)
         for (int side = 0; side < 2; ++side) {
-            const double b = side ? (double)hi[a] : (double)lo[a];
+            const float b = side ? hi[a] : lo[a];
             int m = 0;
             for (int i = 0; i < n; ++i) {
-                const double* p = poly[i];
-                const double* q = poly[(i + 1) % n];
+                const float* p = poly[i];
+                const float* q = poly[(i + 1) % n];
                 const bool pin = side ? p[a] <= b : p[a] >= b;
                 const bool qin = side ? q[a] <= b : q[a] >= b;
                 if (pin) {
                     for (int c = 0; c < 3; ++c) tmp[m][c] = p[c];
                     ++m;
                 }
-                if (pin != qin) {
-                    const double t = (b - p[a]) / (q[a] - p[a]);
-                    for (int c = 0; c < 3; ++c) tmp[m][c] = p[c] + t * (q[c] - p[c]);
+                if (pin != qin) {  // p[a] != q[a]: they lie on either side of b
+                    const float t = __fdiv_rn(__fsub_rn(b, p[a]), __fsub_rn(q[a], p[a]));
+                    for (int c = 0; c < 3; ++c) tmp[m][c] = __fmaf_rn(t, __fsub_rn(q[c], p[c]), p[c]);
                     tmp[m][a] = b;  // on the plane exactly
                     ++m;
                 }
@@ -245,28 +253,32 @@ __device__ bool clip_triangle_box(const double (&v)[3][3], const float lo[3], co
             for (int i = 0; i < n; ++i)
                 for (int c = 0; c < 3; ++c) poly[i][c] = tmp[i][c];
         }
-    double l[3] = {poly[0][0], poly[0][1], poly[0][2]}, h[3] = {poly[0][0], poly[0][1], poly[0][2]};
+    float l[3] = {poly[0][0], poly[0][1], poly[0][2]}, h[3] = {poly[0][0], poly[0][1], poly[0][2]};
     for (int i = 1; i < n; ++i)
         for (int c = 0; c < 3; ++c) {
-            l[c] = fmin(l[c], poly[i][c]);
-            h[c] = fmax(h[c], poly[i][c]);
+            l[c] = fminf(l[c], poly[i][c]);
+            h[c] = fmaxf(h[c], poly[i][c]);
         }
-    olo = make_float3(__double2float_rd(l[0]), __double2float_rd(l[1]), __double2float_rd(l[2]));
-    ohi = make_float3(__double2float_ru(h[0]), __double2float_ru(h[1]), __double2float_ru(h[2]));
+    olo = make_float3(l[0], l[1], l[2]);
+    ohi = make_float3(h[0], h[1], h[2]);
     return true;
 }
 
 // The references of triangle `id` (exact boxes, in emission order); returns
-// their number. With rlo/rhi null it only counts. Counting and writing run
-// the same steps, so they agree.
+// their number. With rlo/rhi null it only counts; otherwise it writes at most
+// `cap` of them. Counting and writing run the same steps, so they agree.
 __device__ int split_triangle(const float* __restrict__ tri, uint32_t id, int max_refs, float4* __restrict__ rlo,
-                              float4* __restrict__ rhi) {
+                              float4* __restrict__ rhi, int cap) {
     const float* f = tri + 9 * (int64_t)id;
-    double v[3][3];
+    float v[3][3];
     for (int i = 0; i < 3; ++i)
         for (int a = 0; a < 3; ++a) v[i][a] = f[3 * i + a];
-    const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
-    const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+    // The split test compares areas in double, a few operations per triangle
+    // and per piece: in float, the cross product of a long thin triangle's
+    // edges loses digits and moves the decisions (measured: forest 2.7 %
+    // slower). Only the clipping, the bulk of the work, runs in float.
+    const double e1[3] = {(double)v[1][0] - v[0][0], (double)v[1][1] - v[0][1], (double)v[1][2] - v[0][2]};
+    const double e2[3] = {(double)v[2][0] - v[0][0], (double)v[2][1] - v[0][1], (double)v[2][2] - v[0][2]};
     const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
                  cz = e1[0] * e2[1] - e1[1] * e2[0];
     const double tri_area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
@@ -284,7 +296,7 @@ __device__ int split_triangle(const float* __restrict__ tri, uint32_t id, int ma
         const double box_area = dx * dy + dy * dz + dz * dx;
         // a split adds at most one box to the outstanding ones: keep <= max_refs
         if (tri_area <= 0.0 || n_out + sp + 2 > max_refs || box_area <= SPLIT_RATIO * tri_area) {
-            if (rlo) {
+            if (rlo && n_out < cap) {
                 rlo[n_out] = make_float4(l[0], l[1], l[2], 0.f);
                 rhi[n_out] = make_float4(h[0], h[1], h[2], 0.f);
             }
@@ -292,7 +304,7 @@ __device__ int split_triangle(const float* __restrict__ tri, uint32_t id, int ma
             continue;
         }
         const int ax = (dx >= dy && dx >= dz) ? 0 : (dy >= dz ? 1 : 2);
-        const float mid = 0.5f * (l[ax] + h[ax]);
+        const float mid = __fmul_rn(0.5f, __fadd_rn(l[ax], h[ax]));
         const int sp0 = sp;
         for (int half = 1; half >= 0; --half) {
             float cl[3] = {l[0], l[1], l[2]}, ch[3] = {h[0], h[1], h[2]};
@@ -306,7 +318,7 @@ __device__ int split_triangle(const float* __restrict__ tri, uint32_t id, int ma
             }
         }
         if (sp == sp0) {  // neither half kept a part (rounding): keep the box itself
-            if (rlo) {
+            if (rlo && n_out < cap) {
                 rlo[n_out] = make_float4(l[0], l[1], l[2], 0.f);
                 rhi[n_out] = make_float4(h[0], h[1], h[2], 0.f);
             }
@@ -320,19 +332,27 @@ __device__ int split_triangle(const float* __restrict__ tri, uint32_t id, int ma
 __global__ void k_split_count(const float* __restrict__ tri, int64_t T, int64_t N, int max_refs,
                               unsigned long long* __restrict__ counts) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        counts[i] = i < T ? (unsigned long long)split_triangle(tri, (uint32_t)i, max_refs, nullptr, nullptr) : 1ull;
+        counts[i] = i < T ? (unsigned long long)split_triangle(tri, (uint32_t)i, max_refs, nullptr, nullptr, 0) : 1ull;
 }
 
-// Write the references at their offsets (exclusive prefix sum of the counts).
+// Write the references at their offsets (exclusive prefix sum of the counts,
+// R in all). A primitive writes at most the slots its count gave it; a count
+// that differs sets *err and the build fails.
 __global__ void k_split_write(const float* __restrict__ tri, int64_t T, int64_t N, int max_refs,
-                              const unsigned long long* __restrict__ offsets, const float4* __restrict__ plo,
-                              const float4* __restrict__ phi, float4* __restrict__ rlo, float4* __restrict__ rhi,
-                              uint32_t* __restrict__ rprim) {
+                              const unsigned long long* __restrict__ offsets, int64_t R,
+                              const float4* __restrict__ plo, const float4* __restrict__ phi,
+                              float4* __restrict__ rlo, float4* __restrict__ rhi, uint32_t* __restrict__ rprim,
+                              int* __restrict__ err) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (int64_t)offsets[i];
+        const int cap = (int)((i + 1 < N ? (int64_t)offsets[i + 1] : R) - o);
         int n = 1;
         if (i < T) {
-            n = split_triangle(tri, (uint32_t)i, max_refs, rlo + o, rhi + o);
+            n = split_triangle(tri, (uint32_t)i, max_refs, rlo + o, rhi + o, cap);
+            if (n != cap) {
+                atomicAdd(err, 1);
+                n = min(n, cap);
+            }
         } else {
             rlo[o] = plo[i];
             rhi[o] = phi[i];
@@ -359,30 +379,30 @@ __global__ void k_split_write(const float* __restrict__ tri, int64_t T, int64_t 
 constexpr int PART_MAX = 9;  // a triangle clipped by the 6 planes of a box has <= 9 vertices
 constexpr uint32_t PART_END = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t quantize_uv(double u, double v) {
-    const double su = fmin(fmax(u, 0.0), 1.0) * 65535.0, sv = fmin(fmax(v, 0.0), 1.0) * 65535.0;
-    return (uint32_t)__double2uint_rn(su) | ((uint32_t)__double2uint_rn(sv) << 16);
+__device__ __forceinline__ uint32_t quantize_uv(float u, float v) {
+    const float su = __fmul_rn(fminf(fmaxf(u, 0.f), 1.f), 65535.f), sv = __fmul_rn(fminf(fmaxf(v, 0.f), 1.f), 65535.f);
+    return __float2uint_rn(su) | (__float2uint_rn(sv) << 16);
 }
 
-// The part of triangle v inside [lo, hi] (Sutherland-Hodgman in double, the
-// vertices carrying their (u, v)), written to out[0..PART_MAX) with its end
-// marker; returns the vertex count (0: no area left, nothing written).
-__device__ int clip_triangle_uv(const double (&v)[3][3], const float lo[3], const float hi[3],
+// The part of triangle v inside [lo, hi] (Sutherland-Hodgman in float as
+// above, the vertices carrying their (u, v)), written to out[0..PART_MAX) with
+// its end marker; returns the vertex count (0: no area left, nothing written).
+__device__ int clip_triangle_uv(const float (&v)[3][3], const float lo[3], const float hi[3],
                                 uint32_t* __restrict__ out) {
-    double poly[PART_MAX + 1][5], tmp[PART_MAX + 1][5];
+    float poly[PART_MAX + 1][5], tmp[PART_MAX + 1][5];
     for (int i = 0; i < 3; ++i) {
         for (int a = 0; a < 3; ++a) poly[i][a] = v[i][a];
-        poly[i][3] = i == 1 ? 1.0 : 0.0;
-        poly[i][4] = i == 2 ? 1.0 : 0.0;
+        poly[i][3] = i == 1 ? 1.f : 0.f;
+        poly[i][4] = i == 2 ? 1.f : 0.f;
     }
     int n = 3;
     for (int a = 0; a < 3; ++a)
         for (int side = 0; side < 2; ++side) {
-            const double b = side ? (double)hi[a] : (double)lo[a];
+            const float b = side ? hi[a] : lo[a];
             int m = 0;
             for (int i = 0; i < n; ++i) {
-                const double* p = poly[i];
-                const double* q = poly[(i + 1) % n];
+                const float* p = poly[i];
+                const float* q = poly[(i + 1) % n];
                 const bool pin = side ? p[a] <= b : p[a] >= b;
                 const bool qin = side ? q[a] <= b : q[a] >= b;
                 if (pin) {
@@ -390,8 +410,8 @@ __device__ int clip_triangle_uv(const double (&v)[3][3], const float lo[3], cons
                     ++m;
                 }
                 if (pin != qin) {
-                    const double t = (b - p[a]) / (q[a] - p[a]);
-                    for (int c = 0; c < 5; ++c) tmp[m][c] = p[c] + t * (q[c] - p[c]);
+                    const float t = __fdiv_rn(__fsub_rn(b, p[a]), __fsub_rn(q[a], p[a]));
+                    for (int c = 0; c < 5; ++c) tmp[m][c] = __fmaf_rn(t, __fsub_rn(q[c], p[c]), p[c]);
                     tmp[m][a] = b;
                     ++m;
                 }
@@ -424,7 +444,7 @@ __global__ void k_record_parts(const float4* __restrict__ prims, int64_t R, cons
             const float4 l = rec_box[2 * r], h = rec_box[2 * r + 1];
             if (l.x > tl.x || l.y > tl.y || l.z > tl.z || h.x < th.x || h.y < th.y || h.z < th.z) {
                 const float* f = tri + 9 * (int64_t)idb;
-                double v[3][3];
+                float v[3][3];
                 for (int i = 0; i < 3; ++i)
                     for (int a = 0; a < 3; ++a) v[i][a] = f[3 * i + a];
                 const float lo[3] = {l.x, l.y, l.z}, hi[3] = {h.x, h.y, h.z};
@@ -1394,9 +1414,18 @@ rcp_status build_bvh(Scene& sc, cudaStream_t st) {
         RCP_CUDA(rlo.alloc(R));
         RCP_CUDA(rhi.alloc(R));
         RCP_CUDA(rprim.alloc(R));
-        k_split_write<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(sc.d_tri, T, N, sc.split_max, counts.p,
-                                                                              plo.p, phi.p, rlo.p, rhi.p, rprim.p);
+        DevBuf<int> split_err;
+        RCP_CUDA(split_err.alloc(1));
+        RCP_CUDA(cudaMemsetAsync(split_err.p, 0, sizeof(int), st));
+        k_split_write<<<grid_for(N, BUILD_BLOCK, cap), BUILD_BLOCK, 0, st>>>(
+            sc.d_tri, T, N, sc.split_max, counts.p, R, plo.p, phi.p, rlo.p, rhi.p, rprim.p, split_err.p);
+        int h_err = 0;
+        RCP_CUDA(cudaMemcpyAsync(&h_err, split_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         RCP_CUDA(cudaStreamSynchronize(st));  // counts and aux are freed on leaving this block
+        if (h_err) {
+            set_error("BVH build: split references counted and written differently");
+            return RCP_ERR_STATE;
+        }
         ref_lo = rlo.p;
         ref_hi = rhi.p;
     }
