@@ -902,8 +902,8 @@ def main(argv=None):
     ap.add_argument("--collapse", default="auto", choices=["auto", "area", "sah"],
                     help="BVH collapse policy; auto: sah for the forest workloads, area for the terrains")
     ap.add_argument("--split", default="auto", choices=["auto"] + [str(i) for i in range(9)],
-                    help="references per triangle at most (early split clipping); auto: 8 for the static "
-                         "forests, 0 otherwise")
+                    help="references per triangle at most (early split clipping); auto: 8 for the forests "
+                         "(static and swaying), 0 for the terrains")
     ap.add_argument("--count-poses", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
