@@ -190,7 +190,13 @@ rcp_status rcp_scene_validate(const rcp_scene* scene);
 void rcp_scene_destroy(rcp_scene* scene);
 
 /* K passes I_1..I_K from I_0 = 0.5 (§2-§3); writes I_K's RGB to out_rgb (host,
- * width*height*3 floats). Synchronous. */
+ * width*height*3 floats, row-major from the top row). Synchronous.
+ * Where the device reads and writes pageable host memory coherently (a
+ * Grace-class host), the last pass stores the RGB straight into out_rgb while
+ * it traces; elsewhere, and for RCP_MAP_IMAGE, the image is packed on the
+ * device and copied. Either way the values are the same. Before the render the
+ * calling thread reads and writes back one byte of every page of out_rgb, so a
+ * bad pointer faults on the host, as a copy into it would. */
 rcp_status rcp_render(const rcp_scene* scene, const rcp_camera* cam, int width, int height, int K,
                       const rcp_params* params, float* out_rgb);
 
@@ -339,7 +345,10 @@ typedef struct {
 } rcp_server_stats;
 
 rcp_status rcp_server_create(int64_t mem_budget_bytes, int max_slots, rcp_server** out);
-/* out_rgb: host, width*height*3 floats, caller-owned until the request is done. */
+/* out_rgb: host, width*height*3 floats, caller-owned until the request is done.
+ * As in rcp_render, a device that reads and writes pageable host memory
+ * coherently writes the RGB into out_rgb itself during the request's last
+ * pass; the submitting thread touches every page of out_rgb first. */
 rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_camera* cam,
                              int width, int height, int K, const rcp_params* params, float* out_rgb,
                              int64_t* ticket);
