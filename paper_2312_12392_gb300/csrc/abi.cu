@@ -673,7 +673,10 @@ rcp_status rcp_render(const rcp_scene* csc, const rcp_camera* cam, int W, int H,
         touch_pages(out_rgb, sizeof(float) * 3 * P);
         float* rgbs[1] = {out_rgb};
         r = render_views(*sc, 1, cam, &W, &H, K, p, ins, outs, nullptr, st, nullptr, nullptr, rgbs);
-        if (r != RCP_OK) return r;
+        if (r != RCP_OK) {
+            cudaStreamSynchronize(st);  // no pass may still write the caller's buffer after we return
+            return r;
+        }
         return check_status(*ctx, st);
     }
     r = render_views(*sc, 1, cam, &W, &H, K, p, ins, outs, nullptr, st);

@@ -287,6 +287,11 @@ void rcp_server::copy_out() {
                                     cudaMemcpyDeviceToHost, st_copy);
             if (e == cudaSuccess && !direct) e = cudaStreamSynchronize(st_copy);
             if (e != cudaSuccess) st = cuda_fail(e, "server copy-out");
+        } else {
+            // A failed request may have passes still queued (a step that failed
+            // part-way): let the device drain before its images are freed and
+            // the caller, whose buffer a last pass may write, is told.
+            cudaDeviceSynchronize();
         }
         free_request(*q, st_copy);
         const double t = now_s();
