@@ -14,8 +14,10 @@
  *    allocated by the caller. "host" buffers are ordinary CPU memory; "device"
  *    buffers are CUDA device pointers on the current device.
  *  - Images are row-major, row 0 at the top. "rgbz" images hold 4 floats per
- *    pixel: linear RGB in [0,1] and the hit distance t of the pixel's primary
- *    ray (0 on a miss). "rgb" images hold 3 floats per pixel.
+ *    pixel: linear RGB in [0,1] and the z-depth of the pixel's primary hit,
+ *    its distance from the pixel's eye along the base camera's unit view axis
+ *    F, t (d . F) for a hit at distance t along the unit ray direction d (0 on
+ *    a miss; §4's z-depth). "rgb" images hold 3 floats per pixel.
  *  - Primitive ids: triangles 0..T-1, spheres T..T+S-1; -1 marks a miss.
  *  - Valid arguments: 1 <= width, height <= 8192; 1 <= K <= 16; k >= 0;
  *    focal_dist > 0; finite coordinates. Degenerate (zero-area) triangles are
@@ -70,7 +72,7 @@ typedef struct {
  *                  P_p (at focal_dist along the view axis).
  *  RCP_MAP_TARGET: P'_e = P_e, P'_p = P_p + V (the paper's §3 example).
  *  RCP_MAP_DEPTH:  P'_e = P_e, P'_p = P_p + |z - z0| * V, z = the previous
- *                  pass's hit distance (§4, Eq. 7).
+ *                  pass's z-depth (§4, Eq. 7).
  *  RCP_MAP_IMAGE:  the image-space reduction of §6 (V_e = 0): pass 1 is traced;
  *                  every later pass re-samples pass 1's image at the pixel
  *                  displaced by k * (2r - 1) to the right and k * (2g - 1) up
@@ -81,8 +83,14 @@ typedef struct {
  *                  pixel's undisplaced pinhole direction, N = the previous
  *                  pass's hit normal (facing its ray). For this mapping the
  *                  fourth float of every rgbz pixel holds, as raw bits, a 32-bit
- *                  octahedral code of that normal (two 16-bit fields q + 32768,
- *                  q = round(32767 p)); code 0 = no normal (I_0, misses). */
+ *                  octahedral code of that normal instead of the z-depth:
+ *                  p = (n.x, n.y) / (|n.x| + |n.y| + |n.z|), folded when n.z < 0
+ *                  to ((1 - |p.y|) sgn p.x, (1 - |p.x|) sgn p.y) (sgn 0 = +1);
+ *                  q = round(32767 p); bits 0-15 hold q.x + 32768 and bits
+ *                  16-31 q.y + 32768. Decoding unfolds p (z = 1 - |p.x| - |p.y|,
+ *                  and where z < 0 the same fold) and normalises; the round
+ *                  trip is within 1e-4 of the unit normal. Code 0 = no normal
+ *                  (I_0, misses); no unit normal encodes to 0. */
 typedef enum {
     RCP_MAP_EYE = 0,
     RCP_MAP_TARGET = 1,
@@ -230,12 +238,17 @@ rcp_status rcp_imagespace_pass_device(const float* d_base, const float* d_prev, 
 
 /* Many views of one scene in one persistent launch per pass (§2's per-(u,v)
  * cameras for every view at once). cams, widths, heights: host arrays of
- * n_views; d_outs: host array of n_views device pointers (rgbz, width*height*4
- * floats each). All views run K passes; the K-pass recursion is captured in a
- * CUDA graph keyed by the view shapes. Enqueued on `stream`. */
+ * n_views. d_ins: NULL (every view starts from I_0) or a host array of n_views
+ * device pointers, each a view's previous rgbz image or NULL (I_0); the same
+ * aliasing rule as rcp_render_device. d_outs: host array of n_views device
+ * pointers (rgbz, width*height*4 floats each). d_prims: NULL or a host array of
+ * n_views device pointers (width*height int32 each, or NULL) receiving the
+ * last pass's hit ids. All views run K passes; the K-pass recursion is
+ * captured in a CUDA graph keyed by the view shapes. Enqueued on `stream`. */
 rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rcp_camera* cams,
                                    const int* widths, const int* heights, int K,
-                                   const rcp_params* params, float* const* d_outs, void* stream);
+                                   const rcp_params* params, const float* const* d_ins,
+                                   float* const* d_outs, int32_t* const* d_prims, void* stream);
 
 /* Traversal tuning. block: threads per block (64, 128, 256); blocks_per_sm:
  * resident blocks of the persistent launch (0 = occupancy maximum); chunk:
@@ -305,26 +318,31 @@ rcp_status rcp_debug_morton(const float* xyz, int64_t n, const float* lo, const 
 
 /* Allocation-free sort. The paper has no counterpart: this is a library
  * facility. Some callers cannot allocate device memory at the point where they
- * need to sort: code running while a CUDA graph is being captured (where
- * cudaMalloc is not allowed), real-time loops that must not allocate once they
- * are running, and hosts that hand the library no allocator of its own. This
- * entry point does the same stable LSD radix sort as rcp_debug_sort_pairs
- * (keys and values are device arrays of n uint32, sorted in place on the low
- * `bits` bits of the keys, enqueued on `stream`), but all of its scratch
- * lives in one fixed device array compiled into the library, of about 8.7 MB,
- * which every GPU that loads the library holds until the process exits; it
- * calls no cudaMalloc or cudaFree.
- *  - n may be at most RCP_SORT_STATIC_MAX_PAIRS; larger n returns
- *    RCP_ERR_ARG with a message saying so.
+ * need to sort: real-time loops that must not allocate once they are running
+ * (an allocation can block on the device or fail late), and hosts that own all
+ * device memory and hand the library no allocator of its own. This entry
+ * point does the same stable LSD radix sort as rcp_debug_sort_pairs (keys and
+ * values are device arrays of n uint32, sorted in place on the low `bits` bits
+ * of the keys, enqueued on `stream`), but all of its scratch lives in one fixed
+ * device array compiled into the library, of about 8.7 MB, which every GPU that
+ * loads the library holds until the process exits; it calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *  - n may be at most RCP_SORT_STATIC_MAX_PAIRS (also returned by
+ *    rcp_sort_static_capacity); larger n returns RCP_ERR_ARG with a message
+ *    saying so.
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
  *    stream capture begins.
- *  - Every call reuses the same array, so calls whose work overlaps on the GPU
- *    (other streams, other host threads) race on it: serialise them.
+ *  - Every call reuses the same array and clears what must start at zero;
+ *    calls whose work overlaps on the GPU (other streams, other host threads)
+ *    race on it: serialise them.
  *  - The call waits for the sort to finish before it returns (it reads the
  *    sort's error flag); RCP_ERR_TIMEOUT reports a look-back wait that ran out. */
 #define RCP_SORT_STATIC_MAX_PAIRS 1048576
 rcp_status rcp_sort_pairs_static(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream);
+/* The largest n rcp_sort_pairs_static accepts (RCP_SORT_STATIC_MAX_PAIRS of
+ * the library as built). */
+int64_t rcp_sort_static_capacity(void);
 
 /* ------------------------------------------------------------ serving ---
  * A request = one K-pass render of a resident scene. Requests are admitted

@@ -6,7 +6,9 @@ the CUDA library and its Python binding never import it. It shares no code with
 the CUDA path: ``rcp_oracle.c`` is plain C, compiled here with gcc.
 
 Images exchanged with the oracle are (H, W, 4) float32 arrays: RGB in [0, 1]
-and the hit distance (0 on a miss) in the fourth lane.
+and the z-depth of the primary hit along the camera's view axis (0 on a miss)
+in the fourth lane. The normal mapping's previous hit normals travel beside
+the image as (H, W, 3) float64 unit vectors (zero = no normal).
 """
 from __future__ import annotations
 
@@ -27,7 +29,9 @@ _lib = None
 
 MAP_EYE, MAP_TARGET, MAP_DEPTH, MAP_NORMAL = 0, 1, 2, 4
 LIGHT_POINT, LIGHT_DIRECTIONAL = 0, 1
+FLAG_ID, FLAG_SHADOW, FLAG_POINT = 1, 2, 4
 TOL = 1e-5
+IMG_TOL = 2.0 ** -21
 
 
 def build(force: bool = False, extra_flags=()) -> str:
@@ -58,32 +62,31 @@ def _bind(lib):
     lib.orc_scene_diam.restype = d
     lib.orc_scene_diam.argtypes = [C.c_void_p]
     lib.orc_camera_ray.restype = i32
-    lib.orc_camera_ray.argtypes = [dp, i32, i32, i32, i32, i32, d, d, d, dp, d, dp, dp]
+    lib.orc_camera_ray.argtypes = [dp, i32, i32, i32, i32, i32, d, d, d, dp, d, dp, dp, dp]
     lib.orc_hit_triangle.argtypes = [dp, dp, dp, dp, dp, d, d, dp]
     lib.orc_hit_sphere.argtypes = [dp, d, dp, dp, d, d, dp]
     lib.orc_trace_closest.argtypes = [C.c_void_p, dp, dp, d, d, dp, lp, C.POINTER(C.c_int)]
     lib.orc_trace_any.argtypes = [C.c_void_p, dp, dp, d, d, d, C.POINTER(C.c_int), C.POINTER(C.c_int)]
-    lib.orc_shade_ray.argtypes = [C.c_void_p, dp, dp, dp, lp, C.POINTER(C.c_int)]
+    lib.orc_shade_ray.argtypes = [C.c_void_p, dp, dp, dp, dp, lp, C.POINTER(C.c_int)]
     lib.orc_render_pass.restype = i32
-    lib.orc_render_pass.argtypes = [C.c_void_p, dp, i32, i32, i32, d, d, d, fp, lp, i64, dp, ip, up, i32]
+    lib.orc_render_pass.argtypes = [C.c_void_p, dp, i32, i32, i32, d, d, d, fp, dp, lp, i64, dp, dp, ip, up, i32]
     lib.orc_imagespace_pass.restype = i32
-    lib.orc_imagespace_pass.argtypes = [fp, fp, i32, i32, C.c_float, lp, i64, fp]
+    lib.orc_imagespace_pass.argtypes = [fp, fp, i32, i32, d, lp, i64, fp, up]
     lib.orc_mirror_index.restype = i64
     lib.orc_mirror_index.argtypes = [i64, i64]
-    lib.orc_normal_encode.restype = C.c_uint32
-    lib.orc_normal_encode.argtypes = [dp]
-    lib.orc_normal_decode.restype = i32
-    lib.orc_normal_decode.argtypes = [C.c_uint32, dp]
     lib.orc_render_pass_ms.restype = i32
-    lib.orc_render_pass_ms.argtypes = [C.c_void_p, dp, i32, i32, i32, d, d, d, i32, fp, fp, lp, i64, dp, ip, up, i32]
+    lib.orc_render_pass_ms.argtypes = [C.c_void_p, dp, i32, i32, i32, d, d, d, i32, fp, fp, dp, lp, i64, dp, dp, ip,
+                                       up, i32]
     lib.orc_render_ms.restype = i32
-    lib.orc_render_ms.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, i32, fp, dp, up, i32]
+    lib.orc_render_ms.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, i32, fp, dp, dp, up, i32]
     lib.orc_sample_image.restype = i32
-    lib.orc_sample_image.argtypes = [fp, i32, i32, d, d, i32, dp]
+    lib.orc_sample_image.argtypes = [fp, i32, i32, d, d, dp]
+    lib.orc_nearest_pixel.restype = i64
+    lib.orc_nearest_pixel.argtypes = [i32, i32, d, d]
     lib.orc_camera_ray_at.restype = i32
-    lib.orc_camera_ray_at.argtypes = [dp, i32, i32, d, d, i32, d, d, d, dp, d, dp, dp]
+    lib.orc_camera_ray_at.argtypes = [dp, i32, i32, d, d, i32, d, d, d, dp, d, dp, dp, dp]
     lib.orc_render.restype = i32
-    lib.orc_render.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, lp, i64, dp, ip, up, i32]
+    lib.orc_render.argtypes = [C.c_void_p, dp, i32, i32, i32, i32, d, d, d, lp, i64, dp, dp, ip, up, i32]
     return lib
 
 
@@ -149,89 +152,128 @@ class OracleScene:
         self._lib.orc_trace_any(self.h, _dp(_vec(o)), _dp(_vec(d)), tmin, tmax, extra, C.byref(occ), C.byref(f))
         return occ.value, f.value
 
-    def shade_ray(self, o, d):
+    def shade_ray(self, o, d, want_normal=False):
+        """(rgbt, prim, flag[, unit normal facing the ray]) of one primary ray."""
         out = np.zeros(4)
+        nrm = np.zeros(3)
         p = C.c_int64()
         f = C.c_int()
-        self._lib.orc_shade_ray(self.h, _dp(_vec(o)), _dp(_vec(d)), _dp(out), C.byref(p), C.byref(f))
-        return out, p.value, f.value
+        self._lib.orc_shade_ray(self.h, _dp(_vec(o)), _dp(_vec(d)), _dp(out), _dp(nrm), C.byref(p), C.byref(f))
+        return (out, p.value, f.value, nrm) if want_normal else (out, p.value, f.value)
 
     # -- passes
-    def render_pass(self, cam, W, H, mapping, k, f, in_rgbz=None, pix=None, z0=0.0, nthreads=0):
-        """One pass; returns (rgbz (n,4) float64, prim (n,) int32, flag (n,) uint8)."""
+    def render_pass(self, cam, W, H, mapping, k, f, in_rgbz=None, pix=None, z0=0.0, nthreads=0, in_normal=None,
+                    want_normal=False):
+        """One pass; returns (rgbz (n,4) float64, prim (n,) int32, flag (n,) uint8[, normal (n,3)]).
+        in_normal: the previous pass's hit normals, (H, W, 3) float64 (normal mapping)."""
         cam = _vec(cam)
         n = W * H if pix is None else len(pix)
         out = np.zeros((n, 4))
+        nrm = np.zeros((n, 3))
         prim = np.zeros(n, np.int32)
         flag = np.zeros(n, np.uint8)
-        inp = None
-        if in_rgbz is not None:
-            inp = np.ascontiguousarray(in_rgbz, dtype=np.float32).reshape(H * W * 4)
+        inp = _img_f32(in_rgbz, W, H)
+        inn = _normals(in_normal, W, H)
         pp = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
         rc = self._lib.orc_render_pass(
-            self.h, _dp(cam), W, H, mapping, k, f, z0,
-            None if inp is None else inp.ctypes.data_as(C.POINTER(C.c_float)),
-            None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n, _dp(out),
+            self.h, _dp(cam), W, H, mapping, k, f, z0, _fp(inp), None if inn is None else _dp(inn),
+            None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n, _dp(out), _dp(nrm),
             prim.ctypes.data_as(C.POINTER(C.c_int32)), flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
         if rc != 0:
             raise ValueError("orc_render_pass rejected its arguments")
-        return out, prim, flag
+        return (out, prim, flag, nrm) if want_normal else (out, prim, flag)
 
-    def render_pass_ms(self, cam, W, H, mapping, k, f, jitter, in_rgbz=None, pix=None, z0=0.0, nthreads=0):
-        """Multi-sample pass; jitter (spp, 2) offsets in [0,1). Returns (rgbz, prim of sample 0, flag)."""
+    def render_pass_ms(self, cam, W, H, mapping, k, f, jitter, in_rgbz=None, pix=None, z0=0.0, nthreads=0,
+                       in_normal=None, want_normal=False):
+        """Multi-sample pass; jitter (spp, 2) offsets in [0,1). Returns (rgbz, prim of sample 0, flag[, normal])."""
         cam = _vec(cam)
         jit = np.ascontiguousarray(jitter, dtype=np.float32).reshape(-1)
         n = W * H if pix is None else len(pix)
         out = np.zeros((n, 4))
+        nrm = np.zeros((n, 3))
         prim = np.zeros(n, np.int32)
         flag = np.zeros(n, np.uint8)
-        inp = None if in_rgbz is None else np.ascontiguousarray(in_rgbz, dtype=np.float32).reshape(-1)
+        inp = _img_f32(in_rgbz, W, H)
+        inn = _normals(in_normal, W, H)
         pp = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
-        fptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
         rc = self._lib.orc_render_pass_ms(
-            self.h, _dp(cam), W, H, mapping, k, f, z0, jit.size // 2, fptr(jit), None if inp is None else fptr(inp),
-            None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n, _dp(out),
-            prim.ctypes.data_as(C.POINTER(C.c_int32)), flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
+            self.h, _dp(cam), W, H, mapping, k, f, z0, jit.size // 2, _fp(jit), _fp(inp),
+            None if inn is None else _dp(inn), None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n,
+            _dp(out), _dp(nrm), prim.ctypes.data_as(C.POINTER(C.c_int32)), flag.ctypes.data_as(C.POINTER(C.c_uint8)),
+            nthreads)
         if rc != 0:
             raise ValueError("orc_render_pass_ms rejected its arguments")
-        return out, prim, flag
+        return (out, prim, flag, nrm) if want_normal else (out, prim, flag)
 
-    def render_ms(self, cam, W, H, K, mapping, k, f, jitter, z0=0.0, nthreads=0):
-        """K multi-sample passes over the whole image: (rgbz (W*H, 4), OR of flags)."""
+    def render_ms(self, cam, W, H, K, mapping, k, f, jitter, z0=0.0, nthreads=0, want_normal=False):
+        """K multi-sample passes over the whole image: (rgbz (W*H, 4), OR of flags[, normal (W*H, 3)])."""
         cam = _vec(cam)
         jit = np.ascontiguousarray(jitter, dtype=np.float32).reshape(-1)
         out = np.zeros((W * H, 4))
+        nrm = np.zeros((W * H, 3))
         flag = np.zeros(W * H, np.uint8)
-        rc = self._lib.orc_render_ms(self.h, _dp(cam), W, H, K, mapping, k, f, z0, jit.size // 2,
-                                     jit.ctypes.data_as(C.POINTER(C.c_float)), _dp(out),
-                                     flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
+        rc = self._lib.orc_render_ms(self.h, _dp(cam), W, H, K, mapping, k, f, z0, jit.size // 2, _fp(jit), _dp(out),
+                                     _dp(nrm), flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
         if rc != 0:
             raise ValueError("orc_render_ms rejected its arguments")
-        return out, flag
+        return (out, flag, nrm) if want_normal else (out, flag)
 
-    def render(self, cam, W, H, K, mapping, k, f, pix=None, z0=0.0, nthreads=0):
-        """K passes from I_0; returns (rgbz of the last pass, prim of the last pass, OR of flags)."""
+    def render(self, cam, W, H, K, mapping, k, f, pix=None, z0=0.0, nthreads=0, want_normal=False):
+        """K passes from I_0; returns (rgbz of the last pass, prim of the last pass, OR of flags[, normal])."""
         cam = _vec(cam)
         n = W * H if pix is None else len(pix)
         out = np.zeros((n, 4))
+        nrm = np.zeros((n, 3))
         prim = np.zeros(n, np.int32)
         flag = np.zeros(n, np.uint8)
         pp = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
         rc = self._lib.orc_render(
             self.h, _dp(cam), W, H, K, mapping, k, f, z0,
-            None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n, _dp(out),
+            None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n, _dp(out), _dp(nrm),
             prim.ctypes.data_as(C.POINTER(C.c_int32)), flag.ctypes.data_as(C.POINTER(C.c_uint8)), nthreads)
         if rc != 0:
             raise ValueError("orc_render rejected its arguments")
-        return out, prim, flag
+        return (out, prim, flag, nrm) if want_normal else (out, prim, flag)
 
 
-def camera_ray(cam, W, H, x, y, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, libpath=None):
-    """Per-pixel camera of the oracle: returns (origin, unit direction, degenerate)."""
+def _fp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _img_f32(img, W, H):
+    if img is None:
+        return None
+    a = np.ascontiguousarray(img, dtype=np.float32).reshape(-1)
+    if a.size != W * H * 4:
+        raise ValueError("images must be H*W*4 floats")
+    return a
+
+
+def _normals(nrm, W, H):
+    if nrm is None:
+        return None
+    a = np.ascontiguousarray(nrm, dtype=np.float64).reshape(-1)
+    if a.size != W * H * 3:
+        raise ValueError("normals must be H*W*3 doubles")
+    return a
+
+
+def camera_ray(cam, W, H, x, y, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, n=None, libpath=None):
+    """Per-pixel camera of the oracle: returns (origin, unit direction, degenerate).
+    n: the previous hit normal (normal mapping), None = no normal."""
     L = lib(libpath)
     o = np.zeros(3)
     d = np.zeros(3)
-    rc = L.orc_camera_ray(_dp(_vec(cam)), W, H, x, y, mapping, k, f, z0, _dp(_vec(c)), z, _dp(o), _dp(d))
+    rc = L.orc_camera_ray(_dp(_vec(cam)), W, H, x, y, mapping, k, f, z0, _dp(_vec(c)), z,
+                          None if n is None else _dp(_vec(n)), _dp(o), _dp(d))
+    return o, d, rc
+
+
+def camera_ray_at(cam, W, H, px, py, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, n=None, libpath=None):
+    o = np.zeros(3)
+    d = np.zeros(3)
+    rc = lib(libpath).orc_camera_ray_at(_dp(_vec(cam)), W, H, float(px), float(py), mapping, k, f, z0, _dp(_vec(c)),
+                                        z, None if n is None else _dp(_vec(n)), _dp(o), _dp(d))
     return o, d, rc
 
 
@@ -252,56 +294,38 @@ def mirror_index(i, n, libpath=None):
     return lib(libpath).orc_mirror_index(int(i), int(n))
 
 
-def imagespace_pass(base, prev, W, H, k_px, pix=None, libpath=None):
-    """One image-space pass: returns (n, 4) float32 (n = W*H or len(pix))."""
+def imagespace_pass(base, prev, W, H, k_px, pix=None, libpath=None, want_flag=False):
+    """One image-space pass: returns (n, 4) float32 (n = W*H or len(pix)), and
+    with want_flag the (n,) uint8 rounding-band flags."""
     b = np.ascontiguousarray(base, dtype=np.float32).reshape(-1)
     p = np.ascontiguousarray(prev, dtype=np.float32).reshape(-1)
     if b.size != W * H * 4 or p.size != W * H * 4:
         raise ValueError("base and prev must be H*W*4 floats")
     n = W * H if pix is None else len(pix)
     out = np.zeros((n, 4), np.float32)
+    flag = np.zeros(n, np.uint8)
     pp = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
-    fptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
-    rc = lib(libpath).orc_imagespace_pass(fptr(b), fptr(p), W, H, float(np.float32(k_px)),
+    rc = lib(libpath).orc_imagespace_pass(_fp(b), _fp(p), W, H, float(k_px),
                                           None if pp is None else pp.ctypes.data_as(C.POINTER(C.c_int64)), n,
-                                          fptr(out))
+                                          _fp(out), flag.ctypes.data_as(C.POINTER(C.c_uint8)))
     if rc != 0:
         raise ValueError("orc_imagespace_pass rejected its arguments")
-    return out
+    return (out, flag) if want_flag else out
 
 
-def normal_encode(n, libpath=None):
-    return int(lib(libpath).orc_normal_encode(_dp(_vec(n))))
+def rgbz_to_image(rgbz):
+    """Oracle pass output (n, 4) float64 -> float32 image rows."""
+    return np.asarray(rgbz, dtype=np.float32).copy()
 
 
-def normal_decode(code, libpath=None):
-    out = np.zeros(3)
-    ok = lib(libpath).orc_normal_decode(int(code) & 0xffffffff, _dp(out))
-    return out, bool(ok)
-
-
-def rgbz_to_image(rgbz, mapping):
-    """Oracle pass output (n, 4) float64 -> float32 image rows; for the normal
-    mapping the fourth lane's value is the 32-bit normal code, stored as bits."""
-    out = np.asarray(rgbz, dtype=np.float32).copy()
-    if mapping == MAP_NORMAL:
-        out[:, 3] = np.asarray(rgbz[:, 3], dtype=np.uint64).astype(np.uint32).view(np.float32)
-    return out
-
-
-def sample_image(img, W, H, px, py, mapping=MAP_EYE, libpath=None):
+def sample_image(img, W, H, px, py, libpath=None):
     a = np.ascontiguousarray(img, dtype=np.float32).reshape(-1)
     out = np.zeros(4)
-    rc = lib(libpath).orc_sample_image(a.ctypes.data_as(C.POINTER(C.c_float)), W, H, float(px), float(py), mapping,
-                                       _dp(out))
+    rc = lib(libpath).orc_sample_image(_fp(a), W, H, float(px), float(py), _dp(out))
     if rc != 0:
         raise ValueError("orc_sample_image rejected its arguments")
     return out
 
 
-def camera_ray_at(cam, W, H, px, py, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, libpath=None):
-    o = np.zeros(3)
-    d = np.zeros(3)
-    rc = lib(libpath).orc_camera_ray_at(_dp(_vec(cam)), W, H, float(px), float(py), mapping, k, f, z0, _dp(_vec(c)),
-                                        z, _dp(o), _dp(d))
-    return o, d, rc
+def nearest_pixel(W, H, px, py, libpath=None):
+    return int(lib(libpath).orc_nearest_pixel(W, H, float(px), float(py)))

@@ -138,19 +138,21 @@ double orc_scene_diam(const orc_scene* s) { return s ? s->diam : 0.0; }
  *                                          first line the paper prints as P'_p)
  * TARGET: P'_e = P_e,     P'_p = P_p + V   (V_e = 0; §3's example)
  * DEPTH:  P'_e = P_e,     P'_p = P_p + |z - z0| V   (§4, Eq. 7)
+ * NORMAL: P'_e = P_e,     P'_p = P_p + k (C x N)    (§5, Eq. 8), C = the unit
+ *         pinhole direction (P_p - P_e)/|P_p - P_e|, N = the previous normal
  * Ray: origin P'_e, direction (P'_p - P'_e) / |P'_p - P'_e|   (Eq. 2).
  */
 int orc_camera_ray(const double cam[10], int W, int H, int x, int y, int mapping,
-                   double k, double f, double z0, const double c[3], double z,
+                   double k, double f, double z0, const double c[3], double z, const double nrm[3],
                    double o[3], double d[3]) {
-    return orc_camera_ray_at(cam, W, H, (double)x + 0.5, (double)y + 0.5, mapping, k, f, z0, c, z, o, d);
+    return orc_camera_ray_at(cam, W, H, (double)x + 0.5, (double)y + 0.5, mapping, k, f, z0, c, z, nrm, o, d);
 }
 
 /* The same camera for a sample at pixel coordinates (px, py): (u, v) =
  * (px/W, py/H); the pixel centre is (x + 0.5, y + 0.5) (§2 allows any number
  * of jittered samples per pixel). */
 int orc_camera_ray_at(const double cam[10], int W, int H, double px, double py, int mapping,
-                      double k, double f, double z0, const double c[3], double z,
+                      double k, double f, double z0, const double c[3], double z, const double nrm[3],
                       double o[3], double d[3]) {
     const double* Pe = cam;
     double F[3], R[3], U[3];
@@ -170,11 +172,12 @@ int orc_camera_ray_at(const double cam[10], int W, int H, double px, double py, 
     const double dr = 2.0 * c[0] - 1.0, dg = 2.0 * c[1] - 1.0, db = 2.0 * c[2] - 1.0;
     for (int a = 0; a < 3; ++a) V[a] = k * (dr * R[a] + dg * U[a] + db * F[a]);
     if (mapping == ORC_MAP_NORMAL) {
-        /* §5, Eq. 8: V_p = k (C x N); z carries the previous pass's normal code */
-        double N[3], C[3], X[3];
+        /* §5, Eq. 8: V_p = k (C x N), C the undisplaced pinhole direction and
+           N the previous pass's hit normal (none: no displacement) */
+        double N[3] = {0.0, 0.0, 0.0}, C[3], X[3];
+        if (nrm) memcpy(N, nrm, sizeof(N));
         sub3(Pp, Pe, C);
         normalize3(C);
-        orc_normal_decode((uint32_t)z, N);
         cross3(C, N, X);
         for (int a = 0; a < 3; ++a) V[a] = k * X[a];
     }
@@ -411,7 +414,24 @@ int orc_trace_closest(const orc_scene* s, const double o[3], const double d[3],
                 ts[r] - tb <= band_b * (1.0 / cos_b + 1.0 / cz)) amb = 1;
         }
     }
-    *flag = amb;
+    int fl = amb ? ORC_FLAG_ID : 0;
+    /* The hit point of the best primitive itself: a sphere hit near its
+     * silhouette (the two roots nearly meet) or with a root near t_min (the
+     * near and far roots may swap) is ill-conditioned, so even the same sphere
+     * may be hit at another point and shaded differently. */
+    if (best_id >= s->T) {
+        const double* sp = s->sph + 4 * (best_id - s->T);
+        double t0, t1, pl, oc[3];
+        sub3(o, sp, oc);
+        const double bc = band_at(-dot3(oc, d), on, 0.0);
+        sphere_roots(sp, o, d, &t0, &t1, &pl);
+        int ill = fabs(pl - sp[3]) <= bc;
+        const double ts[2] = {t0, t1};
+        for (int r = 0; r < 2; ++r)
+            if (fabs(ts[r] - tmin) <= band_at(ts[r], on, 0.0) / hit_cos(s, best_id, o, d, ts[r])) ill = 1;
+        if (ill) fl |= ORC_FLAG_ID | ORC_FLAG_POINT;
+    }
+    *flag = fl;
     return 0;
 }
 
@@ -482,9 +502,10 @@ int orc_trace_any(const orc_scene* s, const double o[3], const double d[3], doub
  *    and runs over (0, |light - (p + eps N)|) (point) or (0, inf).
  *  - miss: sky(d) = (1 - s) (1,1,1) + s (0.5, 0.7, 1.0), s = (d_y + 1) / 2.
  *  - each channel clamped to [0, 1] (the paper's low-dynamic-range images, §3).
- * rgbz[3] = hit distance, or -1 on a miss.
+ * rgbz[3] = hit distance along d, or -1 on a miss; nrm (nullable) = the unit
+ * normal N facing the ray (zero on a miss).
  */
-int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], double rgbz[4],
+int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], double rgbz[4], double nrm[3],
                   int64_t* prim, int* flag) {
     const double tmin = 1e-6 * s->diam;
     const double eps = 1e-4 * s->diam;
@@ -493,6 +514,7 @@ int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], doub
     int amb = 0;
     orc_trace_closest(s, o, d, tmin, INFINITY, &t, &id, &amb);
     *prim = id;
+    if (nrm) nrm[0] = nrm[1] = nrm[2] = 0.0;
     if (id < 0) {
         const double sv = 0.5 * (d[1] + 1.0);
         rgbz[0] = (1.0 - sv) + sv * 0.5;
@@ -503,6 +525,7 @@ int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], doub
         double p[3], N[3], L[3];
         for (int a = 0; a < 3; ++a) p[a] = o[a] + t * d[a];
         hit_normal(s, id, p, d, N);
+        if (nrm) memcpy(nrm, N, sizeof(N));
         if (s->light_type == ORC_LIGHT_POINT) {
             sub3(s->light, p, L);
             normalize3(L);
@@ -524,7 +547,7 @@ int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], doub
             int occ = 0, samb = 0;
             orc_trace_any(s, ps, ls, 0.0, tmax, t + norm3(o), &occ, &samb);
             vis = occ ? 0.0 : 1.0;
-            amb |= samb;
+            if (samb) amb |= ORC_FLAG_SHADOW;
         }
         const double lam = ndl > 0.0 ? ndl : 0.0;
         const double* alb = s->albedo + 3 * id;
@@ -543,76 +566,44 @@ typedef struct {
     const double* cam;
     int W, H, K, mapping;
     double k, f, z0;
-    const float* in;
-    const double* in_d;  /* previous image in double (multi-sample chains) */
-    int spp;             /* samples per pixel, 0 = one at the centre */
-    const float* jitter; /* spp (dx, dy) offsets inside the pixel */
+    const float* in;       /* previous image (float32 H*W*4), NULL = I_0 */
+    const double* in_d;    /* previous image in double (multi-sample chains) */
+    const double* in_n;    /* previous hit normals (H*W*3), NULL = none */
+    int spp;               /* samples per pixel, 0 = one at the centre */
+    const float* jitter;   /* spp (dx, dy) offsets inside the pixel */
     const int64_t* pix;
     int64_t npix;
     double* out;
+    double* out_n;
     int32_t* prim;
     uint8_t* flag;
     int64_t next, chunk;
     pthread_mutex_t mu;
 } job_t;
 
-/* ---------------------------------------------------------------- normals */
-
-/* Octahedral map of a unit vector (the sphere folded onto the octahedron
- * |x|+|y|+|z| = 1 and unfolded into the square [-1,1]^2), then 16 bits per
- * coordinate. Reading: §5 stores normals with the image; the code packs one
- * into the image's fourth float lane. */
-uint32_t orc_normal_encode(const double n[3]) {
-    const double s = fabs(n[0]) + fabs(n[1]) + fabs(n[2]);
-    if (!(s > 0.0)) return 0;
-    double px = n[0] / s, py = n[1] / s;
-    if (n[2] < 0.0) {
-        const double ox = px, oy = py;
-        px = (1.0 - fabs(oy)) * (ox >= 0.0 ? 1.0 : -1.0);
-        py = (1.0 - fabs(ox)) * (oy >= 0.0 ? 1.0 : -1.0);
-    }
-    const long qx = lround(px * 32767.0), qy = lround(py * 32767.0);
-    return (uint32_t)(qx + 32768) | ((uint32_t)(qy + 32768) << 16);
+/* Unit view axis F = (look_at - eye)/|look_at - eye| of the base camera. */
+static void camera_forward(const double cam[10], double F[3]) {
+    sub3(cam + 3, cam, F);
+    normalize3(F);
 }
 
-int orc_normal_decode(uint32_t code, double n[3]) {
-    if (code == 0) {
-        n[0] = n[1] = n[2] = 0.0;
-        return 0;
-    }
-    const double px = ((double)(code & 0xffffu) - 32768.0) / 32767.0;
-    const double py = ((double)(code >> 16) - 32768.0) / 32767.0;
-    double x = px, y = py;
-    const double zz = 1.0 - fabs(px) - fabs(py);
-    if (zz < 0.0) {
-        x = (1.0 - fabs(py)) * (px >= 0.0 ? 1.0 : -1.0);
-        y = (1.0 - fabs(px)) * (py >= 0.0 ? 1.0 : -1.0);
-    }
-    n[0] = x;
-    n[1] = y;
-    n[2] = zz;
-    normalize3(n);
-    return 1;
-}
-
-/* The facing geometric normal of the primary hit of ray (o, d), 0 on a miss. */
-static uint32_t hit_normal_code(const orc_scene* s, const double o[3], const double d[3], int64_t id, double t) {
-    if (id < 0) return 0;
-    double p[3], N[3];
-    for (int a = 0; a < 3; ++a) p[a] = o[a] + t * d[a];
-    hit_normal(s, id, p, d, N);
-    return orc_normal_encode(N);
+/*
+ * z-depth of a primary hit (reading of §4 and §6: "z-depth" is depth along the
+ * camera's view axis, as a game engine's scene depth is): the hit point's
+ * distance from the pixel's eye measured along the base camera's forward axis
+ * F, z = t (d . F); 0 on a miss.
+ */
+static double z_depth(const double d[3], const double F[3], int64_t id, double t) {
+    return id < 0 ? 0.0 : t * dot3(d, F);
 }
 
 /*
  * The previous image seen by a sample at pixel coordinates (px, py): bilinear
  * between the four nearest pixel centres, indices clamped at the edges (§2's
- * (u,v) need not sit on a pixel centre). For the normal mapping the fourth
- * lane is a code, so it comes from the nearest pixel instead. in_f or in_d
- * (float or double H*W*4 image); both NULL = I_0.
+ * (u,v) need not sit on a pixel centre). in_f or in_d (float or double H*W*4
+ * image); both NULL = I_0.
  */
-static void sample_prev(const float* in_f, const double* in_d, int W, int H, double px, double py, int mapping,
-                        double c[4]) {
+static void sample_prev(const float* in_f, const double* in_d, int W, int H, double px, double py, double c[4]) {
     if (!in_f && !in_d) {
         c[0] = c[1] = c[2] = 0.5;
         c[3] = 0.0;
@@ -636,82 +627,81 @@ static void sample_prev(const float* in_f, const double* in_d, int W, int H, dou
             }
         c[a] = acc;
     }
-    if (mapping == ORC_MAP_NORMAL) {
-        int64_t nx = (int64_t)floor(qx + 0.5), ny = (int64_t)floor(qy + 0.5);
-        nx = nx < 0 ? 0 : (nx >= W ? W - 1 : nx);
-        ny = ny < 0 ? 0 : (ny >= H ? H - 1 : ny);
-        const int64_t idx = 4 * (ny * W + nx) + 3;
-        if (in_f) {
-            uint32_t bits;
-            memcpy(&bits, in_f + idx, 4);
-            c[3] = (double)bits;
-        } else {
-            c[3] = in_d[idx];
-        }
-    }
 }
 
-int orc_sample_image(const float* in, int W, int H, double px, double py, int mapping, double c[4]) {
+/* The pixel whose centre is nearest to (px, py), clamped to the image: a
+ * normal is a direction, not a quantity to blend, so a sample takes its
+ * nearest pixel's. */
+int64_t orc_nearest_pixel(int W, int H, double px, double py) {
+    int64_t nx = (int64_t)floor(px), ny = (int64_t)floor(py);
+    nx = nx < 0 ? 0 : (nx >= W ? W - 1 : nx);
+    ny = ny < 0 ? 0 : (ny >= H ? H - 1 : ny);
+    return ny * W + nx;
+}
+
+int orc_sample_image(const float* in, int W, int H, double px, double py, double c[4]) {
     if (!in || W < 1 || H < 1) return -1;
-    sample_prev(in, NULL, W, H, px, py, mapping, c);
+    sample_prev(in, NULL, W, H, px, py, c);
     return 0;
 }
 
 /* One pass of one pixel with J->spp jittered samples: each sample reads I_{n-1}
  * at its own (u,v), gets its own camera and is traced and shaded; the pixel is
- * the mean of its samples (colour and depth; the normal mapping keeps sample
- * 0's normal code). Reading: §2's anti-aliasing samples are averaged. */
+ * the mean of its samples (colour and depth; the normal is sample 0's).
+ * Reading: §2's anti-aliasing samples are averaged. */
 static void run_pixel_ms(const job_t* J, int64_t i) {
     const int64_t p = J->pix ? J->pix[i] : i;
     const int x = (int)(p % J->W), y = (int)(p / J->W);
-    double acc[4] = {0, 0, 0, 0};
+    double F[3];
+    camera_forward(J->cam, F);
+    double acc[4] = {0, 0, 0, 0}, n0[3] = {0, 0, 0};
     uint8_t fl = 0;
     int64_t id0 = -1;
-    double code0 = 0.0;
     for (int s = 0; s < J->spp; ++s) {
         const double px = (double)x + (double)J->jitter[2 * s], py = (double)y + (double)J->jitter[2 * s + 1];
-        double c[4], o[3], d[3], rgbz[4];
-        sample_prev(J->in, J->in_d, J->W, J->H, px, py, J->mapping, c);
+        double c[4], o[3], d[3], rgbt[4], ns[3];
+        const double* nin = J->in_n ? J->in_n + 3 * orc_nearest_pixel(J->W, J->H, px, py) : NULL;
+        sample_prev(J->in, J->in_d, J->W, J->H, px, py, c);
         int amb = 0;
         int64_t id = -1;
-        if (orc_camera_ray_at(J->cam, J->W, J->H, px, py, J->mapping, J->k, J->f, J->z0, c, c[3], o, d)) fl = 1;
-        orc_shade_ray(J->s, o, d, rgbz, &id, &amb);
+        if (orc_camera_ray_at(J->cam, J->W, J->H, px, py, J->mapping, J->k, J->f, J->z0, c, c[3], nin, o, d))
+            fl |= ORC_FLAG_ID | ORC_FLAG_POINT;
+        orc_shade_ray(J->s, o, d, rgbt, ns, &id, &amb);
         fl |= (uint8_t)amb;
-        if (rgbz[3] < 0.0) rgbz[3] = 0.0;
-        for (int a = 0; a < 4; ++a) acc[a] += rgbz[a];
+        for (int a = 0; a < 3; ++a) acc[a] += rgbt[a];
+        acc[3] += z_depth(d, F, id, rgbt[3]);
         if (s == 0) {
             id0 = id;
-            if (J->mapping == ORC_MAP_NORMAL) code0 = (double)hit_normal_code(J->s, o, d, id, rgbz[3]);
+            memcpy(n0, ns, sizeof(n0));
         }
     }
     for (int a = 0; a < 4; ++a) J->out[4 * i + a] = acc[a] / (double)J->spp;
-    if (J->mapping == ORC_MAP_NORMAL) J->out[4 * i + 3] = code0;
+    if (J->out_n) memcpy(J->out_n + 3 * i, n0, sizeof(n0));
     if (J->prim) J->prim[i] = (int32_t)id0;
     if (J->flag) J->flag[i] = fl;
 }
 
-/* One pixel's chain of `passes` passes starting from colour c (I_{n-1}). */
-static void run_pixel(const job_t* J, int64_t i, double c[4], int passes) {
+/* One pixel's chain of `passes` passes starting from I_{n-1} = (c, nrm):
+ * colour and z-depth in c, the hit normal in nrm. */
+static void run_pixel(const job_t* J, int64_t i, double c[4], double nrm[3], int passes) {
     const int64_t p = J->pix ? J->pix[i] : i;
     const int x = (int)(p % J->W), y = (int)(p / J->W);
+    double F[3];
+    camera_forward(J->cam, F);
     uint8_t fl = 0;
     int64_t id = -1;
     for (int n = 0; n < passes; ++n) {
-        double o[3], d[3], rgbz[4];
+        double o[3], d[3], rgbt[4];
         int amb = 0;
-        if (orc_camera_ray(J->cam, J->W, J->H, x, y, J->mapping, J->k, J->f, J->z0, c, c[3], o, d)) fl = 1;
-        orc_shade_ray(J->s, o, d, rgbz, &id, &amb);
+        if (orc_camera_ray(J->cam, J->W, J->H, x, y, J->mapping, J->k, J->f, J->z0, c, c[3], nrm, o, d))
+            fl |= ORC_FLAG_ID | ORC_FLAG_POINT;
+        orc_shade_ray(J->s, o, d, rgbt, nrm, &id, &amb);
         fl |= (uint8_t)amb;
-        memcpy(c, rgbz, sizeof(double) * 4);
-        if (J->mapping == ORC_MAP_NORMAL)
-            c[3] = (double)hit_normal_code(J->s, o, d, id, rgbz[3]); /* the lane carries the normal code */
-        else if (c[3] < 0.0)
-            c[3] = 0.0; /* a miss carries depth 0 into the next pass */
+        memcpy(c, rgbt, sizeof(double) * 3);
+        c[3] = z_depth(d, F, id, rgbt[3]);
     }
-    J->out[4 * i + 0] = c[0];
-    J->out[4 * i + 1] = c[1];
-    J->out[4 * i + 2] = c[2];
-    J->out[4 * i + 3] = c[3];
+    memcpy(J->out + 4 * i, c, sizeof(double) * 4);
+    if (J->out_n) memcpy(J->out_n + 3 * i, nrm, sizeof(double) * 3);
     if (J->prim) J->prim[i] = (int32_t)id;
     if (J->flag) J->flag[i] = fl;
 }
@@ -730,17 +720,12 @@ static void* worker(void* arg) {
             continue;
         }
         for (int64_t i = i0; i < i1; ++i) {
-            double c[4] = {0.5, 0.5, 0.5, 0.0};
-            if (J->in) {
-                const int64_t p = J->pix ? J->pix[i] : i;
+            const int64_t p = J->pix ? J->pix[i] : i;
+            double c[4] = {0.5, 0.5, 0.5, 0.0}, nrm[3] = {0.0, 0.0, 0.0};
+            if (J->in)
                 for (int a = 0; a < 4; ++a) c[a] = (double)J->in[4 * p + a];
-                if (J->mapping == ORC_MAP_NORMAL) {
-                    uint32_t bits;
-                    memcpy(&bits, J->in + 4 * p + 3, 4);
-                    c[3] = (double)bits;
-                }
-            }
-            run_pixel(J, i, c, J->K);
+            if (J->in_n) memcpy(nrm, J->in_n + 3 * p, sizeof(nrm));
+            run_pixel(J, i, c, nrm, J->K);
         }
     }
     return NULL;
@@ -774,32 +759,37 @@ static int check_common(const orc_scene* s, const double* cam, int W, int H, int
     return 0;
 }
 
-int orc_render_pass(const orc_scene* s, const double cam[10], int W, int H, int mapping,
-                    double k, double f, double z0, const float* in_rgbz, const int64_t* pix,
-                    int64_t npix, double* out_rgbz, int32_t* out_prim, uint8_t* out_flag,
-                    int nthreads) {
-    if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz) return -1;
-    if (!pix) npix = (int64_t)W * H;
+static int check_pix(const int64_t* pix, int64_t npix, int W, int H) {
     for (int64_t i = 0; pix && i < npix; ++i)
         if (pix[i] < 0 || pix[i] >= (int64_t)W * H) return -1;
+    return 0;
+}
+
+int orc_render_pass(const orc_scene* s, const double cam[10], int W, int H, int mapping,
+                    double k, double f, double z0, const float* in_rgbz, const double* in_normal,
+                    const int64_t* pix, int64_t npix, double* out_rgbz, double* out_normal,
+                    int32_t* out_prim, uint8_t* out_flag, int nthreads) {
+    if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz) return -1;
+    if (!pix) npix = (int64_t)W * H;
+    if (check_pix(pix, npix, W, H)) return -1;
     job_t J;
     memset(&J, 0, sizeof(J));
     J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = 1; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
-    J.in = in_rgbz; J.pix = pix; J.npix = npix; J.out = out_rgbz; J.prim = out_prim; J.flag = out_flag;
+    J.in = in_rgbz; J.in_n = in_normal; J.pix = pix; J.npix = npix; J.out = out_rgbz; J.out_n = out_normal;
+    J.prim = out_prim; J.flag = out_flag;
     return run_job(&J, nthreads);
 }
 
 int orc_render(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping,
                double k, double f, double z0, const int64_t* pix, int64_t npix,
-               double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads) {
+               double* out_rgbz, double* out_normal, int32_t* out_prim, uint8_t* out_flag, int nthreads) {
     if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz || K < 1) return -1;
     if (!pix) npix = (int64_t)W * H;
-    for (int64_t i = 0; pix && i < npix; ++i)
-        if (pix[i] < 0 || pix[i] >= (int64_t)W * H) return -1;
+    if (check_pix(pix, npix, W, H)) return -1;
     job_t J;
     memset(&J, 0, sizeof(J));
     J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = K; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
-    J.in = NULL; J.pix = pix; J.npix = npix; J.out = out_rgbz; J.prim = out_prim; J.flag = out_flag;
+    J.pix = pix; J.npix = npix; J.out = out_rgbz; J.out_n = out_normal; J.prim = out_prim; J.flag = out_flag;
     return run_job(&J, nthreads);
 }
 
@@ -811,31 +801,37 @@ static int check_jitter(int spp, const float* jitter) {
 }
 
 int orc_render_pass_ms(const orc_scene* s, const double cam[10], int W, int H, int mapping, double k, double f,
-                       double z0, int spp, const float* jitter, const float* in_rgbz, const int64_t* pix,
-                       int64_t npix, double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads) {
+                       double z0, int spp, const float* jitter, const float* in_rgbz, const double* in_normal,
+                       const int64_t* pix, int64_t npix, double* out_rgbz, double* out_normal, int32_t* out_prim,
+                       uint8_t* out_flag, int nthreads) {
     if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz || check_jitter(spp, jitter)) return -1;
     if (!pix) npix = (int64_t)W * H;
-    for (int64_t i = 0; pix && i < npix; ++i)
-        if (pix[i] < 0 || pix[i] >= (int64_t)W * H) return -1;
+    if (check_pix(pix, npix, W, H)) return -1;
     job_t J;
     memset(&J, 0, sizeof(J));
     J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = 1; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
-    J.in = in_rgbz; J.spp = spp; J.jitter = jitter;
-    J.pix = pix; J.npix = npix; J.out = out_rgbz; J.prim = out_prim; J.flag = out_flag;
+    J.in = in_rgbz; J.in_n = in_normal; J.spp = spp; J.jitter = jitter;
+    J.pix = pix; J.npix = npix; J.out = out_rgbz; J.out_n = out_normal; J.prim = out_prim; J.flag = out_flag;
     return run_job(&J, nthreads);
 }
 
 /* K multi-sample passes from I_0 over the whole image (a sample reads its
  * neighbours' previous values, so chains are no longer per pixel); the image
- * is carried in double between passes. out_flag = OR over the passes. */
+ * and the normals are carried in double between passes. out_flag = OR over
+ * the passes. */
 int orc_render_ms(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping, double k, double f,
-                  double z0, int spp, const float* jitter, double* out_rgbz, uint8_t* out_flag, int nthreads) {
+                  double z0, int spp, const float* jitter, double* out_rgbz, double* out_normal, uint8_t* out_flag,
+                  int nthreads) {
     if (check_common(s, cam, W, H, mapping, k, f) || !out_rgbz || K < 1 || check_jitter(spp, jitter)) return -1;
     const int64_t P = (int64_t)W * H;
     double* prev = (double*)malloc(sizeof(double) * 4 * P);
+    double* nprev = (double*)malloc(sizeof(double) * 3 * P);
+    double* ncur = (double*)malloc(sizeof(double) * 3 * P);
     uint8_t* fl = (uint8_t*)calloc((size_t)P, 1);
-    if (!prev || !fl) {
+    if (!prev || !nprev || !ncur || !fl) {
         free(prev);
+        free(nprev);
+        free(ncur);
         free(fl);
         return -1;
     }
@@ -844,13 +840,17 @@ int orc_render_ms(const orc_scene* s, const double cam[10], int W, int H, int K,
         job_t J;
         memset(&J, 0, sizeof(J));
         J.s = s; J.cam = cam; J.W = W; J.H = H; J.K = 1; J.mapping = mapping; J.k = k; J.f = f; J.z0 = z0;
-        J.in_d = n == 0 ? NULL : prev; J.spp = spp; J.jitter = jitter;
-        J.npix = P; J.out = out_rgbz; J.flag = fl;
+        J.in_d = n == 0 ? NULL : prev; J.in_n = n == 0 ? NULL : nprev; J.spp = spp; J.jitter = jitter;
+        J.npix = P; J.out = out_rgbz; J.out_n = ncur; J.flag = fl;
         run_job(&J, nthreads);
         memcpy(prev, out_rgbz, sizeof(double) * 4 * P);
+        memcpy(nprev, ncur, sizeof(double) * 3 * P);
         for (int64_t i = 0; out_flag && i < P; ++i) out_flag[i] |= fl[i];
     }
+    if (out_normal) memcpy(out_normal, ncur, sizeof(double) * 3 * P);
     free(prev);
+    free(nprev);
+    free(ncur);
     free(fl);
     return 0;
 }
@@ -875,27 +875,39 @@ int64_t orc_mirror_index(int64_t i, int64_t n) {
 /*
  * One image-space pass (§6, §6.1). Reading: the displacement is Eq. 5's
  * k (2c - 1) restricted to the screen plane (B moves along the view axis and
- * does not move a pixel), k_px being k in pixels; the sample is the nearest
- * pixel. float32 arithmetic with no fused multiply-add (built with
- * -ffp-contract=off) decides the pixel, in the order written here.
+ * does not move a pixel), k_px being k in pixels, red to the right and green
+ * up (towards row 0); the sample is the nearest pixel, halves rounding up.
+ * Computed in double from the float32 inputs.
+ *
+ * The flag marks samples whose displaced coordinate lies within
+ * ORC_IMG_TOL (|x| + k_px + 1) of a half-integer, the boundary between two
+ * nearest pixels: evaluating x + k (2c - 1) and the rounding in float32 errs by
+ * at most a few units of 2^-24 of those magnitudes, so outside the band every
+ * correct float32 evaluation takes the same pixel.
  */
-int orc_imagespace_pass(const float* base, const float* prev, int W, int H, float k_px, const int64_t* pix,
-                        int64_t npix, float* out) {
-    if (!base || !prev || !out || W < 1 || H < 1 || !(k_px >= 0.0f)) return -1;
+static int near_half(double s, double band) {
+    const double frac = s - floor(s); /* in [0, 1) */
+    return fabs(frac - 0.5) <= band;
+}
+
+int orc_imagespace_pass(const float* base, const float* prev, int W, int H, double k_px, const int64_t* pix,
+                        int64_t npix, float* out, uint8_t* out_flag) {
+    if (!base || !prev || !out || W < 1 || H < 1 || !(k_px >= 0.0)) return -1;
     if (!pix) npix = (int64_t)W * H;
     for (int64_t i = 0; i < npix; ++i) {
         const int64_t p = pix ? pix[i] : i;
         if (p < 0 || p >= (int64_t)W * H) return -1;
-        const int x = (int)(p % W), y = (int)(p / W);
+        const int64_t x = p % W, y = p / W;
         const float* c = prev + 4 * p;
-        const float dr = 2.0f * c[0] - 1.0f;
-        const float dg = 2.0f * c[1] - 1.0f;
-        const float sx = (float)x + k_px * dr;
-        const float sy = (float)y - k_px * dg;
-        const int64_t ix = orc_mirror_index((int64_t)floorf(sx + 0.5f), W);
-        const int64_t iy = orc_mirror_index((int64_t)floorf(sy + 0.5f), H);
+        const double sx = (double)x + k_px * (2.0 * (double)c[0] - 1.0);
+        const double sy = (double)y - k_px * (2.0 * (double)c[1] - 1.0);
+        const int64_t ix = orc_mirror_index((int64_t)floor(sx + 0.5), W);
+        const int64_t iy = orc_mirror_index((int64_t)floor(sy + 0.5), H);
         if (ix < 0 || ix >= W || iy < 0 || iy >= H) return -1;
         memcpy(out + 4 * i, base + 4 * (iy * W + ix), 4 * sizeof(float));
+        if (out_flag)
+            out_flag[i] = (uint8_t)(near_half(sx, ORC_IMG_TOL * ((double)x + k_px + 1.0)) ||
+                                    near_half(sy, ORC_IMG_TOL * ((double)y + k_px + 1.0)));
     }
     return 0;
 }

@@ -40,20 +40,29 @@ extern "C" {
  * ORC_MAP_TARGET: V_e = 0, V_p = k*(2c-1) in (right, up, forward): the paper's
  *                 own example in §3.
  * ORC_MAP_DEPTH:  V_e = 0, V_p = k*|z - z0|*(2c-1) (§4, Eq. 7); z is the
- *                 previous pass's hit distance, stored beside the colour.
+ *                 previous pass's z-depth, stored beside the colour.
  * ORC_MAP_NORMAL: V_e = 0, V_p = k*(C x N) (§5, Eq. 8); C = the pixel's
  *                 undisplaced pinhole direction, N = the previous pass's hit
- *                 normal (facing its ray), carried in the image's fourth lane
- *                 as a 32-bit octahedral code (0 = no normal: I_0 and misses). */
+ *                 normal (facing its ray), carried between passes as a unit
+ *                 vector in double precision (the zero vector = no normal: I_0
+ *                 and misses). */
 enum { ORC_MAP_EYE = 0, ORC_MAP_TARGET = 1, ORC_MAP_DEPTH = 2, ORC_MAP_NORMAL = 4 };
-
-/* Octahedral unit-vector code (two 16-bit fields, each q + 32768 with
- * q = round(32767 p) in [-32767, 32767], p the octahedral coordinates), so a
- * real normal never has code 0. */
-uint32_t orc_normal_encode(const double n[3]);
-/* Returns 0 and zeroes n for code 0, else writes the unit vector and returns 1. */
-int orc_normal_decode(uint32_t code, double n[3]);
 enum { ORC_LIGHT_POINT = 0, ORC_LIGHT_DIRECTIONAL = 1 };
+
+/* Per-ray ambiguity flags (bits). A float32 renderer may legitimately differ
+ * from this oracle only where a flag is set:
+ *  ORC_FLAG_ID:     the primary hit's primitive may differ (the ray passes near
+ *                   an outline or silhouette, near an end of its t interval, or
+ *                   two surfaces are hit at nearly the same depth; also a
+ *                   degenerate camera, P'_p == P'_e);
+ *  ORC_FLAG_SHADOW: the shadow ray's occlusion may differ;
+ *  ORC_FLAG_POINT:  the primary hit point itself is ill-conditioned (a sphere
+ *                   hit grazing its silhouette or with a root near t_min, or a
+ *                   degenerate camera): even the same primitive may then be
+ *                   shaded differently. */
+#define ORC_FLAG_ID 1
+#define ORC_FLAG_SHADOW 2
+#define ORC_FLAG_POINT 4
 
 /* Relative distance under which a ray counts as ambiguous (near an edge, a
  * silhouette, an interval end or a depth tie): distance <= ORC_TOL * (t + |o|). */
@@ -74,23 +83,27 @@ double orc_scene_diam(const orc_scene* s);
 
 /* Per-pixel camera (§2 Eq. 2-4, §3 Eq. 5). cam = eye[3], look_at[3], up[3],
  * fov_y_deg. Pixel (x, y), row 0 at the top; c = previous colour (RGB in [0,1]),
- * z = previous depth (DEPTH mapping only), z0 = focus depth. Writes origin o and
- * unit direction d. Returns 0, or 1 when P'_p == P'_e (direction set to the
- * forward axis). */
+ * z = previous z-depth (DEPTH mapping), z0 = focus depth, nrm = previous unit
+ * hit normal (NORMAL mapping; NULL or the zero vector = no normal). Writes
+ * origin o and unit direction d. Returns 0, or 1 when P'_p == P'_e (direction
+ * set to the forward axis). */
 int orc_camera_ray(const double cam[10], int W, int H, int x, int y, int mapping,
-                   double k, double f, double z0, const double c[3], double z,
+                   double k, double f, double z0, const double c[3], double z, const double nrm[3],
                    double o[3], double d[3]);
 
 /* The same camera for a sample at pixel coordinates (px, py) (pixel centre =
  * (x + 0.5, y + 0.5)). */
 int orc_camera_ray_at(const double cam[10], int W, int H, double px, double py, int mapping,
-                      double k, double f, double z0, const double c[3], double z,
+                      double k, double f, double z0, const double c[3], double z, const double nrm[3],
                       double o[3], double d[3]);
 
 /* I_{n-1} as seen by a sample at pixel coordinates (px, py): bilinear between
- * the nearest pixel centres with edge clamping (the normal mapping's code lane
- * from the nearest pixel). */
-int orc_sample_image(const float* in, int W, int H, double px, double py, int mapping, double c[4]);
+ * the four nearest pixel centres (all four lanes), indices clamped to the
+ * image. */
+int orc_sample_image(const float* in, int W, int H, double px, double py, double c[4]);
+/* Index y*W + x of the pixel whose centre is nearest to (px, py), clamped to
+ * the image (halves round up): where a sample reads the previous normal. */
+int64_t orc_nearest_pixel(int W, int H, double px, double py);
 
 /* Single-primitive tests (exposed for closed-form pins). Return 1 on a hit with
  * t in (tmin, tmax) and write t. */
@@ -101,61 +114,74 @@ int orc_hit_sphere(const double c[3], double r, const double o[3], const double 
                    double tmin, double tmax, double* t);
 
 /* Closest hit over every primitive, t in (tmin, tmax). Ties in t go to the lower
- * id. prim = -1 on a miss. flag = 1 when the answer is ambiguous at ORC_TOL. */
+ * id. prim = -1 on a miss. flag = ORC_FLAG_ID and/or ORC_FLAG_POINT bits. */
 int orc_trace_closest(const orc_scene* s, const double o[3], const double d[3],
                       double tmin, double tmax, double* t, int64_t* prim, int* flag);
-/* Any hit in (tmin, tmax): occluded = 0/1, flag as above; extra_scale is added
- * to (t + |o|) in the ambiguity band (the primary ray's scale, for shadow rays). */
+/* Any hit in (tmin, tmax): occluded = 0/1, flag = 1 when the answer is
+ * ambiguous at ORC_TOL; extra_scale is added to (t + |o|) in the ambiguity band
+ * (the primary ray's scale, for shadow rays). */
 int orc_trace_any(const orc_scene* s, const double o[3], const double d[3], double tmin,
                   double tmax, double extra_scale, int* occluded, int* flag);
 
 /* Shade one primary ray: closest hit, shadow ray, Lambert + ambient, sky on a
- * miss, clamp to [0,1]. rgbz = colour and hit distance (-1 on a miss). */
-int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], double rgbz[4],
+ * miss, clamp to [0,1]. rgbt = colour and hit distance t along d (-1 on a
+ * miss); nrm (nullable) = the hit's unit normal facing the ray (zero on a
+ * miss); flag = ORC_FLAG_* bits. */
+int orc_shade_ray(const orc_scene* s, const double o[3], const double d[3], double rgbt[4], double nrm[3],
                   int64_t* prim, int* flag);
 
 /* One pass I_n = F(I_{n-1}, S) over the listed pixels (pix = NULL: all W*H in
- * row-major order; npix ignored). in_rgbz: H*W*4 floats (RGB + depth) of
- * I_{n-1}, or NULL for I_0 = (0.5,0.5,0.5), depth 0. Outputs per listed pixel:
- * out_rgbz[npix*4], out_prim[npix] (nullable), out_flag[npix] (nullable).
- * nthreads <= 0: all cores. */
+ * row-major order; npix ignored). in_rgbz: H*W*4 floats (RGB + z-depth) of
+ * I_{n-1}, or NULL for I_0 = (0.5,0.5,0.5), depth 0. in_normal: H*W*3 doubles,
+ * the previous pass's hit normals (NORMAL mapping; NULL = none). Outputs per
+ * listed pixel: out_rgbz[npix*4] (colour, z-depth of the primary hit along the
+ * base camera's view axis, 0 on a miss), out_normal[npix*3] (nullable; zero on
+ * a miss), out_prim[npix] (nullable), out_flag[npix] (nullable, ORC_FLAG_*
+ * bits). nthreads <= 0: all cores. */
 int orc_render_pass(const orc_scene* s, const double cam[10], int W, int H, int mapping,
-                    double k, double f, double z0, const float* in_rgbz, const int64_t* pix,
-                    int64_t npix, double* out_rgbz, int32_t* out_prim, uint8_t* out_flag,
-                    int nthreads);
+                    double k, double f, double z0, const float* in_rgbz, const double* in_normal,
+                    const int64_t* pix, int64_t npix, double* out_rgbz, double* out_normal,
+                    int32_t* out_prim, uint8_t* out_flag, int nthreads);
 
 /* K passes from I_0 for the listed pixels. Each pixel's chain depends only on
- * its own previous value (§3), so a subset is exact. Colour is carried in
- * double. Outputs the last pass; out_prim = last pass's prim; out_flag = OR of
- * the flags over all passes. */
+ * its own previous value (§3), so a subset is exact. Colour, depth and normal
+ * are carried in double. Outputs the last pass; out_prim = last pass's prim;
+ * out_flag = OR of the flags over all passes. */
 int orc_render(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping,
                double k, double f, double z0, const int64_t* pix, int64_t npix,
-               double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads);
+               double* out_rgbz, double* out_normal, int32_t* out_prim, uint8_t* out_flag, int nthreads);
 
 /* Multi-sample pass: spp (1..16) samples per pixel at pixel offsets jitter
  * (2*spp floats in [0,1)); each sample reads in_rgbz (full H*W*4 image or NULL
- * = I_0) at its own position, is traced and shaded; the pixel is the mean
- * (normal mapping: sample 0's code). Outputs per listed pixel as
+ * = I_0) bilinearly at its own position and in_normal (H*W*3 or NULL) at the
+ * nearest pixel, is traced and shaded; the pixel is the mean of its samples
+ * (colour and depth; the normal is sample 0's). Outputs per listed pixel as
  * orc_render_pass; out_prim = sample 0's hit. */
 int orc_render_pass_ms(const orc_scene* s, const double cam[10], int W, int H, int mapping, double k, double f,
-                       double z0, int spp, const float* jitter, const float* in_rgbz, const int64_t* pix,
-                       int64_t npix, double* out_rgbz, int32_t* out_prim, uint8_t* out_flag, int nthreads);
-/* K multi-sample passes from I_0 over the whole image (W*H*4 doubles out). */
+                       double z0, int spp, const float* jitter, const float* in_rgbz, const double* in_normal,
+                       const int64_t* pix, int64_t npix, double* out_rgbz, double* out_normal, int32_t* out_prim,
+                       uint8_t* out_flag, int nthreads);
+/* K multi-sample passes from I_0 over the whole image (W*H*4 doubles out;
+ * out_normal W*H*3, nullable). */
 int orc_render_ms(const orc_scene* s, const double cam[10], int W, int H, int K, int mapping, double k, double f,
-                  double z0, int spp, const float* jitter, double* out_rgbz, uint8_t* out_flag, int nthreads);
+                  double z0, int spp, const float* jitter, double* out_rgbz, double* out_normal, uint8_t* out_flag,
+                  int nthreads);
 
 /* Image-space pass (§6: with V_e = 0 a pass reduces to re-sampling the
- * rendered image at a displaced pixel; §6.1: mirrored screen edges). base = the frame's
- * rendered image (H*W*4), prev = I_{n-1} (H*W*4), both float32. For pixel
- * (x, y) with previous colour c, the displacement in pixels is
- *   dx = k_px * (2 c.r - 1),  dy = -k_px * (2 c.g - 1)   (R right, G up: Eq. 5)
- * the sample is the nearest pixel to (x + dx, y + dy), reflected into the
- * image without repeating the edge pixel (-1 -> 0, W -> W-1, repeatedly), and
- * I_n(x, y) = base at that pixel (all four lanes). The displacement and the
- * rounding are done in float32, the precision of the pixel grid decision.
+ * rendered image at a displaced pixel; §6.1: mirrored screen edges). base = the
+ * frame's rendered image (H*W*4), prev = I_{n-1} (H*W*4), both float32,
+ * widened exactly. For pixel (x, y) with previous colour c, in double:
+ *   sx = x + k_px * (2 c.r - 1),  sy = y - k_px * (2 c.g - 1)  (R right, G up: Eq. 5)
+ * the sample is the nearest pixel (floor(s + 1/2)) to (sx, sy), reflected into
+ * the image without repeating the edge pixel (-1 -> 0, W -> W-1, repeatedly),
+ * and I_n(x, y) = base at that pixel (all four lanes).
+ * out_flag (nullable) = 1 where sx or sy lies within ORC_IMG_TOL * (|x| or |y|
+ * + k_px + 1) of a rounding boundary (a half-integer): there a renderer that
+ * evaluates the displacement in float32 may take the neighbouring pixel.
  * Writes npix*4 floats to out (pix = NULL: every pixel). */
-int orc_imagespace_pass(const float* base, const float* prev, int W, int H, float k_px, const int64_t* pix,
-                        int64_t npix, float* out);
+#define ORC_IMG_TOL 4.76837158203125e-07 /* 2^-21 */
+int orc_imagespace_pass(const float* base, const float* prev, int W, int H, double k_px, const int64_t* pix,
+                        int64_t npix, float* out, uint8_t* out_flag);
 /* The reflection of an integer pixel index into [0, n). */
 int64_t orc_mirror_index(int64_t i, int64_t n);
 

@@ -142,6 +142,7 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
         v.kR[a] = (float)(k * R[a]);
         v.kU[a] = (float)(k * U[a]);
         v.kF[a] = (float)(k * F[a]);
+        v.Fw[a] = (float)F[a];
     }
     v.W = W;
     v.H = H;
@@ -622,15 +623,16 @@ rcp_status rcp_render_device(const rcp_scene* csc, const rcp_camera* cam, int W,
 }
 
 rcp_status rcp_render_batch_device(const rcp_scene* csc, int n_views, const rcp_camera* cams, const int* Ws,
-                                   const int* Hs, int K, const rcp_params* p, float* const* d_outs, void* stream) {
+                                   const int* Hs, int K, const rcp_params* p, const float* const* d_ins,
+                                   float* const* d_outs, int32_t* const* d_prims, void* stream) {
     if (!csc || !cams || !Ws || !Hs || !d_outs || n_views < 1) {
         set_error("rcp_render_batch_device: NULL argument or no views");
         return RCP_ERR_ARG;
     }
     rcp_scene* sc = const_cast<rcp_scene*>(csc);
     std::lock_guard<std::mutex> lk(sc->mu);
-    return render_views(*sc, n_views, cams, Ws, Hs, K, p, nullptr, (float4* const*)d_outs, nullptr,
-                        (cudaStream_t)stream);
+    return render_views(*sc, n_views, cams, Ws, Hs, K, p, (const float4* const*)d_ins, (float4* const*)d_outs,
+                        d_prims, (cudaStream_t)stream);
 }
 
 static rcp_status ensure_io(RenderCtx& ctx, bool rgb, bool prim) {

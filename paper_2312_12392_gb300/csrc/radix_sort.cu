@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <string>
 
 #include "rcp_internal.cuh"
 
@@ -292,6 +293,8 @@ rcp_status static_scratch(unsigned char** out) {
 }  // namespace
 }  // namespace rcp
 
+extern "C" int64_t rcp_sort_static_capacity(void) { return rcp::STATIC_MAX; }
+
 extern "C" rcp_status rcp_sort_pairs_static(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream) {
     using namespace rcp;
     if (n < 0 || bits < 1 || bits > 32 || (n > 0 && (!keys || !values))) {
@@ -299,8 +302,9 @@ extern "C" rcp_status rcp_sort_pairs_static(uint32_t* keys, uint32_t* values, in
         return RCP_ERR_ARG;
     }
     if (n > STATIC_MAX) {
-        set_error("rcp_sort_pairs_static: n exceeds the static scratch capacity of RCP_SORT_STATIC_MAX_PAIRS "
-                  "(1048576) pairs");
+        set_error("rcp_sort_pairs_static: n = " + std::to_string(n) +
+                  " exceeds the static scratch capacity of RCP_SORT_STATIC_MAX_PAIRS (" + std::to_string(STATIC_MAX) +
+                  ") pairs");
         return RCP_ERR_ARG;
     }
     if (n <= 1) return RCP_OK;

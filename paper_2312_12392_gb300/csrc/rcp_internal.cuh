@@ -73,6 +73,7 @@ struct ViewDev {
     float E[3];
     float fF[3], fR[3], fU[3];
     float kR[3], kU[3], kF[3];
+    float Fw[3];  // unit view axis F: the z-depth of a hit is t (d . F)
     int W, H;
     int mapping;
     float z0;

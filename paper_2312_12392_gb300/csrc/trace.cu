@@ -50,13 +50,13 @@ __global__ void __launch_bounds__(256) k_camera(const ViewDev* __restrict__ view
     }
 }
 
-// Primary + shadow trace and shading of one pass. FUSED: rays are made here
-// from I_{n-1}; otherwise they are read from the camera kernel's buffer.
-// Trace, shadow and shade one camera ray; returns the pixel value.
+// Trace, shadow and shade one camera ray; returns the pixel value: RGB and
+// the hit's z-depth t (d . F) along the view axis F (0 on a miss).
 template <bool COUNT>
-__device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, uint2* stack, int stride,
-                                              int stack_entries, bool& overflow, WorkCount& wc, uint32_t& n_shadow,
-                                              uint32_t& code, int32_t& prim, const uint8_t* order_lut) {
+__device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, const float* Fw, uint2* stack,
+                                              int stride, int stack_entries, bool& overflow, WorkCount& wc,
+                                              uint32_t& n_shadow, uint32_t& code, int32_t& prim,
+                                              const uint8_t* order_lut) {
     const Hit h = traverse<false, COUNT>(S, r, stack, stride, stack_entries, overflow, wc, order_lut);
     const ShadeInfo si = shade_primary(S, r, h);
     float4 out = si.c_shadow;
@@ -65,6 +65,7 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
         const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, stride, stack_entries, overflow, wc, order_lut);
         if (hs.rec < 0) out = si.c_lit;
     }
+    out.w = h.rec < 0 ? 0.f : __fmul_rn(h.t, fdot(r.dx, r.dy, r.dz, Fw[0], Fw[1], Fw[2]));
     code = si.normal_code;
     prim = h.rec < 0 ? -1 : (int32_t)h.id;
     return out;
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                     const RayF r = camera_ray(v, px, py, c, S.tmin);
                     uint32_t code;
                     int32_t prim;
-                    const float4 o = trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow,
-                                                        code, prim, s_order);
+                    const float4 o = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stack_entries, overflow, wc,
+                                                        n_shadow, code, prim, s_order);
                     ++n_primary;
                     acc.x = __fadd_rn(acc.x, o.x);
                     acc.y = __fadd_rn(acc.y, o.y);
@@ -155,8 +156,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
             }
             uint32_t code;
             int32_t prim;
-            float4 out =
-                trace_shade<COUNT>(S, r, stack, BLOCK, stack_entries, overflow, wc, n_shadow, code, prim, s_order);
+            float4 out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stack_entries, overflow, wc, n_shadow, code,
+                                            prim, s_order);
             ++n_primary;
             if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
             v.out[p] = out;

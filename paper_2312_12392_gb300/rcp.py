@@ -94,7 +94,7 @@ _SIGS = {
     "rcp_render_device": [_vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.c_int, C.POINTER(rcp_params), _vp, _vp,
                           _vp, _vp],
     "rcp_render_batch_device": [_vp, C.c_int, C.POINTER(rcp_camera), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                C.c_int, C.POINTER(rcp_params), C.POINTER(_vp), _vp],
+                                C.c_int, C.POINTER(rcp_params), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp],
     "rcp_get_tuning": [_vp, C.POINTER(rcp_tuning)],
     "rcp_set_tuning": [_vp, C.POINTER(rcp_tuning)],
     "rcp_autotune": [_vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.POINTER(rcp_params), C.c_char_p,
@@ -109,6 +109,7 @@ _SIGS = {
     "rcp_debug_morton": [_vp, C.c_int64, _vp, _vp, _vp, _vp],
     "rcp_imagespace_pass_device": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp],
     "rcp_sort_pairs_static": [_vp, _vp, C.c_int64, C.c_int, _vp],
+    "rcp_sort_static_capacity": [],
     "rcp_server_create": [C.c_int64, C.c_int, C.POINTER(_vp)],
     "rcp_server_submit": [_vp, _vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.c_int, C.POINTER(rcp_params), _vp,
                           C.POINTER(C.c_int64)],
@@ -137,6 +138,7 @@ def lib():
             L.rcp_last_error.restype = C.c_char_p
             L.rcp_version.restype = C.c_char_p
             L.rcp_render_h2d_bytes.restype = C.c_int64
+            L.rcp_sort_static_capacity.restype = C.c_int64
             L.rcp_scene_destroy.restype = None
             L.rcp_server_destroy.restype = None
             _lib = L
@@ -285,13 +287,17 @@ def rcp_render_device(scene, cam: rcp_camera, width, height, K, params: rcp_para
                                    _ptr(d_prim), _stream(stream)), "rcp_render_device")
 
 
-def rcp_render_batch_device(scene, cams, widths, heights, K, params: rcp_params, d_outs, stream=None):
+def rcp_render_batch_device(scene, cams, widths, heights, K, params: rcp_params, d_outs, stream=None, d_ins=None,
+                            d_prims=None):
+    """d_ins / d_prims: None, or one entry per view (a device buffer or None)."""
     n = len(cams)
     ca = (rcp_camera * n)(*cams)
     wa = (C.c_int * n)(*[int(w) for w in widths])
     ha = (C.c_int * n)(*[int(h) for h in heights])
     oa = (C.c_void_p * n)(*[_ptr(o) for o in d_outs])
-    _check(lib().rcp_render_batch_device(scene, n, ca, wa, ha, K, C.byref(params), oa, _stream(stream)),
+    ia = None if d_ins is None else (C.c_void_p * n)(*[_ptr(x) for x in d_ins])
+    pa = None if d_prims is None else (C.c_void_p * n)(*[_ptr(x) for x in d_prims])
+    _check(lib().rcp_render_batch_device(scene, n, ca, wa, ha, K, C.byref(params), ia, oa, pa, _stream(stream)),
            "rcp_render_batch_device")
 
 
@@ -359,11 +365,13 @@ def rcp_debug_morton(xyz, n, lo, hi, codes, stream=None):
            "rcp_debug_morton")
 
 
-RCP_SORT_STATIC_MAX_PAIRS = 1048576
+def rcp_sort_static_capacity() -> int:
+    """The largest n rcp_sort_pairs_static accepts, as the library was built."""
+    return int(lib().rcp_sort_static_capacity())
 
 
 def rcp_sort_pairs_static(keys, values, n, bits, stream=None):
-    """Allocation-free radix sort (device arrays, n <= RCP_SORT_STATIC_MAX_PAIRS)."""
+    """Allocation-free radix sort (device arrays, n <= rcp_sort_static_capacity())."""
     _check(lib().rcp_sort_pairs_static(_ptr(keys), _ptr(values), n, bits, _stream(stream)), "rcp_sort_pairs_static")
 
 

@@ -21,8 +21,8 @@ import oracle as O
 CAM_Z = np.array([0.0, 0.0, 0.0, 0.0, 0.0, -1.0, 0.0, 1.0, 0.0, 60.0])
 
 
-def _ray(cam, W, H, x, y, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, lp=None):
-    o, d, _ = O.camera_ray(cam, W, H, x, y, mapping, k, f, c, z, z0, libpath=lp)
+def _ray(cam, W, H, x, y, mapping, k, f, c=(0.5, 0.5, 0.5), z=0.0, z0=0.0, n=None, lp=None):
+    o, d, _ = O.camera_ray(cam, W, H, x, y, mapping, k, f, c, z, z0, n=n, libpath=lp)
     return o, d
 
 
@@ -298,10 +298,10 @@ def check_closest_and_ties(lp=None):
         assert p == want and abs(t - 5) < 1e-14 and f == 0
     sc = _scene(tris=[far, near, near], albedo=[[0.5] * 3] * 3, lp=lp)
     t, p, f = sc.trace_closest([0, 0, 5], [0, 0, -1], 1e-6)
-    assert p == 1 and f == 1  # exact depth tie -> lower id, flagged
+    assert p == 1 and f == O.FLAG_ID  # exact depth tie -> lower id, flagged (same plane: point well defined)
     sc = _scene(tris=[near], spheres=[[0, 0, -1, 1]], albedo=[[0.5] * 3] * 2, lp=lp)
     t, p, f = sc.trace_closest([0, 0, 5], [0, 0, -1], 1e-6)
-    assert p == 0 and f == 1  # sphere top touches the triangle at t = 5
+    assert p == 0 and f == O.FLAG_ID  # sphere top touches the triangle at t = 5
     t, p, f = sc.trace_closest([0, 0, 5], [0, 0, -1], 5.5)
     assert p == 1 and abs(t - 7.0) < 1e-14  # t_min skips the triangle; far root of the sphere
     sc = _scene(spheres=[[0, 0, 0, 1], [0, 0, -3, 1]], albedo=[[0.5] * 3] * 2, lp=lp)
@@ -321,10 +321,22 @@ def check_flags(lp=None):
     _, p, f = sc.trace_closest([10 + 3 * band, 5, 0], [0, -1, 0], 1e-6)
     assert f == 0 and p == -1
     sc = _scene(spheres=[[0, 0, 0, 1]], albedo=[[0.5] * 3], lp=lp)
-    _, p, f = sc.trace_closest([1.0, 0, 10], [0, 0, -1], 1e-6)  # grazing the silhouette
-    assert f == 1
+    _, p, f = sc.trace_closest([1.0, 0, 10], [0, 0, -1], 1e-6)  # grazing the silhouette: hit point ill-conditioned
+    assert p == 0 and f == O.FLAG_ID | O.FLAG_POINT
+    _, p, f = sc.trace_closest([1.0 + 1e-9, 0, 10], [0, 0, -1], 1e-6)  # just outside: a miss, id ambiguous
+    assert p == -1 and f == O.FLAG_ID
     _, p, f = sc.trace_closest([0.5, 0, 10], [0, 0, -1], 1e-6)
     assert f == 0 and p == 0
+    t, p, f = sc.trace_closest([0.0, 0.0, 0.0], [0, 0, -1], 1.0 - 1e-9)  # from the centre: the root at t_min
+    assert p == 0 and t == 1.0 and f == O.FLAG_ID | O.FLAG_POINT
+    # the flag bits of a shaded ray: the ground point (1, 0, -2) seen from
+    # straight above is clear of the sphere, but its shadow ray towards
+    # L = (0, 1, 1)/sqrt(2) is tangent to the sphere (distance 1 from (0, 2, 0))
+    sc = _scene(tris=GROUND, spheres=[[0, 2, 0, 1]], albedo=[[0.5] * 3] * 3, light=(0, 1, 1), lp=lp)
+    _, p, f = sc.shade_ray([1, 10, -2], [0, -1, 0])
+    assert p in (0, 1) and f == O.FLAG_SHADOW
+    _, p, f = sc.shade_ray([1, 10, -2.5], [0, -1, 0])  # clear of the tangent: nothing ambiguous
+    assert p in (0, 1) and f == 0
 
 
 def check_any_hit(lp=None):
@@ -457,7 +469,7 @@ def check_sphere_silhouette_image(lp=None):
             # depth: the near root of the textbook quadratic
             b = np.dot(d, [0, 0, 10.0])  # d . (o - c)
             t = -b - math.sqrt(b * b - 99.0)
-            assert abs(rgbz[p, 3] - t) < 1e-9
+            assert abs(rgbz[p, 3] - t * -d[2]) < 1e-9  # z-depth along the view axis (0, 0, -1)
     assert n > 20
 
 
@@ -485,7 +497,9 @@ def check_permutation(lp=None):
 
 def check_ground_plane_image(lp=None):
     """Looking straight down on the lit ground: every pixel's colour is
-    albedo (a + (1-a) L_y) and its depth is the plane distance h / |d_y|."""
+    albedo (a + (1-a) L_y) and its z-depth (along the view axis, §4) is the
+    camera's height above the plane, whatever the pixel; the hit distance
+    along the ray is h / |d_y|."""
     L = np.array([0.3, 0.8, 0.2])
     L /= np.linalg.norm(L)
     sc = _scene(tris=GROUND, albedo=[[0.6, 0.4, 0.2]] * 2, light=L, lp=lp)
@@ -496,9 +510,19 @@ def check_ground_plane_image(lp=None):
     for p in range(W * H):
         if flag[p]:
             continue
-        _, d = _ray(cam, W, H, p % W, p // W, O.MAP_EYE, 0.0, 1.0, lp=lp)
+        o, d = _ray(cam, W, H, p % W, p // W, O.MAP_EYE, 0.0, 1.0, lp=lp)
         assert np.allclose(rgbz[p, :3], want, atol=1e-12)
-        assert abs(rgbz[p, 3] - 4.0 / -d[1]) < 1e-12
+        assert abs(rgbz[p, 3] - 4.0) < 1e-12
+        rgbt, _, _ = sc.shade_ray(o, d)
+        assert abs(rgbt[3] - 4.0 / -d[1]) < 1e-12
+    # EYE mapping: a blue displacement moves each pixel's eye along the view
+    # axis by k (2b - 1), so the plane's z-depth becomes 4 - k (2b - 1)
+    prev = np.zeros((H, W, 4), np.float32)
+    prev[..., :3] = (0.5, 0.5, 0.9)
+    rgbz, _, flag = sc.render_pass(cam, W, H, O.MAP_EYE, 0.5, 1.0, in_rgbz=prev)
+    ok = flag == 0
+    assert ok.mean() > 0.9
+    assert np.allclose(rgbz[ok, 3], 4.0 - 0.5 * (2 * np.float32(0.9) - 1), atol=1e-9)
 
 
 # --------------------------------------------------------------------------- image space (§6, §6.1)
@@ -561,9 +585,11 @@ def check_imagespace_rounding(lp=None):
     base = _ramp(W, H)
     prev = np.full((H, W, 4), 0.5, np.float32)
     prev[..., 0] = 1.0
-    for kk, shift in [(1.4, 1), (1.6, 2), (0.5, 1), (0.49, 0), (2.5, 3)]:
-        out = O.imagespace_pass(base, prev, W, H, kk, libpath=lp).reshape(H, W, 4)
+    for kk, shift, at_half in [(1.4, 1, 0), (1.6, 2, 0), (0.5, 1, 1), (0.49, 0, 0), (2.5, 3, 1)]:
+        out, fl = O.imagespace_pass(base, prev, W, H, kk, libpath=lp, want_flag=True)
+        out = out.reshape(H, W, 4)
         assert out[2, 3, 0] == 3 + shift, (kk, out[2, 3, 0])
+        assert fl.reshape(H, W)[2, 3] == at_half, kk  # a sample exactly between two pixels is flagged
     prev[..., 0] = 0.0
     out = O.imagespace_pass(base, prev, W, H, 0.5, libpath=lp).reshape(H, W, 4)
     assert out[2, 3, 0] == 3  # x - 0.5 rounds half up to x
@@ -574,59 +600,90 @@ def check_imagespace_rounding(lp=None):
 
 # --------------------------------------------------------------------------- normal mapping (§5, Eq. 8)
 
-def check_normal_codes(lp=None):
-    """Octahedral codes: round trip within 1e-4, never 0 for a real normal,
-    0 decodes to 'no normal'; the six axes come back exactly."""
-    rng = np.random.default_rng(8)
-    for _ in range(500):
-        n = rng.normal(size=3)
-        n /= np.linalg.norm(n)
-        c = O.normal_encode(n, libpath=lp)
-        m, ok = O.normal_decode(c, libpath=lp)
-        assert c != 0 and ok and np.linalg.norm(m - n) < 1e-4
-    for ax in np.vstack([np.eye(3), -np.eye(3)]):
-        m, ok = O.normal_decode(O.normal_encode(ax, libpath=lp), libpath=lp)
-        assert ok and np.allclose(m, ax, atol=1e-12)
-    m, ok = O.normal_decode(0, libpath=lp)
-    assert not ok and not m.any()
+def check_imagespace_band(lp=None):
+    """The flag marks exactly the samples within IMG_TOL (x + k + 1) of a
+    half-integer: just inside the band flagged, just outside not, and a
+    displacement that lands near an integer (a pixel centre) never flagged."""
+    W, H, x, y = 64, 3, 40, 1
+    base = _ramp(W, H)
+    prev = np.full((H, W, 4), 0.5, np.float32)
+    prev[..., 0] = 1.0  # sx = x + k exactly
+    for frac, want in [(0.5, 1), (0.5 + 0.5 * O.IMG_TOL * 48, 1), (0.5 - 0.9 * O.IMG_TOL * 48, 1),
+                       (0.5 + 1.5 * O.IMG_TOL * 48, 0), (0.0, 0), (0.999999, 0), (0.25, 0)]:
+        k = 6.0 + frac  # x + k + 1 = 47 + frac ~ 47.5
+        _, fl = O.imagespace_pass(base, prev, W, H, k, libpath=lp, want_flag=True)
+        assert fl.reshape(H, W)[y, x] == want, (frac, want)
+    # the row coordinate has its own band (y - k (2g - 1))
+    prev[..., 0] = 0.5
+    prev[..., 1] = 0.0  # sy = y + k
+    _, fl = O.imagespace_pass(base, prev, W, H, 0.5, libpath=lp, want_flag=True)
+    assert fl.reshape(H, W)[y, x] == 1
+    _, fl = O.imagespace_pass(base, prev, W, H, 0.7, libpath=lp, want_flag=True)
+    assert fl.reshape(H, W)[y, x] == 0
 
 
 def check_normal_mapping_camera(lp=None):
     """V_p = k (C x N): for the centre ray C = (0,0,-1) and N = +y the target
-    moves by +k along x (right); N along C does not move it; no normal (code
-    0, as in I_0) gives the pinhole ray."""
+    moves by +k along x (right); N along C does not move it; no normal (as in
+    I_0, or after a miss) gives the pinhole ray."""
     W, H, k, f = 21, 21, 0.7, 4.0
     x, y = W // 2, H // 2
     _, d0 = _ray(CAM_Z, W, H, x, y, O.MAP_TARGET, 0.0, f, lp=lp)
-    code_up = O.normal_encode([0.0, 1.0, 0.0], libpath=lp)
-    o, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, z=float(code_up), lp=lp)
+    o, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, n=[0.0, 1.0, 0.0], lp=lp)
     P = o + d * (f / -d[2])  # where the ray meets the focal plane z = -f
-    assert np.allclose(P, [k, 0.0, -f], atol=1e-4 * k)
-    code_back = O.normal_encode([0.0, 0.0, 1.0], libpath=lp)
-    _, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, z=float(code_back), lp=lp)
-    assert np.allclose(d, d0, atol=1e-12)
-    _, d = _ray(CAM_Z, W, H, 3, 5, O.MAP_NORMAL, k, f, z=0.0, lp=lp)
-    _, e = _ray(CAM_Z, W, H, 3, 5, O.MAP_TARGET, 0.0, f, lp=lp)
-    assert np.array_equal(d, e)
+    assert np.allclose(P, [k, 0.0, -f], atol=1e-12)
+    o, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, n=[1.0, 0.0, 0.0], lp=lp)
+    P = o + d * (f / -d[2])  # C x (+x) = (0,0,-1) x (1,0,0) = (0,-1,0): down
+    assert np.allclose(P, [0.0, -k, -f], atol=1e-12)
+    _, d = _ray(CAM_Z, W, H, x, y, O.MAP_NORMAL, k, f, n=[0.0, 0.0, 1.0], lp=lp)
+    assert np.allclose(d, d0, atol=1e-15)
+    for n in (None, [0.0, 0.0, 0.0]):
+        _, d = _ray(CAM_Z, W, H, 3, 5, O.MAP_NORMAL, k, f, n=n, lp=lp)
+        _, e = _ray(CAM_Z, W, H, 3, 5, O.MAP_TARGET, 0.0, f, lp=lp)
+        assert np.array_equal(d, e)
 
 
 def check_normal_mapping_render(lp=None):
-    """Pass 1 is pinhole (I_0 has no normal); a ground plane seen straight on
-    from above has N parallel to C at the centre, so the centre pixel keeps its
-    colour; the fourth lane carries the hit normal's code (0 on a miss)."""
+    """Pass 1 is pinhole (I_0 has no normal) and outputs each hit's normal
+    facing its ray (the ground seen from above: +y; a miss: zero); a ground
+    plane seen straight on from above has N parallel to C at the centre, so
+    the centre pixel keeps its colour in pass 2."""
     L = np.array([0.3, 0.8, 0.2])
     sc = _scene(tris=GROUND, albedo=[[0.6, 0.4, 0.2]] * 2, light=L, lp=lp)
     cam = np.array([0.3, 4.0, 0.2, 0.3, 0.0, 0.2, 0.0, 0.0, -1.0, 40.0])
     W, H = 9, 7
-    a, pa, _ = sc.render_pass(cam, W, H, O.MAP_NORMAL, 0.5, 1.0)
+    a, pa, _, na = sc.render_pass(cam, W, H, O.MAP_NORMAL, 0.5, 1.0, want_normal=True)
     b, pb, _ = sc.render_pass(cam, W, H, O.MAP_TARGET, 0.0, 1.0)
-    assert np.array_equal(a[:, :3], b[:, :3]) and np.array_equal(pa, pb)
-    up = O.normal_encode([0.0, 1.0, 0.0], libpath=lp)
-    assert np.all(a[:, 3] == up)
-    img = O.rgbz_to_image(a, O.MAP_NORMAL).reshape(H, W, 4)
-    c2, _, _ = sc.render_pass(cam, W, H, O.MAP_NORMAL, 0.5, 1.0, in_rgbz=img)
+    assert np.array_equal(a, b) and np.array_equal(pa, pb)
+    assert np.array_equal(na, np.tile([0.0, 1.0, 0.0], (W * H, 1)))
+    c2, _, _ = sc.render_pass(cam, W, H, O.MAP_NORMAL, 0.5, 1.0, in_rgbz=O.rgbz_to_image(a), in_normal=na)
     centre = (H // 2) * W + W // 2
     assert np.allclose(c2[centre, :3], a[centre, :3], atol=1e-12)
+    sky = _scene(spheres=[[30, -50, 0, 1]], albedo=[[0.5] * 3], lp=lp)  # out of view
+    _, p, _, n = sky.render_pass(cam, 3, 3, O.MAP_NORMAL, 0.5, 1.0, want_normal=True)
+    assert np.all(p == -1) and not n.any()
+
+
+def check_normal_chain(lp=None):
+    """The K-pass normal-mapping render carries each pass's hit normal into the
+    next pass's camera: it equals passes chained by hand with the normals
+    handed over, and differs from a chain that drops them."""
+    sc = _tiny(lp)
+    W, H, K, k = 18, 12, 3, 0.8
+    full, pf, ff, nf = sc.render(TINY_CAM, W, H, K, O.MAP_NORMAL, k, 6.0, want_normal=True)
+    img, nrm = None, None
+    for _ in range(K):
+        out, pr, fl, nrm = sc.render_pass(TINY_CAM, W, H, O.MAP_NORMAL, k, 6.0, in_rgbz=img, in_normal=nrm,
+                                          want_normal=True)
+        img = O.rgbz_to_image(out)
+    ok = ff == 0
+    assert ok.mean() > 0.9
+    assert np.abs(out[ok, :3] - full[ok, :3]).max() < 1e-5 and np.array_equal(pr[ok], pf[ok])
+    assert np.abs(nrm[ok] - nf[ok]).max() < 1e-9
+    lost, _, _ = sc.render_pass(TINY_CAM, W, H, O.MAP_NORMAL, k, 6.0, in_rgbz=img)  # no normals: pinhole
+    pin, _, _ = sc.render_pass(TINY_CAM, W, H, O.MAP_TARGET, 0.0, 6.0)
+    assert np.array_equal(lost[:, :3], pin[:, :3])
+    assert np.abs(full[ok, :3] - pin[ok, :3]).max() > 0.01
 
 
 # --------------------------------------------------------------------------- multi-sample passes (§2 jitter)
@@ -637,7 +694,7 @@ def check_ms_centre_is_single(lp=None):
     sc = _tiny(lp)
     W, H, k = 20, 14, 1.4
     ref, pref, _ = sc.render_pass(TINY_CAM, W, H, O.MAP_EYE, k, 6.0)
-    img = O.rgbz_to_image(ref, O.MAP_EYE).reshape(H, W, 4)
+    img = O.rgbz_to_image(ref).reshape(H, W, 4)
     for jit in ([[0.5, 0.5]], [[0.5, 0.5]] * 4):
         a, pa, _ = sc.render_pass_ms(TINY_CAM, W, H, O.MAP_EYE, k, 6.0, jit)
         assert np.array_equal(a, ref) and np.array_equal(pa, pref)
@@ -647,6 +704,10 @@ def check_ms_centre_is_single(lp=None):
     full, _ = sc.render_ms(TINY_CAM, W, H, 3, O.MAP_EYE, k, 6.0, [[0.5, 0.5]])
     chain, _, _ = sc.render(TINY_CAM, W, H, 3, O.MAP_EYE, k, 6.0)
     assert np.array_equal(full, chain)
+    # the normal mapping: a centre sample reads its own pixel's normal
+    full, _, nf = sc.render_ms(TINY_CAM, W, H, 3, O.MAP_NORMAL, k, 6.0, [[0.5, 0.5]], want_normal=True)
+    chain, _, _, nc = sc.render(TINY_CAM, W, H, 3, O.MAP_NORMAL, k, 6.0, want_normal=True)
+    assert np.array_equal(full, chain) and np.array_equal(nf, nc)
 
 
 def check_bilinear_reads(lp=None):
@@ -657,7 +718,7 @@ def check_bilinear_reads(lp=None):
     img = np.zeros((H, W, 4), np.float32)
     img[..., 0] = 0.1 * np.arange(W)[None, :]
     img[..., 1] = 0.05 * np.arange(H)[:, None]
-    img[..., 3] = (np.arange(W * H).reshape(H, W) + 1).astype(np.uint32).view(np.float32)
+    img[..., 3] = 0.01 * np.arange(W * H).reshape(H, W)
     for px, py in [(1.5, 1.5), (3.25, 2.75), (6.9, 4.1), (4.0, 3.0)]:
         c = O.sample_image(img, W, H, px, py, libpath=lp)
         assert abs(c[0] - 0.1 * (px - 0.5)) < 1e-7 and abs(c[1] - 0.05 * (py - 0.5)) < 1e-7
@@ -665,8 +726,12 @@ def check_bilinear_reads(lp=None):
     assert np.allclose(c[:2], img[0, 0, :2])
     c = O.sample_image(img, W, H, W + 3.0, H + 0.4, libpath=lp)
     assert np.allclose(c[:2], img[H - 1, W - 1, :2])
-    c = O.sample_image(img, W, H, 3.9, 2.2, O.MAP_NORMAL, libpath=lp)
-    assert int(c[3]) == 2 * W + 3 + 1
+    c = O.sample_image(img, W, H, 2.5, 1.5, libpath=lp)  # a pixel centre: that pixel, all four lanes
+    assert np.allclose(c, img[1, 2], atol=1e-7)
+    # the nearest pixel (where a sample reads a normal): the one whose square holds the point
+    assert O.nearest_pixel(W, H, 3.9, 2.2, libpath=lp) == 2 * W + 3
+    assert O.nearest_pixel(W, H, 4.0, 3.0, libpath=lp) == 3 * W + 4
+    assert O.nearest_pixel(W, H, -2.0, H + 5.0, libpath=lp) == (H - 1) * W
 
 
 def check_ms_sphere_coverage(lp=None):

@@ -82,3 +82,12 @@ def test_render_h2d_bytes(lib):
     assert rcp.rcp_render_h2d_bytes(0, 6) == -1
     assert rcp.rcp_render_h2d_bytes(1, 0) == -1
     assert rcp.rcp_render_h2d_bytes(1, 17) == -1
+
+
+def test_static_sort_capacity_matches_header(lib):
+    """The allocation-free sort's capacity as built equals the header's
+    RCP_SORT_STATIC_MAX_PAIRS, so neither the binding nor the error message can
+    go stale (a constant returned without touching the GPU)."""
+    m = re.search(r"#define\s+RCP_SORT_STATIC_MAX_PAIRS\s+(\d+)", open(HEADER).read())
+    assert m and rcp.rcp_sort_static_capacity() == int(m.group(1))
+    assert lib.rcp_sort_pairs_static(None, None, -1, 30, None) == rcp.RCP_ERR_ARG

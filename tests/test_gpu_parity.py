@@ -4,18 +4,31 @@ Workloads (seeded, see paper_2312_12392_gb300.scenes):
   * tiny: 3 spheres + ground quad, point light, 128x128, K=6, EYE mapping,
     k = 0.05 * diameter, f = 6 -- compared on every pixel;
   * mid: 133,472-triangle terrain + boxes, 1920x1080, K=6, k = 0.02 * diameter,
-    f = 0.1 * diameter -- compared on a seeded 4,096-pixel sample (each pixel's
-    chain depends only on its own previous value, so a sample is exact);
-  * forest: 1,065,522 triangles, 1920x1080, K=6 -- 1,024-pixel sample;
-  * the TARGET and DEPTH mappings on tiny, and ragged image sizes.
+    f = 0.1 * diameter -- a seeded 16,384-pixel sample on each of 3 poses (each
+    pixel's chain depends only on its own previous value, so a sample is
+    exact), the oracle run live;
+  * forest: 1,065,522 triangles, 1920x1080, K=6, in the benchmark's build
+    (surface-area collapse, split <= 8) -- 16,384 pixels on each of 3 poses,
+    against values the oracle wrote beforehand
+    (tests/golden/make_oracle_golden.py: the brute-force oracle needs about
+    ten minutes of the host's cores for them);
+  * the TARGET, DEPTH and NORMAL mappings, and ragged image sizes.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
 from paper_2312_12392_gb300 import rcp, scenes
 import gpu_util as U
 
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import make_oracle_golden as G  # noqa: E402
+
 pytestmark = pytest.mark.gpu
+
+MID_SAMPLE = 16384
 
 
 @pytest.fixture(scope="module")
@@ -58,67 +71,94 @@ def test_ragged_sizes(tiny, W, H):
     rep.assert_ok(f"tiny {W}x{H}")
 
 
+@pytest.fixture(scope="module")
+def mid_gpu(mid):
+    g = U.gpu_scene(mid)
+    yield g
+    rcp.rcp_scene_destroy(g)
+
+
 @pytest.mark.parametrize("pose", [0, 21, 42])
-def test_mid_per_pass_sample(mid, pose):
+def test_mid_per_pass_sample(mid, mid_gpu, pose):
     d = mid.diameter()
     W, H = 1920, 1080
-    pix = scenes.pixel_subset(W, H, 4096, seed=100 + pose)
-    rep = U.per_pass_parity(mid, mid.poses[pose], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix)
+    pix = scenes.pixel_subset(W, H, MID_SAMPLE, seed=100 + pose)
+    rep = U.per_pass_parity(mid, mid.poses[pose], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix, g=mid_gpu)
     print(rep.assert_ok(f"mid pose {pose}"))
 
 
-def test_mid_end_to_end_psnr(mid):
+def test_mid_end_to_end_psnr(mid, mid_gpu):
     d = mid.diameter()
     W, H = 1920, 1080
-    pix = scenes.pixel_subset(W, H, 4096, seed=7)
-    p, fl = U.end_to_end_psnr(mid, mid.poses[5], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix)
+    pix = scenes.pixel_subset(W, H, MID_SAMPLE, seed=7)
+    p, fl = U.end_to_end_psnr(mid, mid.poses[5], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix, g=mid_gpu)
     print(f"mid K=6 PSNR {p:.1f} dB, flagged chains {fl:.4f}")
     assert p >= U.PSNR_MIN
 
 
-def test_forest_per_pass_and_psnr():
-    """The forest in the bench's build (surface-area collapse, split <= 8)."""
+@pytest.fixture(scope="module")
+def forest_golden():
     sc = scenes.forest_scene()
-    d = sc.diameter()
-    W, H = 1920, 1080
-    pix = scenes.pixel_subset(W, H, 1024, seed=3)
+    d, meta = G.load("forest")
+    cams = [sc.poses[p].as_array().astype(np.float32).astype(np.float64) for p in meta["poses"]]
+    pixs = [d[f"pix_{i}"] for i in range(len(meta["poses"]))]
+    k, f = G.params_of(dict(diam=sc.diameter()))
+    assert G.input_hash(sc.tris, sc.albedo, cams, pixs, (k, f)) == meta["inputs"], "forest golden inputs differ"
     g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
-    o = U.oracle_scene(sc)
-    try:
-        rep = U.per_pass_parity(sc, sc.poses[10], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix, g=g, o=o)
-        print(rep.assert_ok("forest pose 10"))
-        p, fl = U.end_to_end_psnr(sc, sc.poses[10], W, H, 6, rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d, pix=pix, g=g, o=o)
-        print(f"forest K=6 PSNR {p:.1f} dB, flagged chains {fl:.4f}")
-        assert p >= U.PSNR_MIN
-    finally:
-        rcp.rcp_scene_destroy(g)
+    yield sc, g, d, meta
+    rcp.rcp_scene_destroy(g)
+
+
+@pytest.mark.parametrize("i", [0, 1, 2])
+def test_forest_per_pass_sample(forest_golden, i):
+    """The forest in the benchmark's build, 16,384 pixels of one pose, each
+    pass from the oracle's previous values."""
+    sc, g, d, meta = forest_golden
+    W, H, K = meta["W"], meta["H"], meta["K"]
+    pose = meta["poses"][i]
+    params = rcp.make_params(rcp.RCP_MAP_EYE, meta["k"], meta["f"])
+    cam = rcp.camera_from(sc.poses[pose])
+    pix = d[f"pix_{i}"]
+    rep = U.PassReport()
+    img = None
+    for n in range(K):
+        prim = np.empty(H * W, np.int32)
+        out = rcp.rcp_render_pass(g, cam, W, H, params, in_rgbz=img, out_prim=prim)
+        o_rgbz = d[f"rgbz_{i}"][n].astype(np.float64)
+        rep.add(out.reshape(-1, 4)[pix], prim[pix], o_rgbz, d[f"prim_{i}"][n], d[f"flag_{i}"][n])
+        img = U.next_image(out, pix, o_rgbz, rcp.RCP_MAP_EYE).reshape(H, W, 4)
+    print(rep.assert_ok(f"forest pose {pose}"))
+
+
+def test_forest_end_to_end_psnr(forest_golden):
+    sc, g, d, meta = forest_golden
+    i = int(d["e2e_index"])
+    W, H, K = meta["W"], meta["H"], meta["K"]
+    out = rcp.rcp_render(g, rcp.camera_from(sc.poses[meta["poses"][i]]), W, H, K,
+                         rcp.make_params(rcp.RCP_MAP_EYE, meta["k"], meta["f"]))
+    p = U.psnr(out.reshape(-1, 3)[d[f"pix_{i}"]], d["e2e_rgb"])
+    print(f"forest K={K} PSNR {p:.1f} dB, flagged chains {float((d['e2e_flag'] != 0).mean()):.4f}")
+    assert p >= U.PSNR_MIN
 
 
 @pytest.mark.parametrize("scene_name", ["tiny", "mid"])
 def test_normal_mapping(scene_name, tiny, mid):
-    """§5, Eq. 8 (V_p = k C x N): per-pass parity, and the normal codes the GPU
-    writes decode to the oracle's normals within the code's resolution."""
-    import oracle as O
+    """§5, Eq. 8 (V_p = k C x N): per-pass parity, the normal handed to both
+    sides being the oracle's previous normal in the ABI's code; the normals
+    the GPU writes decode to the oracle's within the code's resolution."""
     sc = tiny if scene_name == "tiny" else mid
     d = sc.diameter()
     if scene_name == "tiny":
         W, H, pix, f = 128, 96, None, 6.0
     else:
         W, H, f = 1920, 1080, 0.1 * d
-        pix = scenes.pixel_subset(W, H, 2048, seed=77)
+        pix = scenes.pixel_subset(W, H, 4096, seed=77)
     rep = U.per_pass_parity(sc, sc.poses[0], W, H, 4, rcp.RCP_MAP_NORMAL, 0.03 * d, f, pix=pix)
     print(rep.assert_ok(f"{scene_name} NORMAL"))
+    assert rep.normal_err > 0  # the normals were compared
     g_rgbz, o_rgbz, o_flag, g_prim, o_prim = rep.last
-    ok = (o_flag == 0) & (o_prim >= 0) & (g_prim == o_prim)
-    codes_g = g_rgbz[:, 3].view(np.uint32)
-    worst = 0.0
-    for cg, co in zip(codes_g[ok], o_rgbz[ok, 3].astype(np.uint64)):
-        ng, okg = O.normal_decode(int(cg))
-        no, oko = O.normal_decode(int(co))
-        assert okg and oko
-        worst = max(worst, float(np.linalg.norm(ng - no)))
-    assert worst < 2e-4, worst
-    assert np.all(codes_g[o_prim < 0] == 0) or not (o_prim < 0).any()
+    miss = (o_prim < 0) & (g_prim < 0)
+    assert np.all(g_rgbz[miss, 3].view(np.uint32) == 0)  # a miss carries no normal
     p, _ = U.end_to_end_psnr(sc, sc.poses[0], W, H, 4, rcp.RCP_MAP_NORMAL, 0.03 * d, f, pix=pix)
     print(f"{scene_name} NORMAL K=4 PSNR {p:.1f} dB")
     assert p >= U.PSNR_MIN

@@ -33,36 +33,60 @@ def _requests(two_scenes, n=24, seed=0):
         K = int(rng.integers(1, 9))
         cam = sc.poses[int(rng.integers(0, len(sc.poses)))]
         d = sc.diameter()
-        f = 6.0 if sc.name == "tiny" else 0.1 * d
-        p = rcp.make_params(rcp.RCP_MAP_EYE, float(rng.uniform(0, 0.05)) * d, f)
-        out.append((g, rcp.camera_from(cam), W, H, K, p))
+        f = U.f32(6.0 if sc.name == "tiny" else 0.1 * d)
+        k = U.f32(float(rng.uniform(0, 0.05)) * d)
+        p = rcp.make_params(rcp.RCP_MAP_EYE, k, f)
+        out.append(dict(sc=sc, g=g, cam=cam, W=W, H=H, K=K, k=k, f=f, p=p))
     return out
 
 
-def test_alone_equals_in_mix(two_scenes):
-    reqs = _requests(two_scenes)
-    alone = [rcp.rcp_render(g, c, W, H, K, p) for g, c, W, H, K, p in reqs]
-    srv = rcp.rcp_server_create(4 << 30, 8)
+def _serve(reqs, slots=8):
+    srv = rcp.rcp_server_create(4 << 30, slots)
     try:
         outs, tickets = [], []
-        for i, (g, c, W, H, K, p) in enumerate(reqs):
-            o = np.full((H, W, 3), -1.0, np.float32)
+        for i, r in enumerate(reqs):
+            o = np.full((r["H"], r["W"], 3), -1.0, np.float32)
             outs.append(o)
-            tickets.append(rcp.rcp_server_submit(srv, g, c, W, H, K, p, o))
+            tickets.append(rcp.rcp_server_submit(srv, r["g"], rcp.camera_from(r["cam"]), r["W"], r["H"], r["K"],
+                                                 r["p"], o))
             if i % 5 == 4:
                 time.sleep(0.002)  # arrivals while others are in flight
         for t in tickets:
             rcp.rcp_server_wait(srv, t, 60.0)
             assert rcp.rcp_server_poll(srv, t)
-        for a, o in zip(alone, outs):
-            assert np.array_equal(a, o)
-        st = rcp.rcp_server_stats_get(srv)
-        assert st.completed == len(reqs) and st.rejected == 0 and st.in_flight == 0 and st.queued == 0
-        assert st.p99_ms >= st.p50_ms > 0 and st.frames_per_s > 0 and st.mrays_per_s > 0
-        assert st.steps >= max(K for *_, K, _ in reqs)
-        assert st.device_bytes_in_use == 0 and st.device_bytes_peak > 0
+        return outs, rcp.rcp_server_stats_get(srv)
     finally:
         rcp.rcp_server_destroy(srv)
+
+
+def test_alone_equals_in_mix(two_scenes):
+    reqs = _requests(two_scenes)
+    alone = [rcp.rcp_render(r["g"], rcp.camera_from(r["cam"]), r["W"], r["H"], r["K"], r["p"]) for r in reqs]
+    outs, st = _serve(reqs)
+    for a, o in zip(alone, outs):
+        assert np.array_equal(a, o)
+    assert st.completed == len(reqs) and st.rejected == 0 and st.in_flight == 0 and st.queued == 0
+    assert st.p99_ms >= st.p50_ms > 0 and st.frames_per_s > 0 and st.mrays_per_s > 0
+    assert st.steps >= max(r["K"] for r in reqs)
+    assert st.device_bytes_in_use == 0 and st.device_bytes_peak > 0
+
+
+def test_mix_against_oracle(two_scenes):
+    """Every request of a mixed run (two scenes, uneven sizes, K from 1 to 8,
+    arrivals while others are in flight) against the FP64 oracle's K-pass
+    chains on a seeded pixel sample of its own image."""
+    reqs = _requests(two_scenes, n=24, seed=1)
+    outs, _ = _serve(reqs)
+    oscenes = {}
+    worst = np.inf
+    for i, (r, out) in enumerate(zip(reqs, outs)):
+        o = oscenes.setdefault(r["sc"].name, U.oracle_scene(r["sc"]))
+        pix = scenes.pixel_subset(r["W"], r["H"], 512, seed=i)
+        ref, _, fl = o.render(U.cam_f32(r["cam"]), r["W"], r["H"], r["K"], rcp.RCP_MAP_EYE, r["k"], r["f"], pix=pix)
+        p = U.psnr(out.reshape(-1, 3)[pix], ref[:, :3])
+        worst = min(worst, p)
+        assert p >= U.PSNR_MIN, (i, r["sc"].name, r["W"], r["H"], r["K"], p)
+    print(f"{len(reqs)} served requests against the oracle: worst PSNR {worst:.1f} dB")
 
 
 def test_memory_admission(two_scenes):

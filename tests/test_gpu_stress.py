@@ -1,6 +1,9 @@
 """Per-frame refit under wind sway (the stress workload at reduced size): after
 every swayed frame the refitted BVH is valid, its walk equals brute force over
 every primitive, and a rendered pass matches the oracle on the moved scene."""
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -8,6 +11,9 @@ torch = pytest.importorskip("torch")
 
 from paper_2312_12392_gb300 import rcp, scenes  # noqa: E402
 import gpu_util as U  # noqa: E402
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import make_oracle_golden as G  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -103,13 +109,18 @@ def test_full_size_stress_parity():
     cone trees (12.57M triangles), surface-area collapse with split <= 8,
     refitted to a swayed frame. The refitted tree validates; its walk equals
     brute force over every record on rays aimed at vertices and edges; and
-    sampled pixels of a 3840x2160, K=8 chain match the oracle pass by pass."""
+    4,096 sampled pixels of a 3840x2160, K=8 chain match the oracle pass by
+    pass (values the oracle wrote beforehand, tests/golden/make_oracle_golden.py:
+    the brute-force oracle needs about ten minutes of the host's cores for
+    them)."""
+    gd, meta = G.load("stress")
     sc = scenes.forest_scene(25_000, seed=5)
     g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
     try:
         info = rcp.rcp_scene_get_info(g)
         assert info.n_tris == 12_565_522 and info.n_records > 4 * info.n_tris
         frame = 123
+        assert meta["poses"] == [frame % len(sc.poses)]
         moved = scenes.sway_vertices(sc.tris, sc.sway_amp, sc.sway_phase, frame)
         rcp.rcp_scene_update_vertices(g, moved)
         rcp.rcp_scene_validate(g)
@@ -124,12 +135,21 @@ def test_full_size_stress_parity():
         assert (res[1][1] >= 0).sum() > n // 2
         assert np.array_equal(res[0][1], res[1][1])
         assert np.array_equal(res[0][0].view(np.uint32), res[1][0].view(np.uint32))
-        d = sc.diameter()
-        W, H = 3840, 2160
-        msc = scenes.Scene("stress moved", moved, sc.spheres, sc.albedo, sc.light, sc.poses)
-        pix = scenes.pixel_subset(W, H, 160, seed=frame)
-        rep = U.per_pass_parity(msc, sc.poses[frame % len(sc.poses)], W, H, 8, rcp.RCP_MAP_EYE, 0.02 * d,
-                                0.1 * d, pix=pix, g=g)
+        W, H, K = meta["W"], meta["H"], meta["K"]
+        cam_o = sc.poses[meta["poses"][0]].as_array().astype(np.float32).astype(np.float64)
+        pix = gd["pix_0"]
+        k, f = G.params_of(dict(diam=sc.diameter()))
+        assert G.input_hash(moved, sc.albedo, [cam_o], [pix], (k, f)) == meta["inputs"], "stress golden inputs differ"
+        params = rcp.make_params(rcp.RCP_MAP_EYE, k, f)
+        cam = rcp.camera_from(sc.poses[meta["poses"][0]])
+        rep = U.PassReport()
+        img = None
+        for n in range(K):
+            prim = np.empty(H * W, np.int32)
+            out = rcp.rcp_render_pass(g, cam, W, H, params, in_rgbz=img, out_prim=prim)
+            o_rgbz = gd["rgbz_0"][n].astype(np.float64)
+            rep.add(out.reshape(-1, 4)[pix], prim[pix], o_rgbz, gd["prim_0"][n], gd["flag_0"][n])
+            img = U.next_image(out, pix, o_rgbz, rcp.RCP_MAP_EYE).reshape(H, W, 4)
         print(rep.assert_ok(f"stress frame {frame}"))
     finally:
         rcp.rcp_scene_destroy(g)

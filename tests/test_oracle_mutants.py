@@ -40,18 +40,30 @@ MUTANTS = {
     "sky_reversed": ("rgbz[0] = (1.0 - sv) + sv * 0.5;", "rgbz[0] = sv + (1.0 - sv) * 0.5;"),
     "tie_to_higher_id": ("t > tmin && t < best) { best = t; best_id = i; }", "t > tmin && t <= best) { best = t; best_id = i; }"),
     "no_clamp": ("rgbz[a] = rgbz[a] < 0.0 ? 0.0 : (rgbz[a] > 1.0 ? 1.0 : rgbz[a]);", "(void)0;"),
-    "no_recursion": ("memcpy(c, rgbz, sizeof(double) * 4);", "(void)rgbz;"),
+    "no_recursion": ("memcpy(c, rgbt, sizeof(double) * 3);", "(void)rgbt;"),
     "sphere_id_offset": ("best_id = s->T + j;", "best_id = j;"),
-    "flag_dropped": ("    *flag = amb;\n    return 0;\n}\n\n/*\n * Any hit", "    *flag = 0;\n    return 0;\n}\n\n/*\n * Any hit"),
-    "image_green_sign": ("const float sy = (float)y - k_px * dg;", "const float sy = (float)y + k_px * dg;"),
-    "image_uses_blue": ("const float dg = 2.0f * c[1] - 1.0f;", "const float dg = 2.0f * c[2] - 1.0f;"),
-    "image_round_down": ("(int64_t)floorf(sx + 0.5f)", "(int64_t)floorf(sx)"),
+    "flag_dropped": ("    *flag = fl;\n    return 0;\n}\n\n/*\n * Any hit", "    *flag = 0;\n    return 0;\n}\n\n/*\n * Any hit"),
+    "point_flag_dropped": ("if (ill) fl |= ORC_FLAG_ID | ORC_FLAG_POINT;", "if (ill) fl |= ORC_FLAG_ID;"),
+    "shadow_flag_as_id": ("if (samb) amb |= ORC_FLAG_SHADOW;", "if (samb) amb |= ORC_FLAG_ID;"),
+    "image_green_sign": ("const double sy = (double)y - k_px", "const double sy = (double)y + k_px"),
+    "image_uses_blue": ("(2.0 * (double)c[1] - 1.0)", "(2.0 * (double)c[2] - 1.0)"),
+    "image_round_down": ("(int64_t)floor(sx + 0.5)", "(int64_t)floor(sx)"),
     "mirror_repeats_edge": ("return m < n ? m : period - 1 - m;", "return m < n ? m : period - m;"),
-    "image_no_centering": ("const float dr = 2.0f * c[0] - 1.0f;", "const float dr = c[0];"),
+    "image_no_centering": ("k_px * (2.0 * (double)c[0] - 1.0)", "k_px * (double)c[0]"),
+    "image_band_dropped": ("return fabs(frac - 0.5) <= band;", "return fabs(frac - 0.5) < 0.0 * band;"),
+    "image_band_at_integers": ("return fabs(frac - 0.5) <= band;", "return frac <= band || 1.0 - frac <= band;"),
+    "image_band_row_uses_x": ("near_half(sy, ORC_IMG_TOL * ((double)y + k_px + 1.0))",
+                              "near_half(sx, ORC_IMG_TOL * ((double)y + k_px + 1.0))"),
     "normal_cross_swapped": ("cross3(C, N, X);", "cross3(N, C, X);"),
-    "normal_no_fold": ("    if (zz < 0.0) {\n        x = (1.0 - fabs(py))", "    if (0) {\n        x = (1.0 - fabs(py))"),
-    "normal_code_no_offset": ("return (uint32_t)(qx + 32768) | ((uint32_t)(qy + 32768) << 16);",
-                              "return (uint32_t)(qx & 0xffff) | ((uint32_t)(qy & 0xffff) << 16);"),
+    "normal_not_carried": ("orc_shade_ray(J->s, o, d, rgbt, nrm, &id, &amb);",
+                           "orc_shade_ray(J->s, o, d, rgbt, NULL, &id, &amb);"),
+    "normal_ms_wrong_pixel": ("orc_nearest_pixel(J->W, J->H, px, py) : NULL;",
+                              "orc_nearest_pixel(J->W, J->H, px + 1.0, py) : NULL;"),
+    "nearest_pixel_half_shift": ("int64_t nx = (int64_t)floor(px), ny = (int64_t)floor(py);",
+                                 "int64_t nx = (int64_t)floor(px - 0.5), ny = (int64_t)floor(py - 0.5);"),
+    "normal_not_output": ("        if (nrm) memcpy(nrm, N, sizeof(N));\n", "\n"),
+    "depth_along_ray": ("return id < 0 ? 0.0 : t * dot3(d, F);", "return id < 0 ? 0.0 : t;"),
+    "depth_wrong_axis": ("    sub3(cam + 3, cam, F);\n    normalize3(F);\n}", "    sub3(cam + 6, cam, F);\n    normalize3(F);\n}"),
     "jitter_sign": ("const double px = (double)x + (double)J->jitter[2 * s]", "const double px = (double)x - (double)J->jitter[2 * s]"),
     "bilinear_weights_swapped": ("{{(1.0 - wx) * (1.0 - wy), wx * (1.0 - wy)}", "{{wx * (1.0 - wy), (1.0 - wx) * (1.0 - wy)}"),
     "ms_mean_wrong": ("J->out[4 * i + a] = acc[a] / (double)J->spp;", "J->out[4 * i + a] = acc[a] / (double)(J->spp + 1);"),
