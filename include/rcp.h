@@ -252,22 +252,28 @@ rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rc
 
 /* Traversal tuning. block: threads per block (64, 128, 256); blocks_per_sm:
  * resident blocks of the persistent launch (0 = occupancy maximum); chunk:
- * pixels a warp claims per fetch (32 or 64); fused_camera: 1 = rays are made
- * inside the trace kernel, 0 = a separate camera kernel writes a ray buffer. */
+ * pixels a warp claims per fetch (32 or 64, the rays per warp); fused_camera:
+ * 1 = rays are made inside the trace kernel, 0 = a separate camera kernel
+ * writes a ray buffer; stack_entries: traversal-stack entries per thread kept
+ * in shared memory (0 = one per tree level, the walk's deepest need; fewer
+ * entries spill the deeper levels to a library-owned global-memory region).
+ * No choice changes any result. */
 typedef struct {
     int32_t block;
     int32_t blocks_per_sm;
     int32_t chunk;
     int32_t fused_camera;
+    int32_t stack_entries;
 } rcp_tuning;
 
 rcp_status rcp_get_tuning(const rcp_scene* scene, rcp_tuning* out);
 rcp_status rcp_set_tuning(rcp_scene* scene, const rcp_tuning* tuning);
 
-/* Time every tuning candidate on this scene and view, keep the fastest in the
- * scene and return it. cache_path (nullable): a JSON file of earlier results,
- * keyed by GPU name, scene size class and view size; read before and updated
- * after the search. */
+/* Time every tuning candidate (block x chunk x fused camera x shared stack
+ * depth, the depth a full tree walk needs or half of it) on this scene and
+ * view, keep the fastest in the scene and return it. cache_path (nullable): a
+ * JSON file of earlier results, keyed by GPU name, scene size class, tree depth
+ * and view size; read before and updated after the search. */
 rcp_status rcp_autotune(rcp_scene* scene, const rcp_camera* cam, int width, int height,
                         const rcp_params* params, const char* cache_path, rcp_tuning* out);
 
@@ -304,17 +310,26 @@ int64_t rcp_render_h2d_bytes(int n_views, int K);
  *  rcp_debug_trace: n rays, orig_tmin[n*4] = (origin, t_min), dir_tmax[n*4] =
  *    (unit direction, t_max); any_hit 0 = closest hit (t_out, prim_out), 1 =
  *    any hit (prim_out = 1 occluded / 0 free, t_out unused); brute 1 tests
- *    every primitive instead of walking the BVH.
+ *    every primitive instead of walking the BVH; stack_entries: the walk's
+ *    stack (0 = 64 entries); a walk that needs more drops the deeper groups and
+ *    the call returns RCP_ERR_STACK.
  *  rcp_debug_sort_pairs: stable LSD radix sort of n (key, value) pairs on the
  *    low `bits` bits of the keys, in place.
  *  rcp_debug_morton: 30-bit Morton codes of n points (xyz[n*3]) in the cube
  *    with corner lo[3] and side max_a(hi[a] - lo[a]) (host arrays). */
 rcp_status rcp_debug_trace(const rcp_scene* scene, int64_t n, const float* orig_tmin,
                            const float* dir_tmax, int any_hit, int brute, float* t_out,
-                           int32_t* prim_out, void* stream);
+                           int32_t* prim_out, int stack_entries, void* stream);
 rcp_status rcp_debug_sort_pairs(uint32_t* keys, uint32_t* values, int64_t n, int bits, void* stream);
 rcp_status rcp_debug_morton(const float* xyz, int64_t n, const float* lo, const float* hi,
                             uint32_t* codes, void* stream);
+/* Test of the radix sort's bounded wait: one block of a sort pass takes the
+ * second of two tiles while the first never runs, so its look-back waits for
+ * counts that are never published. Each wait gives up after spin_limit polls
+ * (1 <= spin_limit <= 2^20; a real sort allows 2^26), sets the sort's error
+ * flag and the block finishes. Returns RCP_ERR_TIMEOUT when the flag was set,
+ * as a sort whose wait ran out does. Synchronous; allocates its own buffers. */
+rcp_status rcp_debug_sort_lookback_timeout(int64_t spin_limit, void* stream);
 
 /* Allocation-free sort. The paper has no counterpart: this is a library
  * facility. Some callers cannot allocate device memory at the point where they

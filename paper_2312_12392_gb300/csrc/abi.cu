@@ -78,6 +78,7 @@ RenderCtx::~RenderCtx() {
     if (io) cudaFree(io);
     if (io_prim) cudaFree(io_prim);
     if (base_img) cudaFree(base_img);
+    if (hints) cudaFree(hints);
     if (done) {
         cudaEventSynchronize(done);
         cudaEventDestroy(done);
@@ -90,7 +91,8 @@ RenderCtx::~RenderCtx() {
 Scene::~Scene() {
     ctx.clear();
     for (void* p : {(void*)d_tri, (void*)d_sph, (void*)d_albedo, d_nodes, (void*)d_nbox, (void*)d_prims,
-                    (void*)d_refbox, (void*)d_part_uv, (void*)d_rec_id, (void*)d_rbox})
+                    (void*)d_refbox, (void*)d_part_uv, (void*)d_rec_id, (void*)d_rbox, (void*)d_dev,
+                    (void*)d_spill})
         if (p) cudaFree(p);
 }
 
@@ -155,6 +157,9 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.out = nullptr;
     v.prim = nullptr;
     v.rgb = nullptr;
+    v.hint = nullptr;
+    v.scene = nullptr;
+    v.status = nullptr;
     v.tiles_x = (W + 7) / 8;
     v.pix_begin = 0;
     v.chunk_begin = 0;
@@ -230,22 +235,64 @@ rcp_status check_view(const rcp_camera* cam, int W, int H, const rcp_params* p) 
     return RCP_OK;
 }
 
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0)
+        sms = 1;
+    return sms;
+}
+
+// Stack entries a walk of this tree can need: one group per level, rounded up
+// to a multiple of 4.
+int full_stack(const Scene& sc) {
+    const int st = std::max(sc.depth, 4);
+    return std::min((st + 3) & ~3, MAX_STACK);
+}
+
 LaunchCfg cfg_of(const Scene& sc) {
     LaunchCfg c;
     c.block = sc.tuning.block;
     c.blocks_per_sm = sc.tuning.blocks_per_sm;
     c.chunk = sc.tuning.chunk >= 64 ? 64 : 32;
     c.fused = sc.tuning.fused_camera != 0;
-    int st = std::max(sc.depth, 4);
-    st = (st + 3) & ~3;
-    c.stack = std::min(st, MAX_STACK);
+    const int full = full_stack(sc);
+    c.stack = sc.tuning.stack_entries > 0 ? std::min(sc.tuning.stack_entries, full) : full;
+    c.spill_entries = full - c.stack;
     return c;
+}
+
+// The global-memory region of a short shared stack: spill_entries per thread
+// of the largest persistent grid a launch can have (the SMs' resident
+// threads, or the tuned blocks per SM). Grown before any capture, never during
+// one; the graph key names the region.
+rcp_status ensure_spill(Scene& sc, LaunchCfg& c) {
+    if (c.spill_entries <= 0) return RCP_OK;
+    const int64_t per_sm = std::max<int64_t>(2048, (int64_t)c.blocks_per_sm * c.block);
+    const int64_t need = (int64_t)device_sms() * per_sm * c.spill_entries;
+    if (sc.spill_cap < need) {
+        if (sc.d_spill) {
+            RCP_CUDA(cudaDeviceSynchronize());  // no launch may still use the old region
+            cudaFree(sc.d_spill);
+            sc.d_spill = nullptr;
+            sc.spill_cap = 0;
+            for (auto& kv : sc.ctx) {  // graphs captured with the old region
+                if (kv.second->graph) cudaGraphExecDestroy(kv.second->graph);
+                kv.second->graph = nullptr;
+            }
+        }
+        RCP_CUDA(cudaMalloc((void**)&sc.d_spill, sizeof(uint2) * need));
+        sc.spill_cap = need;
+    }
+    c.spill = sc.d_spill;
+    c.spill_cap = sc.spill_cap;
+    return RCP_OK;
 }
 
 std::string cfg_key(const LaunchCfg& c) {
     std::ostringstream o;
-    o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/" << c.count
-      << "/" << c.ms;
+    o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/"
+      << c.spill_entries << "/" << (const void*)c.spill << "/" << c.count << "/" << c.ms;
     return o.str();
 }
 
@@ -277,7 +324,8 @@ rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t tot
         *out = it->second.get();
         return RCP_OK;
     }
-    const int64_t need = total_pix * (int64_t)(sizeof(float4) * 4) + (int64_t)sizeof(ViewDev) * K * n_views;
+    const int64_t need =
+        total_pix * (int64_t)(sizeof(float4) * 4 + sizeof(int2)) + (int64_t)sizeof(ViewDev) * K * n_views;
     for (;;) {
         int64_t held = 0;
         for (auto& kv : sc.ctx) held += kv.second->bytes;
@@ -298,6 +346,8 @@ rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t tot
     RCP_CUDA(cudaMalloc((void**)&c->img[0], sizeof(float4) * total_pix));
     RCP_CUDA(cudaMalloc((void**)&c->img[1], sizeof(float4) * total_pix));
     RCP_CUDA(cudaMalloc((void**)&c->rays, sizeof(float4) * 2 * total_pix));
+    RCP_CUDA(cudaMalloc((void**)&c->hints, sizeof(int2) * total_pix));
+    RCP_CUDA(cudaMemset(c->hints, 0xff, sizeof(int2) * total_pix));  // -1: no earlier hit
     RCP_CUDA(cudaMalloc((void**)&c->d_views, sizeof(ViewDev) * (size_t)K * n_views));
     RCP_CUDA(cudaMallocHost((void**)&c->h_views, sizeof(ViewDev) * (size_t)K * n_views));
     RCP_CUDA(cudaMalloc((void**)&c->d_work, sizeof(unsigned) * (K + 1)));
@@ -329,8 +379,7 @@ rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg,
         rcp_status r = (ctx.image_mode && n > 0)
                            ? launch_imagespace(ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix, st)
                            : launch_pass(S, cfg, ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix,
-                                         ctx.total_chunks, ctx.rays, ctx.d_work + n, ctx.d_status, ctx.d_rays,
-                                         counters, st);
+                                         ctx.total_chunks, ctx.rays, ctx.d_work + n, ctx.d_rays, counters, st);
         if (r != RCP_OK) return r;
         RCP_CUDA(record(ctx.pass_ev[n + 1]));
     }
@@ -387,6 +436,8 @@ rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const f
             }
             v.in = prev;
             v.out = cur;
+            v.hint = ctx.hints + off;  // read and rewritten by each traced pass, per pixel
+            v.status = ctx.d_status;
             v.prim = (n == K - 1 && prims && !ctx.image_mode) ? prims[i] : nullptr;
             v.rgb = (n == K - 1 && rgbs && !ctx.image_mode) ? rgbs[i] : nullptr;
             ctx.h_views[(size_t)n * nv + i] = v;
@@ -440,6 +491,8 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     if (r != RCP_OK) return r;
     LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
     cfg.ms = p->spp > 0;
+    r = ensure_spill(sc, cfg);
+    if (r != RCP_OK) return r;
     r = run_graph(sc, *ctx, cfg, st);
     sc.last = ctx;
     if (ctx_out) *ctx_out = ctx;
@@ -541,6 +594,9 @@ rcp_status rcp_scene_create_ex(const float* tri, int64_t T, const float* sph, in
     // tree is only handed out once every index in it is known to be in range
     r = validate_bvh(*sc, st);
     if (r != RCP_OK) return r;
+    const SceneDev dv = sc->dev();
+    RCP_CUDA(cudaMalloc((void**)&sc->d_dev, sizeof(SceneDev)));
+    RCP_CUDA(cudaMemcpy(sc->d_dev, &dv, sizeof(SceneDev), cudaMemcpyHostToDevice));
     *out = sc.release();
     return RCP_OK;
 }
@@ -759,8 +815,10 @@ rcp_status rcp_set_tuning(rcp_scene* sc, const rcp_tuning* t) {
         return RCP_ERR_ARG;
     }
     if ((t->block != 64 && t->block != 128 && t->block != 256) || (t->chunk != 32 && t->chunk != 64) ||
-        t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || (t->fused_camera != 0 && t->fused_camera != 1)) {
-        set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32, fused 0/1");
+        t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || (t->fused_camera != 0 && t->fused_camera != 1) ||
+        t->stack_entries < 0 || t->stack_entries > MAX_STACK) {
+        set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32, fused 0/1, "
+                  "0 <= stack_entries <= 64");
         return RCP_ERR_ARG;
     }
     std::lock_guard<std::mutex> lk(sc->mu);
@@ -797,6 +855,8 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
     LaunchCfg cfg = cfg_of(*sc);
     cfg.count = true;
     cfg.ms = p->spp > 0;
+    r = ensure_spill(*sc, cfg);
+    if (r != RCP_OK) return r;
     r = enqueue_passes(*sc, *ctx, cfg, d_cnt.p, st, false);
     if (r != RCP_OK) return r;
     unsigned long long h[8] = {0};
@@ -813,9 +873,13 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
 }
 
 rcp_status rcp_debug_trace(const rcp_scene* sc, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
-                           int brute, float* t_out, int32_t* prim_out, void* stream) {
+                           int brute, float* t_out, int32_t* prim_out, int stack_entries, void* stream) {
     if (!sc || n < 0 || (n > 0 && (!orig_tmin || !dir_tmax || !t_out || !prim_out))) {
         set_error("rcp_debug_trace: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    if (stack_entries < 0 || stack_entries > MAX_STACK) {
+        set_error("rcp_debug_trace: stack_entries outside [0, 64]");
         return RCP_ERR_ARG;
     }
     if (((uintptr_t)orig_tmin | (uintptr_t)dir_tmax) & 15) {
@@ -830,7 +894,8 @@ rcp_status rcp_debug_trace(const rcp_scene* sc, int64_t n, const float* orig_tmi
     DevBuf<int> d_status;
     RCP_CUDA(d_status.alloc(1));
     RCP_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
-    rcp_status r = launch_debug_trace(sc->dev(), n, orig_tmin, dir_tmax, any, brute, t_out, prim_out, d_status.p, st);
+    rcp_status r = launch_debug_trace(sc->dev(), n, orig_tmin, dir_tmax, any, brute, t_out, prim_out,
+                                      stack_entries > 0 ? stack_entries : MAX_STACK, d_status.p, st);
     if (r != RCP_OK) return r;
     int h = 0;
     RCP_CUDA(cudaMemcpyAsync(&h, d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -947,7 +1012,7 @@ std::string gpu_name() {
     return prop.name;
 }
 
-// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, us], ...}
+// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, stack_entries, us], ...}
 std::map<std::string, std::vector<double>> read_cache(const char* path) {
     std::map<std::string, std::vector<double>> m;
     if (!path) return m;
@@ -1004,11 +1069,12 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     int cls = 0;
     for (int64_t n = sc->T + sc->S; n > 1; n >>= 1) ++cls;
     std::ostringstream key;
-    key << gpu_name() << "|prims2^" << cls << "|" << W << "x" << H << "|map" << p->mapping;
+    key << gpu_name() << "|prims2^" << cls << "|depth" << sc->depth << "|" << W << "x" << H << "|map" << p->mapping;
     auto cache = read_cache(cache_path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
-        rcp_tuning t{(int)it->second[0], (int)it->second[1], (int)it->second[2], (int)it->second[3]};
+        const auto& v = it->second;
+        rcp_tuning t{(int)v[0], (int)v[1], (int)v[2], (int)v[3], v.size() >= 6 ? (int)v[4] : 0};
         r = rcp_set_tuning(sc, &t);
         if (r == RCP_OK && out) *out = t;
         if (r == RCP_OK) return RCP_OK;
@@ -1022,35 +1088,39 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     RCP_CUDA(ev.create());
     double best_us = 1e30;
     rcp_tuning best = sc->tuning;
-    const int blocks[3] = {64, 128, 256};
-    for (int b : blocks)
+    const int full = full_stack(*sc);
+    std::vector<int> stacks{0};  // 0: one entry per tree level
+    if (full / 2 >= 4) stacks.push_back(((full / 2) + 3) & ~3);
+    for (int b : {64, 128, 256})
         for (int fused = 0; fused < 2; ++fused)
-            for (int chunk : {32, 64}) {
-                rcp_tuning t{b, 0, chunk, fused};
-                sc->tuning = t;
-                const float4* ins[1] = {nullptr};
-                float4* outs[1] = {d_img.p};
-                double us = 1e30;
-                // K = 2 so the second pass reads a real image; best of 3
-                for (int rep = 0; rep < 4 && r == RCP_OK; ++rep) {
-                    cudaEventRecord(ev.a, st);
-                    r = render_views(*sc, 1, cam, &W, &H, 2, p, ins, outs, nullptr, st);
-                    cudaEventRecord(ev.b, st);
-                    if (cudaEventSynchronize(ev.b) != cudaSuccess) r = RCP_ERR_CUDA;
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, ev.a, ev.b);
-                    if (rep > 0) us = std::min(us, 1000.0 * ms);
+            for (int chunk : {32, 64})
+                for (int stk : stacks) {
+                    if (stk >= full) continue;
+                    rcp_tuning t{b, 0, chunk, fused, stk};
+                    sc->tuning = t;
+                    const float4* ins[1] = {nullptr};
+                    float4* outs[1] = {d_img.p};
+                    double us = 1e30;
+                    // K = 2 so the second pass reads a real image; best of 3
+                    for (int rep = 0; rep < 4 && r == RCP_OK; ++rep) {
+                        cudaEventRecord(ev.a, st);
+                        r = render_views(*sc, 1, cam, &W, &H, 2, p, ins, outs, nullptr, st);
+                        cudaEventRecord(ev.b, st);
+                        if (cudaEventSynchronize(ev.b) != cudaSuccess) r = RCP_ERR_CUDA;
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, ev.a, ev.b);
+                        if (rep > 0) us = std::min(us, 1000.0 * ms);
+                    }
+                    if (r != RCP_OK) break;
+                    if (us < best_us) {
+                        best_us = us;
+                        best = t;
+                    }
                 }
-                if (r != RCP_OK) break;
-                if (us < best_us) {
-                    best_us = us;
-                    best = t;
-                }
-            }
     sc->tuning = best;
     if (r != RCP_OK) return r;
     cache[key.str()] = {(double)best.block, (double)best.blocks_per_sm, (double)best.chunk, (double)best.fused_camera,
-                        best_us};
+                        (double)best.stack_entries, best_us};
     write_cache(cache_path, cache);
     if (out) *out = best;
     return RCP_OK;

@@ -8,9 +8,9 @@
 // every earlier tile is already running), and scatters through shared memory
 // so that writes of one digit run are contiguous.
 //
-// Every wait on another tile's status is bounded: after SPIN_LIMIT polls the
-// kernel records an error flag and proceeds, so a fault in the protocol shows
-// up as an error status instead of a hang.
+// Every wait on another tile's status is bounded: after spin_limit polls
+// (SPIN_LIMIT in a sort) the kernel records an error flag and proceeds, so a
+// fault in the protocol shows up as an error status instead of a hang.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_onesweep(const uint32_t* __restr
                                                          uint32_t* __restrict__ vals_out, int64_t n, int shift,
                                                          const uint32_t* __restrict__ bucket_base,
                                                          uint32_t* status, uint32_t* tile_counter,
-                                                         int* error_flag) {
+                                                         int* error_flag, long long spin_limit) {
     __shared__ uint32_t s_keys[TILE];
     __shared__ uint32_t s_vals[TILE];
     __shared__ uint32_t s_wcnt[SORT_WARPS][RADIX];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(SORT_BLOCK) k_onesweep(const uint32_t* __restr
                 const uint32_t sv = ((volatile uint32_t*)status)[(size_t)t * RADIX + d];
                 const uint32_t flag = sv & ~COUNT_MASK;
                 if (flag == 0) {
-                    if (++spins > SPIN_LIMIT) {
+                    if (++spins > spin_limit) {
                         atomicExch(error_flag, 1);
                         break;
                     }
@@ -222,7 +222,7 @@ rcp_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* alt_keys, 
     for (int p = 0; p < passes; ++p) {
         RCP_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)tiles * RADIX, stream));
         k_onesweep<<<(int)tiles, SORT_BLOCK, 0, stream>>>(ki, vi, ko, vo, n, 8 * p, hist + p * RADIX, status,
-                                                           counters + p, d_error);
+                                                           counters + p, d_error, SPIN_LIMIT);
         uint32_t* t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
@@ -322,6 +322,56 @@ extern "C" rcp_status rcp_sort_pairs_static(uint32_t* keys, uint32_t* values, in
     RCP_CUDA(cudaStreamSynchronize(st));
     if (h) {
         set_error("rcp_sort_pairs_static: look-back wait ran out");
+        return RCP_ERR_TIMEOUT;
+    }
+    return RCP_OK;
+}
+
+// ---------------------------------------------------------------- test of the bounded wait
+//
+// rcp_debug_sort_lookback_timeout: one onesweep block takes tile 1 of a
+// two-tile pass while tile 0 never runs, so every one of its look-back waits
+// polls a status that nothing publishes. After spin_limit polls each wait
+// gives up and sets the error flag, and the block finishes its tile with a
+// partial offset. With every key 0 all of the block's keys go to digit 0,
+// whose bucket starts at 0, so its writes land at indices [0, TILE) of the
+// 2 TILE-element output arrays.
+
+extern "C" rcp_status rcp_debug_sort_lookback_timeout(int64_t spin_limit, void* stream) {
+    using namespace rcp;
+    if (spin_limit < 1 || spin_limit > (1ll << 20)) {
+        set_error("rcp_debug_sort_lookback_timeout: spin_limit outside [1, 2^20]");
+        return RCP_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = 2 * (int64_t)TILE;
+    DevBuf<uint32_t> keys, vals, ko, vo, scratch;
+    DevBuf<int> err;
+    RCP_CUDA(keys.alloc(n));
+    RCP_CUDA(vals.alloc(n));
+    RCP_CUDA(ko.alloc(n));
+    RCP_CUDA(vo.alloc(n));
+    RCP_CUDA(scratch.alloc(4 * RADIX + 8 + 2 * RADIX));
+    RCP_CUDA(err.alloc(1));
+    uint32_t* hist = scratch.p;
+    uint32_t* counter = hist + 4 * RADIX;
+    uint32_t* status = counter + 8;
+    RCP_CUDA(cudaMemsetAsync(keys.p, 0, sizeof(uint32_t) * n, st));
+    RCP_CUDA(cudaMemsetAsync(vals.p, 0, sizeof(uint32_t) * n, st));
+    RCP_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(uint32_t) * (4 * RADIX + 8 + 2 * RADIX), st));
+    RCP_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    k_histogram<<<2, SORT_BLOCK, 0, st>>>(keys.p, n, 1, hist);
+    k_scan_histogram<<<1, RADIX, 0, st>>>(hist, 1);
+    const uint32_t one = 1;  // the block claims tile 1; tile 0 is never claimed
+    RCP_CUDA(cudaMemcpyAsync(counter, &one, sizeof(one), cudaMemcpyHostToDevice, st));
+    k_onesweep<<<1, SORT_BLOCK, 0, st>>>(keys.p, vals.p, ko.p, vo.p, n, 0, hist, status, counter, err.p,
+                                         (long long)spin_limit);
+    RCP_CUDA(cudaGetLastError());
+    int h = 0;
+    RCP_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCP_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("radix sort: look-back wait ran out");
         return RCP_ERR_TIMEOUT;
     }
     return RCP_OK;

@@ -70,6 +70,8 @@ struct SceneDev {
 //   g(x, y) = fF + (2x + 1 - W) fR + (H - 2y - 1) fU  (eye -> focal-plane point)
 //   V(c)    = (2c.r - 1) kR + (2c.g - 1) kU + (2c.b - 1) kF
 struct ViewDev {
+    const struct SceneDev* scene;  // the view's scene (launches over views of several scenes)
+    int* status;                   // set to 1 when a walk of this view overflowed its stack
     float E[3];
     float fF[3], fR[3], fU[3];
     float kR[3], kU[3], kF[3];
@@ -85,6 +87,8 @@ struct ViewDev {
     int32_t* prim;     // nullable hit ids
     float* rgb;        // nullable: this pass also writes R, G, B (3 floats per pixel, row-major) here,
                        // host memory that the device reads and writes coherently
+    int2* hint;        // nullable: per pixel, the record of its latest primary hit and of its latest
+                       // shadow occluder (-1 none); tested first, rewritten by every traced pass
     int64_t pix_begin;  // first global pixel index of this view
     int64_t chunk_begin;  // first work chunk (8x4 tile) of this view
     int tiles_x;

@@ -34,6 +34,7 @@ struct RenderCtx {
     float4* base_img = nullptr;  // image-space mapping: the traced pass-1 image
     bool image_mode = false;     // passes 2..K are image-space gathers
     int32_t* io_prim = nullptr;  // host-API hit ids
+    int2* hints = nullptr;       // per pixel: latest primary-hit and shadow-occluder records (-1 none)
     cudaEvent_t staged = nullptr;
     cudaEvent_t pass_ev[17] = {};  // timing events around every pass (recorded inside the graph)
     cudaGraphExec_t graph = nullptr;
@@ -66,11 +67,14 @@ struct Scene {
     float diam = 0.f;
     float build_ms = 0.f;
     LightDev light{};
-    rcp_tuning tuning{128, 0, 32, 1};
+    rcp_tuning tuning{128, 0, 32, 1, 0};
     std::mutex mu;
     std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
     RenderCtx* last = nullptr;  // context of the most recent render
     uint64_t use_clock = 0;
+    SceneDev* d_dev = nullptr;  // device copy of dev(), named by views of multi-scene launches
+    uint2* d_spill = nullptr;   // global-memory traversal stack entries of a short shared stack
+    int64_t spill_cap = 0;
     ~Scene();
     SceneDev dev() const;
     int64_t device_bytes() const;
@@ -91,17 +95,23 @@ struct LaunchCfg {
     int blocks_per_sm = 0;
     int chunk = 32;
     bool fused = true;
-    int stack = 32;  // entries per thread
+    int stack = 32;  // shared-memory stack entries per thread
+    int spill_entries = 0;  // global-memory stack entries per thread above those
+    uint2* spill = nullptr;  // their region (spill_cap entries)
+    int64_t spill_cap = 0;
     bool count = false;
     bool ms = false;  // jittered multi-sample kernel
+    bool multi = false;  // views of several scenes (each view names its scene)
 };
 
-// One pass over n_views views whose descriptors are at d_views (device).
+// One pass over n_views views whose descriptors are at d_views (device). A
+// walk that overflows its stack sets its view's status word.
 rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
-                       int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work, int* d_status,
+                       int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work,
                        unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st);
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
-                              int brute, float* t_out, int32_t* prim_out, int* d_status, cudaStream_t st);
+                              int brute, float* t_out, int32_t* prim_out, int stack_entries, int* d_status,
+                              cudaStream_t st);
 rcp_status launch_pack_rgb(const float4* img, float* rgb, int64_t n, cudaStream_t st);
 
 // Whether kernels on the current device read and write pageable host memory

@@ -2,21 +2,22 @@
 //
 // Two host threads own the device work:
 //  * the scheduler admits queued requests (FIFO) while a slot is free and the
-//    request's device memory -- two rgbz images and an RGB staging buffer,
-//    allocated stream-ordered from the device's memory pool -- fits the
-//    budget, then enqueues ONE pass of every admitted request per step: the
-//    requests are grouped by scene and each group is one launch of the pass
-//    kernels (one work queue over all of the group's views, whatever their
-//    size), groups on their own streams so they overlap on the device. Which
+//    request's device memory -- two rgbz images, per-pixel hit hints and a
+//    status word (plus an RGB staging buffer where the device cannot write
+//    host memory), allocated stream-ordered from the device's memory pool --
+//    fits the budget, then enqueues ONE pass of every admitted request per
+//    step as ONE persistent launch: a single tile queue over every request's
+//    view, whatever its scene, size or K (each view names its scene). Which
 //    requests finish at a step is known when it is enqueued (pass count = K),
 //    so the scheduler never waits for the device except to bound how far it
 //    runs ahead (STEPS_AHEAD steps);
-//  * the copy-out thread waits for each finished request's last pass, copies
-//    its RGB image to the caller's buffer, releases its memory and records
-//    its latency, while the device already runs the next steps. Where the
-//    device writes pageable host memory coherently, a request's last pass
-//    writes its RGB into the caller's buffer itself (no staging buffer, no
-//    pack kernel, no copy), and the copy-out thread only waits for it.
+//  * the copy-out thread waits for each finished request's last pass, reads
+//    its status word (a walk that overflowed its stack fails the request),
+//    copies its RGB image to the caller's buffer where needed, releases its
+//    memory and records its latency, while the device already runs the next
+//    steps. Where the device writes pageable host memory coherently, a
+//    request's last pass writes its RGB into the caller's buffer itself (no
+//    staging buffer, no pack kernel, no copy).
 // New requests join at the next step while others are mid-recursion, so short
 // and long requests share every launch.
 #include <cuda_runtime.h>
@@ -29,6 +30,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -43,17 +45,6 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-LaunchCfg server_cfg(const Scene& sc) {
-    LaunchCfg c;
-    c.block = sc.tuning.block;
-    c.blocks_per_sm = sc.tuning.blocks_per_sm;
-    c.chunk = sc.tuning.chunk >= 64 ? 64 : 32;
-    c.fused = true;  // no ray buffer per request
-    const int st = std::max(sc.depth, 4);
-    c.stack = std::min((st + 3) & ~3, MAX_STACK);
-    return c;
-}
-
 }  // namespace
 
 struct Request {
@@ -66,26 +57,22 @@ struct Request {
     int passes_done = 0;  // passes enqueued so far
     float4* img[2] = {nullptr, nullptr};
     float* rgb = nullptr;
+    int2* hint = nullptr;    // per pixel: latest primary-hit and shadow-occluder records, then the status word
+    int* d_status = nullptr;  // inside the hint allocation
+    int status_slot = -1;     // index of the request's pinned host status word
     int64_t bytes = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     rcp_status status = RCP_OK;
     bool done = false;
-    cudaEvent_t ready = nullptr;  // the RGB image (packed, or in the caller's buffer) is complete
+    cudaEvent_t ready = nullptr;  // the RGB image (packed, or in the caller's buffer) and status word are complete
 };
 
-// Launch resources of one scene group in one step slot.
-struct GroupRes {
-    cudaStream_t st = nullptr;
+// Launch resources of one step: the views of every in-flight request.
+struct StepSlot {
     ViewDev* d_views = nullptr;
-    ViewDev* h_views = nullptr;
+    ViewDev* h_views = nullptr;  // pinned staging
     int cap = 0;
     unsigned* d_work = nullptr;
-    int* d_status = nullptr;
-    cudaEvent_t end = nullptr;
-};
-
-struct StepSlot {
-    std::vector<GroupRes> groups;
     cudaEvent_t done = nullptr;
     bool used = false;
 };
@@ -116,6 +103,8 @@ struct rcp_server {
     int64_t step_no = 0;
     int device = 0;
     bool direct = false;  // last passes write the callers' RGB buffers (host_coherent)
+    int* h_status = nullptr;  // pinned: one status word per admitted, unfinished request
+    std::vector<int> free_status;
 
     void run();
     void copy_out();
@@ -125,17 +114,22 @@ struct rcp_server {
 
 namespace {
 
-// Device memory of a request: two rgbz images, and the RGB staging buffer
-// unless its last pass writes the caller's buffer directly.
+// Device memory of a request: two rgbz images, the per-pixel hit hints and its
+// status word, and the RGB staging buffer unless its last pass writes the
+// caller's buffer directly.
 int64_t request_bytes(int W, int H, bool direct) {
     const int64_t P = (int64_t)W * H;
-    return P * (2 * 16 + (direct ? 0 : 12)) + 3 * 256;
+    return P * (2 * 16 + 8 + (direct ? 0 : 12)) + 4 * 256;
 }
 
 rcp_status alloc_request(Request& r, bool direct, cudaStream_t st) {
     const int64_t P = (int64_t)r.W * r.H;
     RCP_CUDA(cudaMallocAsync((void**)&r.img[0], sizeof(float4) * P, st));
     RCP_CUDA(cudaMallocAsync((void**)&r.img[1], sizeof(float4) * P, st));
+    RCP_CUDA(cudaMallocAsync((void**)&r.hint, sizeof(int2) * (P + 1), st));
+    RCP_CUDA(cudaMemsetAsync(r.hint, 0xff, sizeof(int2) * P, st));  // -1: no earlier hit
+    r.d_status = (int*)(r.hint + P);
+    RCP_CUDA(cudaMemsetAsync(r.d_status, 0, sizeof(int), st));
     if (!direct) RCP_CUDA(cudaMallocAsync((void**)&r.rgb, sizeof(float) * 3 * P, st));
     if (!r.ready) RCP_CUDA(cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming));
     return RCP_OK;
@@ -151,22 +145,28 @@ void free_request(Request& r, cudaStream_t st) {
         cudaFreeAsync(r.rgb, st);
         r.rgb = nullptr;
     }
+    if (r.hint) {
+        cudaFreeAsync(r.hint, st);
+        r.hint = nullptr;
+        r.d_status = nullptr;
+    }
 }
 
-rcp_status ensure_group(GroupRes& g, int n) {
-    if (!g.st) {
-        RCP_CUDA(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
-        RCP_CUDA(cudaMalloc((void**)&g.d_work, sizeof(unsigned) * 2));
-        RCP_CUDA(cudaMalloc((void**)&g.d_status, sizeof(int) * 2));
-        RCP_CUDA(cudaMemset(g.d_status, 0, sizeof(int) * 2));
-        RCP_CUDA(cudaEventCreateWithFlags(&g.end, cudaEventDisableTiming));
+rcp_status ensure_slot(StepSlot& s, int n) {
+    if (!s.d_work) {
+        RCP_CUDA(cudaMalloc((void**)&s.d_work, sizeof(unsigned)));
+        RCP_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
     }
-    if (g.cap < n) {
-        if (g.d_views) cudaFree(g.d_views);
-        if (g.h_views) cudaFreeHost(g.h_views);
-        g.cap = std::max(n, 16);
-        RCP_CUDA(cudaMalloc((void**)&g.d_views, sizeof(ViewDev) * g.cap));
-        RCP_CUDA(cudaMallocHost((void**)&g.h_views, sizeof(ViewDev) * g.cap));
+    if (s.cap < n) {
+        if (s.d_views) cudaFree(s.d_views);
+        if (s.h_views) cudaFreeHost(s.h_views);
+        s.d_views = nullptr;
+        s.h_views = nullptr;
+        s.cap = 0;
+        const int cap = std::max(n, 16);
+        RCP_CUDA(cudaMalloc((void**)&s.d_views, sizeof(ViewDev) * cap));
+        RCP_CUDA(cudaMallocHost((void**)&s.h_views, sizeof(ViewDev) * cap));
+        s.cap = cap;
     }
     return RCP_OK;
 }
@@ -182,80 +182,68 @@ double percentile(std::vector<double> v, double q) {
 
 }  // namespace
 
-// Enqueue one pass of every request in the batch (slot's resources are free:
-// its previous step has completed).
+// Enqueue one pass of every request in the batch as one launch (the slot's
+// resources are free: its previous step has completed).
 rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot) {
-    std::map<const rcp_scene*, std::vector<Request*>> by_scene;
-    for (Request* r : batch) by_scene[r->scene].push_back(r);
-    if (slot.groups.size() < by_scene.size()) slot.groups.resize(by_scene.size());
-    if (!slot.done) RCP_CUDA(cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming));
-    cudaEvent_t ready;
-    RCP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    RCP_CUDA(cudaEventRecord(ready, st_main));  // this step's allocations are visible
-    int gi = 0;
-    rcp_status res = RCP_OK;
-    for (auto& kv : by_scene) {
-        const rcp_scene* sc = kv.first;
-        auto& reqs = kv.second;
-        GroupRes& g = slot.groups[gi++];
-        rcp_status r = ensure_group(g, (int)reqs.size());
-        if (r != RCP_OK) {
-            res = r;
-            break;
-        }
-        if (sc->depth > MAX_STACK) {
-            for (Request* q : reqs) q->status = RCP_ERR_STACK;
-            continue;
-        }
-        int64_t total_pix = 0, total_chunks = 0;
-        for (size_t i = 0; i < reqs.size(); ++i) {
-            Request* q = reqs[i];
-            ViewDev v;
-            make_view(v, q->cam, q->W, q->H, q->p);
-            v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
-            v.out = q->img[q->passes_done & 1];
-            if (direct && q->passes_done + 1 == q->K) v.rgb = q->out_rgb;
-            v.pix_begin = total_pix;
-            v.chunk_begin = total_chunks;
-            total_pix += (int64_t)q->W * q->H;
-            total_chunks += (int64_t)v.tiles_x * ((q->H + 3) / 4);
-            g.h_views[i] = v;
-        }
-        RCP_CUDA(cudaStreamWaitEvent(g.st, ready, 0));
-        RCP_CUDA(cudaMemcpyAsync(g.d_views, g.h_views, sizeof(ViewDev) * reqs.size(), cudaMemcpyHostToDevice, g.st));
-        RCP_CUDA(cudaMemsetAsync(g.d_work, 0, sizeof(unsigned), g.st));
-        LaunchCfg cfg = server_cfg(*sc);
-        for (Request* q : reqs) cfg.ms = cfg.ms || q->p.spp > 0;
-        r = launch_pass(sc->dev(), cfg, g.d_views, (int)reqs.size(), total_pix, total_chunks, nullptr, g.d_work,
-                        g.d_status, d_rays, nullptr, g.st);
-        if (r != RCP_OK) {
-            res = r;
-            break;
-        }
-        for (Request* q : reqs) {
-            if (q->passes_done + 1 == q->K) {
-                if (!direct) {
-                    r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, g.st);
-                    if (r != RCP_OK) {
-                        res = r;
-                        break;
-                    }
-                }
-                RCP_CUDA(cudaEventRecord(q->ready, g.st));
-            }
-        }
-        RCP_CUDA(cudaEventRecord(g.end, g.st));
-        RCP_CUDA(cudaStreamWaitEvent(st_main, g.end, 0));
+    rcp_status r = ensure_slot(slot, (int)batch.size());
+    if (r != RCP_OK) return r;
+    std::set<const rcp_scene*> scenes;
+    int stack = 4;
+    bool ms = false;
+    for (Request* q : batch) {
+        scenes.insert(q->scene);
+        stack = std::max(stack, q->scene->depth);
+        ms = ms || q->p.spp > 0;
     }
-    cudaEventDestroy(ready);
+    LaunchCfg cfg;  // 128 threads, 32-pixel chunks, fused camera: no ray buffer per request
+    cfg.stack = std::min((stack + 3) & ~3, MAX_STACK);  // one entry per level of the deepest tree
+    cfg.ms = ms;
+    cfg.multi = scenes.size() > 1;
+    int64_t total_pix = 0, total_chunks = 0;
+    for (size_t i = 0; i < batch.size(); ++i) {
+        Request* q = batch[i];
+        ViewDev v;
+        make_view(v, q->cam, q->W, q->H, q->p);
+        v.scene = q->scene->d_dev;
+        v.status = q->d_status;
+        v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
+        v.out = q->img[q->passes_done & 1];
+        v.hint = q->hint;
+        if (direct && q->passes_done + 1 == q->K) v.rgb = q->out_rgb;
+        v.pix_begin = total_pix;
+        v.chunk_begin = total_chunks;
+        total_pix += (int64_t)q->W * q->H;
+        total_chunks += (int64_t)v.tiles_x * ((q->H + 3) / 4);
+        slot.h_views[i] = v;
+    }
+    RCP_CUDA(cudaMemcpyAsync(slot.d_views, slot.h_views, sizeof(ViewDev) * batch.size(), cudaMemcpyHostToDevice,
+                             st_main));
+    RCP_CUDA(cudaMemsetAsync(slot.d_work, 0, sizeof(unsigned), st_main));
+    r = launch_pass((*scenes.begin())->dev(), cfg, slot.d_views, (int)batch.size(), total_pix, total_chunks, nullptr,
+                    slot.d_work, d_rays, nullptr, st_main);
+    if (r != RCP_OK) return r;
+    for (Request* q : batch) {
+        if (q->passes_done + 1 != q->K) continue;
+        if (!direct) {
+            r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, st_main);
+            if (r != RCP_OK) return r;
+        }
+        RCP_CUDA(cudaMemcpyAsync(h_status + q->status_slot, q->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                 st_main));
+        RCP_CUDA(cudaEventRecord(q->ready, st_main));
+    }
     RCP_CUDA(cudaEventRecord(slot.done, st_main));
     slot.used = true;
-    return res;
+    return RCP_OK;
 }
 
 void rcp_server::finish(Request* q, rcp_status st, double t) {
     // called with mu held
     bytes_in_use -= q->bytes;
+    if (q->status_slot >= 0) {
+        free_status.push_back(q->status_slot);
+        q->status_slot = -1;
+    }
     q->t_done = t;
     if (q->status == RCP_OK) q->status = st;
     q->done = true;
@@ -282,10 +270,14 @@ void rcp_server::copy_out() {
         rcp_status st = RCP_OK;
         if (q->status == RCP_OK) {
             cudaError_t e = cudaEventSynchronize(q->ready);
-            if (e == cudaSuccess && !direct)
+            if (e == cudaSuccess && h_status[q->status_slot]) {
+                set_error("server: a traversal stack overflowed; the request's image is incomplete");
+                st = RCP_ERR_STACK;
+            }
+            if (e == cudaSuccess && st == RCP_OK && !direct)
                 e = cudaMemcpyAsync(q->out_rgb, q->rgb, sizeof(float) * 3 * (int64_t)q->W * q->H,
                                     cudaMemcpyDeviceToHost, st_copy);
-            if (e == cudaSuccess && !direct) e = cudaStreamSynchronize(st_copy);
+            if (e == cudaSuccess && st == RCP_OK && !direct) e = cudaStreamSynchronize(st_copy);
             if (e != cudaSuccess) st = cuda_fail(e, "server copy-out");
         } else {
             // A failed request may have passes still queued (a step that failed
@@ -318,7 +310,7 @@ void rcp_server::run() {
                 return;
             }
             // admission: FIFO while a slot is free and the memory fits
-            while (!stop && !queue.empty() && (int)inflight.size() < max_slots) {
+            while (!stop && !queue.empty() && (int)inflight.size() < max_slots && !free_status.empty()) {
                 Request* q = queue.front();
                 if (q->bytes > budget) {  // can never fit
                     queue.pop_front();
@@ -328,11 +320,21 @@ void rcp_server::run() {
                     cv_done.notify_all();
                     continue;
                 }
+                if (q->scene->depth > MAX_STACK) {
+                    queue.pop_front();
+                    q->status = RCP_ERR_STACK;
+                    q->done = true;
+                    cv_done.notify_all();
+                    continue;
+                }
                 if (bytes_in_use + q->bytes > budget) break;
                 queue.pop_front();
                 bytes_in_use += q->bytes;
                 bytes_peak = std::max(bytes_peak, bytes_in_use);
                 q->t_admit = now_s();
+                q->status_slot = free_status.back();
+                free_status.pop_back();
+                h_status[q->status_slot] = 0;
                 inflight.push_back(q);
             }
             batch = inflight;
@@ -383,6 +385,11 @@ rcp_status rcp_server_create(int64_t budget, int max_slots, rcp_server** out) {
     RCP_CUDA(cudaStreamCreateWithFlags(&s->st_copy, cudaStreamNonBlocking));
     RCP_CUDA(cudaMalloc((void**)&s->d_rays, sizeof(unsigned long long) * 2));
     RCP_CUDA(cudaMemset(s->d_rays, 0, sizeof(unsigned long long) * 2));
+    // admitted, unfinished requests: at most max_slots in flight and as many
+    // again waiting for copy-out (admission waits for a free word)
+    const int n_status = 2 * max_slots + 16;
+    RCP_CUDA(cudaMallocHost((void**)&s->h_status, sizeof(int) * n_status));
+    for (int i = n_status - 1; i >= 0; --i) s->free_status.push_back(i);
     cudaMemPool_t pool = nullptr;
     RCP_CUDA(cudaDeviceGetDefaultMemPool(&pool, s->device));
     uint64_t thr = (uint64_t)budget;
@@ -511,19 +518,12 @@ void rcp_server_destroy(rcp_server* srv) {
     cudaStreamSynchronize(srv->st_main);
     cudaStreamSynchronize(srv->st_copy);
     for (auto& sl : srv->slots) {
-        for (auto& g : sl.groups) {
-            if (g.st) {
-                cudaStreamSynchronize(g.st);
-                cudaStreamDestroy(g.st);
-            }
-            if (g.d_views) cudaFree(g.d_views);
-            if (g.h_views) cudaFreeHost(g.h_views);
-            if (g.d_work) cudaFree(g.d_work);
-            if (g.d_status) cudaFree(g.d_status);
-            if (g.end) cudaEventDestroy(g.end);
-        }
+        if (sl.d_views) cudaFree(sl.d_views);
+        if (sl.h_views) cudaFreeHost(sl.h_views);
+        if (sl.d_work) cudaFree(sl.d_work);
         if (sl.done) cudaEventDestroy(sl.done);
     }
+    if (srv->h_status) cudaFreeHost(srv->h_status);
     for (auto& kv : srv->all)
         if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     if (srv->d_rays) cudaFree(srv->d_rays);

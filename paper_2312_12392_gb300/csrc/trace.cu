@@ -52,18 +52,23 @@ __global__ void __launch_bounds__(256) k_camera(const ViewDev* __restrict__ view
 
 // Trace, shadow and shade one camera ray; returns the pixel value: RGB and
 // the hit's z-depth t (d . F) along the view axis F (0 on a miss).
+// hint: the records of this pixel's previous primary hit and shadow occluder
+// (-1 none), tested first; updated to this ray's.
 template <bool COUNT>
 __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, const float* Fw, uint2* stack,
-                                              int stride, int stack_entries, bool& overflow, WorkCount& wc,
+                                              int stride, const StackCfg& stk, bool& overflow, WorkCount& wc,
                                               uint32_t& n_shadow, uint32_t& code, int32_t& prim,
-                                              const uint8_t* order_lut) {
-    const Hit h = traverse<false, COUNT>(S, r, stack, stride, stack_entries, overflow, wc, order_lut);
+                                              const uint8_t* order_lut, int2& hint) {
+    const Hit h = traverse<false, COUNT>(S, r, stack, stride, stk, overflow, wc, order_lut, hint.x);
     const ShadeInfo si = shade_primary(S, r, h);
     float4 out = si.c_shadow;
+    hint.x = h.rec;
     if (si.need_shadow) {
         ++n_shadow;
-        const Hit hs = traverse<true, COUNT>(S, si.shadow, stack, stride, stack_entries, overflow, wc, order_lut);
+        const Hit hs =
+            traverse<true, COUNT>(S, si.shadow, stack, stride, stk, overflow, wc, order_lut, hint.y);
         if (hs.rec < 0) out = si.c_lit;
+        hint.y = hs.rec;
     }
     out.w = h.rec < 0 ? 0.f : __fmul_rn(h.t, fdot(r.dx, r.dy, r.dz, Fw[0], Fw[1], Fw[2]));
     code = si.normal_code;
@@ -71,12 +76,13 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
     return out;
 }
 
-template <int BLOCK, bool FUSED, bool COUNT, bool MS>
-__global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __restrict__ views, int n_views,
+// MULTI: every view names its own scene (views of several scenes in one
+// launch); otherwise all views render the launch's scene S0.
+template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI>
+__global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __restrict__ views, int n_views,
                                                  int64_t total_chunks, int chunk_tiles,
-                                                 const float4* __restrict__ rays, unsigned* work, int stack_entries,
-                                                 int* status, unsigned long long* ray_counts,
-                                                 unsigned long long* counters) {
+                                                 const float4* __restrict__ rays, unsigned* work, StackCfg stk,
+                                                 unsigned long long* ray_counts, unsigned long long* counters) {
     extern __shared__ uint2 s_stack[];
     __shared__ uint8_t s_order[ORDER_LUT_BYTES];
     fill_order_lut<BLOCK>(s_order);
@@ -95,6 +101,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
             const int64_t chunk = (int64_t)c0 + sub;
             if (chunk >= total_chunks) break;
             const ViewDev& v = views[find_view_by_chunk(views, n_views, chunk)];
+            const SceneDev& S = MULTI ? *v.scene : S0;
             const int64_t tile = chunk - v.chunk_begin;
             const int tx = (int)(tile % v.tiles_x), ty = (int)(tile / v.tiles_x);
             const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
@@ -106,6 +113,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 uint32_t code0 = 0;
                 int32_t prim0 = -1;
+                int2 hint = v.hint ? v.hint[p] : make_int2(-1, -1);
                 for (int s = 0; s < ns; ++s) {
                     const float jx = v.spp > 0 ? v.jit[2 * s] : 0.5f, jy = v.spp > 0 ? v.jit[2 * s + 1] : 0.5f;
                     const float px = __fadd_rn((float)x, jx), py = __fadd_rn((float)y, jy);
@@ -114,8 +122,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                     const RayF r = camera_ray(v, px, py, c, S.tmin);
                     uint32_t code;
                     int32_t prim;
-                    const float4 o = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stack_entries, overflow, wc,
-                                                        n_shadow, code, prim, s_order);
+                    const float4 o = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc,
+                                                        n_shadow, code, prim, s_order, hint);
                     ++n_primary;
                     acc.x = __fadd_rn(acc.x, o.x);
                     acc.y = __fadd_rn(acc.y, o.y);
@@ -131,11 +139,16 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
                                          __fdiv_rn(acc.w, fn));
                 if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code0);
                 v.out[p] = out;
+                if (v.hint) v.hint[p] = hint;
                 if (v.prim) v.prim[p] = prim0;
                 if (v.rgb) {
                     v.rgb[3 * p] = out.x;
                     v.rgb[3 * p + 1] = out.y;
                     v.rgb[3 * p + 2] = out.z;
+                }
+                if (overflow) {  // this view's image is incomplete
+                    atomicExch(v.status, 1);
+                    overflow = false;
                 }
                 continue;
             }
@@ -156,20 +169,25 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S, const ViewDev* __re
             }
             uint32_t code;
             int32_t prim;
-            float4 out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stack_entries, overflow, wc, n_shadow, code,
-                                            prim, s_order);
+            int2 hint = v.hint ? v.hint[p] : make_int2(-1, -1);
+            float4 out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc, n_shadow, code,
+                                            prim, s_order, hint);
             ++n_primary;
             if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
             v.out[p] = out;
+            if (v.hint) v.hint[p] = hint;
             if (v.prim) v.prim[p] = prim;
             if (v.rgb) {
                 v.rgb[3 * p] = out.x;
                 v.rgb[3 * p + 1] = out.y;
                 v.rgb[3 * p + 2] = out.z;
             }
+            if (overflow) {  // this view's image is incomplete
+                atomicExch(v.status, 1);
+                overflow = false;
+            }
         }
     }
-    if (overflow) atomicExch(&status[0], 1);
     {
         const unsigned np = __reduce_add_sync(0xffffffffu, n_primary);
         const unsigned ns = __reduce_add_sync(0xffffffffu, n_shadow);
@@ -193,12 +211,13 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_debug_trace(SceneDev S, int64_t n, const float4* __restrict__ ot,
                                                        const float4* __restrict__ dt, int any, int brute,
                                                        float* __restrict__ t_out, int32_t* __restrict__ prim_out,
-                                                       int* status) {
+                                                       int stack_entries, int* status) {
     extern __shared__ uint2 s_stack[];
     __shared__ uint8_t s_order[ORDER_LUT_BYTES];
     fill_order_lut<BLOCK>(s_order);
     __syncthreads();
     uint2* stack = s_stack + threadIdx.x;
+    const StackCfg stk{stack_entries, 0, nullptr};
     bool overflow = false;
     WorkCount wc{0, 0, 0, 0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -206,8 +225,8 @@ __global__ void __launch_bounds__(BLOCK) k_debug_trace(SceneDev S, int64_t n, co
         RayF r{a.x, a.y, a.z, b.x, b.y, b.z, a.w, b.w};
         Hit h;
         if (brute) h = any ? traverse_brute<true>(S, r) : traverse_brute<false>(S, r);
-        else h = any ? traverse<true, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc, s_order)
-                     : traverse<false, false>(S, r, stack, BLOCK, MAX_STACK, overflow, wc, s_order);
+        else h = any ? traverse<true, false>(S, r, stack, BLOCK, stk, overflow, wc, s_order)
+                     : traverse<false, false>(S, r, stack, BLOCK, stk, overflow, wc, s_order);
         if (any) {
             prim_out[i] = h.rec >= 0 ? 1 : 0;
             t_out[i] = 0.f;
@@ -309,11 +328,11 @@ int sm_count() {
     return sms;
 }
 
-template <int BLOCK, bool FUSED, bool COUNT, bool MS>
+template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI>
 rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
-                          int64_t total_chunks, const float4* rays, unsigned* d_work, int* d_status,
-                          unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
-    auto kern = k_trace<BLOCK, FUSED, COUNT, MS>;
+                          int64_t total_chunks, const float4* rays, unsigned* d_work, unsigned long long* d_rays,
+                          unsigned long long* d_counters, cudaStream_t st) {
+    auto kern = k_trace<BLOCK, FUSED, COUNT, MS, MULTI>;
     const size_t smem = sizeof(uint2) * (size_t)cfg.stack * BLOCK;
     if (smem > 48 * 1024) RCP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = cfg.blocks_per_sm;
@@ -324,34 +343,45 @@ rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
     int64_t grid = (int64_t)sm_count() * per_sm;
     const int64_t need = (total_chunks * 32 + BLOCK - 1) / BLOCK;
     if (grid > need) grid = need > 0 ? need : 1;
-    kern<<<(int)grid, BLOCK, smem, st>>>(S, d_views, n_views, total_chunks, cfg.chunk / 32, rays, d_work, cfg.stack,
-                                         d_status, d_rays, d_counters);
+    StackCfg stk{cfg.stack, cfg.spill ? cfg.spill_entries : 0, cfg.spill};
+    if (stk.spill_entries > 0 && grid * BLOCK * (int64_t)stk.spill_entries > cfg.spill_cap) {
+        set_error("traversal spill region too small for the launch");
+        return RCP_ERR_STATE;
+    }
+    kern<<<(int)grid, BLOCK, smem, st>>>(S, d_views, n_views, total_chunks, cfg.chunk / 32, rays, d_work, stk, d_rays,
+                                         d_counters);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }
 
-template <bool FUSED, bool COUNT, bool MS>
+template <bool FUSED, bool COUNT, bool MS, bool MULTI>
 rcp_status launch_trace_b(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
-                          int64_t total_chunks, const float4* rays, unsigned* d_work, int* d_status,
-                          unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
+                          int64_t total_chunks, const float4* rays, unsigned* d_work, unsigned long long* d_rays,
+                          unsigned long long* d_counters, cudaStream_t st) {
     switch (cfg.block) {
         case 64:
-            return launch_trace_t<64, FUSED, COUNT, MS>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
-                                                    d_rays, d_counters, st);
+            return launch_trace_t<64, FUSED, COUNT, MS, MULTI>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                               d_rays, d_counters, st);
         case 256:
-            return launch_trace_t<256, FUSED, COUNT, MS>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
-                                                     d_rays, d_counters, st);
+            return launch_trace_t<256, FUSED, COUNT, MS, MULTI>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                                d_rays, d_counters, st);
         default:
-            return launch_trace_t<128, FUSED, COUNT, MS>(S, cfg, d_views, n_views, total_chunks, rays, d_work, d_status,
-                                                     d_rays, d_counters, st);
+            return launch_trace_t<128, FUSED, COUNT, MS, MULTI>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                                d_rays, d_counters, st);
     }
 }
 
 }  // namespace
 
 rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
-                       int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work, int* d_status,
+                       int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work,
                        unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st) {
+    if (cfg.multi) {  // views of several scenes: fused camera, no counters
+        return cfg.ms ? launch_trace_b<true, false, true, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                                d_rays, nullptr, st)
+                      : launch_trace_b<true, false, false, true>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                 d_work, d_rays, nullptr, st);
+    }
     if (!cfg.fused && !cfg.ms) {
         int64_t g = (total_pix + 255) / 256;
         if (g > (int64_t)sm_count() * 16) g = (int64_t)sm_count() * 16;
@@ -360,31 +390,32 @@ rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d
         RCP_CUDA(cudaGetLastError());
     }
     if (cfg.ms) {  // jittered samples: camera inside the trace kernel
-        return cfg.count ? launch_trace_b<true, true, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                            d_status, d_rays, d_counters, st)
-                         : launch_trace_b<true, false, true>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                             d_status, d_rays, d_counters, st);
+        return cfg.count ? launch_trace_b<true, true, true, false>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                   d_work, d_rays, d_counters, st)
+                         : launch_trace_b<true, false, true, false>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                    d_work, d_rays, d_counters, st);
     }
     if (cfg.count)
-        return cfg.fused ? launch_trace_b<true, true, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                             d_status, d_rays, d_counters, st)
-                         : launch_trace_b<false, true, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                              d_status, d_rays, d_counters, st);
-    return cfg.fused ? launch_trace_b<true, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                          d_status, d_rays, d_counters, st)
-                     : launch_trace_b<false, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                           d_status, d_rays, d_counters, st);
+        return cfg.fused ? launch_trace_b<true, true, false, false>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                    d_work, d_rays, d_counters, st)
+                         : launch_trace_b<false, true, false, false>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                     d_work, d_rays, d_counters, st);
+    return cfg.fused ? launch_trace_b<true, false, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                                 d_rays, d_counters, st)
+                     : launch_trace_b<false, false, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
+                                                                  d_rays, d_counters, st);
 }
 
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
-                              int brute, float* t_out, int32_t* prim_out, int* d_status, cudaStream_t st) {
+                              int brute, float* t_out, int32_t* prim_out, int stack_entries, int* d_status,
+                              cudaStream_t st) {
     if (n <= 0) return RCP_OK;
     const size_t smem = sizeof(uint2) * MAX_STACK * 128;
     RCP_CUDA(cudaFuncSetAttribute(k_debug_trace<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t g = (n + 127) / 128;
     if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
     k_debug_trace<128><<<(int)g, 128, smem, st>>>(S, n, (const float4*)orig_tmin, (const float4*)dir_tmax, any, brute,
-                                                 t_out, prim_out, d_status);
+                                                 t_out, prim_out, stack_entries, d_status);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }

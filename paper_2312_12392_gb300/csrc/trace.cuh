@@ -259,14 +259,59 @@ __device__ __forceinline__ void fill_order_lut(uint8_t* lut) {
 #define RCP_FAR_SCALE 1.000000476837158203125f
 #define RCP_BOX_SLACK 1.0000076f
 
+// The traversal stack of one thread: `entries` groups in shared memory at
+// stack[i * stride], and above those `spill_entries` more in global memory,
+// entry i at spill[(i - entries) * T + t] for the launch's thread t of T
+// (both from the launch's own indices, so no pointer stays live in a
+// register). A stack as deep as the tree (one group per level) never
+// reaches the spill region; a shorter shared stack trades the spill traffic of
+// deep walks for less shared memory per block. Pushing past both sets
+// `overflow` and drops the group, which ends the walk early.
+struct StackCfg {
+    int entries;        // shared-memory entries per thread
+    int spill_entries;  // global-memory entries per thread above those
+    uint2* spill;       // spill_entries * (gridDim.x * blockDim.x) entries, or null
+};
+
+__device__ __forceinline__ uint2* spill_slot(const StackCfg& sc, int i) {
+    const uint32_t T = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;
+    return sc.spill + (size_t)(i - sc.entries) * T + t;
+}
+
+// first_rec: a record to test before the walk (-1 none), in practice the one
+// this pixel's ray hit in the previous pass. A hit there starts the walk with
+// a far limit at its distance, so boxes behind it are never entered, and ends
+// an any-hit walk at once. The result does not depend on it: the walk still
+// keeps the least (t, id) over every record in a box the ray enters up to
+// t (1 + 2^-17), and an any-hit answer is a yes/no.
 template <bool ANY, bool COUNT>
-__device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2* stack, int stride, int stack_limit,
-                                        bool& overflow, WorkCount& wc, const uint8_t* order_lut) {
+__device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2* stack, int stride,
+                                        const StackCfg& stk, bool& overflow, WorkCount& wc, const uint8_t* order_lut,
+                                        int32_t first_rec = -1) {
     Hit h;
     h.t = r.tmax;
     h.id = 0xffffffffu;
     h.rec = -1;
     if (S.n_nodes == 0) return h;
+    if (first_rec >= 0 && first_rec < S.n_records) {
+        const float4* pp = S.prims + 3 * (size_t)first_rec;
+        const float4 w0 = __ldg(pp), w1 = __ldg(pp + 1), w2 = __ldg(pp + 2);
+        const uint32_t idb = __float_as_uint(w2.y);
+        float t;
+        if (idb & SPHERE_BIT) {
+            t = hit_sphere(r, w0);
+            if (COUNT) wc.spheres++;
+        } else {
+            t = hit_triangle(r, w0, w1, w2);
+            if (COUNT) wc.tris++;
+        }
+        if (t > r.tmin && t < r.tmax) {
+            h.t = t;
+            h.id = idb & ~SPHERE_BIT;
+            h.rec = first_rec;
+            if (ANY) return h;
+        }
+    }
     // A zero component stays zero (as +0, so that the octant bit and the sign
     // of 1/d agree) and its reciprocal is +inf: the ray is parallel to that
     // axis's planes. Its slab terms are then +-inf, or NaN where inf - inf
@@ -291,7 +336,7 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
     const int rxn = (oct & 1u) ? 2 : 0, rxf = 2 - rxn;
     const int ryn = (oct & 2u) ? 6 : 4, ryf = 10 - ryn;
     const int rzn = (oct & 4u) ? 10 : 8, rzf = 18 - rzn;
-    float tfar_lim = __fmul_rn(h.t, RCP_BOX_SLACK);
+    float tfar_lim = __fmul_rn(h.t, RCP_BOX_SLACK);  // +inf without a first hit
 
     // node group: x = first child node index, y = imask | (slots still to visit) << 8;
     // the root is slot 0 of a group of one
@@ -314,15 +359,18 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
         if (group.y <= 0xffu) {
             if (sp == 0) break;
             --sp;
-            group = stack[sp * stride];
+            group = sp < stk.entries ? stack[sp * stride] : *spill_slot(stk, sp);
         }
         {
             const uint32_t slot = ord[group.y >> 8];
             group.y &= ~(1u << (slot + 8));
             const uint32_t node = group.x + __popc(group.y & 0xffu & ((1u << slot) - 1u));
             if (group.y > 0xffu) {
-                if (sp < stack_limit) {
+                if (sp < stk.entries) {
                     stack[sp * stride] = group;
+                    ++sp;
+                } else if (sp < stk.entries + stk.spill_entries) {
+                    *spill_slot(stk, sp) = group;
                     ++sp;
                 } else {
                     overflow = true;

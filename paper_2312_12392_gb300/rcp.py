@@ -61,7 +61,7 @@ class rcp_build_options(C.Structure):
 
 class rcp_tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
-                ("fused_camera", C.c_int32)]
+                ("fused_camera", C.c_int32), ("stack_entries", C.c_int32)]
 
 
 class rcp_counters(C.Structure):
@@ -104,9 +104,10 @@ _SIGS = {
                        C.POINTER(rcp_counters)],
     "rcp_last_pass_times": [_vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)],
     "rcp_render_h2d_bytes": [C.c_int, C.c_int],
-    "rcp_debug_trace": [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp],
+    "rcp_debug_trace": [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_int, _vp, _vp, C.c_int, _vp],
     "rcp_debug_sort_pairs": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_debug_morton": [_vp, C.c_int64, _vp, _vp, _vp, _vp],
+    "rcp_debug_sort_lookback_timeout": [C.c_int64, _vp],
     "rcp_imagespace_pass_device": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp],
     "rcp_sort_pairs_static": [_vp, _vp, C.c_int64, C.c_int, _vp],
     "rcp_sort_static_capacity": [],
@@ -349,9 +350,9 @@ def rcp_last_pass_times(scene, max_passes=16):
     return list(ms)[: n.value]
 
 
-def rcp_debug_trace(scene, n, orig_tmin, dir_tmax, any_hit, brute, t_out, prim_out, stream=None):
+def rcp_debug_trace(scene, n, orig_tmin, dir_tmax, any_hit, brute, t_out, prim_out, stream=None, stack_entries=0):
     _check(lib().rcp_debug_trace(scene, n, _ptr(orig_tmin), _ptr(dir_tmax), int(any_hit), int(brute), _ptr(t_out),
-                                 _ptr(prim_out), _stream(stream)), "rcp_debug_trace")
+                                 _ptr(prim_out), int(stack_entries), _stream(stream)), "rcp_debug_trace")
 
 
 def rcp_debug_sort_pairs(keys, values, n, bits, stream=None):
@@ -363,6 +364,10 @@ def rcp_debug_morton(xyz, n, lo, hi, codes, stream=None):
     hi = _host(hi, np.float32, 3)
     _check(lib().rcp_debug_morton(_ptr(xyz), n, _ptr(lo), _ptr(hi), _ptr(codes), _stream(stream)),
            "rcp_debug_morton")
+
+
+def rcp_debug_sort_lookback_timeout(spin_limit, stream=None):
+    _check(lib().rcp_debug_sort_lookback_timeout(int(spin_limit), _stream(stream)), "rcp_debug_sort_lookback_timeout")
 
 
 def rcp_sort_static_capacity() -> int:

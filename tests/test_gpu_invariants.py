@@ -61,6 +61,29 @@ def test_launch_shapes_identical(tiny_g):
                     if ref is None:
                         ref = out
                     assert np.array_equal(out, ref), (block, fused, chunk)
+        # shorter shared stacks: the deeper levels spill to global memory
+        for stack in (4, 2, 1):
+            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, stack))
+            assert np.array_equal(_render(g, cam, 640, 360, 3, p), ref), stack
+    finally:
+        rcp.rcp_scene_destroy(g)
+
+
+def test_short_stack_spills_identical():
+    """The forest in the benchmark's build (13 levels): a 4-entry shared stack
+    spills twelve levels to global memory and renders the same image, also
+    batched and with the separate camera kernel."""
+    sc = scenes.forest_scene()
+    g = U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
+    try:
+        assert rcp.rcp_scene_get_info(g).depth > 8
+        cam = rcp.camera_from(sc.poses[20])
+        d = sc.diameter()
+        p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+        ref = _render(g, cam, 480, 270, 4, p)
+        for t in (rcp.rcp_tuning(128, 0, 32, 1, 4), rcp.rcp_tuning(256, 0, 64, 0, 8), rcp.rcp_tuning(64, 0, 32, 1, 1)):
+            rcp.rcp_set_tuning(g, t)
+            assert np.array_equal(_render(g, cam, 480, 270, 4, p), ref), (t.block, t.stack_entries)
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -184,13 +207,23 @@ def test_ray_counts_and_counters(tiny_g):
     assert out.shape == (128, 128, 3)
 
 
-def test_autotune_cache(tmp_path, tiny_g):
-    sc, g = tiny_g
-    cam = rcp.camera_from(sc.poses[0])
-    p = rcp.make_params(rcp.RCP_MAP_EYE, 1.4, 6.0)
-    path = str(tmp_path / "tune.json")
-    t = rcp.rcp_autotune(g, cam, 256, 256, p, path)
-    assert t.block in (64, 128, 256) and t.chunk in (32, 64)
-    t2 = rcp.rcp_autotune(g, cam, 256, 256, p, path)  # from the cache
-    assert (t2.block, t2.chunk, t2.fused_camera) == (t.block, t.chunk, t.fused_camera)
-    rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1))
+def test_autotune_cache(tmp_path):
+    """The autotuner searches block, chunk, camera kernel and shared stack
+    depth (mid: 7 levels, so 8 or 4 entries), and the cache returns its pick."""
+    sc = scenes.mid_scene()
+    g = U.gpu_scene(sc)
+    try:
+        cam = rcp.camera_from(sc.poses[0])
+        d = sc.diameter()
+        p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+        path = str(tmp_path / "tune.json")
+        ref = _render(g, cam, 320, 180, 3, p)
+        t = rcp.rcp_autotune(g, cam, 320, 180, p, path)
+        assert t.block in (64, 128, 256) and t.chunk in (32, 64) and t.stack_entries in (0, 4)
+        assert np.array_equal(_render(g, cam, 320, 180, 3, p), ref)
+        t2 = rcp.rcp_autotune(g, cam, 320, 180, p, path)  # from the cache
+        assert (t2.block, t2.chunk, t2.fused_camera, t2.stack_entries) == (t.block, t.chunk, t.fused_camera,
+                                                                            t.stack_entries)
+        assert "depth7" in open(path).read()
+    finally:
+        rcp.rcp_scene_destroy(g)

@@ -94,7 +94,7 @@ def test_memory_admission(two_scenes):
     cam = rcp.camera_from(sc.poses[0])
     p = rcp.make_params(rcp.RCP_MAP_EYE, 1.0, 6.0)
     W, H = 256, 256
-    per_req = W * H * 44 + 768
+    per_req = W * H * 52 + 1024  # two rgbz images, hit hints and RGB staging (the larger, copy-out form)
     srv = rcp.rcp_server_create(2 * per_req + 100, 16)  # room for two at a time
     try:
         outs = [np.empty((H, W, 3), np.float32) for _ in range(6)]
