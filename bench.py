@@ -8,16 +8,22 @@ frame = K passes (camera + primary ray + shadow ray + shading for every pixel),
 replayed from the library's captured CUDA graph with the scene resident in HBM.
 L2 is flushed (a 256 MB write) between steps, outside the timed events.
 
+At one GPU the same line also carries the other workloads, each measured in
+this run: "forest" (the 1.07M-triangle forest, 1080p K=6 over its 64-pose
+walk-through, with its own roofline, end-to-end figure and clock record),
+"batched" (64 uneven forest views, one launch per pass, against per-view
+launches), "served" (Poisson arrivals over four resident terrains of 0.1-5M
+triangles, the continuous-batching server against the plain per-request path,
+1,000 requests per rate) and "stress" (the 12.57M-triangle swaying forest at
+4K, K=8, refit and render per frame).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload mid|forest|batched|served|stress|imagespace]
-                    [--collapse auto|area|sah] [--tuning auto|block,chunk,fused]
+                    [--collapse auto|area|sah] [--tuning auto|block,chunk,fused[,stack]]
+                    [--no-extras]
 
-The other workloads print their own line: the 1.07M-triangle forest, 64
-batched forest views in one persistent launch, Poisson-arrival serving
-against the plain per-request path, the 12.57M-triangle swaying forest at 4K
-with per-frame refit (device-only, one stream and the serving path end to
-end), and the image-space gather passes. --collapse auto builds the forests'
-BVHs with the surface-area slot assignment and the terrains' with the
+--workload prints one workload's line alone. --collapse auto builds the
+forests' BVHs with the surface-area slot assignment and the terrains' with the
 largest-area rule (the faster for each, as measured); the choice is printed in
 each line's config.
 
@@ -102,17 +108,17 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per trace launch from the committed ncu summary, if it was
-    taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "trace_dram_traffic.json")
+def profiled(workload):
+    """The committed ncu record of the trace kernel on this workload (DRAM
+    bytes per launch, issue and pipe utilisation, L1 hit rate), if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "k_trace_ncu.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    e = d.get(workload)
+    e = json.load(open(p)).get(workload)
     if not e or e.get("csrc_hash") != csrc_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
 
 
 class ClockSampler:
@@ -255,6 +261,138 @@ def cpu_oracle_sample(sc, poses, target_s, nthreads=0, min_px=64, max_px=8192):
     return fps, total_px, total_t
 
 
+# ------------------------------------------------------------------ measurement helpers
+
+def parse_tuning(spec):
+    from paper_2312_12392_gb300 import rcp
+    v = [int(x) for x in spec.split(",")]
+    return rcp.rcp_tuning(v[0], 0, v[1], v[2], v[3] if len(v) > 3 else 0, v[4] if len(v) > 4 else 3)
+
+
+def tuning_dict(t):
+    return {"block": t.block, "chunk": t.chunk, "fused_camera": t.fused_camera, "stack_entries": t.stack_entries,
+            "hints": t.hints}
+
+
+def time_frames(g, cams, W, H, K, params, stream, flush):
+    """Render one frame per camera (K passes each) through the device path,
+    L2 flushed before each (outside the events). Returns per-frame ms (CUDA
+    events on the launching stream), per-pass ms (events inside the captured
+    graph) and the rays traced."""
+    import torch
+
+    from paper_2312_12392_gb300 import rcp
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    step_ms, pass_ms, rays = [], [], 0
+    for c in cams:
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        rcp.rcp_render_device(g, c, W, H, K, params, None, out, None, stream)
+        e.record(stream)
+        e.synchronize()
+        step_ms.append(s.elapsed_time(e))
+        pass_ms.extend(rcp.rcp_last_pass_times(g))
+        p_, s_ = rcp.rcp_last_ray_counts(g)
+        rays += p_ + s_
+    return step_ms, pass_ms, rays
+
+
+def count_work(g, cams, W, H, K, params):
+    """The algorithmic work of the timed frames: an instrumented copy of the
+    trace kernel run over the same cameras, K chained passes each."""
+    import torch
+
+    from paper_2312_12392_gb300 import rcp
+    tot = dict(box=0, tri=0, sph=0, nodes=0, prim_rays=0, rays=0, launches=0)
+    a = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for c in cams:
+        prev = None
+        for n in range(K):
+            dst = a if n % 2 == 0 else b
+            cnt = rcp.rcp_count_pass(g, c, W, H, params, prev, dst)
+            tot["box"] += cnt.box_tests
+            tot["tri"] += cnt.tri_tests
+            tot["sph"] += cnt.sphere_tests
+            tot["nodes"] += cnt.nodes
+            tot["prim_rays"] += cnt.primary_rays
+            tot["rays"] += cnt.rays
+            tot["launches"] += 1
+            prev = dst
+    return tot
+
+
+def roofline(work, pass_ms, workload, clk, sms):
+    """The trace kernel's roofline: algorithmic FP32 lane-operations per launch
+    over the mean launch time, against SMs x 128 lanes x the maximum SM clock
+    (the kernel is bound by instruction issue and the ALU pipe, ncu); the byte
+    view charges every node, primitive and image fetch at the measured HBM
+    peak; the ncu view (issue, pipes, L1) comes from the committed profile when
+    it was taken on the current sources."""
+    hbm_gbs, sm_max_mhz, peak_src = measured_peaks()
+    n = max(work["launches"], 1)
+    ops = (OPS_BOX * work["box"] + OPS_TRI * work["tri"] + OPS_SPH * work["sph"] + OPS_PIXEL * work["prim_rays"]) / n
+    byts = (BYTES_NODE * work["nodes"] + BYTES_PRIM * (work["tri"] + work["sph"]) +
+            BYTES_PIXEL_PASS * work["prim_rays"]) / n
+    launch_s = statistics.mean(pass_ms) / 1000.0
+    peak = sms * 128 * sm_max_mhz * 1e6
+    prof = profiled(workload)
+    roof = {"bound": "alu", "achieved": ops / launch_s / 1e12, "peak": peak / 1e12,
+            "unit": "Tops/s (algorithmic FP32 lane-ops)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = prof.get("dram_bytes_per_launch") if prof else None
+    roof["kernel"] = "k_trace (camera + primary + shadow + shade, one launch per pass)"
+    roof["launch_ms"] = launch_s * 1e3
+    roof["launches_counted"] = work["launches"]
+    roof["algorithmic_ops_per_launch"] = ops
+    roof["algorithmic_bytes_per_launch"] = byts
+    roof["peak_source"] = f"{sms} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"
+    roof["hbm_view"] = {"achieved_gbs": byts / launch_s / 1e9, "peak_gbs": hbm_gbs,
+                        "frac": byts / launch_s / 1e9 / hbm_gbs, "peak_source": peak_src,
+                        "note": "algorithmic node/primitive/image bytes charged at HBM peak; they are served "
+                                "from L1/L2 (see traffic)"}
+    if prof:
+        roof["ncu_view"] = {k: prof[k] for k in ("issue_active_pct", "alu_pipe_pct", "fma_pipe_pct",
+                                                 "l1tex_throughput_pct", "l1_hit_pct", "dram_throughput_pct",
+                                                 "warp_lanes_active")
+                            if k in prof}
+        roof["ncu_view"]["source"] = "profiles/k_trace_ncu.json (" + prof.get("command", "") + ")"
+    if clk and clk.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = roof["frac"] * sm_max_mhz / clk["sm_mhz"]
+    r = max(work["rays"], 1)
+    roof["per_ray"] = {"nodes": work["nodes"] / r, "box_tests": work["box"] / r, "tri_tests": work["tri"] / r}
+    return roof
+
+
+def e2e_host(g, cams, W, H, K, params, flush, n):
+    """Frames/s through rcp_render with a host RGB buffer: the per-call
+    view-descriptor upload and the image's delivery to host memory are inside
+    the timed call."""
+    import torch
+
+    from paper_2312_12392_gb300 import rcp
+    host = np.empty((H, W, 3), np.float32)
+    t = 0.0
+    for i in range(n + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rcp.rcp_render(g, cams[i % len(cams)], W, H, K, params, host)
+        if i > 0:
+            t += time.perf_counter() - t0
+    return n / t, t
+
+
+def e2e_record(value, t_unit, W, H, K):
+    from paper_2312_12392_gb300 import rcp
+    return {"value": value, "unit": t_unit, "h2d_bytes_per_step": rcp.rcp_render_h2d_bytes(1, K),
+            "d2h_bytes_per_step": W * H * 3 * 4 + 4,  # the RGB image and the status word
+            "api": "rcp_render (host RGB output; view descriptors H2D, RGB device-to-host inside the timed call: "
+                   "written into host memory by the last pass where the device reads pageable memory "
+                   "coherently, else packed and copied)"}
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -285,17 +423,14 @@ def run_ours(args):
         t = rcp.rcp_autotune(g, rcp.camera_from(sc.poses[0]), W_IMG, H_IMG, params,
                              os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
     else:
-        b, c, fz = (int(x) for x in args.tuning.split(","))
-        t = rcp.rcp_tuning(b, 0, c, fz)
+        t = parse_tuning(args.tuning)
         rcp.rcp_set_tuning(g, t)
-    log(f"[rank {rank}] tuning block={t.block} chunk={t.chunk} fused_camera={t.fused_camera}")
+    log(f"[rank {rank}] tuning {tuning_dict(t)}")
     poses = [sc.poses[i] for i in shard_poses(rank, world, args.steps, len(sc.poses))]
     cams = [rcp.camera_from(p) for p in poses]
     stream = torch.cuda.current_stream()
-    out = torch.empty((H_IMG, W_IMG, 4), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    for i in range(args.warmup):
-        rcp.rcp_render_device(g, cams[i % len(cams)], W_IMG, H_IMG, K_PASSES, params, None, out, None, stream)
+    time_frames(g, [cams[i % len(cams)] for i in range(args.warmup)], W_IMG, H_IMG, K_PASSES, params, stream, flush)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -303,18 +438,8 @@ def run_ours(args):
     clocks = ClockSampler(physical_gpu(local))
     clocks.start()
     time.sleep(0.3)
-    step_ms, pass_ms = [], []
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        s, e = evs[i]
-        s.record(stream)
-        rcp.rcp_render_device(g, cams[i], W_IMG, H_IMG, K_PASSES, params, None, out, None, stream)
-        e.record(stream)
-        e.synchronize()
-        step_ms.append(s.elapsed_time(e))
-        pass_ms.extend(rcp.rcp_last_pass_times(g))
+    step_ms, pass_ms, rays = time_frames(g, cams, W_IMG, H_IMG, K_PASSES, params, stream, flush)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
@@ -323,77 +448,12 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
     tmax = max_over_ranks(total_ms, "cuda")
-
-    # rays traced per timed frame (deterministic per pose): replay each frame once more
-    rays = 0
-    for c in cams:
-        rcp.rcp_render_device(g, c, W_IMG, H_IMG, K_PASSES, params, None, out, None, stream)
-        torch.cuda.synchronize()
-        p_, s_ = rcp.rcp_last_ray_counts(g)
-        rays += p_ + s_
     rays = sum_over_ranks(rays, "cuda")
-
-    # algorithmic work of a launch: chained counted passes over a few poses
-    n_cnt = min(args.count_poses, len(cams))
-    tot = dict(box=0, tri=0, sph=0, nodes=0, prim_rays=0, rays=0)
-    a = torch.empty_like(out)
-    b = torch.empty_like(out)
-    for c in cams[:n_cnt]:
-        prev = None
-        for n in range(K_PASSES):
-            dst = a if n % 2 == 0 else b
-            cnt = rcp.rcp_count_pass(g, c, W_IMG, H_IMG, params, prev, dst)
-            tot["box"] += cnt.box_tests
-            tot["tri"] += cnt.tri_tests
-            tot["sph"] += cnt.sphere_tests
-            tot["nodes"] += cnt.nodes
-            tot["prim_rays"] += cnt.primary_rays
-            tot["rays"] += cnt.rays
-            prev = dst
-    n_launch_cnt = n_cnt * K_PASSES
-    ops_launch = (OPS_BOX * tot["box"] + OPS_TRI * tot["tri"] + OPS_SPH * tot["sph"] +
-                  OPS_PIXEL * tot["prim_rays"]) / n_launch_cnt
-    bytes_launch = (BYTES_NODE * tot["nodes"] + BYTES_PRIM * (tot["tri"] + tot["sph"]) +
-                    BYTES_PIXEL_PASS * tot["prim_rays"]) / n_launch_cnt
-    launch_s = statistics.mean(pass_ms) / 1000.0
-    hbm_gbs, sm_max_mhz, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    alu_peak = sms * 128 * sm_max_mhz * 1e6  # FP32 lanes x clock (ops/s)
-    # The kernel is bound by arithmetic issue (ncu: integer/logic and FMA pipes
-    # busy, DRAM idle because the BVH and images stay in L2), so the roofline
-    # is the FP32-lane one. The byte view (every node and primitive fetch
-    # charged at HBM peak) is reported beside it.
-    roof = {"bound": "alu", "achieved": ops_launch / launch_s / 1e12, "peak": alu_peak / 1e12,
-            "unit": "Tops/s (algorithmic FP32 lane-ops)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = profiled_traffic(args.workload)
-    roof["kernel"] = "k_trace (camera + primary + shadow + shade, one launch per pass)"
-    roof["launch_ms"] = launch_s * 1e3
-    roof["algorithmic_ops_per_launch"] = ops_launch
-    roof["algorithmic_bytes_per_launch"] = bytes_launch
-    roof["peak_source"] = f"{sms} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"
-    roof["hbm_view"] = {"achieved_gbs": bytes_launch / launch_s / 1e9, "peak_gbs": hbm_gbs,
-                        "frac": bytes_launch / launch_s / 1e9 / hbm_gbs, "peak_source": peak_src,
-                        "note": "algorithmic node/primitive/image bytes charged at HBM peak; they are served "
-                                "from L1/L2 (see traffic)"}
-    if clk and clk.get("sm_mhz"):
-        roof["frac_at_sampled_clock"] = roof["frac"] * sm_max_mhz / clk["sm_mhz"]
-    roof["per_ray"] = {"nodes": tot["nodes"] / max(tot["rays"], 1), "box_tests": tot["box"] / max(tot["rays"], 1),
-                       "tri_tests": tot["tri"] / max(tot["rays"], 1)}
-
-    # end to end through the host API (host output buffer, copies timed)
-    e2e_steps = max(3, min(args.steps, 16))
-    host = np.empty((H_IMG, W_IMG, 3), np.float32)
-    e2e_t = 0.0
-    for i in range(e2e_steps + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rcp.rcp_render(g, cams[i % len(cams)], W_IMG, H_IMG, K_PASSES, params, host)
-        if i > 0:
-            e2e_t += time.perf_counter() - t0
-    e2e_fps = world * e2e_steps / max_over_ranks(e2e_t, "cuda")
-
+    # algorithmic work of the timed launches: the same poses, counted
+    roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, args.workload, clk, sms)
+    e2e_fps, e2e_t = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, max(3, min(args.steps, 16)))
+    e2e_fps = world * max(3, min(args.steps, 16)) / max_over_ranks(e2e_t, "cuda")
     frames = args.steps * world
     value = frames / (tmax / 1000.0)
     res = {
@@ -411,35 +471,42 @@ def run_ours(args):
         "data": "synthetic (seeded procedural scene and walk-through)",
         "config": {"workload": desc, "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
-                   "tuning": {"block": t.block, "chunk": t.chunk, "fused_camera": t.fused_camera},
+                   "tuning": tuning_dict(t),
+                   "tuning_source": "rcp_autotune (block x chunk x fused camera x shared stack depth x hints)"
+                   if args.tuning == "auto" else "fixed by --tuning",
                    "parallelism": f"replicas x{world} (poses split across ranks, no collective on the data path)"},
         "mrays_per_s": rays / (tmax / 1000.0) / 1e6,
         "rays_per_frame": rays / frames,
         "roofline": roof,
-        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": rcp.rcp_render_h2d_bytes(1, K_PASSES),
-                "d2h_bytes_per_step": W_IMG * H_IMG * 3 * 4 + 4,  # the RGB image and the status word
-                "api": "rcp_render (host RGB output; view descriptors H2D, RGB device-to-host inside the timed call: written into host memory by the last pass where the device reads pageable memory coherently, else packed and copied)"},
+        "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES),
         "gpu_launches": args.steps * K_PASSES * (1 if t.fused_camera else 2),
         "clocks": clk,
         "wall_s": wall,
     }
+    rcp.rcp_scene_destroy(g)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fps, npx, secs = cpu_oracle_sample(sc, poses[:2], target_s=args.cpu_seconds / 2)
         res["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"{npx} seeded pixels (full K=6 chains) over 2 poses in {secs:.1f} s, "
                                          f"extrapolated to 1920x1080 frames"}
-    if args.extra_forest and args.workload == "mid" and world == 1:
-        res["forest"] = forest_extra(args)
-    rcp.rcp_scene_destroy(g)
+    if args.extras and args.workload == "mid" and world == 1:
+        for name, fn in (("forest", forest_summary), ("batched", batched_summary), ("served", served_summary),
+                         ("stress", stress_summary)):
+            t1 = time.perf_counter()
+            res[name] = fn(args)
+            res[name]["bench_wall_s"] = time.perf_counter() - t1
+            log(f"{name}: {json.dumps(res[name])[:400]}")
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def forest_extra(args):
-    """The 1.07M-triangle forest at 1080p K=6 over its whole 64-pose walk-through
-    (same protocol as the headline: L2 flushed between frames, CUDA events)."""
+def forest_summary(args):
+    """The 1.07M-triangle forest at 1080p K=6 over its whole 64-pose
+    walk-through (same protocol as the headline: L2 flushed between frames,
+    CUDA events), with its own clock record, roofline (work counted on the same
+    64 poses) and end-to-end figure through rcp_render with host output."""
     import torch
 
     from paper_2312_12392_gb300 import rcp
@@ -450,30 +517,33 @@ def forest_extra(args):
     split = split_for(args, "forest")
     g = rcp.scene_from(sc, collapse, split)
     try:
-        cams = [rcp.camera_from(p) for p in sc.poses]
+        cams = [rcp.camera_from(p) for p in sc.poses[: max(1, args.forest_poses)]]
+        if args.tuning == "auto":
+            t = rcp.rcp_autotune(g, cams[0], W_IMG, H_IMG, params,
+                                 os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
+        else:
+            t = parse_tuning(args.tuning)
+            rcp.rcp_set_tuning(g, t)
         stream = torch.cuda.current_stream()
-        out = torch.empty((H_IMG, W_IMG, 4), dtype=torch.float32, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-        for c in cams[:3]:
-            rcp.rcp_render_device(g, c, W_IMG, H_IMG, K_PASSES, params, None, out, None, stream)
+        time_frames(g, cams[:3], W_IMG, H_IMG, K_PASSES, params, stream, flush)
         torch.cuda.synchronize()
-        ms, rays = [], 0
-        for c in cams:
-            flush.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            rcp.rcp_render_device(g, c, W_IMG, H_IMG, K_PASSES, params, None, out, None, stream)
-            e.record(stream)
-            e.synchronize()
-            ms.append(s.elapsed_time(e))
-            p_, s_ = rcp.rcp_last_ray_counts(g)
-            rays += p_ + s_
+        clocks = ClockSampler(physical_gpu(0))
+        clocks.start()
+        time.sleep(0.3)
+        ms, pass_ms, rays = time_frames(g, cams, W_IMG, H_IMG, K_PASSES, params, stream, flush)
+        clk = clocks.stop()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, "forest", clk, sms)
+        e2e_fps, _ = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, 16)
         tot = sum(ms) / 1000.0
         info = rcp.rcp_scene_get_info(g)
         return {"workload": desc, "frames_per_s": len(cams) / tot, "mrays_per_s": rays / tot / 1e6,
-                "ms_per_frame": 1000 * tot / len(cams), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
+                "ms_per_frame": 1000 * tot / len(cams), "frames": len(cams), "roofline": roof,
+                "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES), "clocks": clk,
+                "tuning": tuning_dict(t), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
                 "depth": info.depth, "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
-                "records": info.n_records}
+                "records": info.n_records, "gpu_launches": len(cams) * K_PASSES}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -531,195 +601,197 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
-# ------------------------------------------------------------------ batched and served modes
+# ------------------------------------------------------------------ batched, served and stress workloads
 
-def run_batched(args):
+def one_line(metric, value, unit, args, steps, extra):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+           "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic"}
+    out.update(extra)
+    return out
+
+
+def batched_summary(args):
     """64 views of uneven size (W in [256,1920], H in [256,1080], seeded) of the
     1.07M-triangle forest, K = 6: one persistent launch per pass over all views
     (graph-captured, autotuned), against rendering the same views one after
     another with the single-view device path."""
     import torch
 
-    from paper_2312_12392_gb300 import build as B
     from paper_2312_12392_gb300 import rcp, scenes
-    torch.cuda.set_device(0)
-    B.build()
     sc, _ = make_workload("forest")
     d = sc.diameter()
     params = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
     collapse, collapse_name = collapse_for(args, "batched")
     split = split_for(args, "batched")
     g = rcp.scene_from(sc, collapse, split)
-    sizes = scenes.batched_view_sizes(64, seed=3)
-    cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(len(sizes))]
-    t = rcp.rcp_autotune(g, cams[0], 960, 540, params,
-                         os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
-    outs = [torch.empty((h, w, 4), dtype=torch.float32, device="cuda") for w, h in sizes]
-    Ws, Hs = [w for w, _ in sizes], [h for _, h in sizes]
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    try:
+        sizes = scenes.batched_view_sizes(64, seed=3)
+        cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(len(sizes))]
+        t = rcp.rcp_autotune(g, cams[0], 960, 540, params,
+                             os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
+        outs = [torch.empty((h, w, 4), dtype=torch.float32, device="cuda") for w, h in sizes]
+        Ws, Hs = [w for w, _ in sizes], [h for _, h in sizes]
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def batch_once():
-        rcp.rcp_render_batch_device(g, cams, Ws, Hs, K_PASSES, params, outs, stream)
+        def batch_once():
+            rcp.rcp_render_batch_device(g, cams, Ws, Hs, K_PASSES, params, outs, stream)
 
-    def plain_once():
-        for c, (w, h), o in zip(cams, sizes, outs):
-            rcp.rcp_render_device(g, c, w, h, K_PASSES, params, None, o, None, stream)
+        def plain_once():
+            for c, (w, h), o in zip(cams, sizes, outs):
+                rcp.rcp_render_device(g, c, w, h, K_PASSES, params, None, o, None, stream)
 
-    res = {}
-    for name, fn in (("batched", batch_once), ("plain", plain_once)):
-        for _ in range(args.warmup):
-            fn()
+        steps = max(3, min(args.steps, 20))
+        res = {}
+        for name, fn in (("batched", batch_once), ("plain", plain_once)):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                fn()
+                e.record(stream)
+                e.synchronize()
+                ms.append(s.elapsed_time(e))
+            res[name] = statistics.mean(ms)
+        pix = sum(w * h for w, h in sizes)
+        batch_once()
         torch.cuda.synchronize()
-        ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            fn()
-            e.record(stream)
-            e.synchronize()
-            ms.append(s.elapsed_time(e))
-        res[name] = statistics.mean(ms)
-    pix = sum(w * h for w, h in sizes)
-    batch_once()
-    torch.cuda.synchronize()
-    p_, s_ = rcp.rcp_last_ray_counts(g)
-    out = {
-        "metric": "views_per_s (64 uneven views, K=6 each, one launch per pass)",
-        "value": len(sizes) / (res["batched"] / 1000.0),
-        "unit": "views/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res["batched"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, graph-captured",
-                   "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
-                   "l2": "flushed between steps", "tuning": {"block": t.block, "chunk": t.chunk,
-                                                             "fused_camera": t.fused_camera}},
-        "mrays_per_s": (p_ + s_) / (res["batched"] / 1000.0) / 1e6,
-        "plain_ms_per_step": res["plain"],
-        "plain_views_per_s": len(sizes) / (res["plain"] / 1000.0),
-        "speedup_vs_plain": res["plain"] / res["batched"],
-        "gpu_launches": args.steps * K_PASSES,
-    }
-    rcp.rcp_scene_destroy(g)
-    print(json.dumps(out), flush=True)
+        p_, s_ = rcp.rcp_last_ray_counts(g)
+        return {"views_per_s": len(sizes) / (res["batched"] / 1000.0), "ms_per_batch": res["batched"],
+                "plain_views_per_s": len(sizes) / (res["plain"] / 1000.0), "plain_ms_per_batch": res["plain"],
+                "speedup_vs_plain": res["plain"] / res["batched"],
+                "mrays_per_s": (p_ + s_) / (res["batched"] / 1000.0) / 1e6, "steps": steps,
+                "workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, one launch per "
+                            "pass over all views, graph-captured",
+                "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1), "tuning": tuning_dict(t),
+                "l2": "flushed between steps", "gpu_launches": steps * K_PASSES}
+    finally:
+        rcp.rcp_scene_destroy(g)
 
 
-def run_served(args):
+class BufferPool:
+    """Host output buffers reused across requests of one resolution; a buffer
+    is handed out again only after the request that last used it is done."""
+
+    def __init__(self, per_shape):
+        self.per_shape = per_shape
+        self.bufs = {}
+        self.owner = {}
+
+    def get(self, i, w, h, wait):
+        pool = self.bufs.setdefault((w, h), [np.zeros((h, w, 3), np.float32) for _ in range(self.per_shape)])
+        j = i % self.per_shape
+        prev = self.owner.get((w, h, j))
+        if prev is not None:
+            wait(prev)
+        self.owner[(w, h, j)] = i
+        return pool[j]
+
+
+def served_summary(args):
     """Poisson arrivals over 4 resident terrain scenes (0.1M, 1M, 3M, 5M tris);
     each request: a walk-through pose, 720p/1080p/1440p/2160p, K in 1..8,
     k in [0, 0.05] * diameter. The continuous-batching server against the plain
-    path (one request at a time, FIFO, each its own launch sequence), same
-    arrivals. Reports frames/s and p50/p99 latency per arrival rate."""
+    path (one request at a time, FIFO, each its own K-pass launch sequence),
+    same arrivals, at each rate."""
     import threading
 
-    import torch
-
-    from paper_2312_12392_gb300 import build as B
     from paper_2312_12392_gb300 import rcp, scenes
-    torch.cuda.set_device(0)
-    B.build()
     grids = [221, 706, 1224, 1580]
     scs = [scenes.terrain_scene(gsz, seed=4) for gsz in grids]
     collapse, collapse_name = collapse_for(args, "served")
     gs = [rcp.scene_from(s, collapse) for s in scs]
-    n_req = args.steps
-    reqs = scenes.served_requests(n_req, len(scs), 64, seed=4)
-    diams = [s.diameter() for s in scs]
-    # one output buffer per request, allocated and touched before any timing
-    outs = [np.zeros((r["height"], r["width"], 3), np.float32) for r in reqs]
+    try:
+        n_req = args.served_requests
+        reqs = scenes.served_requests(n_req, len(scs), 64, seed=4)
+        diams = [s.diameter() for s in scs]
+        prepared = [(rcp.camera_from(scs[r["scene"]].poses[r["pose"]]),
+                     rcp.make_params(rcp.RCP_MAP_EYE, r["k_frac"] * diams[r["scene"]], 0.1 * diams[r["scene"]]))
+                    for r in reqs]
+        pool = BufferPool(24)
+        # warm both paths: every distinct request shape once through the plain
+        # path (its render contexts and graphs), a burst through a server
+        seen = set()
+        for i, r in enumerate(reqs):
+            key = (r["scene"], r["width"], r["height"], r["K"])
+            if key not in seen:
+                seen.add(key)
+                rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"], prepared[i][1],
+                               pool.get(i, r["width"], r["height"], lambda t: None))
+        srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+        tks = [rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"],
+                                     prepared[i][1], np.zeros((r["height"], r["width"], 3), np.float32))
+               for i, r in enumerate(reqs[:16])]
+        for tk in tks:
+            rcp.rcp_server_wait(srv, tk, 600.0)
+        rcp.rcp_server_destroy(srv)
+        table = []
+        for lam in [float(x) for x in args.rates.split(",")]:
+            arr = scenes.poisson_arrivals(lam, n_req, seed=4)
+            # -- plain: FIFO worker, one request at a time
+            lat = [0.0] * n_req
+            pool = BufferPool(2)
+            t0 = time.perf_counter()
 
-    def buf(i):
-        return outs[i]
+            def plain_worker():
+                for i, r in enumerate(reqs):
+                    wait = arr[i] - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(wait)
+                    rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"],
+                                   prepared[i][1], pool.get(i, r["width"], r["height"], lambda t: None))
+                    lat[i] = time.perf_counter() - t0 - arr[i]
 
-    def params_of(r):
-        d = diams[r["scene"]]
-        return rcp.make_params(rcp.RCP_MAP_EYE, r["k_frac"] * d, 0.1 * d)
-
-    def cam_of(r):
-        return rcp.camera_from(scs[r["scene"]].poses[r["pose"]])
-
-    prepared = [(cam_of(r), params_of(r)) for r in reqs]
-
-    # warm both paths: every request once through the plain path (render
-    # contexts and graphs), a short burst through a server (memory pool)
-    for i, r in enumerate(reqs):
-        rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"], prepared[i][1], buf(i))
-    srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
-    tks = [rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"],
-                                 prepared[i][1], buf(i)) for i, r in enumerate(reqs[:16])]
-    for tk in tks:
-        rcp.rcp_server_wait(srv, tk, 600.0)
-    rcp.rcp_server_destroy(srv)
-    rates = [float(x) for x in args.rates.split(",")]
-    table = []
-    for lam in rates:
-        arr = scenes.poisson_arrivals(lam, n_req, seed=4)
-        # -- plain: FIFO worker, one request at a time
-        lat = [0.0] * n_req
-        t0 = time.perf_counter()
-
-        def plain_worker():
+            th = threading.Thread(target=plain_worker)
+            th.start()
+            th.join()
+            plain_span = time.perf_counter() - t0
+            plain = {"frames_per_s": n_req / plain_span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                     "p99_ms": 1000 * float(np.percentile(lat, 99))}
+            # -- server: submit at the arrival times
+            srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+            pool = BufferPool(24)
+            tickets = []
+            t0 = time.perf_counter()
             for i, r in enumerate(reqs):
                 wait = arr[i] - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(wait)
-                rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"], prepared[i][1],
-                               buf(i))
-                lat[i] = time.perf_counter() - t0 - arr[i]
-
-        th = threading.Thread(target=plain_worker)
-        th.start()
-        th.join()
-        plain_span = time.perf_counter() - t0
-        plain = {"frames_per_s": n_req / plain_span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
-                 "p99_ms": 1000 * float(np.percentile(lat, 99))}
-        # -- server: submit at the arrival times
-        srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
-        t0 = time.perf_counter()
-        tickets = []
-        for i, r in enumerate(reqs):
-            wait = arr[i] - (time.perf_counter() - t0)
-            if wait > 0:
-                time.sleep(wait)
-            tickets.append(rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"],
-                                                 r["K"], prepared[i][1], buf(i)))
-        for tk in tickets:
-            rcp.rcp_server_wait(srv, tk, 600.0)
-        st = rcp.rcp_server_stats_get(srv)
-        rcp.rcp_server_destroy(srv)
-        served = {"frames_per_s": st.frames_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-                  "mrays_per_s": st.mrays_per_s, "steps": st.steps, "peak_gb": st.device_bytes_peak / 2 ** 30}
-        table.append({"rate_req_s": lam, "served": served, "plain": plain})
-        log(f"lambda={lam}: served {served} | plain {plain}")
-    best = max(table, key=lambda r: r["served"]["frames_per_s"])
-    out = {
-        "metric": "served frames_per_s and p50/p99 latency vs the plain per-request path",
-        "value": best["served"]["frames_per_s"], "unit": "frames/s",
-        "n_gpus": 1, "steps": n_req, "warmup": 1, "ms_per_step": 1000.0 / best["served"]["frames_per_s"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"bvh_collapse": collapse_name,
-                   "workload": "4 resident terrain scenes (100,082 / 999,272 / 2,998,752 / 4,995,200 tris); "
-                               "720p-2160p, K in 1..8, Poisson arrivals",
-                   "requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb},
-        "sweep": table,
-    }
-    for g in gs:
-        rcp.rcp_scene_destroy(g)
-    print(json.dumps(out), flush=True)
+                buf = pool.get(i, r["width"], r["height"], lambda j: rcp.rcp_server_wait(srv, tickets[j], 600.0))
+                tickets.append(rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"],
+                                                     r["K"], prepared[i][1], buf))
+            for tk in tickets:
+                rcp.rcp_server_wait(srv, tk, 600.0)
+            st = rcp.rcp_server_stats_get(srv)
+            rcp.rcp_server_destroy(srv)
+            served = {"frames_per_s": st.frames_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                      "mrays_per_s": st.mrays_per_s, "steps": st.steps, "peak_gb": st.device_bytes_peak / 2 ** 30}
+            table.append({"rate_req_s": lam, "served": served, "plain": plain})
+            log(f"lambda={lam}: served {served} | plain {plain}")
+        return {"requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+                "bvh_collapse": collapse_name,
+                "workload": "4 resident terrain scenes (100,082 / 999,272 / 2,998,752 / 4,995,200 tris); "
+                            "720p-2160p, K in 1..8, k in [0, 0.05]*diam, Poisson arrivals; latency from arrival "
+                            "to the image in the caller's host buffer",
+                "plain_path": "one rcp_render per request (host output), FIFO, one worker thread",
+                "sweep": table}
+    finally:
+        for g in gs:
+            rcp.rcp_scene_destroy(g)
 
 
-def run_stress(args):
+def stress_summary(args):
     """25,000-tree forest (12.57M triangles), 3840x2160, K=8: every frame the
     wind sways the trees (input generated on the device with torch), the BVH is
     refitted (rcp_scene_update_vertices_device) and the frame is rendered."""
     import torch
 
-    from paper_2312_12392_gb300 import build as B
     from paper_2312_12392_gb300 import rcp, scenes
-    torch.cuda.set_device(0)
-    B.build()
     t0 = time.perf_counter()
     sc = scenes.forest_scene(25_000, seed=5)
     gen_s = time.perf_counter() - t0
@@ -729,108 +801,135 @@ def run_stress(args):
     collapse, collapse_name = collapse_for(args, "stress")
     split = split_for(args, "stress")
     g = rcp.scene_from(sc, collapse, split)
-    info = rcp.rcp_scene_get_info(g)
-    base = torch.from_numpy(sc.tris).cuda().reshape(-1, 3, 3)
-    amp = torch.from_numpy(sc.sway_amp).cuda()
-    phase = torch.from_numpy(sc.sway_phase).cuda()
-    moved = torch.empty_like(base)
-    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(args.steps + args.warmup)]
+    g2 = None
+    try:
+        info = rcp.rcp_scene_get_info(g)
+        base = torch.from_numpy(sc.tris).cuda().reshape(-1, 3, 3)
+        amp = torch.from_numpy(sc.sway_amp).cuda()
+        phase = torch.from_numpy(sc.sway_phase).cuda()
+        moved = torch.empty_like(base)
+        out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+        steps = max(3, args.stress_steps)
+        cams = [rcp.camera_from(sc.poses[i % len(sc.poses)]) for i in range(steps + args.warmup)]
 
-    def sway(frame):
-        ang = 2.0 * np.pi * 0.5 * (frame / 60.0) + phase
-        moved.copy_(base)
-        moved[:, :, 0] += amp * torch.sin(ang)[:, None]
-        moved[:, :, 2] += amp * torch.cos(ang)[:, None]
+        def sway(frame):
+            ang = 2.0 * np.pi * 0.5 * (frame / 60.0) + phase
+            moved.copy_(base)
+            moved[:, :, 0] += amp * torch.sin(ang)[:, None]
+            moved[:, :, 2] += amp * torch.cos(ang)[:, None]
 
-    for i in range(args.warmup):
-        sway(i)
-        rcp.rcp_scene_update_vertices_device(g, moved, stream)
-        rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
-    torch.cuda.synchronize()
-    refit_ms, render_ms, frame_ms, rays = [], [], [], 0
-    for i in range(args.warmup, args.warmup + args.steps):
-        sway(i)  # input generation, outside the timed events
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        rcp.rcp_scene_update_vertices_device(g, moved, stream)
-        e1.record(stream)
-        rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
-        e2.record(stream)
-        e2.synchronize()
-        refit_ms.append(e0.elapsed_time(e1))
-        render_ms.append(e1.elapsed_time(e2))
-        frame_ms.append(e0.elapsed_time(e2))
-        p_, s_ = rcp.rcp_last_ray_counts(g)
-        rays += p_ + s_
-    rcp.rcp_scene_validate(g)
-    tot = sum(frame_ms) / 1000.0
-
-    # End to end, every frame's RGB delivered to host memory, the same frames:
-    # (1) one stream: sway, refit, render, copy out, frame after frame;
-    # (2) the serving path with two copies of the scene used in turn, so that
-    #     frame f's sway and refit overlap frame f-1's render and copy-out (a
-    #     copy is refitted only once the request two frames back, its last
-    #     user, is done). Three host buffers rotate (at most two in flight).
-    n = args.steps
-    frames = [args.warmup + i for i in range(n)]
-    bufs = {k: [np.zeros((H, W, 3), np.float32) for _ in range(3)] for k in ("single", "served")}
-    t0 = time.perf_counter()
-    for i, f in enumerate(frames):
-        sway(f)
-        rcp.rcp_scene_update_vertices_device(g, moved, stream)
-        torch.cuda.synchronize()  # the render runs on the library's stream
-        rcp.rcp_render(g, cams[f], W, H, K, params, bufs["single"][i % 3])
-    single_s = time.perf_counter() - t0
-    g2 = rcp.scene_from(sc, collapse, split)
-    copies = [g, g2]
-    budget = int(args.serve_budget_gb * (1 << 30))
-    # warm the device memory pool with one request per copy on a server of its
-    # own, so that the timed server's latency figures hold the timed frames only
-    srv = rcp.rcp_server_create(budget, args.serve_slots)
-    for j in range(2):
-        rcp.rcp_server_wait(srv, rcp.rcp_server_submit(srv, copies[j], cams[0], W, H, K, params,
-                                                       bufs["served"][j]), 600.0)
-    rcp.rcp_server_destroy(srv)
-    srv = rcp.rcp_server_create(budget, args.serve_slots)
-    tickets = []
-    t0 = time.perf_counter()
-    for i, f in enumerate(frames):
-        if i >= 2:
-            rcp.rcp_server_wait(srv, tickets[i - 2], 600.0)
-        sway(f)
-        rcp.rcp_scene_update_vertices_device(copies[i % 2], moved, stream)
+        for i in range(args.warmup):
+            sway(i)
+            rcp.rcp_scene_update_vertices_device(g, moved, stream)
+            rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
         torch.cuda.synchronize()
-        tickets.append(rcp.rcp_server_submit(srv, copies[i % 2], cams[f], W, H, K, params, bufs["served"][i % 3]))
-    for tk in tickets[-2:]:
-        rcp.rcp_server_wait(srv, tk, 600.0)
-    served_s = time.perf_counter() - t0
-    st = rcp.rcp_server_stats_get(srv)
-    rcp.rcp_server_destroy(srv)
-    same_last = bool(np.array_equal(bufs["single"][(n - 1) % 3], bufs["served"][(n - 1) % 3]))
-    rcp.rcp_scene_destroy(g2)
-    out_bytes = H * W * 3 * 4
-    res = {
-        "metric": "frames_per_s (3840x2160, K=8, per-frame refit)",
-        "value": args.steps / tot, "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"bvh_collapse": collapse_name, "bvh_split_max": split, "records": info.n_records,
-                   "workload": f"stress: {info.n_tris:,} tris (25,000 swaying cone trees), 3840x2160, K=8, "
-                               "wind sway A=0.02*h_tree at 0.5 Hz, refit every frame",
-                   "scene_generation_s": gen_s, "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
-                   "depth": info.depth},
-        "refit_ms": statistics.mean(refit_ms), "render_ms": statistics.mean(render_ms),
-        "mrays_per_s": rays / tot / 1e6, "gpu_launches_per_step": K + 2 + info.depth,
-        "e2e": {"value": n / single_s, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": out_bytes,
-                "api": "single stream: rcp_scene_update_vertices_device + rcp_render (host RGB) per frame"},
-        "served_e2e": {"value": n / served_s, "unit": "frames/s", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-                       "d2h_bytes_per_step": out_bytes, "last_frame_identical_to_single_stream": same_last,
-                       "api": "rcp_server_submit (host RGB), two scene copies refitted in turn"},
-    }
-    rcp.rcp_scene_destroy(g)
-    print(json.dumps(res), flush=True)
+        refit_ms, render_ms, frame_ms, rays = [], [], [], 0
+        for i in range(args.warmup, args.warmup + steps):
+            sway(i)  # input generation, outside the timed events
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            rcp.rcp_scene_update_vertices_device(g, moved, stream)
+            e1.record(stream)
+            rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
+            e2.record(stream)
+            e2.synchronize()
+            refit_ms.append(e0.elapsed_time(e1))
+            render_ms.append(e1.elapsed_time(e2))
+            frame_ms.append(e0.elapsed_time(e2))
+            p_, s_ = rcp.rcp_last_ray_counts(g)
+            rays += p_ + s_
+        rcp.rcp_scene_validate(g)
+        tot = sum(frame_ms) / 1000.0
+        # End to end, every frame's RGB delivered to host memory, the same frames:
+        # (1) one stream: sway, refit, render, copy out, frame after frame;
+        # (2) the serving path with two copies of the scene used in turn, so that
+        #     frame f's sway and refit overlap frame f-1's render and copy-out (a
+        #     copy is refitted only once the request two frames back, its last
+        #     user, is done). Three host buffers rotate (at most two in flight).
+        frames = [args.warmup + i for i in range(steps)]
+        bufs = {k: [np.zeros((H, W, 3), np.float32) for _ in range(3)] for k in ("single", "served")}
+        t0 = time.perf_counter()
+        for i, f in enumerate(frames):
+            sway(f)
+            rcp.rcp_scene_update_vertices_device(g, moved, stream)
+            torch.cuda.synchronize()  # the render runs on the library's stream
+            rcp.rcp_render(g, cams[f], W, H, K, params, bufs["single"][i % 3])
+        single_s = time.perf_counter() - t0
+        g2 = rcp.scene_from(sc, collapse, split)
+        copies = [g, g2]
+        budget = int(args.serve_budget_gb * (1 << 30))
+        srv = rcp.rcp_server_create(budget, args.serve_slots)
+        for j in range(2):
+            rcp.rcp_server_wait(srv, rcp.rcp_server_submit(srv, copies[j], cams[0], W, H, K, params,
+                                                           bufs["served"][j]), 600.0)
+        rcp.rcp_server_destroy(srv)
+        srv = rcp.rcp_server_create(budget, args.serve_slots)
+        tickets = []
+        t0 = time.perf_counter()
+        for i, f in enumerate(frames):
+            if i >= 2:
+                rcp.rcp_server_wait(srv, tickets[i - 2], 600.0)
+            sway(f)
+            rcp.rcp_scene_update_vertices_device(copies[i % 2], moved, stream)
+            torch.cuda.synchronize()
+            tickets.append(rcp.rcp_server_submit(srv, copies[i % 2], cams[f], W, H, K, params,
+                                                 bufs["served"][i % 3]))
+        for tk in tickets[-2:]:
+            rcp.rcp_server_wait(srv, tk, 600.0)
+        served_s = time.perf_counter() - t0
+        st = rcp.rcp_server_stats_get(srv)
+        rcp.rcp_server_destroy(srv)
+        same_last = bool(np.array_equal(bufs["single"][(steps - 1) % 3], bufs["served"][(steps - 1) % 3]))
+        out_bytes = H * W * 3 * 4
+        return {"frames_per_s": steps / tot, "ms_per_frame": 1000 * tot / steps, "frames": steps,
+                "refit_ms": statistics.mean(refit_ms), "render_ms": statistics.mean(render_ms),
+                "mrays_per_s": rays / tot / 1e6,
+                "workload": f"stress: {info.n_tris:,} tris (25,000 swaying cone trees), 3840x2160, K=8, wind sway "
+                            "A=0.02*h_tree at 0.5 Hz, refit every frame",
+                "bvh_collapse": collapse_name, "bvh_split_max": split, "records": info.n_records,
+                "scene_generation_s": gen_s, "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
+                "depth": info.depth, "gpu_launches_per_step": K + 2 + info.depth,
+                "e2e": {"value": steps / single_s, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": out_bytes,
+                        "api": "single stream: rcp_scene_update_vertices_device + rcp_render (host RGB) per frame"},
+                "served_e2e": {"value": steps / served_s, "unit": "frames/s", "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+                               "d2h_bytes_per_step": out_bytes, "last_frame_identical_to_single_stream": same_last,
+                               "api": "rcp_server_submit (host RGB), two scene copies refitted in turn"}}
+    finally:
+        if g2:
+            rcp.rcp_scene_destroy(g2)
+        rcp.rcp_scene_destroy(g)
+
+
+def run_workload_line(args, name):
+    """One workload's own line (--workload forest|batched|served|stress)."""
+    import torch
+
+    from paper_2312_12392_gb300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    if name == "forest":
+        r = forest_summary(args)
+        out = one_line("frames_per_s (forest, 1080p, K=6)", r["frames_per_s"], "frames/s", args, r["frames"], r)
+        out.update(ms_per_step=r["ms_per_frame"], e2e=r["e2e"], roofline=r["roofline"], clocks=r["clocks"])
+    elif name == "batched":
+        r = batched_summary(args)
+        out = one_line("views_per_s (64 uneven views, K=6 each, one launch per pass)", r["views_per_s"], "views/s",
+                       args, r["steps"], r)
+        out["ms_per_step"] = r["ms_per_batch"]
+    elif name == "served":
+        r = served_summary(args)
+        best = max(r["sweep"], key=lambda x: x["served"]["frames_per_s"])
+        out = one_line("served frames_per_s and p50/p99 latency vs the plain per-request path",
+                       best["served"]["frames_per_s"], "frames/s", args, r["requests_per_rate"], r)
+        out["ms_per_step"] = 1000.0 / best["served"]["frames_per_s"]
+    else:
+        r = stress_summary(args)
+        out = one_line("frames_per_s (3840x2160, K=8, per-frame refit)", r["frames_per_s"], "frames/s", args,
+                       r["frames"], r)
+        out.update(ms_per_step=r["ms_per_frame"], e2e=r["e2e"])
+    print(json.dumps(out), flush=True)
 
 
 def run_imagespace(args):
@@ -899,17 +998,23 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress", "imagespace"])
-    ap.add_argument("--tuning", default="128,32,1", help="'auto' or block,chunk,fused_camera")
+    ap.add_argument("--tuning", default="auto",
+                    help="'auto' (the library's autotuner, cached per GPU, scene size, tree depth and view) or "
+                         "block,chunk,fused_camera[,stack_entries[,hints]] (stack 0 = one entry per tree level; "
+                         "hints: bit 0 primary, bit 1 shadow, default 3)")
     ap.add_argument("--collapse", default="auto", choices=["auto", "area", "sah"],
                     help="BVH collapse policy; auto: sah for the forest workloads, area for the terrains")
     ap.add_argument("--split", default="auto", choices=["auto"] + [str(i) for i in range(9)],
                     help="references per triangle at most (early split clipping); auto: 8 for the forests "
                          "(static and swaying), 0 for the terrains")
-    ap.add_argument("--count-poses", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra-forest", dest="extra_forest", action="store_false")
-    ap.add_argument("--rates", default="10,25,50,100,200,400", help="served: arrival rates (req/s)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="the headline line without the forest, batched, served and stress summaries")
+    ap.add_argument("--rates", default="100,200,400", help="served: arrival rates (req/s)")
+    ap.add_argument("--served-requests", type=int, default=1000, help="served: requests per rate")
+    ap.add_argument("--stress-steps", type=int, default=20, help="stress: timed frames")
+    ap.add_argument("--forest-poses", type=int, default=64, help="forest: walk-through poses timed (all 64)")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     args = ap.parse_args(argv)
@@ -918,12 +1023,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batched":
-        run_batched(args)
-    elif args.workload == "served":
-        run_served(args)
-    elif args.workload == "stress":
-        run_stress(args)
+    elif args.workload in ("forest", "batched", "served", "stress"):
+        run_workload_line(args, args.workload)
     elif args.workload == "imagespace":
         run_imagespace(args)
     else:

@@ -256,21 +256,25 @@ rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rc
  * 1 = rays are made inside the trace kernel, 0 = a separate camera kernel
  * writes a ray buffer; stack_entries: traversal-stack entries per thread kept
  * in shared memory (0 = one per tree level, the walk's deepest need; fewer
- * entries spill the deeper levels to a library-owned global-memory region).
- * No choice changes any result. */
+ * entries spill the deeper levels to a library-owned global-memory region);
+ * hints: bit 0 = each pixel's walk first tests the primitive its ray hit in the
+ * previous pass (a closer far limit from the start), bit 1 = its shadow walk
+ * first tests its previous occluder. No choice changes any result. */
 typedef struct {
     int32_t block;
     int32_t blocks_per_sm;
     int32_t chunk;
     int32_t fused_camera;
     int32_t stack_entries;
+    int32_t hints;
 } rcp_tuning;
 
 rcp_status rcp_get_tuning(const rcp_scene* scene, rcp_tuning* out);
 rcp_status rcp_set_tuning(rcp_scene* scene, const rcp_tuning* tuning);
 
 /* Time every tuning candidate (block x chunk x fused camera x shared stack
- * depth, the depth a full tree walk needs or half of it) on this scene and
+ * depth, the depth a full tree walk needs or half of it, x hints on or off) on
+ * this scene and
  * view, keep the fastest in the scene and return it. cache_path (nullable): a
  * JSON file of earlier results, keyed by GPU name, scene size class, tree depth
  * and view size; read before and updated after the search. */
@@ -361,11 +365,14 @@ int64_t rcp_sort_static_capacity(void);
 
 /* ------------------------------------------------------------ serving ---
  * A request = one K-pass render of a resident scene. Requests are admitted
- * while a slot is free and their device memory (two rgbz images and a ray
- * buffer) fits the budget, then advance one pass per scheduler step together
- * with every other in-flight request (continuous batching: one launch per pass
- * stage covers all admitted requests, whatever their scene, size or K). A
- * finished request's image is copied to the caller's host buffer. */
+ * (first come first served) while a slot is free and their device memory (two
+ * rgbz images, per-pixel hit hints and a status word) fits the budget. Each
+ * scheduler step advances admitted requests by one pass in ONE launch over
+ * all of their views, whatever their scene, size or K (continuous batching): in
+ * admission order, the oldest always and the others while the step's pixels
+ * stay within the step budget (rcp_server_set_step_pixels). A finished
+ * request's image is delivered to the caller's host buffer; a request whose
+ * traversal stack overflowed fails with RCP_ERR_STACK. */
 typedef struct rcp_server rcp_server;
 
 typedef struct {
@@ -385,6 +392,10 @@ rcp_status rcp_server_create(int64_t mem_budget_bytes, int max_slots, rcp_server
 rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_camera* cam,
                              int width, int height, int K, const rcp_params* params, float* out_rgb,
                              int64_t* ticket);
+/* Pixels one scheduler step may hold (default 8,500,000, so that a 3840x2160
+ * pass runs alone; 0 = every admitted request in every step). The oldest
+ * admitted request always advances, whatever its size. */
+rcp_status rcp_server_set_step_pixels(rcp_server* srv, int64_t pixels);
 /* done = 1 finished, 0 pending; the request's own status is returned. */
 rcp_status rcp_server_poll(rcp_server* srv, int64_t ticket, int* done);
 rcp_status rcp_server_wait(rcp_server* srv, int64_t ticket, double timeout_s);

@@ -259,6 +259,7 @@ LaunchCfg cfg_of(const Scene& sc) {
     const int full = full_stack(sc);
     c.stack = sc.tuning.stack_entries > 0 ? std::min(sc.tuning.stack_entries, full) : full;
     c.spill_entries = full - c.stack;
+    c.hints = sc.tuning.hints;
     return c;
 }
 
@@ -289,10 +290,19 @@ rcp_status ensure_spill(Scene& sc, LaunchCfg& c) {
     return RCP_OK;
 }
 
+// The separate camera kernel's ray buffer (2 float4 per pixel), allocated
+// before the first capture that needs it.
+rcp_status ensure_rays(RenderCtx& ctx, const LaunchCfg& c) {
+    if (c.fused || c.ms || c.multi || ctx.rays) return RCP_OK;
+    RCP_CUDA(cudaMalloc((void**)&ctx.rays, sizeof(float4) * 2 * ctx.total_pix));
+    ctx.bytes += (int64_t)sizeof(float4) * 2 * ctx.total_pix;
+    return RCP_OK;
+}
+
 std::string cfg_key(const LaunchCfg& c) {
     std::ostringstream o;
     o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/"
-      << c.spill_entries << "/" << (const void*)c.spill << "/" << c.count << "/" << c.ms;
+      << c.spill_entries << "/" << (const void*)c.spill << "/" << c.count << "/" << c.ms << "/" << c.hints;
     return o.str();
 }
 
@@ -312,8 +322,8 @@ void layout_views(std::vector<ViewDev>& v, int64_t& total_pix, int64_t& total_ch
 // Render contexts are cached per launch shape, least recently used first out
 // when the cache exceeds CTX_MAX entries or CTX_BYTES of device memory. A
 // context is freed only after its last launch has completed.
-constexpr size_t CTX_MAX = 24;
-constexpr int64_t CTX_BYTES = (int64_t)8 << 30;
+constexpr size_t CTX_MAX = 64;
+constexpr int64_t CTX_BYTES = (int64_t)16 << 30;
 
 rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t total_chunks, RenderCtx** out) {
     std::ostringstream key;
@@ -325,7 +335,7 @@ rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t tot
         return RCP_OK;
     }
     const int64_t need =
-        total_pix * (int64_t)(sizeof(float4) * 4 + sizeof(int2)) + (int64_t)sizeof(ViewDev) * K * n_views;
+        total_pix * (int64_t)(sizeof(float4) * 2 + sizeof(int2)) + (int64_t)sizeof(ViewDev) * K * n_views;
     for (;;) {
         int64_t held = 0;
         for (auto& kv : sc.ctx) held += kv.second->bytes;
@@ -345,7 +355,6 @@ rcp_status get_ctx(Scene& sc, int n_views, int K, int64_t total_pix, int64_t tot
     c->last_use = ++sc.use_clock;
     RCP_CUDA(cudaMalloc((void**)&c->img[0], sizeof(float4) * total_pix));
     RCP_CUDA(cudaMalloc((void**)&c->img[1], sizeof(float4) * total_pix));
-    RCP_CUDA(cudaMalloc((void**)&c->rays, sizeof(float4) * 2 * total_pix));
     RCP_CUDA(cudaMalloc((void**)&c->hints, sizeof(int2) * total_pix));
     RCP_CUDA(cudaMemset(c->hints, 0xff, sizeof(int2) * total_pix));  // -1: no earlier hit
     RCP_CUDA(cudaMalloc((void**)&c->d_views, sizeof(ViewDev) * (size_t)K * n_views));
@@ -492,6 +501,8 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
     cfg.ms = p->spp > 0;
     r = ensure_spill(sc, cfg);
+    if (r != RCP_OK) return r;
+    r = ensure_rays(*ctx, cfg);
     if (r != RCP_OK) return r;
     r = run_graph(sc, *ctx, cfg, st);
     sc.last = ctx;
@@ -816,9 +827,9 @@ rcp_status rcp_set_tuning(rcp_scene* sc, const rcp_tuning* t) {
     }
     if ((t->block != 64 && t->block != 128 && t->block != 256) || (t->chunk != 32 && t->chunk != 64) ||
         t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || (t->fused_camera != 0 && t->fused_camera != 1) ||
-        t->stack_entries < 0 || t->stack_entries > MAX_STACK) {
+        t->stack_entries < 0 || t->stack_entries > MAX_STACK || t->hints < 0 || t->hints > 3) {
         set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32, fused 0/1, "
-                  "0 <= stack_entries <= 64");
+                  "0 <= stack_entries <= 64, 0 <= hints <= 3");
         return RCP_ERR_ARG;
     }
     std::lock_guard<std::mutex> lk(sc->mu);
@@ -856,6 +867,8 @@ rcp_status rcp_count_pass(const rcp_scene* csc, const rcp_camera* cam, int W, in
     cfg.count = true;
     cfg.ms = p->spp > 0;
     r = ensure_spill(*sc, cfg);
+    if (r != RCP_OK) return r;
+    r = ensure_rays(*ctx, cfg);
     if (r != RCP_OK) return r;
     r = enqueue_passes(*sc, *ctx, cfg, d_cnt.p, st, false);
     if (r != RCP_OK) return r;
@@ -1012,7 +1025,7 @@ std::string gpu_name() {
     return prop.name;
 }
 
-// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, stack_entries, us], ...}
+// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, stack_entries, hints, us], ...}
 std::map<std::string, std::vector<double>> read_cache(const char* path) {
     std::map<std::string, std::vector<double>> m;
     if (!path) return m;
@@ -1074,7 +1087,8 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     auto it = cache.find(key.str());
     if (it != cache.end()) {
         const auto& v = it->second;
-        rcp_tuning t{(int)v[0], (int)v[1], (int)v[2], (int)v[3], v.size() >= 6 ? (int)v[4] : 0};
+        rcp_tuning t{(int)v[0], (int)v[1], (int)v[2], (int)v[3], v.size() >= 6 ? (int)v[4] : 0,
+                     v.size() >= 7 ? (int)v[5] : 3};
         r = rcp_set_tuning(sc, &t);
         if (r == RCP_OK && out) *out = t;
         if (r == RCP_OK) return RCP_OK;
@@ -1094,9 +1108,10 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     for (int b : {64, 128, 256})
         for (int fused = 0; fused < 2; ++fused)
             for (int chunk : {32, 64})
-                for (int stk : stacks) {
+                for (int stk : stacks)
+                for (int hints : {3, 0}) {
                     if (stk >= full) continue;
-                    rcp_tuning t{b, 0, chunk, fused, stk};
+                    rcp_tuning t{b, 0, chunk, fused, stk, hints};
                     sc->tuning = t;
                     const float4* ins[1] = {nullptr};
                     float4* outs[1] = {d_img.p};
@@ -1119,8 +1134,9 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
                 }
     sc->tuning = best;
     if (r != RCP_OK) return r;
-    cache[key.str()] = {(double)best.block, (double)best.blocks_per_sm, (double)best.chunk, (double)best.fused_camera,
-                        (double)best.stack_entries, best_us};
+    cache[key.str()] = {(double)best.block,         (double)best.blocks_per_sm, (double)best.chunk,
+                        (double)best.fused_camera,  (double)best.stack_entries, (double)best.hints,
+                        best_us};
     write_cache(cache_path, cache);
     if (out) *out = best;
     return RCP_OK;

@@ -67,7 +67,7 @@ struct Scene {
     float diam = 0.f;
     float build_ms = 0.f;
     LightDev light{};
-    rcp_tuning tuning{128, 0, 32, 1, 0};
+    rcp_tuning tuning{128, 0, 32, 1, 0, 3};
     std::mutex mu;
     std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
     RenderCtx* last = nullptr;  // context of the most recent render
@@ -102,6 +102,7 @@ struct LaunchCfg {
     bool count = false;
     bool ms = false;  // jittered multi-sample kernel
     bool multi = false;  // views of several scenes (each view names its scene)
+    int hints = 3;    // previous-hit hints: bit 0 primary, bit 1 shadow
 };
 
 // One pass over n_views views whose descriptors are at d_views (device). A

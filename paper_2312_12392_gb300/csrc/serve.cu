@@ -5,12 +5,19 @@
 //    request's device memory -- two rgbz images, per-pixel hit hints and a
 //    status word (plus an RGB staging buffer where the device cannot write
 //    host memory), allocated stream-ordered from the device's memory pool --
-//    fits the budget, then enqueues ONE pass of every admitted request per
-//    step as ONE persistent launch: a single tile queue over every request's
-//    view, whatever its scene, size or K (each view names its scene). Which
-//    requests finish at a step is known when it is enqueued (pass count = K),
-//    so the scheduler never waits for the device except to bound how far it
-//    runs ahead (STEPS_AHEAD steps);
+//    fits the budget. Each step then advances admitted requests by ONE pass in
+//    ONE persistent launch: a single tile queue over the step's views,
+//    whatever their scene, size or K (each view names its scene; views are
+//    grouped by scene for cache locality). A step takes requests in admission
+//    order: the oldest always, the others while the step's pixels stay within
+//    the step budget (others wait, with their images resident, for a later
+//    step). Old requests thus run as soon as they would on their own and new
+//    small ones fill the rest of a step: first come first served with
+//    backfill, like a token budget in LLM continuous batching, rather than
+//    every request sharing every step, which stretches the largest requests.
+//    Which requests finish at a step is known when it is enqueued (pass count
+//    = K), so the scheduler never waits for the device except to bound how
+//    far it runs ahead (STEPS_AHEAD steps);
 //  * the copy-out thread waits for each finished request's last pass, reads
 //    its status word (a walk that overflowed its stack fails the request),
 //    copies its RGB image to the caller's buffer where needed, releases its
@@ -40,6 +47,7 @@ namespace rcp {
 namespace {
 
 constexpr int STEPS_AHEAD = 3;  // steps enqueued before the oldest must finish
+constexpr int64_t DEFAULT_STEP_PIXELS = 8500000;  // a 3840x2160 pass (8.29M) runs without backfill
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -55,6 +63,7 @@ struct Request {
     rcp_params p{};
     float* out_rgb = nullptr;
     int passes_done = 0;  // passes enqueued so far
+    bool in_step = false;  // advanced by the step being enqueued
     float4* img[2] = {nullptr, nullptr};
     float* rgb = nullptr;
     int2* hint = nullptr;    // per pixel: latest primary-hit and shadow-occluder records, then the status word
@@ -105,6 +114,7 @@ struct rcp_server {
     bool direct = false;  // last passes write the callers' RGB buffers (host_coherent)
     int* h_status = nullptr;  // pinned: one status word per admitted, unfinished request
     std::vector<int> free_status;
+    int64_t step_pixels = DEFAULT_STEP_PIXELS;  // pixels per step (0: every admitted request every step)
 
     void run();
     void copy_out();
@@ -187,6 +197,13 @@ double percentile(std::vector<double> v, double q) {
 rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot) {
     rcp_status r = ensure_slot(slot, (int)batch.size());
     if (r != RCP_OK) return r;
+    // views grouped by scene, scenes in order of their oldest request
+    std::vector<const rcp_scene*> order;
+    for (Request* q : batch)
+        if (std::find(order.begin(), order.end(), q->scene) == order.end()) order.push_back(q->scene);
+    std::stable_sort(batch.begin(), batch.end(), [&](Request* a, Request* b) {
+        return std::find(order.begin(), order.end(), a->scene) < std::find(order.begin(), order.end(), b->scene);
+    });
     std::set<const rcp_scene*> scenes;
     int stack = 4;
     bool ms = false;
@@ -345,9 +362,19 @@ void rcp_server::run() {
                 rcp_status r = alloc_request(*q, direct, st_main);
                 if (r != RCP_OK) q->status = r;
             }
+        // the step: admission order, the oldest always, the rest while the
+        // step's pixels fit the budget
         std::vector<Request*> ok;
-        for (Request* q : batch)
-            if (q->status == RCP_OK) ok.push_back(q);
+        int64_t px = 0;
+        for (Request* q : batch) {
+            q->in_step = false;
+            if (q->status != RCP_OK) continue;
+            const int64_t qp = (int64_t)q->W * q->H;
+            if (!ok.empty() && step_pixels > 0 && px + qp > step_pixels) continue;
+            ok.push_back(q);
+            q->in_step = true;
+            px += qp;
+        }
         StepSlot& slot = slots[step_no % STEPS_AHEAD];
         if (slot.used) cudaEventSynchronize(slot.done);  // bound the run-ahead; frees the slot's staging
         rcp_status r = ok.empty() ? RCP_OK : enqueue_step(ok, slot);
@@ -357,7 +384,7 @@ void rcp_server::run() {
         std::vector<Request*> still;
         for (Request* q : inflight) {
             if (r != RCP_OK && q->status == RCP_OK) q->status = r;
-            if (q->status == RCP_OK) q->passes_done++;
+            if (q->status == RCP_OK && q->in_step) q->passes_done++;
             if (q->status != RCP_OK || q->passes_done >= q->K) {
                 copyq.push_back(q);  // the copy-out thread waits for its image
                 cv_copy.notify_one();
@@ -437,6 +464,16 @@ rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_
     srv->queue.push_back(q.get());
     srv->all[q->ticket] = std::move(q);
     srv->cv_work.notify_one();
+    return RCP_OK;
+}
+
+rcp_status rcp_server_set_step_pixels(rcp_server* srv, int64_t pixels) {
+    if (!srv || pixels < 0) {
+        set_error("rcp_server_set_step_pixels: NULL server or negative budget");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->step_pixels = pixels;
     return RCP_OK;
 }
 

@@ -60,6 +60,7 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
                                               uint32_t& n_shadow, uint32_t& code, int32_t& prim,
                                               const uint8_t* order_lut, int2& hint) {
     const Hit h = traverse<false, COUNT>(S, r, stack, stride, stk, overflow, wc, order_lut, hint.x);
+    prefetch_record(S, hint.y);  // the previous occluder, ahead of the shadow walk
     const ShadeInfo si = shade_primary(S, r, h);
     float4 out = si.c_shadow;
     hint.x = h.rec;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
                                                  unsigned long long* ray_counts, unsigned long long* counters) {
     extern __shared__ uint2 s_stack[];
     __shared__ uint8_t s_order[ORDER_LUT_BYTES];
+    __shared__ SceneDev s_scene[MULTI ? BLOCK / 32 : 1];  // MULTI: the scene of each warp's current tile
     fill_order_lut<BLOCK>(s_order);
     __syncthreads();
     uint2* stack = s_stack + threadIdx.x;
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
     bool overflow = false;
     WorkCount wc{0, 0, 0, 0};
     uint32_t n_primary = 0, n_shadow = 0;
+    static_assert(sizeof(SceneDev) % 4 == 0 && sizeof(SceneDev) <= 128, "SceneDev is copied by one warp");
     for (;;) {
         unsigned c0 = 0;
         if (lane == 0) c0 = atomicAdd(work, (unsigned)chunk_tiles);
@@ -101,7 +104,14 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
             const int64_t chunk = (int64_t)c0 + sub;
             if (chunk >= total_chunks) break;
             const ViewDev& v = views[find_view_by_chunk(views, n_views, chunk)];
-            const SceneDev& S = MULTI ? *v.scene : S0;
+            if (MULTI) {  // the warp's tile is one view: copy its scene to the warp's slot
+                __syncwarp();
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(v.scene);
+                uint32_t* dst = reinterpret_cast<uint32_t*>(&s_scene[threadIdx.x >> 5]);
+                for (int i = lane; i < (int)(sizeof(SceneDev) / 4); i += 32) dst[i] = __ldg(src + i);
+                __syncwarp();
+            }
+            const SceneDev& S = MULTI ? s_scene[threadIdx.x >> 5] : S0;
             const int64_t tile = chunk - v.chunk_begin;
             const int tx = (int)(tile % v.tiles_x), ty = (int)(tile / v.tiles_x);
             const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
@@ -113,7 +123,10 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 uint32_t code0 = 0;
                 int32_t prim0 = -1;
-                int2 hint = v.hint ? v.hint[p] : make_int2(-1, -1);
+                int2 hint = v.hint && stk.hints ? v.hint[p] : make_int2(-1, -1);
+                if (!(stk.hints & 1)) hint.x = -1;
+                if (!(stk.hints & 2)) hint.y = -1;
+                prefetch_record(S, hint.x);
                 for (int s = 0; s < ns; ++s) {
                     const float jx = v.spp > 0 ? v.jit[2 * s] : 0.5f, jy = v.spp > 0 ? v.jit[2 * s + 1] : 0.5f;
                     const float px = __fadd_rn((float)x, jx), py = __fadd_rn((float)y, jy);
@@ -152,6 +165,10 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
                 }
                 continue;
             }
+            int2 hint = v.hint && stk.hints ? v.hint[p] : make_int2(-1, -1);
+            if (!(stk.hints & 1)) hint.x = -1;
+            if (!(stk.hints & 2)) hint.y = -1;
+            prefetch_record(S, hint.x);  // its lines arrive while the camera ray is made
             RayF r;
             if (FUSED) {
                 const float4 c = v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
@@ -169,7 +186,6 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
             }
             uint32_t code;
             int32_t prim;
-            int2 hint = v.hint ? v.hint[p] : make_int2(-1, -1);
             float4 out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc, n_shadow, code,
                                             prim, s_order, hint);
             ++n_primary;
@@ -217,7 +233,7 @@ __global__ void __launch_bounds__(BLOCK) k_debug_trace(SceneDev S, int64_t n, co
     fill_order_lut<BLOCK>(s_order);
     __syncthreads();
     uint2* stack = s_stack + threadIdx.x;
-    const StackCfg stk{stack_entries, 0, nullptr};
+    const StackCfg stk{stack_entries, 0, nullptr, 0};
     bool overflow = false;
     WorkCount wc{0, 0, 0, 0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -343,7 +359,7 @@ rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
     int64_t grid = (int64_t)sm_count() * per_sm;
     const int64_t need = (total_chunks * 32 + BLOCK - 1) / BLOCK;
     if (grid > need) grid = need > 0 ? need : 1;
-    StackCfg stk{cfg.stack, cfg.spill ? cfg.spill_entries : 0, cfg.spill};
+    StackCfg stk{cfg.stack, cfg.spill ? cfg.spill_entries : 0, cfg.spill, cfg.hints};
     if (stk.spill_entries > 0 && grid * BLOCK * (int64_t)stk.spill_entries > cfg.spill_cap) {
         set_error("traversal spill region too small for the launch");
         return RCP_ERR_STATE;

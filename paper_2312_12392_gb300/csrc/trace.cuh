@@ -271,7 +271,17 @@ struct StackCfg {
     int entries;        // shared-memory entries per thread
     int spill_entries;  // global-memory entries per thread above those
     uint2* spill;       // spill_entries * (gridDim.x * blockDim.x) entries, or null
+    int hints;          // bit 0: test each pixel's previous primary-hit record first; bit 1: its previous occluder
 };
+
+// Bring the 48-byte record rec (two 128-byte lines at most) towards L1, so
+// that testing it first does not stall the walk's start on its load.
+__device__ __forceinline__ void prefetch_record(const SceneDev& S, int32_t rec) {
+    if (rec < 0 || rec >= S.n_records) return;
+    const char* p = reinterpret_cast<const char*>(S.prims + 3 * (size_t)rec);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + 47));
+}
 
 __device__ __forceinline__ uint2* spill_slot(const StackCfg& sc, int i) {
     const uint32_t T = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;

@@ -61,7 +61,7 @@ class rcp_build_options(C.Structure):
 
 class rcp_tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
-                ("fused_camera", C.c_int32), ("stack_entries", C.c_int32)]
+                ("fused_camera", C.c_int32), ("stack_entries", C.c_int32), ("hints", C.c_int32)]
 
 
 class rcp_counters(C.Structure):
@@ -115,6 +115,7 @@ _SIGS = {
     "rcp_server_submit": [_vp, _vp, C.POINTER(rcp_camera), C.c_int, C.c_int, C.c_int, C.POINTER(rcp_params), _vp,
                           C.POINTER(C.c_int64)],
     "rcp_server_poll": [_vp, C.c_int64, C.POINTER(C.c_int)],
+    "rcp_server_set_step_pixels": [_vp, C.c_int64],
     "rcp_server_wait": [_vp, C.c_int64, C.c_double],
     "rcp_server_stats_get": [_vp, C.POINTER(rcp_server_stats)],
     "rcp_server_destroy": [_vp],
@@ -395,6 +396,10 @@ def rcp_server_submit(srv, scene, cam: rcp_camera, width, height, K, params: rcp
     _check(lib().rcp_server_submit(srv, scene, C.byref(cam), width, height, K, C.byref(params), _ptr(out_rgb),
                                    C.byref(t)), "rcp_server_submit")
     return t.value
+
+
+def rcp_server_set_step_pixels(srv, pixels):
+    _check(lib().rcp_server_set_step_pixels(srv, int(pixels)), "rcp_server_set_step_pixels")
 
 
 def rcp_server_poll(srv, ticket):

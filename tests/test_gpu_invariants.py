@@ -56,15 +56,16 @@ def test_launch_shapes_identical(tiny_g):
         for block in (64, 128, 256):
             for fused in (0, 1):
                 for chunk in (32, 64):
-                    rcp.rcp_set_tuning(g, rcp.rcp_tuning(block, 0, chunk, fused))
+                    rcp.rcp_set_tuning(g, rcp.rcp_tuning(block, 0, chunk, fused, 0, 3))
                     out = _render(g, cam, 640, 360, 3, p)
                     if ref is None:
                         ref = out
                     assert np.array_equal(out, ref), (block, fused, chunk)
-        # shorter shared stacks: the deeper levels spill to global memory
-        for stack in (4, 2, 1):
-            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, stack))
-            assert np.array_equal(_render(g, cam, 640, 360, 3, p), ref), stack
+        # shorter shared stacks (the deeper levels spill to global memory), and
+        # the previous-hit hints off, on for primary or shadow rays only
+        for stack, hints in ((4, 3), (2, 3), (1, 3), (0, 0), (0, 1), (0, 2)):
+            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, stack, hints))
+            assert np.array_equal(_render(g, cam, 640, 360, 3, p), ref), (stack, hints)
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -81,7 +82,8 @@ def test_short_stack_spills_identical():
         d = sc.diameter()
         p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
         ref = _render(g, cam, 480, 270, 4, p)
-        for t in (rcp.rcp_tuning(128, 0, 32, 1, 4), rcp.rcp_tuning(256, 0, 64, 0, 8), rcp.rcp_tuning(64, 0, 32, 1, 1)):
+        for t in (rcp.rcp_tuning(128, 0, 32, 1, 4, 3), rcp.rcp_tuning(256, 0, 64, 0, 8, 0),
+                  rcp.rcp_tuning(64, 0, 32, 1, 1, 3)):
             rcp.rcp_set_tuning(g, t)
             assert np.array_equal(_render(g, cam, 480, 270, 4, p), ref), (t.block, t.stack_entries)
     finally:
@@ -219,11 +221,11 @@ def test_autotune_cache(tmp_path):
         path = str(tmp_path / "tune.json")
         ref = _render(g, cam, 320, 180, 3, p)
         t = rcp.rcp_autotune(g, cam, 320, 180, p, path)
-        assert t.block in (64, 128, 256) and t.chunk in (32, 64) and t.stack_entries in (0, 4)
+        assert t.block in (64, 128, 256) and t.chunk in (32, 64) and t.stack_entries in (0, 4) and t.hints in (0, 3)
         assert np.array_equal(_render(g, cam, 320, 180, 3, p), ref)
         t2 = rcp.rcp_autotune(g, cam, 320, 180, p, path)  # from the cache
-        assert (t2.block, t2.chunk, t2.fused_camera, t2.stack_entries) == (t.block, t.chunk, t.fused_camera,
-                                                                            t.stack_entries)
+        assert (t2.block, t2.chunk, t2.fused_camera, t2.stack_entries, t2.hints) == (
+            t.block, t.chunk, t.fused_camera, t.stack_entries, t.hints)
         assert "depth7" in open(path).read()
     finally:
         rcp.rcp_scene_destroy(g)
