@@ -724,12 +724,16 @@ def served_summary(args):
                 rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"], prepared[i][1],
                                pool.get(i, r["width"], r["height"], lambda t: None))
         srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+        # the device writes each request's RGB into its buffer during the last
+        # pass: every buffer stays alive until its request is done
+        warm_bufs = [np.zeros((r["height"], r["width"], 3), np.float32) for r in reqs[:16]]
         tks = [rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"],
-                                     prepared[i][1], np.zeros((r["height"], r["width"], 3), np.float32))
+                                     prepared[i][1], warm_bufs[i])
                for i, r in enumerate(reqs[:16])]
         for tk in tks:
             rcp.rcp_server_wait(srv, tk, 600.0)
         rcp.rcp_server_destroy(srv)
+        del warm_bufs
         table = []
         for lam in [float(x) for x in args.rates.split(",")]:
             arr = scenes.poisson_arrivals(lam, n_req, seed=4)
