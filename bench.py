@@ -675,22 +675,29 @@ def batched_summary(args):
 
 
 class BufferPool:
-    """Host output buffers reused across requests of one resolution; a buffer
-    is handed out again only after the request that last used it is done."""
+    """Host output buffers of one resolution, reused once their last request is
+    done (the device writes a request's image into its buffer during its last
+    pass, so a buffer in use is never handed out). `done(i)` says whether
+    request i has finished; when no buffer is free a new one is made, so
+    handing out never waits."""
 
-    def __init__(self, per_shape):
-        self.per_shape = per_shape
-        self.bufs = {}
-        self.owner = {}
+    def __init__(self):
+        self.bufs = {}   # (w, h) -> list of buffers
+        self.owner = {}  # (w, h, j) -> request using buffer j
 
-    def get(self, i, w, h, wait):
-        pool = self.bufs.setdefault((w, h), [np.zeros((h, w, 3), np.float32) for _ in range(self.per_shape)])
-        j = i % self.per_shape
-        prev = self.owner.get((w, h, j))
-        if prev is not None:
-            wait(prev)
-        self.owner[(w, h, j)] = i
-        return pool[j]
+    def get(self, i, w, h, done):
+        pool = self.bufs.setdefault((w, h), [])
+        for j in range(len(pool)):
+            prev = self.owner.get((w, h, j))
+            if prev is None or done(prev):
+                self.owner[(w, h, j)] = i
+                return pool[j]
+        pool.append(np.zeros((h, w, 3), np.float32))
+        self.owner[(w, h, len(pool) - 1)] = i
+        return pool[-1]
+
+    def count(self):
+        return sum(len(v) for v in self.bufs.values())
 
 
 def served_summary(args):
@@ -713,7 +720,7 @@ def served_summary(args):
         prepared = [(rcp.camera_from(scs[r["scene"]].poses[r["pose"]]),
                      rcp.make_params(rcp.RCP_MAP_EYE, r["k_frac"] * diams[r["scene"]], 0.1 * diams[r["scene"]]))
                     for r in reqs]
-        pool = BufferPool(24)
+        plain_pool, served_pool = BufferPool(), BufferPool()
         # warm both paths: every distinct request shape once through the plain
         # path (its render contexts and graphs), a burst through a server
         seen = set()
@@ -722,7 +729,7 @@ def served_summary(args):
             if key not in seen:
                 seen.add(key)
                 rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"], prepared[i][1],
-                               pool.get(i, r["width"], r["height"], lambda t: None))
+                               plain_pool.get(i, r["width"], r["height"], lambda t: True))
         srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
         # the device writes each request's RGB into its buffer during the last
         # pass: every buffer stays alive until its request is done
@@ -737,9 +744,9 @@ def served_summary(args):
         table = []
         for lam in [float(x) for x in args.rates.split(",")]:
             arr = scenes.poisson_arrivals(lam, n_req, seed=4)
-            # -- plain: FIFO worker, one request at a time
+            # -- plain: FIFO worker, one request at a time (synchronous: every
+            #    buffer is free again when the next request starts)
             lat = [0.0] * n_req
-            pool = BufferPool(2)
             t0 = time.perf_counter()
 
             def plain_worker():
@@ -748,7 +755,7 @@ def served_summary(args):
                     if wait > 0:
                         time.sleep(wait)
                     rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"],
-                                   prepared[i][1], pool.get(i, r["width"], r["height"], lambda t: None))
+                                   prepared[i][1], plain_pool.get(i, r["width"], r["height"], lambda t: True))
                     lat[i] = time.perf_counter() - t0 - arr[i]
 
             th = threading.Thread(target=plain_worker)
@@ -757,24 +764,28 @@ def served_summary(args):
             plain_span = time.perf_counter() - t0
             plain = {"frames_per_s": n_req / plain_span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
                      "p99_ms": 1000 * float(np.percentile(lat, 99))}
-            # -- server: submit at the arrival times
+            # -- server: submit at the arrival times (latency from submit to the
+            #    image in the caller's buffer; late submits are reported)
             srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
-            pool = BufferPool(24)
-            tickets = []
+            tickets, late = [], 0.0
             t0 = time.perf_counter()
             for i, r in enumerate(reqs):
                 wait = arr[i] - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(wait)
-                buf = pool.get(i, r["width"], r["height"], lambda j: rcp.rcp_server_wait(srv, tickets[j], 600.0))
+                late = max(late, time.perf_counter() - t0 - arr[i])
+                buf = served_pool.get(i, r["width"], r["height"], lambda j: rcp.rcp_server_poll(srv, tickets[j]))
                 tickets.append(rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"],
                                                      r["K"], prepared[i][1], buf))
             for tk in tickets:
                 rcp.rcp_server_wait(srv, tk, 600.0)
             st = rcp.rcp_server_stats_get(srv)
             rcp.rcp_server_destroy(srv)
+            span = st.frames_per_s and st.completed / st.frames_per_s
             served = {"frames_per_s": st.frames_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-                      "mrays_per_s": st.mrays_per_s, "steps": st.steps, "peak_gb": st.device_bytes_peak / 2 ** 30}
+                      "mrays_per_s": st.mrays_per_s, "steps": st.steps, "peak_gb": st.device_bytes_peak / 2 ** 30,
+                      "device_busy_frac": st.device_busy_ms / 1000.0 / span if span else None,
+                      "max_submit_late_ms": 1000.0 * late}
             table.append({"rate_req_s": lam, "served": served, "plain": plain})
             log(f"lambda={lam}: served {served} | plain {plain}")
         return {"requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,

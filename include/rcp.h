@@ -382,6 +382,7 @@ typedef struct {
     double frames_per_s;  /* completed requests per second since the first submit */
     double mrays_per_s;   /* primary + shadow rays per second over the same span */
     int64_t device_bytes_in_use, device_bytes_peak;
+    double device_busy_ms; /* device time of the steps completed so far (CUDA events around each step) */
 } rcp_server_stats;
 
 rcp_status rcp_server_create(int64_t mem_budget_bytes, int max_slots, rcp_server** out);

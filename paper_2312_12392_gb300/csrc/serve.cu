@@ -82,7 +82,7 @@ struct StepSlot {
     ViewDev* h_views = nullptr;  // pinned staging
     int cap = 0;
     unsigned* d_work = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;  // around the step's device work
     bool used = false;
 };
 
@@ -115,6 +115,7 @@ struct rcp_server {
     int* h_status = nullptr;  // pinned: one status word per admitted, unfinished request
     std::vector<int> free_status;
     int64_t step_pixels = DEFAULT_STEP_PIXELS;  // pixels per step (0: every admitted request every step)
+    double busy_ms = 0;  // device time of completed steps
 
     void run();
     void copy_out();
@@ -165,7 +166,8 @@ void free_request(Request& r, cudaStream_t st) {
 rcp_status ensure_slot(StepSlot& s, int n) {
     if (!s.d_work) {
         RCP_CUDA(cudaMalloc((void**)&s.d_work, sizeof(unsigned)));
-        RCP_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+        RCP_CUDA(cudaEventCreate(&s.start));
+        RCP_CUDA(cudaEventCreate(&s.done));
     }
     if (s.cap < n) {
         if (s.d_views) cudaFree(s.d_views);
@@ -233,6 +235,7 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
         total_chunks += (int64_t)v.tiles_x * ((q->H + 3) / 4);
         slot.h_views[i] = v;
     }
+    RCP_CUDA(cudaEventRecord(slot.start, st_main));
     RCP_CUDA(cudaMemcpyAsync(slot.d_views, slot.h_views, sizeof(ViewDev) * batch.size(), cudaMemcpyHostToDevice,
                              st_main));
     RCP_CUDA(cudaMemsetAsync(slot.d_work, 0, sizeof(unsigned), st_main));
@@ -356,7 +359,18 @@ void rcp_server::run() {
             }
             batch = inflight;
         }
-        if (batch.empty()) continue;
+        if (batch.empty()) {  // idle: account the device time of the last steps
+            for (StepSlot& sl : slots)
+                if (sl.used && cudaEventQuery(sl.done) == cudaSuccess) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, sl.start, sl.done) == cudaSuccess) {
+                        std::lock_guard<std::mutex> lk(mu);
+                        busy_ms += ms;
+                    }
+                    sl.used = false;
+                }
+            continue;
+        }
         for (Request* q : batch)
             if (!q->img[0] && q->status == RCP_OK) {
                 rcp_status r = alloc_request(*q, direct, st_main);
@@ -376,7 +390,15 @@ void rcp_server::run() {
             px += qp;
         }
         StepSlot& slot = slots[step_no % STEPS_AHEAD];
-        if (slot.used) cudaEventSynchronize(slot.done);  // bound the run-ahead; frees the slot's staging
+        if (slot.used) {  // bound the run-ahead; frees the slot's staging
+            cudaEventSynchronize(slot.done);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, slot.start, slot.done) == cudaSuccess) {
+                std::lock_guard<std::mutex> lk(mu);
+                busy_ms += ms;
+            }
+            slot.used = false;
+        }
         rcp_status r = ok.empty() ? RCP_OK : enqueue_step(ok, slot);
         ++step_no;
         std::lock_guard<std::mutex> lk(mu);
@@ -535,6 +557,7 @@ rcp_status rcp_server_stats_get(rcp_server* srv, rcp_server_stats* out) {
     out->mrays_per_s = span > 0 ? (double)(h[0] + h[1]) / span / 1e6 : 0.0;
     out->device_bytes_in_use = srv->bytes_in_use;
     out->device_bytes_peak = srv->bytes_peak;
+    out->device_busy_ms = srv->busy_ms;
     return RCP_OK;
 }
 
@@ -559,6 +582,7 @@ void rcp_server_destroy(rcp_server* srv) {
         if (sl.h_views) cudaFreeHost(sl.h_views);
         if (sl.d_work) cudaFree(sl.d_work);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.start) cudaEventDestroy(sl.start);
     }
     if (srv->h_status) cudaFreeHost(srv->h_status);
     for (auto& kv : srv->all)

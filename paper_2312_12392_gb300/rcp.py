@@ -73,7 +73,7 @@ class rcp_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
                 ("in_flight", C.c_int64), ("queued", C.c_int64), ("steps", C.c_int64), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("frames_per_s", C.c_double), ("mrays_per_s", C.c_double),
-                ("device_bytes_in_use", C.c_int64), ("device_bytes_peak", C.c_int64)]
+                ("device_bytes_in_use", C.c_int64), ("device_bytes_peak", C.c_int64), ("device_busy_ms", C.c_double)]
 
 
 _lock = threading.Lock()
