@@ -696,6 +696,10 @@ class BufferPool:
         self.owner[(w, h, len(pool) - 1)] = i
         return pool[-1]
 
+    def release_all(self):
+        """Every request that used a buffer is done: all buffers are free."""
+        self.owner = {}
+
     def count(self):
         return sum(len(v) for v in self.bufs.values())
 
@@ -767,6 +771,7 @@ def served_summary(args):
             # -- server: submit at the arrival times (latency from submit to the
             #    image in the caller's buffer; late submits are reported)
             srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+            served_pool.release_all()
             tickets, late = [], 0.0
             t0 = time.perf_counter()
             for i, r in enumerate(reqs):
