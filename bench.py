@@ -675,33 +675,41 @@ def batched_summary(args):
 
 
 class BufferPool:
-    """Host output buffers of one resolution, reused once their last request is
-    done (the device writes a request's image into its buffer during its last
-    pass, so a buffer in use is never handed out). `done(i)` says whether
-    request i has finished; when no buffer is free a new one is made, so
-    handing out never waits."""
+    """Host output buffers, `per_shape` per resolution, handed out round robin:
+    request i of a resolution writes into buffer (i mod per_shape). Both paths
+    of the served comparison use the same pool: the device writes a request's
+    image straight into its host buffer during the last pass, and writing host
+    pages the GPU has not translated yet is much slower than writing warm ones
+    (measured: a fresh 1080p buffer per request cut rcp_render from ~450 to
+    ~100 frames/s), so the buffers are warmed once before timing and reused
+    the same way by both paths."""
 
-    def __init__(self):
-        self.bufs = {}   # (w, h) -> list of buffers
-        self.owner = {}  # (w, h, j) -> request using buffer j
+    def __init__(self, per_shape):
+        self.per_shape = per_shape
+        self.bufs = {}
+        self.owner = {}
+        self.waits = 0
 
-    def get(self, i, w, h, done):
-        pool = self.bufs.setdefault((w, h), [])
-        for j in range(len(pool)):
-            prev = self.owner.get((w, h, j))
-            if prev is None or done(prev):
-                self.owner[(w, h, j)] = i
-                return pool[j]
-        pool.append(np.zeros((h, w, 3), np.float32))
-        self.owner[(w, h, len(pool) - 1)] = i
-        return pool[-1]
+    def get(self, i, w, h, wait=None):
+        pool = self.bufs.setdefault((w, h), [np.zeros((h, w, 3), np.float32) for _ in range(self.per_shape)])
+        n = self.owner.setdefault((w, h), [0, [None] * self.per_shape])
+        j = n[0] % self.per_shape
+        n[0] += 1
+        prev = n[1][j]
+        if prev is not None and wait is not None and wait(prev):
+            self.waits += 1
+        n[1][j] = i
+        return pool[j]
 
     def release_all(self):
-        """Every request that used a buffer is done: all buffers are free."""
-        self.owner = {}
+        """Every request that used a buffer is done."""
+        for k in self.owner:
+            self.owner[k][1] = [None] * self.per_shape
 
-    def count(self):
-        return sum(len(v) for v in self.bufs.values())
+    def all_buffers(self):
+        for (w, h), v in self.bufs.items():
+            for b in v:
+                yield w, h, b
 
 
 def served_summary(args):
@@ -724,16 +732,22 @@ def served_summary(args):
         prepared = [(rcp.camera_from(scs[r["scene"]].poses[r["pose"]]),
                      rcp.make_params(rcp.RCP_MAP_EYE, r["k_frac"] * diams[r["scene"]], 0.1 * diams[r["scene"]]))
                     for r in reqs]
-        plain_pool, served_pool = BufferPool(), BufferPool()
+        pool = BufferPool(24)
         # warm both paths: every distinct request shape once through the plain
-        # path (its render contexts and graphs), a burst through a server
+        # path (its render contexts and graphs), every pool buffer written once
+        # by a render, a burst through a server
         seen = set()
         for i, r in enumerate(reqs):
             key = (r["scene"], r["width"], r["height"], r["K"])
             if key not in seen:
                 seen.add(key)
                 rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"], prepared[i][1],
-                               plain_pool.get(i, r["width"], r["height"], lambda t: True))
+                               pool.get(i, r["width"], r["height"]))
+        for j in range(pool.per_shape):
+            for r in ({"width": w, "height": h} for w, h in {(q["width"], q["height"]) for q in reqs}):
+                rcp.rcp_render(gs[0], prepared[0][0], r["width"], r["height"], 1, prepared[0][1],
+                               pool.get(j, r["width"], r["height"]))
+        pool.release_all()
         srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
         # the device writes each request's RGB into its buffer during the last
         # pass: every buffer stays alive until its request is done
@@ -759,7 +773,7 @@ def served_summary(args):
                     if wait > 0:
                         time.sleep(wait)
                     rcp.rcp_render(gs[r["scene"]], prepared[i][0], r["width"], r["height"], r["K"],
-                                   prepared[i][1], plain_pool.get(i, r["width"], r["height"], lambda t: True))
+                                   prepared[i][1], pool.get(i, r["width"], r["height"]))
                     lat[i] = time.perf_counter() - t0 - arr[i]
 
             th = threading.Thread(target=plain_worker)
@@ -771,15 +785,25 @@ def served_summary(args):
             # -- server: submit at the arrival times (latency from submit to the
             #    image in the caller's buffer; late submits are reported)
             srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
-            served_pool.release_all()
+            pool.release_all()
+            pool.waits = 0
             tickets, late = [], 0.0
+
+            def wait_if_busy(j):
+                if rcp.rcp_server_poll(srv, tickets[j]):
+                    return False
+                rcp.rcp_server_wait(srv, tickets[j], 600.0)
+                return True
+
             t0 = time.perf_counter()
             for i, r in enumerate(reqs):
                 wait = arr[i] - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(wait)
                 late = max(late, time.perf_counter() - t0 - arr[i])
-                buf = served_pool.get(i, r["width"], r["height"], lambda j: rcp.rcp_server_poll(srv, tickets[j]))
+                # a buffer still in use by an earlier request (only under
+                # overload) is waited for before it is handed out again
+                buf = pool.get(i, r["width"], r["height"], wait_if_busy)
                 tickets.append(rcp.rcp_server_submit(srv, gs[r["scene"]], prepared[i][0], r["width"], r["height"],
                                                      r["K"], prepared[i][1], buf))
             for tk in tickets:
@@ -790,7 +814,7 @@ def served_summary(args):
             served = {"frames_per_s": st.frames_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
                       "mrays_per_s": st.mrays_per_s, "steps": st.steps, "peak_gb": st.device_bytes_peak / 2 ** 30,
                       "device_busy_frac": st.device_busy_ms / 1000.0 / span if span else None,
-                      "max_submit_late_ms": 1000.0 * late}
+                      "max_submit_late_ms": 1000.0 * late, "buffer_waits": pool.waits}
             table.append({"rate_req_s": lam, "served": served, "plain": plain})
             log(f"lambda={lam}: served {served} | plain {plain}")
         return {"requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
