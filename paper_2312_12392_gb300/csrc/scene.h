@@ -118,6 +118,9 @@ rcp_status launch_pack_rgb(const float4* img, float* rgb, int64_t n, cudaStream_
 // Whether kernels on the current device read and write pageable host memory
 // coherently (then a render's last pass can write the caller's RGB directly).
 bool host_coherent();
+// Whether a frame goes straight into host buffer [p, p + bytes) (the host
+// output policy of rcp_set_host_output; records the buffer as written).
+bool use_direct_output(const void* p, size_t bytes);
 // Read and write back one byte in every page of [p, p + bytes).
 void touch_pages(void* p, size_t bytes);
 // Image-space pass over every view (views' base/in/out set).

@@ -22,9 +22,9 @@
 //    its status word (a walk that overflowed its stack fails the request),
 //    copies its RGB image to the caller's buffer where needed, releases its
 //    memory and records its latency, while the device already runs the next
-//    steps. Where the device writes pageable host memory coherently, a
-//    request's last pass writes its RGB into the caller's buffer itself (no
-//    staging buffer, no pack kernel, no copy).
+//    steps. Where the host output policy chooses direct writes
+//    (rcp_set_host_output), a request's last pass writes its RGB into the
+//    caller's buffer itself (no staging buffer, no pack kernel, no copy).
 // New requests join at the next step while others are mid-recursion, so short
 // and long requests share every launch.
 #include <cuda_runtime.h>
@@ -66,6 +66,7 @@ struct Request {
     bool in_step = false;  // advanced by the step being enqueued
     float4* img[2] = {nullptr, nullptr};
     float* rgb = nullptr;
+    bool direct = false;     // the last pass writes out_rgb itself (else pack and copy)
     int2* hint = nullptr;    // per pixel: latest primary-hit and shadow-occluder records, then the status word
     int* d_status = nullptr;  // inside the hint allocation
     int status_slot = -1;     // index of the request's pinned host status word
@@ -111,7 +112,6 @@ struct rcp_server {
     StepSlot slots[STEPS_AHEAD];
     int64_t step_no = 0;
     int device = 0;
-    bool direct = false;  // last passes write the callers' RGB buffers (host_coherent)
     int* h_status = nullptr;  // pinned: one status word per admitted, unfinished request
     std::vector<int> free_status;
     int64_t step_pixels = DEFAULT_STEP_PIXELS;  // pixels per step (0: every admitted request every step)
@@ -228,7 +228,7 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
         v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
         v.out = q->img[q->passes_done & 1];
         v.hint = q->hint;
-        if (direct && q->passes_done + 1 == q->K) v.rgb = q->out_rgb;
+        if (q->direct && q->passes_done + 1 == q->K) v.rgb = q->out_rgb;
         v.pix_begin = total_pix;
         v.chunk_begin = total_chunks;
         total_pix += (int64_t)q->W * q->H;
@@ -244,7 +244,7 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
     if (r != RCP_OK) return r;
     for (Request* q : batch) {
         if (q->passes_done + 1 != q->K) continue;
-        if (!direct) {
+        if (!q->direct) {
             r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, st_main);
             if (r != RCP_OK) return r;
         }
@@ -294,10 +294,10 @@ void rcp_server::copy_out() {
                 set_error("server: a traversal stack overflowed; the request's image is incomplete");
                 st = RCP_ERR_STACK;
             }
-            if (e == cudaSuccess && st == RCP_OK && !direct)
+            if (e == cudaSuccess && st == RCP_OK && !q->direct)
                 e = cudaMemcpyAsync(q->out_rgb, q->rgb, sizeof(float) * 3 * (int64_t)q->W * q->H,
                                     cudaMemcpyDeviceToHost, st_copy);
-            if (e == cudaSuccess && st == RCP_OK && !direct) e = cudaStreamSynchronize(st_copy);
+            if (e == cudaSuccess && st == RCP_OK && !q->direct) e = cudaStreamSynchronize(st_copy);
             if (e != cudaSuccess) st = cuda_fail(e, "server copy-out");
         } else {
             // A failed request may have passes still queued (a step that failed
@@ -373,7 +373,7 @@ void rcp_server::run() {
         }
         for (Request* q : batch)
             if (!q->img[0] && q->status == RCP_OK) {
-                rcp_status r = alloc_request(*q, direct, st_main);
+                rcp_status r = alloc_request(*q, q->direct, st_main);
                 if (r != RCP_OK) q->status = r;
             }
         // the step: admission order, the oldest always, the rest while the
@@ -429,7 +429,6 @@ rcp_status rcp_server_create(int64_t budget, int max_slots, rcp_server** out) {
     s->budget = budget;
     s->max_slots = max_slots;
     RCP_CUDA(cudaGetDevice(&s->device));
-    s->direct = host_coherent();
     RCP_CUDA(cudaStreamCreateWithFlags(&s->st_main, cudaStreamNonBlocking));
     RCP_CUDA(cudaStreamCreateWithFlags(&s->st_copy, cudaStreamNonBlocking));
     RCP_CUDA(cudaMalloc((void**)&s->d_rays, sizeof(unsigned long long) * 2));
@@ -471,8 +470,9 @@ rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_
     q->K = K;
     q->p = *p;
     q->out_rgb = out_rgb;
-    q->bytes = request_bytes(W, H, srv->direct);
-    if (srv->direct) touch_pages(out_rgb, sizeof(float) * 3 * (size_t)W * H);  // mapped before the device writes
+    q->direct = use_direct_output(out_rgb, sizeof(float) * 3 * (size_t)W * H);
+    q->bytes = request_bytes(W, H, q->direct);
+    if (q->direct) touch_pages(out_rgb, sizeof(float) * 3 * (size_t)W * H);  // mapped before the device writes
     q->t_submit = now_s();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) {

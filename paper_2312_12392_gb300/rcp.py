@@ -24,6 +24,7 @@ RCP_OK, RCP_ERR_ARG, RCP_ERR_OOM, RCP_ERR_CUDA, RCP_ERR_STACK, RCP_ERR_TIMEOUT, 
 RCP_LIGHT_POINT, RCP_LIGHT_DIRECTIONAL = 0, 1
 RCP_MAP_EYE, RCP_MAP_TARGET, RCP_MAP_DEPTH, RCP_MAP_IMAGE, RCP_MAP_NORMAL = 0, 1, 2, 3, 4
 RCP_COLLAPSE_AREA, RCP_COLLAPSE_SAH = 0, 1
+RCP_HOST_OUTPUT_AUTO, RCP_HOST_OUTPUT_DIRECT, RCP_HOST_OUTPUT_COPY = 0, 1, 2
 RCP_SPLIT_MAX = 8
 
 
@@ -121,6 +122,8 @@ _SIGS = {
     "rcp_server_destroy": [_vp],
     "rcp_last_error": [],
     "rcp_version": [],
+    "rcp_set_host_output": [C.c_int],
+    "rcp_get_host_output": [],
 }
 
 
@@ -421,6 +424,14 @@ def rcp_server_stats_get(srv) -> rcp_server_stats:
 def rcp_server_destroy(srv):
     if srv:
         lib().rcp_server_destroy(srv)
+
+
+def rcp_set_host_output(mode):
+    _check(lib().rcp_set_host_output(int(mode)), "rcp_set_host_output")
+
+
+def rcp_get_host_output() -> int:
+    return int(lib().rcp_get_host_output())
 
 
 def rcp_last_error() -> str:

@@ -63,6 +63,8 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rcp_render(None, C.byref(cam), 4, 4, 1, C.byref(p), None) == rcp.RCP_ERR_ARG
     assert lib.rcp_server_create(0, 4, C.byref(out)) == rcp.RCP_ERR_ARG
     assert lib.rcp_set_tuning(None, None) == rcp.RCP_ERR_ARG
+    assert lib.rcp_set_host_output(7) == rcp.RCP_ERR_ARG
+    assert rcp.rcp_get_host_output() == rcp.RCP_HOST_OUTPUT_AUTO
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -1,9 +1,10 @@
 """rcp_render's host output. On a device that reads and writes pageable host
-memory coherently, the last pass writes the caller's RGB straight into host
-memory while it traces; elsewhere, and for the image-space mapping, a pack
-kernel and a copy deliver it. Either way the host image must equal the
-device path's image (its RGB lanes) bit for bit: every mapping, jittered
-samples, ragged sizes, K = 1, fresh buffers and a reused one."""
+memory coherently, the last pass may write the caller's RGB straight into host
+memory while it traces (rcp_set_host_output: always, never, or for buffers
+written that way recently); otherwise, and for the image-space mapping, a pack
+kernel and a copy deliver it. Every way the host image must equal the device
+path's image (its RGB lanes) bit for bit: every mapping, jittered samples,
+ragged sizes, K = 1, fresh buffers and a reused one."""
 import numpy as np
 import pytest
 
@@ -43,8 +44,15 @@ def _params(sc, mapping, kf, spp):
     return rcp.make_params(mapping, k, 0.1 * d, jitter=jitter)
 
 
+@pytest.fixture(params=[rcp.RCP_HOST_OUTPUT_AUTO, rcp.RCP_HOST_OUTPUT_DIRECT, rcp.RCP_HOST_OUTPUT_COPY])
+def host_mode(request):
+    rcp.rcp_set_host_output(request.param)
+    yield request.param
+    rcp.rcp_set_host_output(rcp.RCP_HOST_OUTPUT_AUTO)
+
+
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_host_image_equals_device_image(mid_g, case):
+def test_host_image_equals_device_image(mid_g, case, host_mode):
     sc, g = mid_g
     mapping, kf, spp, W, H, K = CASES[case]
     p = _params(sc, mapping, kf, spp)
@@ -58,7 +66,7 @@ def test_host_image_equals_device_image(mid_g, case):
     assert np.array_equal(host.view(np.uint32), ref.view(np.uint32))
 
 
-def test_reused_buffer_is_overwritten(mid_g):
+def test_reused_buffer_is_overwritten(mid_g, host_mode):
     """One buffer through renders of different sizes' worth of poses: every
     call leaves exactly its own image, no pixel of the previous one."""
     sc, g = mid_g

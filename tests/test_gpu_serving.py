@@ -59,7 +59,19 @@ def _serve(reqs, slots=8):
         rcp.rcp_server_destroy(srv)
 
 
-def test_alone_equals_in_mix(two_scenes):
+@pytest.mark.parametrize("mode", [rcp.RCP_HOST_OUTPUT_AUTO, rcp.RCP_HOST_OUTPUT_DIRECT])
+def test_alone_equals_in_mix(two_scenes, mode):
+    """Served images equal the same requests rendered alone, bit for bit, with
+    images delivered by pack-and-copy (fresh buffers under AUTO) or written by
+    the last pass (DIRECT)."""
+    rcp.rcp_set_host_output(mode)
+    try:
+        _alone_equals_in_mix(two_scenes)
+    finally:
+        rcp.rcp_set_host_output(rcp.RCP_HOST_OUTPUT_AUTO)
+
+
+def _alone_equals_in_mix(two_scenes):
     reqs = _requests(two_scenes)
     alone = [rcp.rcp_render(r["g"], rcp.camera_from(r["cam"]), r["W"], r["H"], r["K"], r["p"]) for r in reqs]
     outs, st = _serve(reqs)
