@@ -674,15 +674,22 @@ def batched_summary(args):
         rcp.rcp_scene_destroy(g)
 
 
+def pinned_array(shape):
+    """A float32 numpy array in page-locked host memory (torch's pinned
+    allocator): the GPU writes it through its own page tables."""
+    import torch
+    return torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
+
+
 class BufferPool:
-    """Host output buffers, `per_shape` per resolution, handed out round robin:
-    request i of a resolution writes into buffer (i mod per_shape). Both paths
-    of the served comparison use the same pool: the device writes a request's
-    image straight into its host buffer during the last pass, and writing host
-    pages the GPU has not translated yet is much slower than writing warm ones
-    (measured: a fresh 1080p buffer per request cut rcp_render from ~450 to
-    ~100 frames/s), so the buffers are warmed once before timing and reused
-    the same way by both paths."""
+    """Page-locked host output buffers, `per_shape` per resolution, handed out
+    round robin: request i of a resolution writes into buffer (i mod
+    per_shape). Both paths of the served comparison use the same pool, as a
+    frame server hands its renderer page-locked frame buffers: the last pass
+    writes them directly through the GPU's page tables, whereas pageable
+    buffers the GPU has not written recently cost address-translation misses
+    on every page (measured on the served mix: both paths several times
+    slower)."""
 
     def __init__(self, per_shape):
         self.per_shape = per_shape
@@ -691,7 +698,7 @@ class BufferPool:
         self.waits = 0
 
     def get(self, i, w, h, wait=None):
-        pool = self.bufs.setdefault((w, h), [np.zeros((h, w, 3), np.float32) for _ in range(self.per_shape)])
+        pool = self.bufs.setdefault((w, h), [pinned_array((h, w, 3)) for _ in range(self.per_shape)])
         n = self.owner.setdefault((w, h), [0, [None] * self.per_shape])
         j = n[0] % self.per_shape
         n[0] += 1

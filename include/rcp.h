@@ -404,18 +404,20 @@ rcp_status rcp_server_stats_get(rcp_server* srv, rcp_server_stats* out);
 /* Drop queued requests and stop after the in-flight ones finish. */
 void rcp_server_destroy(rcp_server* srv);
 
-/* How rcp_render and the server deliver a frame into a caller's host buffer,
- * where the device reads and writes pageable host memory coherently (a
- * Grace-class host; elsewhere frames are always packed on the device and
- * copied). A kernel writing host memory goes through the GPU's translation of
- * host addresses: for a buffer the GPU wrote recently the writes overlap the
- * last pass at no cost, for one it has not (a fresh buffer, or one of many
- * used in turn) they are much slower than packing and copying.
- *  RCP_HOST_OUTPUT_AUTO (default): write directly into a buffer that is one of
- *    the last 8 buffers written directly (same address and size); otherwise
- *    pack and copy. A buffer used again is written directly from its second
- *    use on.
- *  RCP_HOST_OUTPUT_DIRECT: always write directly.
+/* How rcp_render and the server deliver a frame into a caller's host buffer:
+ * the last pass writes the RGB into it directly while it traces, or the image
+ * is packed on the device and copied. A page-locked buffer (cudaMallocHost,
+ * cudaHostRegister) is mapped in the GPU's page tables and written directly.
+ * A pageable buffer can be written directly only where the device reads and
+ * writes pageable host memory coherently (a Grace-class host), through the
+ * GPU's translation of host addresses: for a buffer the GPU wrote recently
+ * that costs nothing, for one it has not (a fresh buffer) it is much slower
+ * than packing and copying.
+ *  RCP_HOST_OUTPUT_AUTO (default): page-locked buffers directly; pageable ones
+ *    directly if one of the last 8 pageable buffers written directly (same
+ *    address and size), else pack and copy (a buffer used again is written
+ *    directly from its second use on).
+ *  RCP_HOST_OUTPUT_DIRECT: directly whenever the device can reach the buffer.
  *  RCP_HOST_OUTPUT_COPY: always pack and copy.
  * Process-wide; the images are the same either way. */
 typedef enum { RCP_HOST_OUTPUT_AUTO = 0, RCP_HOST_OUTPUT_DIRECT = 1, RCP_HOST_OUTPUT_COPY = 2 } rcp_host_output;

@@ -40,16 +40,17 @@ bool host_coherent() {
     return cached[dev] != 0;
 }
 
-// How frames reach host buffers (rcp_set_host_output). A kernel writing host
-// memory goes through the GPU's translation of host addresses; for a buffer
-// the GPU wrote recently the translations are cached and the writes overlap
-// the last pass for free, but for a buffer it has not (a fresh one, or one of
-// many used in turn) every page misses and the frame is much slower than a
-// device image and a copy (measured: ~100 against ~450 frames/s at 1080p).
-// AUTO therefore writes directly only into one of the last kHostLru buffers
-// written directly (same address and size), and otherwise packs the image
-// on the device and copies it; a buffer used again is written directly from
-// its second use on.
+// How frames reach host buffers (rcp_set_host_output). A page-locked buffer is
+// mapped in the GPU's own page tables: the last pass writes it directly. A
+// pageable buffer is reached through the GPU's translation of host addresses
+// (where the device reads pageable memory coherently): for a buffer the GPU
+// wrote recently the translations are cached and the writes overlap the last
+// pass for free, but for a fresh one every page misses and the frame is much
+// slower than a device image and a copy (measured: ~100 against ~450
+// frames/s at 1080p). AUTO therefore writes a pageable buffer directly only if
+// it is one of the last kHostLru buffers written directly (same address and
+// size), and otherwise packs the image on the device and copies it; a buffer
+// used again is written directly from its second use on.
 namespace {
 std::atomic<int> g_host_output{RCP_HOST_OUTPUT_AUTO};
 std::mutex g_lru_mu;
@@ -57,10 +58,20 @@ constexpr int kHostLru = 8;
 std::vector<std::pair<const void*, size_t>> g_lru;  // most recent first
 }  // namespace
 
+bool page_locked(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered pointer is not an error to keep
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 bool use_direct_output(const void* p, size_t bytes) {
-    if (!host_coherent()) return false;
     const int mode = g_host_output.load();
     if (mode == RCP_HOST_OUTPUT_COPY) return false;
+    if (page_locked(p)) return true;  // in the GPU's page tables, at the same address
+    if (!host_coherent()) return false;
     std::lock_guard<std::mutex> lk(g_lru_mu);
     auto it = std::find(g_lru.begin(), g_lru.end(), std::make_pair(p, bytes));
     const bool seen = it != g_lru.end();

@@ -82,3 +82,25 @@ def test_reused_buffer_is_overwritten(mid_g, host_mode):
         out = rcp.rcp_render(g, cam, W, H, 6, p, buf)
         assert out is buf
         assert np.array_equal(buf, ref)
+
+
+def test_page_locked_buffer(mid_g):
+    """A page-locked buffer is written directly by the last pass (through the
+    GPU's page tables) under every policy but COPY, with the same image."""
+    sc, g = mid_g
+    W, H = 131, 77
+    p = _params(sc, rcp.RCP_MAP_EYE, 0.03, 0)
+    cam = rcp.camera_from(sc.poses[9])
+    d_out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    rcp.rcp_render_device(g, cam, W, H, 4, p, None, d_out, None, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ref = d_out[..., :3].cpu().numpy()
+    buf = torch.full((H, W, 3), float("nan"), dtype=torch.float32, pin_memory=True).numpy()
+    for mode in (rcp.RCP_HOST_OUTPUT_AUTO, rcp.RCP_HOST_OUTPUT_COPY):
+        rcp.rcp_set_host_output(mode)
+        try:
+            buf[...] = np.nan
+            assert rcp.rcp_render(g, cam, W, H, 4, p, buf) is buf
+            assert np.array_equal(buf, ref)
+        finally:
+            rcp.rcp_set_host_output(rcp.RCP_HOST_OUTPUT_AUTO)
