@@ -400,6 +400,9 @@ rcp_status rcp_server_set_step_pixels(rcp_server* srv, int64_t pixels);
 /* done = 1 finished, 0 pending; the request's own status is returned. */
 rcp_status rcp_server_poll(rcp_server* srv, int64_t ticket, int* done);
 rcp_status rcp_server_wait(rcp_server* srv, int64_t ticket, double timeout_s);
+/* Submit-to-done latency in ms of a finished request (RCP_ERR_STATE while it
+ * is pending). */
+rcp_status rcp_server_latency(rcp_server* srv, int64_t ticket, double* ms);
 rcp_status rcp_server_stats_get(rcp_server* srv, rcp_server_stats* out);
 /* Drop queued requests and stop after the in-flight ones finish. */
 void rcp_server_destroy(rcp_server* srv);

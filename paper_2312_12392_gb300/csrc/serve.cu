@@ -514,6 +514,25 @@ rcp_status rcp_server_poll(rcp_server* srv, int64_t ticket, int* done) {
     return it->second->done ? it->second->status : RCP_OK;
 }
 
+rcp_status rcp_server_latency(rcp_server* srv, int64_t ticket, double* ms) {
+    if (!srv || !ms) {
+        set_error("rcp_server_latency: NULL argument");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(ticket);
+    if (it == srv->all.end()) {
+        set_error("rcp_server_latency: unknown ticket");
+        return RCP_ERR_ARG;
+    }
+    if (!it->second->done) {
+        set_error("rcp_server_latency: request not finished");
+        return RCP_ERR_STATE;
+    }
+    *ms = 1000.0 * (it->second->t_done - it->second->t_submit);
+    return RCP_OK;
+}
+
 rcp_status rcp_server_wait(rcp_server* srv, int64_t ticket, double timeout_s) {
     if (!srv) {
         set_error("rcp_server_wait: NULL server");

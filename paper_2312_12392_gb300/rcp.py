@@ -118,6 +118,7 @@ _SIGS = {
     "rcp_server_poll": [_vp, C.c_int64, C.POINTER(C.c_int)],
     "rcp_server_set_step_pixels": [_vp, C.c_int64],
     "rcp_server_wait": [_vp, C.c_int64, C.c_double],
+    "rcp_server_latency": [_vp, C.c_int64, C.POINTER(C.c_double)],
     "rcp_server_stats_get": [_vp, C.POINTER(rcp_server_stats)],
     "rcp_server_destroy": [_vp],
     "rcp_last_error": [],
@@ -413,6 +414,13 @@ def rcp_server_poll(srv, ticket):
 
 def rcp_server_wait(srv, ticket, timeout_s=60.0):
     _check(lib().rcp_server_wait(srv, ticket, float(timeout_s)), "rcp_server_wait")
+
+
+def rcp_server_latency(srv, ticket) -> float:
+    """Submit-to-done latency (ms) of a finished request."""
+    ms = C.c_double()
+    _check(lib().rcp_server_latency(srv, ticket, C.byref(ms)), "rcp_server_latency")
+    return ms.value
 
 
 def rcp_server_stats_get(srv) -> rcp_server_stats:
