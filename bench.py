@@ -94,13 +94,17 @@ def split_for(args, workload):
     return 8 if workload in FOREST_WORKLOADS else 0
 
 
+TRACE_SOURCES = ("rcp_internal.cuh", "trace.cu", "trace.cuh")  # everything the k_trace kernel compiles from
+
+
 def csrc_hash():
-    """Hash of the CUDA/C++ sources with comments and whitespace removed, so
-    that a recorded ncu figure stays tied to the code it was taken on."""
+    """Hash of the trace kernel's sources with comments and whitespace
+    removed, so that a recorded ncu figure stays tied to the code it was taken
+    on (edits elsewhere, the server or the ABI, do not invalidate it)."""
     import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_12392_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in TRACE_SOURCES:
         src = open(os.path.join(d, f), encoding="utf-8").read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
