@@ -19,7 +19,7 @@ triangles, the continuous-batching server against the plain per-request path,
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload mid|forest|batched|served|stress|imagespace]
-                    [--collapse auto|area|sah] [--tuning auto|block,chunk,fused[,stack]]
+                    [--collapse auto|area|sah] [--tuning auto|block,chunk,fused[,stack[,hints[,chain]]]]
                     [--no-extras]
 
 --workload prints one workload's line alone. --collapse auto builds the
@@ -270,12 +270,13 @@ def cpu_oracle_sample(sc, poses, target_s, nthreads=0, min_px=64, max_px=8192):
 def parse_tuning(spec):
     from paper_2312_12392_gb300 import rcp
     v = [int(x) for x in spec.split(",")]
-    return rcp.rcp_tuning(v[0], 0, v[1], v[2], v[3] if len(v) > 3 else 0, v[4] if len(v) > 4 else 3)
+    return rcp.rcp_tuning(v[0], 0, v[1], v[2], v[3] if len(v) > 3 else 0, v[4] if len(v) > 4 else 3,
+                          v[5] if len(v) > 5 else 0)
 
 
 def tuning_dict(t):
     return {"block": t.block, "chunk": t.chunk, "fused_camera": t.fused_camera, "stack_entries": t.stack_entries,
-            "hints": t.hints}
+            "hints": t.hints, "chain_passes": t.chain_passes}
 
 
 def time_frames(g, cams, W, H, K, params, stream, flush):
@@ -308,7 +309,7 @@ def count_work(g, cams, W, H, K, params):
     import torch
 
     from paper_2312_12392_gb300 import rcp
-    tot = dict(box=0, tri=0, sph=0, nodes=0, prim_rays=0, rays=0, launches=0)
+    tot = dict(box=0, tri=0, sph=0, nodes=0, prim_rays=0, rays=0, frames=len(cams))
     a = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     b = torch.empty_like(a)
     for c in cams:
@@ -322,20 +323,23 @@ def count_work(g, cams, W, H, K, params):
             tot["nodes"] += cnt.nodes
             tot["prim_rays"] += cnt.primary_rays
             tot["rays"] += cnt.rays
-            tot["launches"] += 1
             prev = dst
     return tot
 
 
-def roofline(work, pass_ms, workload, clk, sms):
+def roofline(work, pass_ms, frames, workload, clk, sms):
     """The trace kernel's roofline: algorithmic FP32 lane-operations per launch
     over the mean launch time, against SMs x 128 lanes x the maximum SM clock
     (the kernel is bound by instruction issue and the ALU pipe, ncu); the byte
     view charges every node, primitive and image fetch at the measured HBM
     peak; the ncu view (issue, pipes, L1) comes from the committed profile when
-    it was taken on the current sources."""
+    it was taken on the current sources. A launch is one pass, or all K passes
+    of a frame when they ran chained: pass_ms holds the launches of `frames`
+    timed frames, and the counted work (over the same cameras) is shared out
+    over as many launches."""
     hbm_gbs, sm_max_mhz, peak_src = measured_peaks()
-    n = max(work["launches"], 1)
+    per_frame = len(pass_ms) / max(frames, 1)
+    n = max(work["frames"] * per_frame, 1)
     ops = (OPS_BOX * work["box"] + OPS_TRI * work["tri"] + OPS_SPH * work["sph"] + OPS_PIXEL * work["prim_rays"]) / n
     byts = (BYTES_NODE * work["nodes"] + BYTES_PRIM * (work["tri"] + work["sph"]) +
             BYTES_PIXEL_PASS * work["prim_rays"]) / n
@@ -346,9 +350,11 @@ def roofline(work, pass_ms, workload, clk, sms):
             "unit": "Tops/s (algorithmic FP32 lane-ops)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = prof.get("dram_bytes_per_launch") if prof else None
-    roof["kernel"] = "k_trace (camera + primary + shadow + shade, one launch per pass)"
+    roof["kernel"] = ("k_trace (camera + primary + shadow + shade, " +
+                      ("one launch per pass)" if per_frame > 1 else "all K passes in one launch)"))
     roof["launch_ms"] = launch_s * 1e3
-    roof["launches_counted"] = work["launches"]
+    roof["launches_per_frame"] = per_frame
+    roof["launches_counted"] = n
     roof["algorithmic_ops_per_launch"] = ops
     roof["algorithmic_bytes_per_launch"] = byts
     roof["peak_source"] = f"{sms} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz (max SM clock)"
@@ -455,7 +461,8 @@ def run_ours(args):
     rays = sum_over_ranks(rays, "cuda")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     # algorithmic work of the timed launches: the same poses, counted
-    roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, args.workload, clk, sms)
+    roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, len(cams), args.workload, clk,
+                    sms)
     e2e_fps, e2e_t = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, max(3, min(args.steps, 16)))
     e2e_fps = world * max(3, min(args.steps, 16)) / max_over_ranks(e2e_t, "cuda")
     frames = args.steps * world
@@ -476,14 +483,14 @@ def run_ours(args):
         "config": {"workload": desc, "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
                    "tuning": tuning_dict(t),
-                   "tuning_source": "rcp_autotune (block x chunk x fused camera x shared stack depth x hints)"
+                   "tuning_source": "rcp_autotune (block x chunk x fused camera x shared stack depth x hints x chained passes)"
                    if args.tuning == "auto" else "fixed by --tuning",
                    "parallelism": f"replicas x{world} (poses split across ranks, no collective on the data path)"},
         "mrays_per_s": rays / (tmax / 1000.0) / 1e6,
         "rays_per_frame": rays / frames,
         "roofline": roof,
         "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES),
-        "gpu_launches": args.steps * K_PASSES * (1 if t.fused_camera else 2),
+        "gpu_launches": len(pass_ms) * (1 if t.fused_camera else 2),  # trace launches (+ camera kernels)
         "clocks": clk,
         "wall_s": wall,
     }
@@ -538,7 +545,8 @@ def forest_summary(args):
         ms, pass_ms, rays = time_frames(g, cams, W_IMG, H_IMG, K_PASSES, params, stream, flush)
         clk = clocks.stop()
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, "forest", clk, sms)
+        roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, len(cams), "forest", clk,
+                        sms)
         e2e_fps, _ = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, 16)
         tot = sum(ms) / 1000.0
         info = rcp.rcp_scene_get_info(g)
@@ -547,7 +555,7 @@ def forest_summary(args):
                 "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES), "clocks": clk,
                 "tuning": tuning_dict(t), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
                 "depth": info.depth, "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
-                "records": info.n_records, "gpu_launches": len(cams) * K_PASSES}
+                "records": info.n_records, "gpu_launches": len(pass_ms)}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -666,14 +674,16 @@ def batched_summary(args):
         batch_once()
         torch.cuda.synchronize()
         p_, s_ = rcp.rcp_last_ray_counts(g)
+        launches = len(rcp.rcp_last_pass_times(g))
         return {"views_per_s": len(sizes) / (res["batched"] / 1000.0), "ms_per_batch": res["batched"],
                 "plain_views_per_s": len(sizes) / (res["plain"] / 1000.0), "plain_ms_per_batch": res["plain"],
                 "speedup_vs_plain": res["plain"] / res["batched"],
                 "mrays_per_s": (p_ + s_) / (res["batched"] / 1000.0) / 1e6, "steps": steps,
-                "workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, one launch per "
-                            "pass over all views, graph-captured",
+                "workload": f"forest 1.07M tris, 64 views ({pix / 1e6:.1f} Mpixel total), K=6, " +
+                            ("one launch per pass" if launches > 1 else "one launch for all passes") +
+                            " over all views, graph-captured",
                 "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1), "tuning": tuning_dict(t),
-                "l2": "flushed between steps", "gpu_launches": steps * K_PASSES}
+                "l2": "flushed between steps", "gpu_launches": steps * launches}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -1061,8 +1071,9 @@ def main(argv=None):
     ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress", "imagespace"])
     ap.add_argument("--tuning", default="auto",
                     help="'auto' (the library's autotuner, cached per GPU, scene size, tree depth and view) or "
-                         "block,chunk,fused_camera[,stack_entries[,hints]] (stack 0 = one entry per tree level; "
-                         "hints: bit 0 primary, bit 1 shadow, default 3)")
+                         "block,chunk,fused_camera[,stack_entries[,hints[,chain_passes]]] (stack 0 = one entry per "
+                         "tree level; hints: bit 0 primary, bit 1 shadow, default 3; chain_passes 1 = all K passes "
+                         "in one launch)")
     ap.add_argument("--collapse", default="auto", choices=["auto", "area", "sah"],
                     help="BVH collapse policy; auto: sah for the forest workloads, area for the terrains")
     ap.add_argument("--split", default="auto", choices=["auto"] + [str(i) for i in range(9)],

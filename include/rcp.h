@@ -259,7 +259,11 @@ rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rc
  * entries spill the deeper levels to a library-owned global-memory region);
  * hints: bit 0 = each pixel's walk first tests the primitive its ray hit in the
  * previous pass (a closer far limit from the start), bit 1 = its shadow walk
- * first tests its previous occluder. No choice changes any result. */
+ * first tests its previous occluder; chain_passes: 1 = one launch runs all K
+ * passes, each warp carrying the pixels of its tile from pass to pass in
+ * registers (renders of K >= 2 at one sample per pixel with the fused camera
+ * and any mapping but RCP_MAP_IMAGE; others run one launch per pass). No
+ * choice changes any result. */
 typedef struct {
     int32_t block;
     int32_t blocks_per_sm;
@@ -267,15 +271,17 @@ typedef struct {
     int32_t fused_camera;
     int32_t stack_entries;
     int32_t hints;
+    int32_t chain_passes;
 } rcp_tuning;
 
 rcp_status rcp_get_tuning(const rcp_scene* scene, rcp_tuning* out);
 rcp_status rcp_set_tuning(rcp_scene* scene, const rcp_tuning* tuning);
 
-/* Time every tuning candidate (block x chunk x fused camera x shared stack
- * depth, the depth a full tree walk needs or half of it, x hints on or off) on
- * this scene and
- * view, keep the fastest in the scene and return it. cache_path (nullable): a
+/* Time every tuning candidate on this scene and view (a K = 4 render each):
+ * one launch per pass over block x chunk x fused camera x shared stack depth
+ * (the depth a full tree walk needs, or half of it) x hints on or off, and
+ * chained passes over block x chunk x stack depth x hints. Keep the fastest in
+ * the scene and return it. cache_path (nullable): a
  * JSON file of earlier results, keyed by GPU name, scene size class, tree depth
  * and view size; read before and updated after the search. */
 rcp_status rcp_autotune(rcp_scene* scene, const rcp_camera* cam, int width, int height,
@@ -299,9 +305,10 @@ rcp_status rcp_last_ray_counts(const rcp_scene* scene, int64_t* primary, int64_t
 rcp_status rcp_count_pass(const rcp_scene* scene, const rcp_camera* cam, int width, int height,
                           const rcp_params* params, const float* d_in, float* d_out, rcp_counters* out);
 
-/* Device time (ms) of each pass of the scene's most recent render, from CUDA
- * events recorded on the render's stream between the passes (inside the
- * captured graph). Read after the render has completed. */
+/* Device time (ms) of each launch of the scene's most recent render, from CUDA
+ * events recorded on the render's stream between the launches (inside the
+ * captured graph): one per pass, or one for all K passes when they ran
+ * chained. Read after the render has completed. */
 rcp_status rcp_last_pass_times(const rcp_scene* scene, float* ms, int max_passes, int* n_passes);
 
 /* Bytes that one rcp_render call of K passes over n_views views copies from

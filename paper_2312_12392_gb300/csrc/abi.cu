@@ -302,6 +302,7 @@ LaunchCfg cfg_of(const Scene& sc) {
     c.stack = sc.tuning.stack_entries > 0 ? std::min(sc.tuning.stack_entries, full) : full;
     c.spill_entries = full - c.stack;
     c.hints = sc.tuning.hints;
+    c.chain = sc.tuning.chain_passes != 0;
     return c;
 }
 
@@ -344,7 +345,8 @@ rcp_status ensure_rays(RenderCtx& ctx, const LaunchCfg& c) {
 std::string cfg_key(const LaunchCfg& c) {
     std::ostringstream o;
     o << c.block << "/" << c.blocks_per_sm << "/" << c.chunk << "/" << c.fused << "/" << c.stack << "/"
-      << c.spill_entries << "/" << (const void*)c.spill << "/" << c.count << "/" << c.ms << "/" << c.hints;
+      << c.spill_entries << "/" << (const void*)c.spill << "/" << c.count << "/" << c.ms << "/" << c.hints
+      << "/" << c.chain;
     return o.str();
 }
 
@@ -426,6 +428,15 @@ rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg,
     RCP_CUDA(cudaMemsetAsync(ctx.d_rays, 0, sizeof(unsigned long long) * 2, st));
     const SceneDev S = sc.dev();
     RCP_CUDA(record(ctx.pass_ev[0]));
+    if (cfg.chain && ctx.K > 1 && !ctx.image_mode && cfg.fused && !cfg.ms && !cfg.multi) {
+        rcp_status r = launch_chain(S, cfg, ctx.d_views, ctx.n_views, ctx.K, ctx.total_chunks, ctx.d_work, ctx.d_rays,
+                                    counters, st);
+        if (r != RCP_OK) return r;
+        RCP_CUDA(record(ctx.pass_ev[1]));
+        ctx.launches = 1;
+        return RCP_OK;
+    }
+    ctx.launches = ctx.K;
     for (int n = 0; n < ctx.K; ++n) {
         rcp_status r = (ctx.image_mode && n > 0)
                            ? launch_imagespace(ctx.d_views + (size_t)n * ctx.n_views, ctx.n_views, ctx.total_pix, st)
@@ -880,9 +891,10 @@ rcp_status rcp_set_tuning(rcp_scene* sc, const rcp_tuning* t) {
     }
     if ((t->block != 64 && t->block != 128 && t->block != 256) || (t->chunk != 32 && t->chunk != 64) ||
         t->blocks_per_sm < 0 || t->blocks_per_sm > 32 || (t->fused_camera != 0 && t->fused_camera != 1) ||
-        t->stack_entries < 0 || t->stack_entries > MAX_STACK || t->hints < 0 || t->hints > 3) {
+        t->stack_entries < 0 || t->stack_entries > MAX_STACK || t->hints < 0 || t->hints > 3 ||
+        (t->chain_passes != 0 && t->chain_passes != 1)) {
         set_error("rcp_set_tuning: block in {64,128,256}, chunk in {32,64}, 0 <= blocks_per_sm <= 32, fused 0/1, "
-                  "0 <= stack_entries <= 64, 0 <= hints <= 3");
+                  "0 <= stack_entries <= 64, 0 <= hints <= 3, chain_passes 0/1");
         return RCP_ERR_ARG;
     }
     std::lock_guard<std::mutex> lk(sc->mu);
@@ -1004,7 +1016,7 @@ rcp_status rcp_last_pass_times(const rcp_scene* sc, float* ms, int max_passes, i
         return RCP_ERR_STATE;
     }
     const RenderCtx& c = *sc->last;
-    const int n = std::min(c.K, max_passes);
+    const int n = std::min(c.launches, max_passes);
     for (int i = 0; i < n; ++i) RCP_CUDA(cudaEventElapsedTime(&ms[i], c.pass_ev[i], c.pass_ev[i + 1]));
     *n_passes = n;
     return RCP_OK;
@@ -1078,7 +1090,7 @@ std::string gpu_name() {
     return prop.name;
 }
 
-// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, stack_entries, hints, us], ...}
+// A flat JSON object {"key": [block, blocks_per_sm, chunk, fused, stack_entries, hints, chain_passes, us], ...}
 std::map<std::string, std::vector<double>> read_cache(const char* path) {
     std::map<std::string, std::vector<double>> m;
     if (!path) return m;
@@ -1098,7 +1110,7 @@ std::map<std::string, std::vector<double>> read_cache(const char* path) {
         std::stringstream vs(s.substr(a + 1, b - a - 1));
         std::string tok;
         while (std::getline(vs, tok, ',')) v.push_back(atof(tok.c_str()));
-        if (v.size() >= 5) m[key] = v;
+        if (v.size() >= 8) m[key] = v;  // entries of fewer fields predate a tuning field: searched again
         i = b + 1;
     }
     return m;
@@ -1140,8 +1152,7 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     auto it = cache.find(key.str());
     if (it != cache.end()) {
         const auto& v = it->second;
-        rcp_tuning t{(int)v[0], (int)v[1], (int)v[2], (int)v[3], v.size() >= 6 ? (int)v[4] : 0,
-                     v.size() >= 7 ? (int)v[5] : 3};
+        rcp_tuning t{(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6]};
         r = rcp_set_tuning(sc, &t);
         if (r == RCP_OK && out) *out = t;
         if (r == RCP_OK) return RCP_OK;
@@ -1158,38 +1169,43 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     const int full = full_stack(*sc);
     std::vector<int> stacks{0};  // 0: one entry per tree level
     if (full / 2 >= 4) stacks.push_back(((full / 2) + 3) & ~3);
+    // one launch per pass over block x fused camera x chunk x stack x hints;
+    // chained passes (fused camera) over block x chunk x stack x hints
+    std::vector<rcp_tuning> cands;
     for (int b : {64, 128, 256})
-        for (int fused = 0; fused < 2; ++fused)
-            for (int chunk : {32, 64})
-                for (int stk : stacks)
-                for (int hints : {3, 0}) {
-                    if (stk >= full) continue;
-                    rcp_tuning t{b, 0, chunk, fused, stk, hints};
-                    sc->tuning = t;
-                    const float4* ins[1] = {nullptr};
-                    float4* outs[1] = {d_img.p};
-                    double us = 1e30;
-                    // K = 2 so the second pass reads a real image; best of 3
-                    for (int rep = 0; rep < 4 && r == RCP_OK; ++rep) {
-                        cudaEventRecord(ev.a, st);
-                        r = render_views(*sc, 1, cam, &W, &H, 2, p, ins, outs, nullptr, st);
-                        cudaEventRecord(ev.b, st);
-                        if (cudaEventSynchronize(ev.b) != cudaSuccess) r = RCP_ERR_CUDA;
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, ev.a, ev.b);
-                        if (rep > 0) us = std::min(us, 1000.0 * ms);
-                    }
-                    if (r != RCP_OK) break;
-                    if (us < best_us) {
-                        best_us = us;
-                        best = t;
-                    }
-                }
+        for (int chain = 0; chain < 2; ++chain)
+            for (int fused = chain; fused < 2; ++fused)
+                for (int chunk : {32, 64})
+                    for (int stk : stacks)
+                        for (int hints : {3, 0})
+                            if (stk < full) cands.push_back(rcp_tuning{b, 0, chunk, fused, stk, hints, chain});
+    for (const rcp_tuning& t : cands) {
+        sc->tuning = t;
+        const float4* ins[1] = {nullptr};
+        float4* outs[1] = {d_img.p};
+        double us = 1e30;
+        // K = 4 so later passes read real images and a chained launch has
+        // passes to carry; best of 3
+        for (int rep = 0; rep < 4 && r == RCP_OK; ++rep) {
+            cudaEventRecord(ev.a, st);
+            r = render_views(*sc, 1, cam, &W, &H, 4, p, ins, outs, nullptr, st);
+            cudaEventRecord(ev.b, st);
+            if (cudaEventSynchronize(ev.b) != cudaSuccess) r = RCP_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev.a, ev.b);
+            if (rep > 0) us = std::min(us, 1000.0 * ms);
+        }
+        if (r != RCP_OK) break;
+        if (us < best_us) {
+            best_us = us;
+            best = t;
+        }
+    }
     sc->tuning = best;
     if (r != RCP_OK) return r;
-    cache[key.str()] = {(double)best.block,         (double)best.blocks_per_sm, (double)best.chunk,
-                        (double)best.fused_camera,  (double)best.stack_entries, (double)best.hints,
-                        best_us};
+    cache[key.str()] = {(double)best.block,        (double)best.blocks_per_sm, (double)best.chunk,
+                        (double)best.fused_camera, (double)best.stack_entries, (double)best.hints,
+                        (double)best.chain_passes, best_us};
     write_cache(cache_path, cache);
     if (out) *out = best;
     return RCP_OK;

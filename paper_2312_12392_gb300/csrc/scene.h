@@ -36,7 +36,8 @@ struct RenderCtx {
     int32_t* io_prim = nullptr;  // host-API hit ids
     int2* hints = nullptr;       // per pixel: latest primary-hit and shadow-occluder records (-1 none)
     cudaEvent_t staged = nullptr;
-    cudaEvent_t pass_ev[17] = {};  // timing events around every pass (recorded inside the graph)
+    cudaEvent_t pass_ev[17] = {};  // timing events around every launch (recorded inside the graph)
+    int launches = 0;              // launches of the latest enqueue: K, or 1 when the passes are chained
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
     cudaEvent_t done = nullptr;  // recorded after the context's latest launch
@@ -67,7 +68,7 @@ struct Scene {
     float diam = 0.f;
     float build_ms = 0.f;
     LightDev light{};
-    rcp_tuning tuning{128, 0, 32, 1, 0, 3};
+    rcp_tuning tuning{128, 0, 32, 1, 0, 3, 0};
     std::mutex mu;
     std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
     RenderCtx* last = nullptr;  // context of the most recent render
@@ -103,6 +104,7 @@ struct LaunchCfg {
     bool ms = false;  // jittered multi-sample kernel
     bool multi = false;  // views of several scenes (each view names its scene)
     int hints = 3;    // previous-hit hints: bit 0 primary, bit 1 shadow
+    bool chain = false;  // all K passes in one launch where the render allows it
 };
 
 // One pass over n_views views whose descriptors are at d_views (device). A
@@ -110,6 +112,14 @@ struct LaunchCfg {
 rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                        int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work,
                        unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st);
+// All K passes over n_views views in one launch: d_views holds K descriptors
+// per view, pass-major; each pixel's colour and hints stay in registers from
+// pass to pass and only the last pass's outputs are written. Single-sample,
+// one scene, fused camera, and a mapping that reads only the pixel's own
+// previous value.
+rcp_status launch_chain(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views, int K,
+                        int64_t total_chunks, unsigned* d_work, unsigned long long* d_rays,
+                        unsigned long long* d_counters, cudaStream_t st);
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,
                               int brute, float* t_out, int32_t* prim_out, int stack_entries, int* d_status,
                               cudaStream_t st);

@@ -79,11 +79,20 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
 
 // MULTI: every view names its own scene (views of several scenes in one
 // launch); otherwise all views render the launch's scene S0.
-template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI>
-__global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __restrict__ views, int n_views,
+// CHAIN: one launch runs all K passes. views holds K descriptors per view
+// (pass-major); a warp carries each pixel of its tile through the K passes,
+// its colour and hints in registers, and writes only the last pass's
+// outputs. At one sample per pixel with a camera that reads only the pixel's
+// own previous value (every mapping but the image-space one), this computes
+// exactly what K launches compute.
+template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI, bool CHAIN>
+__global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 warps per SM, as the one-pass kernel
+    k_trace(SceneDev S0, const ViewDev* __restrict__ views, int n_views,
                                                  int64_t total_chunks, int chunk_tiles,
                                                  const float4* __restrict__ rays, unsigned* work, StackCfg stk,
-                                                 unsigned long long* ray_counts, unsigned long long* counters) {
+                                                 unsigned long long* ray_counts, unsigned long long* counters,
+                                                 int K) {
+    static_assert(!CHAIN || (FUSED && !MS && !MULTI), "a chained launch makes its rays itself, one per pixel");
     extern __shared__ uint2 s_stack[];
     __shared__ uint8_t s_order[ORDER_LUT_BYTES];
     __shared__ SceneDev s_scene[MULTI ? BLOCK / 32 : 1];  // MULTI: the scene of each warp's current tile
@@ -103,7 +112,8 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
         for (int sub = 0; sub < chunk_tiles; ++sub) {
             const int64_t chunk = (int64_t)c0 + sub;
             if (chunk >= total_chunks) break;
-            const ViewDev& v = views[find_view_by_chunk(views, n_views, chunk)];
+            const int vi = find_view_by_chunk(views, n_views, chunk);
+            const ViewDev& v = views[vi];
             if (MULTI) {  // the warp's tile is one view: copy its scene to the warp's slot
                 __syncwarp();
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(v.scene);
@@ -168,35 +178,40 @@ __global__ void __launch_bounds__(BLOCK) k_trace(SceneDev S0, const ViewDev* __r
             int2 hint = v.hint && stk.hints ? v.hint[p] : make_int2(-1, -1);
             if (!(stk.hints & 1)) hint.x = -1;
             if (!(stk.hints & 2)) hint.y = -1;
-            prefetch_record(S, hint.x);  // its lines arrive while the camera ray is made
-            RayF r;
-            if (FUSED) {
-                const float4 c = v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
-                r = camera_ray(v, (float)x + 0.5f, (float)y + 0.5f, c, S.tmin);
-            } else {
-                const float4 a = __ldg(rays + 2 * (v.pix_begin + p)), b = __ldg(rays + 2 * (v.pix_begin + p) + 1);
-                r.ox = a.x;
-                r.oy = a.y;
-                r.oz = a.z;
-                r.tmin = a.w;
-                r.dx = b.x;
-                r.dy = b.y;
-                r.dz = b.z;
-                r.tmax = b.w;
-            }
+            // CHAIN: passes 1..K, the camera reading this pixel's own previous value
+            float4 out = FUSED && v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
             uint32_t code;
             int32_t prim;
-            float4 out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc, n_shadow, code,
-                                            prim, s_order, hint);
-            ++n_primary;
-            if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
-            v.out[p] = out;
-            if (v.hint) v.hint[p] = hint;
-            if (v.prim) v.prim[p] = prim;
-            if (v.rgb) {
-                v.rgb[3 * p] = out.x;
-                v.rgb[3 * p + 1] = out.y;
-                v.rgb[3 * p + 2] = out.z;
+            for (int n = 0; n < (CHAIN ? K : 1); ++n) {
+                prefetch_record(S, hint.x);  // its lines arrive while the camera ray is made
+                RayF r;
+                if (FUSED) {
+                    r = camera_ray(v, (float)x + 0.5f, (float)y + 0.5f, out, S.tmin);
+                } else {
+                    const float4 a = __ldg(rays + 2 * (v.pix_begin + p));
+                    const float4 b = __ldg(rays + 2 * (v.pix_begin + p) + 1);
+                    r.ox = a.x;
+                    r.oy = a.y;
+                    r.oz = a.z;
+                    r.tmin = a.w;
+                    r.dx = b.x;
+                    r.dy = b.y;
+                    r.dz = b.z;
+                    r.tmax = b.w;
+                }
+                out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc, n_shadow, code, prim,
+                                         s_order, hint);
+                ++n_primary;
+                if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
+            }
+            const ViewDev& vo = CHAIN ? views[(size_t)(K - 1) * n_views + vi] : v;  // the last pass's outputs
+            vo.out[p] = out;
+            if (vo.hint) vo.hint[p] = hint;
+            if (vo.prim) vo.prim[p] = prim;
+            if (vo.rgb) {
+                vo.rgb[3 * p] = out.x;
+                vo.rgb[3 * p + 1] = out.y;
+                vo.rgb[3 * p + 2] = out.z;
             }
             if (overflow) {  // this view's image is incomplete
                 atomicExch(v.status, 1);
@@ -344,11 +359,11 @@ int sm_count() {
     return sms;
 }
 
-template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI>
+template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI, bool CHAIN>
 rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                           int64_t total_chunks, const float4* rays, unsigned* d_work, unsigned long long* d_rays,
-                          unsigned long long* d_counters, cudaStream_t st) {
-    auto kern = k_trace<BLOCK, FUSED, COUNT, MS, MULTI>;
+                          unsigned long long* d_counters, int K, cudaStream_t st) {
+    auto kern = k_trace<BLOCK, FUSED, COUNT, MS, MULTI, CHAIN>;
     const size_t smem = sizeof(uint2) * (size_t)cfg.stack * BLOCK;
     if (smem > 48 * 1024) RCP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = cfg.blocks_per_sm;
@@ -365,25 +380,25 @@ rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
         return RCP_ERR_STATE;
     }
     kern<<<(int)grid, BLOCK, smem, st>>>(S, d_views, n_views, total_chunks, cfg.chunk / 32, rays, d_work, stk, d_rays,
-                                         d_counters);
+                                         d_counters, K);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }
 
-template <bool FUSED, bool COUNT, bool MS, bool MULTI>
+template <bool FUSED, bool COUNT, bool MS, bool MULTI, bool CHAIN = false>
 rcp_status launch_trace_b(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                           int64_t total_chunks, const float4* rays, unsigned* d_work, unsigned long long* d_rays,
-                          unsigned long long* d_counters, cudaStream_t st) {
+                          unsigned long long* d_counters, cudaStream_t st, int K = 1) {
     switch (cfg.block) {
         case 64:
-            return launch_trace_t<64, FUSED, COUNT, MS, MULTI>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                               d_rays, d_counters, st);
+            return launch_trace_t<64, FUSED, COUNT, MS, MULTI, CHAIN>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                      d_work, d_rays, d_counters, K, st);
         case 256:
-            return launch_trace_t<256, FUSED, COUNT, MS, MULTI>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                                d_rays, d_counters, st);
+            return launch_trace_t<256, FUSED, COUNT, MS, MULTI, CHAIN>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                       d_work, d_rays, d_counters, K, st);
         default:
-            return launch_trace_t<128, FUSED, COUNT, MS, MULTI>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
-                                                                d_rays, d_counters, st);
+            return launch_trace_t<128, FUSED, COUNT, MS, MULTI, CHAIN>(S, cfg, d_views, n_views, total_chunks, rays,
+                                                                       d_work, d_rays, d_counters, K, st);
     }
 }
 
@@ -420,6 +435,19 @@ rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d
                                                                  d_rays, d_counters, st)
                      : launch_trace_b<false, false, false, false>(S, cfg, d_views, n_views, total_chunks, rays, d_work,
                                                                   d_rays, d_counters, st);
+}
+
+rcp_status launch_chain(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views, int K,
+                        int64_t total_chunks, unsigned* d_work, unsigned long long* d_rays,
+                        unsigned long long* d_counters, cudaStream_t st) {
+    if (!cfg.fused || cfg.ms || cfg.multi || K < 1) {
+        set_error("launch_chain: a chained launch is single-sample, one scene, fused camera");
+        return RCP_ERR_STATE;
+    }
+    return cfg.count ? launch_trace_b<true, true, false, false, true>(S, cfg, d_views, n_views, total_chunks,
+                                                                      nullptr, d_work, d_rays, d_counters, st, K)
+                     : launch_trace_b<true, false, false, false, true>(S, cfg, d_views, n_views, total_chunks,
+                                                                       nullptr, d_work, d_rays, d_counters, st, K);
 }
 
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,

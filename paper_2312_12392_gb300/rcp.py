@@ -62,7 +62,8 @@ class rcp_build_options(C.Structure):
 
 class rcp_tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
-                ("fused_camera", C.c_int32), ("stack_entries", C.c_int32), ("hints", C.c_int32)]
+                ("fused_camera", C.c_int32), ("stack_entries", C.c_int32), ("hints", C.c_int32),
+                ("chain_passes", C.c_int32)]
 
 
 class rcp_counters(C.Structure):

@@ -90,6 +90,68 @@ def test_short_stack_spills_identical():
         rcp.rcp_scene_destroy(g)
 
 
+def _full(g, cam, W, H, K, p, d_in=None, d_out=None):
+    """The device path's whole output: rgb + z-depth (or normal code) bits and hit ids."""
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda") if d_out is None else d_out
+    prim = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    rcp.rcp_render_device(g, cam, W, H, K, p, d_in, out, prim, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32).copy(), prim.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["mid", "forest"])
+def test_chained_passes_identical(name):
+    """All K passes in one launch (each warp carrying its tile's pixels from
+    pass to pass in registers) give the per-pass launches' output bit for bit:
+    colours, z-depths, normal codes and hit ids, for every mapping that reads
+    only the pixel's own previous value, every block size, a short stack that
+    spills, hints off, a ragged image, a given first image rendered in place,
+    and a batch of views; a chained render reports one launch."""
+    sc = scenes.mid_scene() if name == "mid" else scenes.forest_scene()
+    g = U.gpu_scene(sc) if name == "mid" else U.gpu_scene(sc, rcp.RCP_COLLAPSE_SAH, 8)
+    try:
+        cam = rcp.camera_from(sc.poses[5])
+        d = sc.diameter()
+        W, H, K = 643, 361, 5  # ragged in both directions
+        for mapping in (rcp.RCP_MAP_EYE, rcp.RCP_MAP_TARGET, rcp.RCP_MAP_DEPTH, rcp.RCP_MAP_NORMAL):
+            p = rcp.make_params(mapping, 0.02 * d, 0.1 * d, z0=0.1 * d if mapping == rcp.RCP_MAP_DEPTH else 0.0)
+            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, 0, 3, 0))
+            ref = _full(g, cam, W, H, K, p)
+            assert len(rcp.rcp_last_pass_times(g)) == K
+            for t in (rcp.rcp_tuning(128, 0, 32, 1, 0, 3, 1), rcp.rcp_tuning(64, 0, 32, 1, 0, 3, 1),
+                      rcp.rcp_tuning(256, 0, 64, 1, 0, 3, 1), rcp.rcp_tuning(128, 0, 32, 1, 2, 3, 1),
+                      rcp.rcp_tuning(64, 0, 64, 1, 1, 0, 1)):
+                rcp.rcp_set_tuning(g, t)
+                got = _full(g, cam, W, H, K, p)
+                key = (mapping, t.block, t.chunk, t.stack_entries, t.hints)
+                assert len(rcp.rcp_last_pass_times(g)) == 1, key
+                assert np.array_equal(got[0], ref[0]), key
+                assert np.array_equal(got[1], ref[1]), key
+        # a given first image, rendered in place (d_in == d_out)
+        p = rcp.make_params(rcp.RCP_MAP_EYE, 0.02 * d, 0.1 * d)
+        first = torch.from_numpy(np.random.default_rng(4).random((H, W, 4), dtype=np.float32)).cuda()
+        res = []
+        for chain in (0, 1):
+            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, 0, 3, chain))
+            buf = first.clone()
+            res.append(_full(g, cam, W, H, 3, p, d_in=buf, d_out=buf))
+        assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+        # a batch of views of several sizes, all passes in one launch
+        sizes = [(97, 33), (256, 144), (31, 7), (400, 300)]
+        cams = [rcp.camera_from(sc.poses[i * 9 + 1]) for i in range(len(sizes))]
+        res = {}
+        for chain in (0, 1):
+            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, 0, 3, chain))
+            outs = [torch.empty((h, w, 4), dtype=torch.float32, device="cuda") for w, h in sizes]
+            rcp.rcp_render_batch_device(g, cams, [w for w, _ in sizes], [h for _, h in sizes], 6, p, outs)
+            torch.cuda.synchronize()
+            res[chain] = [o.cpu().numpy().view(np.uint32) for o in outs]
+        for a, b in zip(res[0], res[1]):
+            assert np.array_equal(a, b)
+    finally:
+        rcp.rcp_scene_destroy(g)
+
+
 def test_device_path_and_graph_replay(tiny_g):
     sc, g = tiny_g
     d = sc.diameter()
