@@ -394,9 +394,10 @@ def e2e_host(g, cams, W, H, K, params, flush, n):
     return n / t, t
 
 
-def e2e_record(value, t_unit, W, H, K):
+def e2e_record(value, t_unit, W, H, K, chained):
+    """chained: the passes ran in one launch (one view descriptor uploaded, not K)."""
     from paper_2312_12392_gb300 import rcp
-    return {"value": value, "unit": t_unit, "h2d_bytes_per_step": rcp.rcp_render_h2d_bytes(1, K),
+    return {"value": value, "unit": t_unit, "h2d_bytes_per_step": rcp.rcp_render_h2d_bytes(1, 1 if chained else K),
             "d2h_bytes_per_step": W * H * 3 * 4 + 4,  # the RGB image and the status word
             "api": "rcp_render (host RGB output; view descriptors H2D, RGB device-to-host inside the timed call: "
                    "written into host memory by the last pass where the device reads pageable memory "
@@ -489,7 +490,8 @@ def run_ours(args):
         "mrays_per_s": rays / (tmax / 1000.0) / 1e6,
         "rays_per_frame": rays / frames,
         "roofline": roof,
-        "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES),
+        "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES,
+                          roof["launches_per_frame"] == 1),
         "gpu_launches": len(pass_ms) * (1 if t.fused_camera else 2),  # trace launches (+ camera kernels)
         "clocks": clk,
         "wall_s": wall,
@@ -552,7 +554,8 @@ def forest_summary(args):
         info = rcp.rcp_scene_get_info(g)
         return {"workload": desc, "frames_per_s": len(cams) / tot, "mrays_per_s": rays / tot / 1e6,
                 "ms_per_frame": 1000 * tot / len(cams), "frames": len(cams), "roofline": roof,
-                "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES), "clocks": clk,
+                "e2e": e2e_record(e2e_fps, "frames/s", W_IMG, H_IMG, K_PASSES,
+                          roof["launches_per_frame"] == 1), "clocks": clk,
                 "tuning": tuning_dict(t), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
                 "depth": info.depth, "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
                 "records": info.n_records, "gpu_launches": len(pass_ms)}
@@ -737,8 +740,9 @@ def served_summary(args):
     """Poisson arrivals over 4 resident terrain scenes (0.1M, 1M, 3M, 5M tris);
     each request: a walk-through pose, 720p/1080p/1440p/2160p, K in 1..8,
     k in [0, 0.05] * diameter. The continuous-batching server against the plain
-    path (one request at a time, FIFO, each its own K-pass launch sequence),
-    same arrivals, at each rate."""
+    path (one request at a time, FIFO, each its own render: all K passes
+    chained in one launch, the scenes' default tuning), same arrivals, at each
+    rate."""
     import threading
 
     from paper_2312_12392_gb300 import rcp, scenes
@@ -806,6 +810,9 @@ def served_summary(args):
             # -- server: submit at the arrival times (latency from submit to the
             #    image in the caller's buffer; late submits are reported)
             srv = rcp.rcp_server_create(int(args.serve_budget_gb * (1 << 30)), args.serve_slots)
+            rcp.rcp_server_set_max_chain(srv, args.serve_max_chain)
+            if args.serve_step_pixels is not None:
+                rcp.rcp_server_set_step_pixels(srv, args.serve_step_pixels)
             pool.release_all()
             pool.waits = 0
             tickets, late, t_sub = [], 0.0, []
@@ -845,11 +852,13 @@ def served_summary(args):
             table.append({"rate_req_s": lam, "served": served, "plain": plain})
             log(f"lambda={lam}: served {served} | plain {plain}")
         return {"requests_per_rate": n_req, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+                "max_chain": args.serve_max_chain, "step_pixel_passes": args.serve_step_pixels,
                 "bvh_collapse": collapse_name,
                 "workload": "4 resident terrain scenes (100,082 / 999,272 / 2,998,752 / 4,995,200 tris); "
                             "720p-2160p, K in 1..8, k in [0, 0.05]*diam, Poisson arrivals; latency from arrival "
                             "to the image in the caller's host buffer",
-                "plain_path": "one rcp_render per request (host output), FIFO, one worker thread",
+                "plain_path": "one rcp_render per request (host output, the K passes chained in one launch), "
+                              "FIFO, one worker thread",
                 "sweep": table}
     finally:
         for g in gs:
@@ -986,8 +995,8 @@ def run_workload_line(args, name):
         out.update(ms_per_step=r["ms_per_frame"], e2e=r["e2e"], roofline=r["roofline"], clocks=r["clocks"])
     elif name == "batched":
         r = batched_summary(args)
-        out = one_line("views_per_s (64 uneven views, K=6 each, one launch per pass)", r["views_per_s"], "views/s",
-                       args, r["steps"], r)
+        out = one_line("views_per_s (64 uneven views, K=6 each, one persistent launch over all views)",
+                       r["views_per_s"], "views/s", args, r["steps"], r)
         out["ms_per_step"] = r["ms_per_batch"]
     elif name == "served":
         r = served_summary(args)
@@ -1088,7 +1097,11 @@ def main(argv=None):
     ap.add_argument("--stress-steps", type=int, default=20, help="stress: timed frames")
     ap.add_argument("--forest-poses", type=int, default=64, help="forest: walk-through poses timed (all 64)")
     ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-max-chain", type=int, default=16,
+                    help="served: passes a request may advance by in one server step (1 = one pass per step)")
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
+    ap.add_argument("--serve-step-pixels", type=int, default=None,
+                    help="served: pixel-passes per server step (default: the library's; 0 = unbounded)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         log("warmup raised to 3 (timing rule)")

@@ -262,8 +262,8 @@ rcp_status rcp_render_batch_device(const rcp_scene* scene, int n_views, const rc
  * first tests its previous occluder; chain_passes: 1 = one launch runs all K
  * passes, each warp carrying the pixels of its tile from pass to pass in
  * registers (renders of K >= 2 at one sample per pixel with the fused camera
- * and any mapping but RCP_MAP_IMAGE; others run one launch per pass). No
- * choice changes any result. */
+ * and any mapping but RCP_MAP_IMAGE; others run one launch per pass). A new
+ * scene starts at {128, 0, 32, 1, 0, 3, 1}. No choice changes any result. */
 typedef struct {
     int32_t block;
     int32_t blocks_per_sm;
@@ -314,7 +314,9 @@ rcp_status rcp_last_pass_times(const rcp_scene* scene, float* ms, int max_passes
 /* Bytes that one rcp_render call of K passes over n_views views copies from
  * host to device: the views' per-pass descriptors (camera terms, image
  * pointers), uploaded once per call. The library's own bookkeeping, not part of
- * the method. Returns -1 when K or n_views is out of range. */
+ * the method. A render whose passes run chained uploads one descriptor per
+ * view: rcp_render_h2d_bytes(n_views, 1). Returns -1 when K or n_views is out
+ * of range. */
 int64_t rcp_render_h2d_bytes(int n_views, int K);
 
 /* Diagnostics used by the tests (all device pointers, enqueued on `stream`):
@@ -374,10 +376,13 @@ int64_t rcp_sort_static_capacity(void);
  * A request = one K-pass render of a resident scene. Requests are admitted
  * (first come first served) while a slot is free and their device memory (two
  * rgbz images, per-pixel hit hints and a status word) fits the budget. Each
- * scheduler step advances admitted requests by one pass in ONE launch over
- * all of their views, whatever their scene, size or K (continuous batching): in
- * admission order, the oldest always and the others while the step's pixels
- * stay within the step budget (rcp_server_set_step_pixels). A finished
+ * scheduler step advances admitted requests in ONE launch over all of their
+ * views, whatever their scene, size or K (continuous batching): in admission
+ * order, the oldest always (by one pass at least), each request by as many of
+ * its remaining passes as the step's pixel-pass budget still holds
+ * (rcp_server_set_step_pixels, at most rcp_server_set_max_chain), which run
+ * chained (each pixel carried from pass to pass in registers); a step that
+ * holds a multi-sample request advances every request by one pass. A finished
  * request's image is delivered to the caller's host buffer; a request whose
  * traversal stack overflowed fails with RCP_ERR_STACK. */
 typedef struct rcp_server rcp_server;
@@ -400,10 +405,14 @@ rcp_status rcp_server_create(int64_t mem_budget_bytes, int max_slots, rcp_server
 rcp_status rcp_server_submit(rcp_server* srv, const rcp_scene* scene, const rcp_camera* cam,
                              int width, int height, int K, const rcp_params* params, float* out_rgb,
                              int64_t* ticket);
-/* Pixels one scheduler step may hold (default 8,500,000, so that a 3840x2160
- * pass runs alone; 0 = every admitted request in every step). The oldest
- * admitted request always advances, whatever its size. */
+/* Pixel-passes one scheduler step may hold (default 67,000,000, so that a
+ * 3840x2160 K=8 request runs to its end in one step; 0 = every admitted
+ * request to its end in every step). The oldest admitted request always
+ * advances, whatever its size. */
 rcp_status rcp_server_set_step_pixels(rcp_server* srv, int64_t pixels);
+/* Passes a request may advance by in one step (1..16, default 16; 1 = one
+ * pass per request per step). */
+rcp_status rcp_server_set_max_chain(rcp_server* srv, int passes);
 /* done = 1 finished, 0 pending; the request's own status is returned. */
 rcp_status rcp_server_poll(rcp_server* srv, int64_t ticket, int* done);
 rcp_status rcp_server_wait(rcp_server* srv, int64_t ticket, double timeout_s);

@@ -193,7 +193,7 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.mapping = p.mapping;
     v.z0 = p.z0;
     v.kpx = (p.mapping == RCP_MAP_IMAGE || p.mapping == RCP_MAP_NORMAL) ? p.k : 0.f;
-    v.pad0_ = 0;
+    v.passes = 1;
     v.base = nullptr;
     v.in = nullptr;
     v.out = nullptr;
@@ -428,8 +428,8 @@ rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg,
     RCP_CUDA(cudaMemsetAsync(ctx.d_rays, 0, sizeof(unsigned long long) * 2, st));
     const SceneDev S = sc.dev();
     RCP_CUDA(record(ctx.pass_ev[0]));
-    if (cfg.chain && ctx.K > 1 && !ctx.image_mode && cfg.fused && !cfg.ms && !cfg.multi) {
-        rcp_status r = launch_chain(S, cfg, ctx.d_views, ctx.n_views, ctx.K, ctx.total_chunks, ctx.d_work, ctx.d_rays,
+    if (ctx.chained) {  // one descriptor per view, all K passes
+        rcp_status r = launch_chain(S, cfg, ctx.d_views, ctx.n_views, ctx.total_chunks, ctx.d_work, ctx.d_rays,
                                     counters, st);
         if (r != RCP_OK) return r;
         RCP_CUDA(record(ctx.pass_ev[1]));
@@ -451,7 +451,7 @@ rcp_status enqueue_passes(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg,
 // Run the K passes through the context's CUDA graph (captured on first use or
 // when the launch configuration changes).
 rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cudaStream_t st) {
-    const std::string key = cfg_key(cfg) + (ctx.image_mode ? "/image" : "/trace");
+    const std::string key = cfg_key(cfg) + (ctx.image_mode ? "/image" : (ctx.chained ? "/chain" : "/trace"));
     if (!ctx.graph || ctx.graph_key != key) {
         if (ctx.graph) {
             cudaGraphExecDestroy(ctx.graph);
@@ -477,12 +477,32 @@ rcp_status run_graph(const Scene& sc, RenderCtx& ctx, const LaunchCfg& cfg, cuda
     return RCP_OK;
 }
 
-// Stage the per-pass view descriptors of one render (n_views views, K passes).
+// Stage the view descriptors of one render (n_views views, K passes): one per
+// view and pass, or, when the passes run chained (chain: the tuning asks for
+// it and the render allows it), one per view that runs all K passes.
 rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const float4* const* ins,
-                       float4* const* outs, int32_t* const* prims, float* const* rgbs, cudaStream_t st) {
+                       float4* const* outs, int32_t* const* prims, float* const* rgbs, cudaStream_t st,
+                       bool chain = false) {
     RCP_CUDA(cudaEventSynchronize(ctx.staged));  // previous copy out of the staging buffer is done
     const int K = ctx.K, nv = ctx.n_views;
     ctx.image_mode = base[0].mapping == RCP_MAP_IMAGE && K > 1;
+    ctx.chained = chain && K > 1 && !ctx.image_mode && base[0].spp == 0;
+    if (ctx.chained) {
+        for (int i = 0; i < nv; ++i) {
+            ViewDev v = base[i];
+            v.in = ins ? ins[i] : nullptr;
+            v.out = outs[i];
+            v.hint = ctx.hints + base[i].pix_begin;
+            v.status = ctx.d_status;
+            v.prim = prims ? prims[i] : nullptr;
+            v.rgb = rgbs ? rgbs[i] : nullptr;
+            v.passes = K;
+            ctx.h_views[i] = v;
+        }
+        RCP_CUDA(cudaMemcpyAsync(ctx.d_views, ctx.h_views, sizeof(ViewDev) * (size_t)nv, cudaMemcpyHostToDevice, st));
+        RCP_CUDA(cudaEventRecord(ctx.staged, st));
+        return RCP_OK;
+    }
     if (ctx.image_mode && !ctx.base_img) RCP_CUDA(cudaMalloc((void**)&ctx.base_img, sizeof(float4) * ctx.total_pix));
     for (int n = 0; n < K; ++n) {
         for (int i = 0; i < nv; ++i) {
@@ -549,10 +569,11 @@ rcp_status render_views(Scene& sc, int n_views, const rcp_camera* cams, const in
     RenderCtx* ctx = nullptr;
     rcp_status r = get_ctx(sc, n_views, K, total_pix, total_chunks, &ctx);
     if (r != RCP_OK) return r;
-    r = stage_views(*ctx, base, ins, outs, prims, rgbs, st);
-    if (r != RCP_OK) return r;
     LaunchCfg cfg = cfg_override ? *cfg_override : cfg_of(sc);
     cfg.ms = p->spp > 0;
+    r = stage_views(*ctx, base, ins, outs, prims, rgbs, st, cfg.chain);
+    if (r != RCP_OK) return r;
+    if (ctx->chained) cfg.fused = true;  // a chained launch makes its rays itself
     r = ensure_spill(sc, cfg);
     if (r != RCP_OK) return r;
     r = ensure_rays(*ctx, cfg);

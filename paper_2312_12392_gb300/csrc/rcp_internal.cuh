@@ -80,7 +80,7 @@ struct ViewDev {
     int mapping;
     float z0;
     float kpx;  // IMAGE: displacement in pixels; NORMAL: k in world units
-    int pad0_;
+    int passes;  // passes a chained launch runs for this view (in: its first input, out: its last output)
     const float4* in;    // previous image, nullptr = I_0
     const float4* base;  // image-space passes: the frame's traced image
     float4* out;         // this pass's image

@@ -33,6 +33,7 @@ struct RenderCtx {
     float4* io = nullptr;        // host-API input / final image
     float4* base_img = nullptr;  // image-space mapping: the traced pass-1 image
     bool image_mode = false;     // passes 2..K are image-space gathers
+    bool chained = false;        // one launch runs all K passes (one descriptor per view)
     int32_t* io_prim = nullptr;  // host-API hit ids
     int2* hints = nullptr;       // per pixel: latest primary-hit and shadow-occluder records (-1 none)
     cudaEvent_t staged = nullptr;
@@ -68,7 +69,7 @@ struct Scene {
     float diam = 0.f;
     float build_ms = 0.f;
     LightDev light{};
-    rcp_tuning tuning{128, 0, 32, 1, 0, 3, 0};
+    rcp_tuning tuning{128, 0, 32, 1, 0, 3, 1};
     std::mutex mu;
     std::map<std::string, std::unique_ptr<RenderCtx>> ctx;
     RenderCtx* last = nullptr;  // context of the most recent render
@@ -112,12 +113,12 @@ struct LaunchCfg {
 rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                        int64_t total_pix, int64_t total_chunks, float4* rays, unsigned* d_work,
                        unsigned long long* d_rays, unsigned long long* d_counters, cudaStream_t st);
-// All K passes over n_views views in one launch: d_views holds K descriptors
-// per view, pass-major; each pixel's colour and hints stay in registers from
-// pass to pass and only the last pass's outputs are written. Single-sample,
-// one scene, fused camera, and a mapping that reads only the pixel's own
-// previous value.
-rcp_status launch_chain(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views, int K,
+// Several passes of n_views views in one launch: view v runs v.passes passes
+// from v.in to v.out, each pixel's colour and hints kept in registers from
+// pass to pass, only the last pass's outputs written. Single-sample, fused
+// camera (cfg.fused is not read), and a mapping that reads only the pixel's
+// own previous value; cfg.multi: the views name their scenes.
+rcp_status launch_chain(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                         int64_t total_chunks, unsigned* d_work, unsigned long long* d_rays,
                         unsigned long long* d_counters, cudaStream_t st);
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,

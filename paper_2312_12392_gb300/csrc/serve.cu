@@ -5,19 +5,22 @@
 //    request's device memory -- two rgbz images, per-pixel hit hints and a
 //    status word (plus an RGB staging buffer where the device cannot write
 //    host memory), allocated stream-ordered from the device's memory pool --
-//    fits the budget. Each step then advances admitted requests by ONE pass in
-//    ONE persistent launch: a single tile queue over the step's views,
-//    whatever their scene, size or K (each view names its scene; views are
-//    grouped by scene for cache locality). A step takes requests in admission
-//    order: the oldest always, the others while the step's pixels stay within
-//    the step budget (others wait, with their images resident, for a later
-//    step). Old requests thus run as soon as they would on their own and new
-//    small ones fill the rest of a step: first come first served with
-//    backfill, like a token budget in LLM continuous batching, rather than
-//    every request sharing every step, which stretches the largest requests.
-//    Which requests finish at a step is known when it is enqueued (pass count
-//    = K), so the scheduler never waits for the device except to bound how
-//    far it runs ahead (STEPS_AHEAD steps);
+//    fits the budget. Each step then advances admitted requests by one or
+//    more passes in ONE persistent launch: a single tile queue over the
+//    step's views, whatever their scene, size or K (each view names its scene;
+//    views are grouped by scene for cache locality). A request that advances
+//    by several passes in a step runs them chained: each warp carries its
+//    tile's pixels from pass to pass in registers. A step takes requests in
+//    admission order: the oldest always (one pass at least), each as many of
+//    its remaining passes as the step's pixel-pass budget still holds (at
+//    most max_chain), the others while one pass of theirs fits; the rest wait,
+//    with their images resident, for a later step. Old requests thus run as
+//    soon as they would on their own and new small ones fill the rest of a
+//    step: first come first served with backfill, like a token budget in LLM
+//    continuous batching, rather than every request sharing every step, which
+//    stretches the largest requests. Which requests finish at a step is known
+//    when it is enqueued, so the scheduler never waits for the device except
+//    to bound how far it runs ahead (STEPS_AHEAD steps);
 //  * the copy-out thread waits for each finished request's last pass, reads
 //    its status word (a walk that overflowed its stack fails the request),
 //    copies its RGB image to the caller's buffer where needed, releases its
@@ -47,7 +50,8 @@ namespace rcp {
 namespace {
 
 constexpr int STEPS_AHEAD = 3;  // steps enqueued before the oldest must finish
-constexpr int64_t DEFAULT_STEP_PIXELS = 8500000;  // a 3840x2160 pass (8.29M) runs without backfill
+// pixel-passes per step: a 3840x2160 K=8 request (66.4M) runs to its end in one step
+constexpr int64_t DEFAULT_STEP_PIXELS = 67000000;
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -63,7 +67,7 @@ struct Request {
     rcp_params p{};
     float* out_rgb = nullptr;
     int passes_done = 0;  // passes enqueued so far
-    bool in_step = false;  // advanced by the step being enqueued
+    int step_passes = 0;  // passes of the step being enqueued (0: not in it)
     float4* img[2] = {nullptr, nullptr};
     float* rgb = nullptr;
     bool direct = false;     // the last pass writes out_rgb itself (else pack and copy)
@@ -114,7 +118,8 @@ struct rcp_server {
     int device = 0;
     int* h_status = nullptr;  // pinned: one status word per admitted, unfinished request
     std::vector<int> free_status;
-    int64_t step_pixels = DEFAULT_STEP_PIXELS;  // pixels per step (0: every admitted request every step)
+    int64_t step_pixels = DEFAULT_STEP_PIXELS;  // pixel-passes per step (0: every admitted request every step)
+    int max_chain = 16;  // passes one request may advance by in one step
     double busy_ms = 0;  // device time of completed steps
 
     void run();
@@ -194,8 +199,11 @@ double percentile(std::vector<double> v, double q) {
 
 }  // namespace
 
-// Enqueue one pass of every request in the batch as one launch (the slot's
-// resources are free: its previous step has completed).
+// Enqueue the step's passes of every request in the batch (q->step_passes
+// each) as one launch (the slot's resources are free: its previous step has
+// completed). Several passes of a request run chained; a step with a
+// multi-sample request runs one pass of each (its jittered samples read
+// neighbouring pixels of the previous image).
 rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot) {
     rcp_status r = ensure_slot(slot, (int)batch.size());
     if (r != RCP_OK) return r;
@@ -225,10 +233,12 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
         make_view(v, q->cam, q->W, q->H, q->p);
         v.scene = q->scene->d_dev;
         v.status = q->d_status;
+        const int last = q->passes_done + q->step_passes;  // passes done after this step
         v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
-        v.out = q->img[q->passes_done & 1];
+        v.out = q->img[(last - 1) & 1];
+        v.passes = q->step_passes;
         v.hint = q->hint;
-        if (q->direct && q->passes_done + 1 == q->K) v.rgb = q->out_rgb;
+        if (q->direct && last == q->K) v.rgb = q->out_rgb;
         v.pix_begin = total_pix;
         v.chunk_begin = total_chunks;
         total_pix += (int64_t)q->W * q->H;
@@ -239,13 +249,16 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
     RCP_CUDA(cudaMemcpyAsync(slot.d_views, slot.h_views, sizeof(ViewDev) * batch.size(), cudaMemcpyHostToDevice,
                              st_main));
     RCP_CUDA(cudaMemsetAsync(slot.d_work, 0, sizeof(unsigned), st_main));
-    r = launch_pass((*scenes.begin())->dev(), cfg, slot.d_views, (int)batch.size(), total_pix, total_chunks, nullptr,
-                    slot.d_work, d_rays, nullptr, st_main);
+    r = ms ? launch_pass((*scenes.begin())->dev(), cfg, slot.d_views, (int)batch.size(), total_pix, total_chunks,
+                         nullptr, slot.d_work, d_rays, nullptr, st_main)
+           : launch_chain((*scenes.begin())->dev(), cfg, slot.d_views, (int)batch.size(), total_chunks, slot.d_work,
+                          d_rays, nullptr, st_main);
     if (r != RCP_OK) return r;
     for (Request* q : batch) {
-        if (q->passes_done + 1 != q->K) continue;
+        const int last = q->passes_done + q->step_passes;
+        if (last != q->K) continue;
         if (!q->direct) {
-            r = launch_pack_rgb(q->img[q->passes_done & 1], q->rgb, (int64_t)q->W * q->H, st_main);
+            r = launch_pack_rgb(q->img[(last - 1) & 1], q->rgb, (int64_t)q->W * q->H, st_main);
             if (r != RCP_OK) return r;
         }
         RCP_CUDA(cudaMemcpyAsync(h_status + q->status_slot, q->d_status, sizeof(int), cudaMemcpyDeviceToHost,
@@ -376,18 +389,24 @@ void rcp_server::run() {
                 rcp_status r = alloc_request(*q, q->direct, st_main);
                 if (r != RCP_OK) q->status = r;
             }
-        // the step: admission order, the oldest always, the rest while the
-        // step's pixels fit the budget
+        // the step: admission order, the oldest always, each request as many
+        // of its remaining passes as the step's pixel-pass budget holds (one
+        // where a multi-sample request is admitted)
+        bool any_ms = false;
+        for (Request* q : batch) any_ms = any_ms || (q->status == RCP_OK && q->p.spp > 0);
         std::vector<Request*> ok;
         int64_t px = 0;
         for (Request* q : batch) {
-            q->in_step = false;
+            q->step_passes = 0;
             if (q->status != RCP_OK) continue;
             const int64_t qp = (int64_t)q->W * q->H;
-            if (!ok.empty() && step_pixels > 0 && px + qp > step_pixels) continue;
+            int m = std::min(q->K - q->passes_done, any_ms ? 1 : max_chain);
+            if (step_pixels > 0) m = (int)std::min<int64_t>(m, (step_pixels - px) / qp);
+            if (ok.empty()) m = std::max(m, 1);
+            if (m <= 0) continue;
             ok.push_back(q);
-            q->in_step = true;
-            px += qp;
+            q->step_passes = m;
+            px += m * qp;
         }
         StepSlot& slot = slots[step_no % STEPS_AHEAD];
         if (slot.used) {  // bound the run-ahead; frees the slot's staging
@@ -406,7 +425,7 @@ void rcp_server::run() {
         std::vector<Request*> still;
         for (Request* q : inflight) {
             if (r != RCP_OK && q->status == RCP_OK) q->status = r;
-            if (q->status == RCP_OK && q->in_step) q->passes_done++;
+            if (q->status == RCP_OK) q->passes_done += q->step_passes;
             if (q->status != RCP_OK || q->passes_done >= q->K) {
                 copyq.push_back(q);  // the copy-out thread waits for its image
                 cv_copy.notify_one();
@@ -496,6 +515,16 @@ rcp_status rcp_server_set_step_pixels(rcp_server* srv, int64_t pixels) {
     }
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->step_pixels = pixels;
+    return RCP_OK;
+}
+
+rcp_status rcp_server_set_max_chain(rcp_server* srv, int passes) {
+    if (!srv || passes < 1 || passes > 16) {
+        set_error("rcp_server_set_max_chain: NULL server or passes outside [1, 16]");
+        return RCP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->max_chain = passes;
     return RCP_OK;
 }
 

@@ -79,20 +79,19 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
 
 // MULTI: every view names its own scene (views of several scenes in one
 // launch); otherwise all views render the launch's scene S0.
-// CHAIN: one launch runs all K passes. views holds K descriptors per view
-// (pass-major); a warp carries each pixel of its tile through the K passes,
-// its colour and hints in registers, and writes only the last pass's
-// outputs. At one sample per pixel with a camera that reads only the pixel's
-// own previous value (every mapping but the image-space one), this computes
-// exactly what K launches compute.
+// CHAIN: one launch runs v.passes passes of each view v (v.in its first
+// input, v.out its last output); a warp carries each pixel of its tile from
+// pass to pass, its colour and hints in registers, and writes only the last
+// pass's outputs. At one sample per pixel with a camera that reads only the
+// pixel's own previous value (every mapping but the image-space one), this
+// computes exactly what one launch per pass computes.
 template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI, bool CHAIN>
 __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 warps per SM, as the one-pass kernel
     k_trace(SceneDev S0, const ViewDev* __restrict__ views, int n_views,
                                                  int64_t total_chunks, int chunk_tiles,
                                                  const float4* __restrict__ rays, unsigned* work, StackCfg stk,
-                                                 unsigned long long* ray_counts, unsigned long long* counters,
-                                                 int K) {
-    static_assert(!CHAIN || (FUSED && !MS && !MULTI), "a chained launch makes its rays itself, one per pixel");
+                                                 unsigned long long* ray_counts, unsigned long long* counters) {
+    static_assert(!CHAIN || (FUSED && !MS), "a chained launch makes its rays itself, one per pixel");
     extern __shared__ uint2 s_stack[];
     __shared__ uint8_t s_order[ORDER_LUT_BYTES];
     __shared__ SceneDev s_scene[MULTI ? BLOCK / 32 : 1];  // MULTI: the scene of each warp's current tile
@@ -112,8 +111,7 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
         for (int sub = 0; sub < chunk_tiles; ++sub) {
             const int64_t chunk = (int64_t)c0 + sub;
             if (chunk >= total_chunks) break;
-            const int vi = find_view_by_chunk(views, n_views, chunk);
-            const ViewDev& v = views[vi];
+            const ViewDev& v = views[find_view_by_chunk(views, n_views, chunk)];
             if (MULTI) {  // the warp's tile is one view: copy its scene to the warp's slot
                 __syncwarp();
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(v.scene);
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
             float4 out = FUSED && v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
             uint32_t code;
             int32_t prim;
-            for (int n = 0; n < (CHAIN ? K : 1); ++n) {
+            for (int n = 0; n < (CHAIN ? v.passes : 1); ++n) {
                 prefetch_record(S, hint.x);  // its lines arrive while the camera ray is made
                 RayF r;
                 if (FUSED) {
@@ -204,14 +202,13 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
                 ++n_primary;
                 if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
             }
-            const ViewDev& vo = CHAIN ? views[(size_t)(K - 1) * n_views + vi] : v;  // the last pass's outputs
-            vo.out[p] = out;
-            if (vo.hint) vo.hint[p] = hint;
-            if (vo.prim) vo.prim[p] = prim;
-            if (vo.rgb) {
-                vo.rgb[3 * p] = out.x;
-                vo.rgb[3 * p + 1] = out.y;
-                vo.rgb[3 * p + 2] = out.z;
+            v.out[p] = out;
+            if (v.hint) v.hint[p] = hint;
+            if (v.prim) v.prim[p] = prim;
+            if (v.rgb) {
+                v.rgb[3 * p] = out.x;
+                v.rgb[3 * p + 1] = out.y;
+                v.rgb[3 * p + 2] = out.z;
             }
             if (overflow) {  // this view's image is incomplete
                 atomicExch(v.status, 1);
@@ -362,7 +359,7 @@ int sm_count() {
 template <int BLOCK, bool FUSED, bool COUNT, bool MS, bool MULTI, bool CHAIN>
 rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                           int64_t total_chunks, const float4* rays, unsigned* d_work, unsigned long long* d_rays,
-                          unsigned long long* d_counters, int K, cudaStream_t st) {
+                          unsigned long long* d_counters, cudaStream_t st) {
     auto kern = k_trace<BLOCK, FUSED, COUNT, MS, MULTI, CHAIN>;
     const size_t smem = sizeof(uint2) * (size_t)cfg.stack * BLOCK;
     if (smem > 48 * 1024) RCP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -380,7 +377,7 @@ rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
         return RCP_ERR_STATE;
     }
     kern<<<(int)grid, BLOCK, smem, st>>>(S, d_views, n_views, total_chunks, cfg.chunk / 32, rays, d_work, stk, d_rays,
-                                         d_counters, K);
+                                         d_counters);
     RCP_CUDA(cudaGetLastError());
     return RCP_OK;
 }
@@ -388,17 +385,17 @@ rcp_status launch_trace_t(const SceneDev& S, const LaunchCfg& cfg, const ViewDev
 template <bool FUSED, bool COUNT, bool MS, bool MULTI, bool CHAIN = false>
 rcp_status launch_trace_b(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                           int64_t total_chunks, const float4* rays, unsigned* d_work, unsigned long long* d_rays,
-                          unsigned long long* d_counters, cudaStream_t st, int K = 1) {
+                          unsigned long long* d_counters, cudaStream_t st) {
     switch (cfg.block) {
         case 64:
             return launch_trace_t<64, FUSED, COUNT, MS, MULTI, CHAIN>(S, cfg, d_views, n_views, total_chunks, rays,
-                                                                      d_work, d_rays, d_counters, K, st);
+                                                                      d_work, d_rays, d_counters, st);
         case 256:
             return launch_trace_t<256, FUSED, COUNT, MS, MULTI, CHAIN>(S, cfg, d_views, n_views, total_chunks, rays,
-                                                                       d_work, d_rays, d_counters, K, st);
+                                                                       d_work, d_rays, d_counters, st);
         default:
             return launch_trace_t<128, FUSED, COUNT, MS, MULTI, CHAIN>(S, cfg, d_views, n_views, total_chunks, rays,
-                                                                       d_work, d_rays, d_counters, K, st);
+                                                                       d_work, d_rays, d_counters, st);
     }
 }
 
@@ -437,17 +434,20 @@ rcp_status launch_pass(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d
                                                                   d_rays, d_counters, st);
 }
 
-rcp_status launch_chain(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views, int K,
+rcp_status launch_chain(const SceneDev& S, const LaunchCfg& cfg, const ViewDev* d_views, int n_views,
                         int64_t total_chunks, unsigned* d_work, unsigned long long* d_rays,
                         unsigned long long* d_counters, cudaStream_t st) {
-    if (!cfg.fused || cfg.ms || cfg.multi || K < 1) {
-        set_error("launch_chain: a chained launch is single-sample, one scene, fused camera");
+    if (cfg.ms) {
+        set_error("launch_chain: a chained launch is single-sample");
         return RCP_ERR_STATE;
     }
+    if (cfg.multi)  // views of several scenes: no counters
+        return launch_trace_b<true, false, false, true, true>(S, cfg, d_views, n_views, total_chunks, nullptr, d_work,
+                                                              d_rays, nullptr, st);
     return cfg.count ? launch_trace_b<true, true, false, false, true>(S, cfg, d_views, n_views, total_chunks,
-                                                                      nullptr, d_work, d_rays, d_counters, st, K)
+                                                                      nullptr, d_work, d_rays, d_counters, st)
                      : launch_trace_b<true, false, false, false, true>(S, cfg, d_views, n_views, total_chunks,
-                                                                       nullptr, d_work, d_rays, d_counters, st, K);
+                                                                       nullptr, d_work, d_rays, d_counters, st);
 }
 
 rcp_status launch_debug_trace(const SceneDev& S, int64_t n, const float* orig_tmin, const float* dir_tmax, int any,

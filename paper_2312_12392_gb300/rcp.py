@@ -118,6 +118,7 @@ _SIGS = {
                           C.POINTER(C.c_int64)],
     "rcp_server_poll": [_vp, C.c_int64, C.POINTER(C.c_int)],
     "rcp_server_set_step_pixels": [_vp, C.c_int64],
+    "rcp_server_set_max_chain": [_vp, C.c_int],
     "rcp_server_wait": [_vp, C.c_int64, C.c_double],
     "rcp_server_latency": [_vp, C.c_int64, C.POINTER(C.c_double)],
     "rcp_server_stats_get": [_vp, C.POINTER(rcp_server_stats)],
@@ -405,6 +406,10 @@ def rcp_server_submit(srv, scene, cam: rcp_camera, width, height, K, params: rcp
 
 def rcp_server_set_step_pixels(srv, pixels):
     _check(lib().rcp_server_set_step_pixels(srv, int(pixels)), "rcp_server_set_step_pixels")
+
+
+def rcp_server_set_max_chain(srv, passes):
+    _check(lib().rcp_server_set_max_chain(srv, int(passes)), "rcp_server_set_max_chain")
 
 
 def rcp_server_poll(srv, ticket):

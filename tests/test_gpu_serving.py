@@ -23,7 +23,8 @@ def two_scenes():
     rcp.rcp_scene_destroy(gb)
 
 
-def _requests(two_scenes, n=24, seed=0):
+def _requests(two_scenes, n=24, seed=0, ms_every=0):
+    """ms_every > 0: every ms_every-th request takes 4 jittered samples per pixel."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -35,14 +36,19 @@ def _requests(two_scenes, n=24, seed=0):
         d = sc.diameter()
         f = U.f32(6.0 if sc.name == "tiny" else 0.1 * d)
         k = U.f32(float(rng.uniform(0, 0.05)) * d)
-        p = rcp.make_params(rcp.RCP_MAP_EYE, k, f)
+        jit = rng.random((4, 2)) if ms_every and i % ms_every == ms_every - 1 else None
+        p = rcp.make_params(rcp.RCP_MAP_EYE, k, f, jitter=jit)
         out.append(dict(sc=sc, g=g, cam=cam, W=W, H=H, K=K, k=k, f=f, p=p))
     return out
 
 
-def _serve(reqs, slots=8):
+def _serve(reqs, slots=8, max_chain=None, step_pixels=None):
     srv = rcp.rcp_server_create(4 << 30, slots)
     try:
+        if max_chain is not None:
+            rcp.rcp_server_set_max_chain(srv, max_chain)
+        if step_pixels is not None:
+            rcp.rcp_server_set_step_pixels(srv, step_pixels)
         outs, tickets = [], []
         for i, r in enumerate(reqs):
             o = np.full((r["H"], r["W"], 3), -1.0, np.float32)
@@ -79,8 +85,30 @@ def _alone_equals_in_mix(two_scenes):
         assert np.array_equal(a, o)
     assert st.completed == len(reqs) and st.rejected == 0 and st.in_flight == 0 and st.queued == 0
     assert st.p99_ms >= st.p50_ms > 0 and st.frames_per_s > 0 and st.mrays_per_s > 0
-    assert st.steps >= max(r["K"] for r in reqs)
+    assert st.steps >= 1
     assert st.device_bytes_in_use == 0 and st.device_bytes_peak > 0
+
+
+@pytest.mark.parametrize("max_chain,step_pixels,ms_every", [(1, None, 0), (3, 60_000, 0), (16, 0, 0),
+                                                            (16, None, 5)])
+def test_step_shapes_equal_alone(two_scenes, max_chain, step_pixels, ms_every):
+    """However a step is shaped -- one pass per request per step, short chains
+    under a small pixel-pass budget, every admitted request chained to the end,
+    or per-pass steps forced by multi-sample requests in the mix -- every
+    served image equals the request rendered alone, bit for bit."""
+    reqs = _requests(two_scenes, n=20, seed=7, ms_every=ms_every)
+    alone = [rcp.rcp_render(r["g"], rcp.camera_from(r["cam"]), r["W"], r["H"], r["K"], r["p"]) for r in reqs]
+    outs, st = _serve(reqs, max_chain=max_chain, step_pixels=step_pixels)
+    for i, (a, o) in enumerate(zip(alone, outs)):
+        assert np.array_equal(a, o), i
+    if max_chain == 1 and not ms_every:
+        assert st.steps >= max(r["K"] for r in reqs)
+    with pytest.raises(rcp.RcpError):
+        srv = rcp.rcp_server_create(1 << 20, 1)
+        try:
+            rcp.rcp_server_set_max_chain(srv, 0)
+        finally:
+            rcp.rcp_server_destroy(srv)
 
 
 def test_mix_against_oracle(two_scenes):
