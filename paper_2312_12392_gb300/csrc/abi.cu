@@ -202,6 +202,8 @@ void make_view(ViewDev& v, const rcp_camera& cam, int W, int H, const rcp_params
     v.hint = nullptr;
     v.scene = nullptr;
     v.status = nullptr;
+    v.done_count = nullptr;
+    v.done_flag = nullptr;
     v.tiles_x = (W + 7) / 8;
     v.pix_begin = 0;
     v.chunk_begin = 0;
@@ -486,7 +488,7 @@ rcp_status stage_views(RenderCtx& ctx, const std::vector<ViewDev>& base, const f
     RCP_CUDA(cudaEventSynchronize(ctx.staged));  // previous copy out of the staging buffer is done
     const int K = ctx.K, nv = ctx.n_views;
     ctx.image_mode = base[0].mapping == RCP_MAP_IMAGE && K > 1;
-    ctx.chained = chain && K > 1 && !ctx.image_mode && base[0].spp == 0;
+    ctx.chained = chain && base[0].mapping != RCP_MAP_IMAGE && base[0].spp == 0;
     if (ctx.chained) {
         for (int i = 0; i < nv; ++i) {
             ViewDev v = base[i];

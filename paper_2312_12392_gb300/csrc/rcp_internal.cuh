@@ -71,7 +71,7 @@ struct SceneDev {
 //   V(c)    = (2c.r - 1) kR + (2c.g - 1) kU + (2c.b - 1) kF
 struct ViewDev {
     const struct SceneDev* scene;  // the view's scene (launches over views of several scenes)
-    int* status;                   // set to 1 when a walk of this view overflowed its stack
+    int* status;                   // set to 1 when a walk of this view overflowed its stack (device or host memory)
     float E[3];
     float fF[3], fR[3], fU[3];
     float kR[3], kU[3], kF[3];
@@ -94,6 +94,8 @@ struct ViewDev {
     int tiles_x;
     int spp;              // samples per pixel, 0 = one at the centre
     float jit[2 * RCP_MAX_SPP];
+    int* done_count;  // nullable: tiles of this view still to finish in the launch (device)
+    int* done_flag;   // set to 1 (host-visible) once they have all finished
 };
 
 // Host-side owner of a built scene.

@@ -103,7 +103,7 @@ struct LaunchCfg {
     int64_t spill_cap = 0;
     bool count = false;
     bool ms = false;  // jittered multi-sample kernel
-    bool multi = false;  // views of several scenes (each view names its scene)
+    bool multi = false;  // each view names its scene (views of several scenes; the server's launches)
     int hints = 3;    // previous-hit hints: bit 0 primary, bit 1 shadow
     bool chain = false;  // all K passes in one launch where the render allows it
 };

@@ -21,19 +21,24 @@
 //    stretches the largest requests. Which requests finish at a step is known
 //    when it is enqueued, so the scheduler never waits for the device except
 //    to bound how far it runs ahead (STEPS_AHEAD steps);
-//  * the copy-out thread waits for each finished request's last pass, reads
-//    its status word (a walk that overflowed its stack fails the request),
-//    copies its RGB image to the caller's buffer where needed, releases its
-//    memory and records its latency, while the device already runs the next
-//    steps. Where the host output policy chooses direct writes
-//    (rcp_set_host_output), a request's last pass writes its RGB into the
-//    caller's buffer itself (no staging buffer, no pack kernel, no copy).
+//  * the copy-out thread waits for each finished request, reads its status
+//    word (a walk that overflowed its stack fails the request), copies its RGB
+//    image to the caller's buffer where needed, releases its memory and
+//    records its latency, while the device already runs the next steps. A
+//    request is finished when the last of its tiles in its final step is: the
+//    warp that completes it sets the request's done word in page-locked host
+//    memory, so a request does not wait for the other views of its launch
+//    (views are queued oldest first). Its last pass writes its RGB into the
+//    caller's buffer where the host output policy chooses direct writes
+//    (rcp_set_host_output), else into a device staging buffer that the
+//    copy-out thread copies.
 // New requests join at the next step while others are mid-recursion, so short
 // and long requests share every launch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -71,9 +76,8 @@ struct Request {
     float4* img[2] = {nullptr, nullptr};
     float* rgb = nullptr;
     bool direct = false;     // the last pass writes out_rgb itself (else pack and copy)
-    int2* hint = nullptr;    // per pixel: latest primary-hit and shadow-occluder records, then the status word
-    int* d_status = nullptr;  // inside the hint allocation
-    int status_slot = -1;     // index of the request's pinned host status word
+    int2* hint = nullptr;    // per pixel: latest primary-hit and shadow-occluder records
+    int status_slot = -1;     // the request's two words in the server's page-locked status array
     int64_t bytes = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     rcp_status status = RCP_OK;
@@ -87,6 +91,8 @@ struct StepSlot {
     ViewDev* h_views = nullptr;  // pinned staging
     int cap = 0;
     unsigned* d_work = nullptr;
+    int* d_counts = nullptr;  // per view: its tiles still to finish (final steps of requests)
+    int* h_counts = nullptr;  // pinned staging
     cudaEvent_t start = nullptr, done = nullptr;  // around the step's device work
     bool used = false;
 };
@@ -116,7 +122,10 @@ struct rcp_server {
     StepSlot slots[STEPS_AHEAD];
     int64_t step_no = 0;
     int device = 0;
-    int* h_status = nullptr;  // pinned: one status word per admitted, unfinished request
+    // page-locked, mapped: per admitted, unfinished request, [2 slot] its
+    // overflow word (written by the device) and [2 slot + 1] its done word
+    int* h_status = nullptr;
+    int* d_hstatus = nullptr;  // the same array as the device addresses it
     std::vector<int> free_status;
     int64_t step_pixels = DEFAULT_STEP_PIXELS;  // pixel-passes per step (0: every admitted request every step)
     int max_chain = 16;  // passes one request may advance by in one step
@@ -130,22 +139,20 @@ struct rcp_server {
 
 namespace {
 
-// Device memory of a request: two rgbz images, the per-pixel hit hints and its
-// status word, and the RGB staging buffer unless its last pass writes the
-// caller's buffer directly.
+// Device memory of a request: two rgbz images, the per-pixel hit hints, and
+// the RGB staging buffer unless its last pass writes the caller's buffer
+// directly.
 int64_t request_bytes(int W, int H, bool direct) {
     const int64_t P = (int64_t)W * H;
-    return P * (2 * 16 + 8 + (direct ? 0 : 12)) + 4 * 256;
+    return P * (2 * 16 + 8 + (direct ? 0 : 12)) + 3 * 256;
 }
 
 rcp_status alloc_request(Request& r, bool direct, cudaStream_t st) {
     const int64_t P = (int64_t)r.W * r.H;
     RCP_CUDA(cudaMallocAsync((void**)&r.img[0], sizeof(float4) * P, st));
     RCP_CUDA(cudaMallocAsync((void**)&r.img[1], sizeof(float4) * P, st));
-    RCP_CUDA(cudaMallocAsync((void**)&r.hint, sizeof(int2) * (P + 1), st));
+    RCP_CUDA(cudaMallocAsync((void**)&r.hint, sizeof(int2) * P, st));
     RCP_CUDA(cudaMemsetAsync(r.hint, 0xff, sizeof(int2) * P, st));  // -1: no earlier hit
-    r.d_status = (int*)(r.hint + P);
-    RCP_CUDA(cudaMemsetAsync(r.d_status, 0, sizeof(int), st));
     if (!direct) RCP_CUDA(cudaMallocAsync((void**)&r.rgb, sizeof(float) * 3 * P, st));
     if (!r.ready) RCP_CUDA(cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming));
     return RCP_OK;
@@ -164,7 +171,6 @@ void free_request(Request& r, cudaStream_t st) {
     if (r.hint) {
         cudaFreeAsync(r.hint, st);
         r.hint = nullptr;
-        r.d_status = nullptr;
     }
 }
 
@@ -177,12 +183,18 @@ rcp_status ensure_slot(StepSlot& s, int n) {
     if (s.cap < n) {
         if (s.d_views) cudaFree(s.d_views);
         if (s.h_views) cudaFreeHost(s.h_views);
+        if (s.d_counts) cudaFree(s.d_counts);
+        if (s.h_counts) cudaFreeHost(s.h_counts);
         s.d_views = nullptr;
         s.h_views = nullptr;
+        s.d_counts = nullptr;
+        s.h_counts = nullptr;
         s.cap = 0;
         const int cap = std::max(n, 16);
         RCP_CUDA(cudaMalloc((void**)&s.d_views, sizeof(ViewDev) * cap));
         RCP_CUDA(cudaMallocHost((void**)&s.h_views, sizeof(ViewDev) * cap));
+        RCP_CUDA(cudaMalloc((void**)&s.d_counts, sizeof(int) * cap));
+        RCP_CUDA(cudaMallocHost((void**)&s.h_counts, sizeof(int) * cap));
         s.cap = cap;
     }
     return RCP_OK;
@@ -207,7 +219,10 @@ double percentile(std::vector<double> v, double q) {
 rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot) {
     rcp_status r = ensure_slot(slot, (int)batch.size());
     if (r != RCP_OK) return r;
-    // views grouped by scene, scenes in order of their oldest request
+    // views grouped by scene (its tree stays in L2 while its views run),
+    // scenes in order of their oldest request, admission order within a
+    // scene: the tile queue runs them in that order, and each request is done
+    // when its own tiles are
     std::vector<const rcp_scene*> order;
     for (Request* q : batch)
         if (std::find(order.begin(), order.end(), q->scene) == order.end()) order.push_back(q->scene);
@@ -225,28 +240,37 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
     LaunchCfg cfg;  // 128 threads, 32-pixel chunks, fused camera: no ray buffer per request
     cfg.stack = std::min((stack + 3) & ~3, MAX_STACK);  // one entry per level of the deepest tree
     cfg.ms = ms;
-    cfg.multi = scenes.size() > 1;
+    cfg.multi = true;  // each view names its scene (and the kernels count each request's tiles)
     int64_t total_pix = 0, total_chunks = 0;
     for (size_t i = 0; i < batch.size(); ++i) {
         Request* q = batch[i];
         ViewDev v;
         make_view(v, q->cam, q->W, q->H, q->p);
         v.scene = q->scene->d_dev;
-        v.status = q->d_status;
+        v.status = d_hstatus + 2 * q->status_slot;
         const int last = q->passes_done + q->step_passes;  // passes done after this step
         v.in = q->passes_done == 0 ? nullptr : q->img[(q->passes_done - 1) & 1];
         v.out = q->img[(last - 1) & 1];
         v.passes = q->step_passes;
         v.hint = q->hint;
-        if (q->direct && last == q->K) v.rgb = q->out_rgb;
+        const int64_t tiles = (int64_t)v.tiles_x * ((q->H + 3) / 4);
+        slot.h_counts[i] = 0;
+        if (last == q->K) {  // its final step: the last pass writes the RGB, its last tile the done word
+            v.rgb = q->direct ? q->out_rgb : q->rgb;
+            slot.h_counts[i] = (int)tiles;
+            v.done_count = slot.d_counts + i;
+            v.done_flag = d_hstatus + 2 * q->status_slot + 1;
+        }
         v.pix_begin = total_pix;
         v.chunk_begin = total_chunks;
         total_pix += (int64_t)q->W * q->H;
-        total_chunks += (int64_t)v.tiles_x * ((q->H + 3) / 4);
+        total_chunks += tiles;
         slot.h_views[i] = v;
     }
     RCP_CUDA(cudaEventRecord(slot.start, st_main));
     RCP_CUDA(cudaMemcpyAsync(slot.d_views, slot.h_views, sizeof(ViewDev) * batch.size(), cudaMemcpyHostToDevice,
+                             st_main));
+    RCP_CUDA(cudaMemcpyAsync(slot.d_counts, slot.h_counts, sizeof(int) * batch.size(), cudaMemcpyHostToDevice,
                              st_main));
     RCP_CUDA(cudaMemsetAsync(slot.d_work, 0, sizeof(unsigned), st_main));
     r = ms ? launch_pass((*scenes.begin())->dev(), cfg, slot.d_views, (int)batch.size(), total_pix, total_chunks,
@@ -254,17 +278,8 @@ rcp_status rcp_server::enqueue_step(std::vector<Request*>& batch, StepSlot& slot
            : launch_chain((*scenes.begin())->dev(), cfg, slot.d_views, (int)batch.size(), total_chunks, slot.d_work,
                           d_rays, nullptr, st_main);
     if (r != RCP_OK) return r;
-    for (Request* q : batch) {
-        const int last = q->passes_done + q->step_passes;
-        if (last != q->K) continue;
-        if (!q->direct) {
-            r = launch_pack_rgb(q->img[(last - 1) & 1], q->rgb, (int64_t)q->W * q->H, st_main);
-            if (r != RCP_OK) return r;
-        }
-        RCP_CUDA(cudaMemcpyAsync(h_status + q->status_slot, q->d_status, sizeof(int), cudaMemcpyDeviceToHost,
-                                 st_main));
-        RCP_CUDA(cudaEventRecord(q->ready, st_main));
-    }
+    for (Request* q : batch)  // after the step, whatever the done words say
+        if (q->passes_done + q->step_passes == q->K) RCP_CUDA(cudaEventRecord(q->ready, st_main));
     RCP_CUDA(cudaEventRecord(slot.done, st_main));
     slot.used = true;
     return RCP_OK;
@@ -302,8 +317,18 @@ void rcp_server::copy_out() {
         }
         rcp_status st = RCP_OK;
         if (q->status == RCP_OK) {
-            cudaError_t e = cudaEventSynchronize(q->ready);
-            if (e == cudaSuccess && h_status[q->status_slot]) {
+            // the done word (set by the request's last tile), or the end of
+            // its step, whichever is seen first
+            const volatile int* done = h_status + 2 * q->status_slot + 1;
+            cudaError_t e = cudaSuccess;
+            for (int spin = 0; !*done; ++spin) {
+                e = cudaEventQuery(q->ready);
+                if (e != cudaErrorNotReady) break;
+                e = cudaSuccess;
+                if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+            std::atomic_thread_fence(std::memory_order_acquire);  // the image and overflow word written before it
+            if (e == cudaSuccess && ((volatile int*)h_status)[2 * q->status_slot]) {
                 set_error("server: a traversal stack overflowed; the request's image is incomplete");
                 st = RCP_ERR_STACK;
             }
@@ -367,7 +392,8 @@ void rcp_server::run() {
                 q->t_admit = now_s();
                 q->status_slot = free_status.back();
                 free_status.pop_back();
-                h_status[q->status_slot] = 0;
+                h_status[2 * q->status_slot] = 0;  // overflow
+                h_status[2 * q->status_slot + 1] = 0;  // done
                 inflight.push_back(q);
             }
             batch = inflight;
@@ -455,12 +481,25 @@ rcp_status rcp_server_create(int64_t budget, int max_slots, rcp_server** out) {
     // admitted, unfinished requests: at most max_slots in flight and as many
     // again waiting for copy-out (admission waits for a free word)
     const int n_status = 2 * max_slots + 16;
-    RCP_CUDA(cudaMallocHost((void**)&s->h_status, sizeof(int) * n_status));
+    RCP_CUDA(cudaHostAlloc((void**)&s->h_status, sizeof(int) * 2 * n_status, cudaHostAllocMapped));
+    RCP_CUDA(cudaHostGetDevicePointer((void**)&s->d_hstatus, s->h_status, 0));
     for (int i = n_status - 1; i >= 0; --i) s->free_status.push_back(i);
     cudaMemPool_t pool = nullptr;
     RCP_CUDA(cudaDeviceGetDefaultMemPool(&pool, s->device));
     uint64_t thr = (uint64_t)budget;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    // Back the pool with memory now (up to 8 GB of the budget, within half of
+    // what is free): growing it while requests are served maps memory inside
+    // the driver, which holds up CUDA calls on other threads for milliseconds.
+    size_t free_b = 0, total_b = 0;
+    RCP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t reserve = std::min<size_t>({(size_t)budget, (size_t)8 << 30, free_b / 2});
+    if (reserve > 0) {
+        void* p = nullptr;
+        RCP_CUDA(cudaMallocAsync(&p, reserve, s->st_main));
+        RCP_CUDA(cudaFreeAsync(p, s->st_main));
+        RCP_CUDA(cudaStreamSynchronize(s->st_main));
+    }
     rcp_server* raw = s.release();
     raw->worker = std::thread([raw] { raw->run(); });
     raw->copier = std::thread([raw] { raw->copy_out(); });
@@ -628,6 +667,8 @@ void rcp_server_destroy(rcp_server* srv) {
     for (auto& sl : srv->slots) {
         if (sl.d_views) cudaFree(sl.d_views);
         if (sl.h_views) cudaFreeHost(sl.h_views);
+        if (sl.d_counts) cudaFree(sl.d_counts);
+        if (sl.h_counts) cudaFreeHost(sl.h_counts);
         if (sl.d_work) cudaFree(sl.d_work);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.start) cudaEventDestroy(sl.start);

@@ -77,6 +77,21 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
     return out;
 }
 
+// A warp counts n finished tiles of view v (with a done counter) at once:
+// every lane's writes for them made visible first, then one atomic; the
+// warp that counts the view's last tiles sets its host-visible done flag.
+// Counting when the warp moves to another view (or ends) keeps the fences,
+// which wait for the writes in flight, to one per run of tiles.
+__device__ __forceinline__ void tiles_done(const ViewDev* v, int n, int lane) {
+    if (!v || n == 0) return;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && atomicSub(v->done_count, n) == n) {
+        __threadfence_system();
+        *(volatile int*)v->done_flag = 1;
+    }
+}
+
 // MULTI: every view names its own scene (views of several scenes in one
 // launch); otherwise all views render the launch's scene S0.
 // CHAIN: one launch runs v.passes passes of each view v (v.in its first
@@ -95,7 +110,17 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
     extern __shared__ uint2 s_stack[];
     __shared__ uint8_t s_order[ORDER_LUT_BYTES];
     __shared__ SceneDev s_scene[MULTI ? BLOCK / 32 : 1];  // MULTI: the scene of each warp's current tile
+    // per warp: the view (with a done counter) whose tiles it finished last,
+    // and how many of them it has not yet counted. Done counters come with
+    // the server's launches, which name each view's scene (MULTI).
+    constexpr bool SIGNAL = MULTI;
+    __shared__ const ViewDev* s_done_v[BLOCK / 32];
+    __shared__ int s_done_n[BLOCK / 32];
     fill_order_lut<BLOCK>(s_order);
+    if ((threadIdx.x & 31) == 0) {
+        s_done_v[threadIdx.x >> 5] = nullptr;
+        s_done_n[threadIdx.x >> 5] = 0;
+    }
     __syncthreads();
     uint2* stack = s_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -120,6 +145,7 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
                 __syncwarp();
             }
             const SceneDev& S = MULTI ? s_scene[threadIdx.x >> 5] : S0;
+            do {  // the tile's pixel of this lane ("continue" leaves the block)
             const int64_t tile = chunk - v.chunk_begin;
             const int tx = (int)(tile % v.tiles_x), ty = (int)(tile / v.tiles_x);
             const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
@@ -168,7 +194,7 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
                     v.rgb[3 * p + 2] = out.z;
                 }
                 if (overflow) {  // this view's image is incomplete
-                    atomicExch(v.status, 1);
+                    *(volatile int*)v.status = 1;
                     overflow = false;
                 }
                 continue;
@@ -211,10 +237,29 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
                 v.rgb[3 * p + 2] = out.z;
             }
             if (overflow) {  // this view's image is incomplete
-                atomicExch(v.status, 1);
+                *(volatile int*)v.status = 1;
                 overflow = false;
             }
+            } while (0);
+            if (SIGNAL && v.done_count) {  // counted when the warp leaves the view
+                const int w = threadIdx.x >> 5;
+                __syncwarp();
+                if (s_done_v[w] != &v) {
+                    tiles_done(s_done_v[w], s_done_n[w], lane);
+                    __syncwarp();
+                    if (lane == 0) {
+                        s_done_v[w] = &v;
+                        s_done_n[w] = 0;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) ++s_done_n[w];
+            }
         }
+    }
+    if (SIGNAL) {
+        __syncwarp();
+        tiles_done(s_done_v[threadIdx.x >> 5], s_done_n[threadIdx.x >> 5], lane);
     }
     {
         const unsigned np = __reduce_add_sync(0xffffffffu, n_primary);
