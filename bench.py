@@ -112,15 +112,16 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def profiled(workload):
+def profiled(workload, chained):
     """The committed ncu record of the trace kernel on this workload (DRAM
     bytes per launch, issue and pipe utilisation, L1 hit rate), if it was taken
-    on the current kernel sources; else None."""
+    on the current kernel sources and on the same kind of launch (all passes
+    chained, or one launch per pass); else None."""
     p = os.path.join(ROOT, "profiles", "k_trace_ncu.json")
     if not os.path.exists(p):
         return None
     e = json.load(open(p)).get(workload)
-    if not e or e.get("csrc_hash") != csrc_hash():
+    if not e or e.get("csrc_hash") != csrc_hash() or bool(e.get("chained")) != chained:
         return None
     return e
 
@@ -345,7 +346,7 @@ def roofline(work, pass_ms, frames, workload, clk, sms):
             BYTES_PIXEL_PASS * work["prim_rays"]) / n
     launch_s = statistics.mean(pass_ms) / 1000.0
     peak = sms * 128 * sm_max_mhz * 1e6
-    prof = profiled(workload)
+    prof = profiled(workload, per_frame == 1)
     roof = {"bound": "alu", "achieved": ops / launch_s / 1e12, "peak": peak / 1e12,
             "unit": "Tops/s (algorithmic FP32 lane-ops)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
