@@ -304,16 +304,19 @@ def time_frames(g, cams, W, H, K, params, stream, flush):
     return step_ms, pass_ms, rays
 
 
-def count_work(g, cams, W, H, K, params):
+def count_work(g, cams, W, H, K, params, sizes=None, frames=None):
     """The algorithmic work of the timed frames: an instrumented copy of the
-    trace kernel run over the same cameras, K chained passes each."""
+    trace kernel run over the same cameras, K passes each, each reading the
+    previous one's image. sizes: one (W, H) per camera (else W x H for all);
+    frames: how many timed frames the cameras make up (default one each)."""
     import torch
 
     from paper_2312_12392_gb300 import rcp
-    tot = dict(box=0, tri=0, sph=0, nodes=0, prim_rays=0, rays=0, frames=len(cams))
-    a = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
-    b = torch.empty_like(a)
-    for c in cams:
+    tot = dict(box=0, tri=0, sph=0, nodes=0, prim_rays=0, rays=0, frames=len(cams) if frames is None else frames)
+    sizes = sizes or [(W, H)] * len(cams)
+    for c, (W, H) in zip(cams, sizes):
+        a = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
         prev = None
         for n in range(K):
             dst = a if n % 2 == 0 else b
@@ -629,9 +632,11 @@ def one_line(metric, value, unit, args, steps, extra):
 
 def batched_summary(args):
     """64 views of uneven size (W in [256,1920], H in [256,1080], seeded) of the
-    1.07M-triangle forest, K = 6: one persistent launch per pass over all views
-    (graph-captured, autotuned), against rendering the same views one after
-    another with the single-view device path."""
+    1.07M-triangle forest, K = 6: one persistent launch over all views (all
+    passes chained, or one launch per pass, as tuned; graph-captured,
+    autotuned), against rendering the same views one after another with the
+    single-view device path. The roofline counts the batch's work over its
+    launches."""
     import torch
 
     from paper_2312_12392_gb300 import rcp, scenes
@@ -659,11 +664,14 @@ def batched_summary(args):
                 rcp.rcp_render_device(g, c, w, h, K_PASSES, params, None, o, None, stream)
 
         steps = max(3, min(args.steps, 20))
-        res = {}
+        res, batch_launch_ms = {}, []
+        clocks = ClockSampler(physical_gpu(0))
         for name, fn in (("batched", batch_once), ("plain", plain_once)):
             for _ in range(args.warmup):
                 fn()
             torch.cuda.synchronize()
+            if name == "batched":
+                clocks.start()
             ms = []
             for _ in range(steps):
                 flush.zero_()
@@ -673,7 +681,14 @@ def batched_summary(args):
                 e.record(stream)
                 e.synchronize()
                 ms.append(s.elapsed_time(e))
+                if name == "batched":
+                    batch_launch_ms.extend(rcp.rcp_last_pass_times(g))
+            if name == "batched":
+                clk = clocks.stop()
             res[name] = statistics.mean(ms)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        roof = roofline(count_work(g, cams, 0, 0, K_PASSES, params, sizes=sizes, frames=1), batch_launch_ms,
+                        steps, "batched", clk, sms)
         pix = sum(w * h for w, h in sizes)
         batch_once()
         torch.cuda.synchronize()
@@ -687,7 +702,7 @@ def batched_summary(args):
                             ("one launch per pass" if launches > 1 else "one launch for all passes") +
                             " over all views, graph-captured",
                 "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1), "tuning": tuning_dict(t),
-                "l2": "flushed between steps", "gpu_launches": steps * launches}
+                "l2": "flushed between steps", "gpu_launches": steps * launches, "roofline": roof, "clocks": clk}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -905,7 +920,10 @@ def stress_summary(args):
             rcp.rcp_scene_update_vertices_device(g, moved, stream)
             rcp.rcp_render_device(g, cams[i], W, H, K, params, None, out, None, stream)
         torch.cuda.synchronize()
-        refit_ms, render_ms, frame_ms, rays = [], [], [], 0
+        refit_ms, render_ms, frame_ms, rays, launch_ms = [], [], [], 0, []
+        work = None
+        clocks = ClockSampler(physical_gpu(0))
+        clocks.start()
         for i in range(args.warmup, args.warmup + steps):
             sway(i)  # input generation, outside the timed events
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -920,6 +938,13 @@ def stress_summary(args):
             frame_ms.append(e0.elapsed_time(e2))
             p_, s_ = rcp.rcp_last_ray_counts(g)
             rays += p_ + s_
+            launch_ms.extend(rcp.rcp_last_pass_times(g))
+            # this frame's work on this frame's tree, counted outside the events
+            w = count_work(g, [cams[i]], W, H, K, params)
+            work = w if work is None else {k: work[k] + w[k] for k in work}
+        clk = clocks.stop()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        roof = roofline(work, launch_ms, steps, "stress", clk, sms)
         rcp.rcp_scene_validate(g)
         tot = sum(frame_ms) / 1000.0
         # End to end, every frame's RGB delivered to host memory, the same frames:
@@ -970,7 +995,8 @@ def stress_summary(args):
                             "A=0.02*h_tree at 0.5 Hz, refit every frame",
                 "bvh_collapse": collapse_name, "bvh_split_max": split, "records": info.n_records,
                 "scene_generation_s": gen_s, "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
-                "depth": info.depth, "gpu_launches_per_step": K + 2 + info.depth,
+                "depth": info.depth, "gpu_launches_per_step": len(launch_ms) // steps + 2 + info.depth,
+                "roofline": roof, "clocks": clk,
                 "e2e": {"value": steps / single_s, "unit": "frames/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": out_bytes,
                         "api": "single stream: rcp_scene_update_vertices_device + rcp_render (host RGB) per frame"},
