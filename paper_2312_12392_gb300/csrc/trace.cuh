@@ -223,6 +223,29 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     return d;
 }
 
+// Two floats in one 64-bit register, and a fused multiply-add of two such
+// pairs at once (each lane exactly the scalar FMA, rounded down or up).
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma_rd(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma_ru(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rp.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Traversal order of a node's children for a ray of octant oct (bit a set when
 // the direction's component a is negative): slot s comes at position s ^ oct,
 // so that slot order, which the collapse lays out front to back for octant 0,
@@ -398,17 +421,33 @@ __device__ __forceinline__ Hit traverse(const SceneDev& S, const RayF& r, uint2*
                 const float4 nx = __ldg(np + rxn + half), fx = __ldg(np + rxf + half);
                 const float4 ny = __ldg(np + ryn + half), fy = __ldg(np + ryf + half);
                 const float4 nz = __ldg(np + rzn + half), fz = __ldg(np + rzf + half);
+                // two slots per instruction: the planes of slots (0,1) and (2,3)
+                // of this half against the ray's terms, each broadcast to a pair
                 const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
                 const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
                 const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float t0x = __fmaf_rd(nxs[k], idx, nox), t1x = __fmaf_ru(fxs[k], fdx, fox);
-                    const float t0y = __fmaf_rd(nys[k], idy, noy), t1y = __fmaf_ru(fys[k], fdy, foy);
-                    const float t0z = __fmaf_rd(nzs[k], idz, noz), t1z = __fmaf_ru(fzs[k], fdz, foz);
-                    const float tn = fmax3(t0x, t0y, fmaxf(t0z, r.tmin));
-                    const float tf = fmin3(t1x, t1y, fminf(t1z, tfar_lim));
-                    hitmask |= (tn <= tf ? 1u : 0u) << (4 * half + k);
+                for (int q = 0; q < 2; ++q) {
+                    const int k = 2 * q;
+                    float t0x[2], t1x[2], t0y[2], t1y[2], t0z[2], t1z[2];
+                    f2_unpack(f2_fma_rd(f2_pack(nxs[k], nxs[k + 1]), f2_pack(idx, idx), f2_pack(nox, nox)), t0x[0],
+                              t0x[1]);
+                    f2_unpack(f2_fma_ru(f2_pack(fxs[k], fxs[k + 1]), f2_pack(fdx, fdx), f2_pack(fox, fox)), t1x[0],
+                              t1x[1]);
+                    f2_unpack(f2_fma_rd(f2_pack(nys[k], nys[k + 1]), f2_pack(idy, idy), f2_pack(noy, noy)), t0y[0],
+                              t0y[1]);
+                    f2_unpack(f2_fma_ru(f2_pack(fys[k], fys[k + 1]), f2_pack(fdy, fdy), f2_pack(foy, foy)), t1y[0],
+                              t1y[1]);
+                    f2_unpack(f2_fma_rd(f2_pack(nzs[k], nzs[k + 1]), f2_pack(idz, idz), f2_pack(noz, noz)), t0z[0],
+                              t0z[1]);
+                    f2_unpack(f2_fma_ru(f2_pack(fzs[k], fzs[k + 1]), f2_pack(fdz, fdz), f2_pack(foz, foz)), t1z[0],
+                              t1z[1]);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float tn = fmax3(t0x[j], t0y[j], fmaxf(t0z[j], r.tmin));
+                        const float tf = fmin3(t1x[j], t1y[j], fminf(t1z[j], tfar_lim));
+                        hitmask |= (tn <= tf ? 1u : 0u) << (4 * half + k + j);
+                    }
                 }
             }
             const uint32_t ml = hd.z, mh = hd.w;
