@@ -5,20 +5,22 @@ Default workload (one JSON line on stdout): the 133,472-triangle fBm terrain +
 200 boxes, 1920x1080, K = 6 passes, EYE mapping with k = 0.02 * diameter and
 f = 0.1 * diameter, cycling through its 64-pose walk-through. One step = one
 frame = K passes (camera + primary ray + shadow ray + shading for every pixel),
-replayed from the library's captured CUDA graph with the scene resident in HBM.
+replayed from the library's captured CUDA graph with the scene resident in HBM
+(by default one launch runs the K passes, chained).
 L2 is flushed (a 256 MB write) between steps, outside the timed events.
 
 At one GPU the same line also carries the other workloads, each measured in
 this run: "forest" (the 1.07M-triangle forest, 1080p K=6 over its 64-pose
 walk-through, with its own roofline, end-to-end figure and clock record),
-"batched" (64 uneven forest views, one launch per pass, against per-view
-launches), "served" (Poisson arrivals over four resident terrains of 0.1-5M
-triangles, the continuous-batching server against the plain per-request path,
-1,000 requests per rate) and "stress" (the 12.57M-triangle swaying forest at
-4K, K=8, refit and render per frame).
+"batched" (64 uneven forest views in one launch, against per-view renders),
+"served" (Poisson arrivals over four resident terrains of 0.1-5M triangles,
+the continuous-batching server against the plain per-request path, 1,000
+requests per rate), "stress" (the 12.57M-triangle swaying forest at 4K, K=8,
+refit and render per frame) and "mappings" (the terrain under the TARGET,
+DEPTH and NORMAL mappings and with 4 jittered samples per pixel).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload mid|forest|batched|served|stress|imagespace]
+                    [--workload mid|forest|batched|served|stress|mappings|imagespace]
                     [--collapse auto|area|sah] [--tuning auto|block,chunk,fused[,stack[,hints[,chain]]]]
                     [--no-extras]
 
@@ -508,7 +510,7 @@ def run_ours(args):
                                          f"extrapolated to 1920x1080 frames"}
     if args.extras and args.workload == "mid" and world == 1:
         for name, fn in (("forest", forest_summary), ("batched", batched_summary), ("served", served_summary),
-                         ("stress", stress_summary)):
+                         ("stress", stress_summary), ("mappings", mappings_summary)):
             t1 = time.perf_counter()
             res[name] = fn(args)
             res[name]["bench_wall_s"] = time.perf_counter() - t1
@@ -563,6 +565,56 @@ def forest_summary(args):
                 "tuning": tuning_dict(t), "bvh_build_ms": info.build_ms, "nodes": info.n_nodes,
                 "depth": info.depth, "bvh_collapse": collapse_name, "bvh_split_max": max(split, 1),
                 "records": info.n_records, "gpu_launches": len(pass_ms)}
+    finally:
+        rcp.rcp_scene_destroy(g)
+
+
+def mappings_summary(args):
+    """The mid terrain at 1080p K=6 under every camera mapping of the paper,
+    each autotuned, timed and counted like the headline over the first 16
+    poses: EYE (the headline's), TARGET (§3), DEPTH (§4, z0 at the focal
+    distance), NORMAL (§5), and EYE with 4 jittered samples per pixel per
+    pass (§2; one launch per pass, the samples reading the previous image
+    bilinearly)."""
+    import torch
+
+    from paper_2312_12392_gb300 import rcp
+    sc, _ = make_workload("mid")
+    d = sc.diameter()
+    k, f = 0.02 * d, 0.1 * d
+    g = rcp.scene_from(sc, collapse_for(args, "mid")[0])
+    jitter = np.random.default_rng(11).random((4, 2))
+    variants = [("eye", rcp.make_params(rcp.RCP_MAP_EYE, k, f)),
+                ("target", rcp.make_params(rcp.RCP_MAP_TARGET, k, f)),
+                ("depth", rcp.make_params(rcp.RCP_MAP_DEPTH, k, f, z0=f)),
+                ("normal", rcp.make_params(rcp.RCP_MAP_NORMAL, k, f)),
+                ("eye_4spp", rcp.make_params(rcp.RCP_MAP_EYE, k, f, jitter=jitter))]
+    try:
+        cams = [rcp.camera_from(p) for p in sc.poses[:16]]
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        out = {}
+        for name, params in variants:
+            t = rcp.rcp_autotune(g, cams[0], W_IMG, H_IMG, params,
+                                 os.path.join(ROOT, "paper_2312_12392_gb300", "tuning_cache.json"))
+            time_frames(g, cams[:3], W_IMG, H_IMG, K_PASSES, params, stream, flush)
+            torch.cuda.synchronize()
+            clocks = ClockSampler(physical_gpu(0))
+            clocks.start()
+            time.sleep(0.3)
+            ms, pass_ms, rays = time_frames(g, cams, W_IMG, H_IMG, K_PASSES, params, stream, flush)
+            clk = clocks.stop()
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, len(cams),
+                            "mid_" + name, clk, sms)
+            tot = sum(ms) / 1000.0
+            out[name] = {"frames_per_s": len(cams) / tot, "mrays_per_s": rays / tot / 1e6,
+                         "ms_per_frame": 1000 * tot / len(cams), "roofline_frac": roof["frac"],
+                         "launch_ms": roof["launch_ms"], "launches_per_frame": roof["launches_per_frame"],
+                         "tuning": tuning_dict(t), "clocks": clk}
+        return {"workload": "mid terrain 133k tris, 1920x1080, K=6, 16 poses of the walk-through; k=0.02*diam, "
+                            "f=0.1*diam, DEPTH z0=f, 4 jittered samples from a seeded table",
+                "frames": len(cams), "variants": out}
     finally:
         rcp.rcp_scene_destroy(g)
 
@@ -1010,7 +1062,7 @@ def stress_summary(args):
 
 
 def run_workload_line(args, name):
-    """One workload's own line (--workload forest|batched|served|stress)."""
+    """One workload's own line (--workload forest|batched|served|stress|mappings)."""
     import torch
 
     from paper_2312_12392_gb300 import build as B
@@ -1025,6 +1077,12 @@ def run_workload_line(args, name):
         out = one_line("views_per_s (64 uneven views, K=6 each, one persistent launch over all views)",
                        r["views_per_s"], "views/s", args, r["steps"], r)
         out["ms_per_step"] = r["ms_per_batch"]
+    elif name == "mappings":
+        r = mappings_summary(args)
+        v = r["variants"]["eye_4spp"]
+        out = one_line("frames_per_s (mid 1080p K=6, 4 jittered samples per pixel; every mapping alongside)",
+                       v["frames_per_s"], "frames/s", args, r["frames"], r)
+        out["ms_per_step"] = v["ms_per_frame"]
     elif name == "served":
         r = served_summary(args)
         best = max(r["sweep"], key=lambda x: x["served"]["frames_per_s"])
@@ -1104,7 +1162,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mid", choices=["mid", "forest", "batched", "served", "stress", "imagespace"])
+    ap.add_argument("--workload", default="mid",
+                    choices=["mid", "forest", "batched", "served", "stress", "mappings", "imagespace"])
     ap.add_argument("--tuning", default="auto",
                     help="'auto' (the library's autotuner, cached per GPU, scene size, tree depth and view) or "
                          "block,chunk,fused_camera[,stack_entries[,hints[,chain_passes]]] (stack 0 = one entry per "
@@ -1118,7 +1177,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="the headline line without the forest, batched, served and stress summaries")
+                    help="the headline line without the forest, batched, served, stress and mappings summaries")
     ap.add_argument("--rates", default="100,200,400", help="served: arrival rates (req/s)")
     ap.add_argument("--served-requests", type=int, default=1000, help="served: requests per rate")
     ap.add_argument("--stress-steps", type=int, default=20, help="stress: timed frames")
@@ -1135,7 +1194,7 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("forest", "batched", "served", "stress"):
+    elif args.workload in ("forest", "batched", "served", "stress", "mappings"):
         run_workload_line(args, args.workload)
     elif args.workload == "imagespace":
         run_imagespace(args)

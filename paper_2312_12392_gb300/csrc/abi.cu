@@ -1170,7 +1170,8 @@ extern "C" rcp_status rcp_autotune(rcp_scene* sc, const rcp_camera* cam, int W, 
     int cls = 0;
     for (int64_t n = sc->T + sc->S; n > 1; n >>= 1) ++cls;
     std::ostringstream key;
-    key << gpu_name() << "|prims2^" << cls << "|depth" << sc->depth << "|" << W << "x" << H << "|map" << p->mapping;
+    key << gpu_name() << "|prims2^" << cls << "|depth" << sc->depth << "|" << W << "x" << H << "|map" << p->mapping
+        << "|spp" << p->spp;
     auto cache = read_cache(cache_path);
     auto it = cache.find(key.str());
     if (it != cache.end()) {
