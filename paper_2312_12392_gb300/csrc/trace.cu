@@ -78,13 +78,15 @@ __device__ __forceinline__ float4 trace_shade(const SceneDev& S, const RayF& r, 
 }
 
 // A warp counts n finished tiles of view v (with a done counter) at once:
-// every lane's writes for them made visible first, then one atomic; the
-// warp that counts the view's last tiles sets its host-visible done flag.
-// Counting when the warp moves to another view (or ends) keeps the fences,
-// which wait for the writes in flight, to one per run of tiles.
+// every lane's writes for them made visible first, at system scope (the RGB
+// may go straight to host memory, which the host reads once the flag is set),
+// then one atomic; the warp that counts the view's last tiles sets its
+// host-visible done flag. Counting when the warp moves to another view (or
+// ends) keeps the fences, which wait for the writes in flight, to one per run
+// of tiles.
 __device__ __forceinline__ void tiles_done(const ViewDev* v, int n, int lane) {
     if (!v || n == 0) return;
-    __threadfence();
+    __threadfence_system();
     __syncwarp();
     if (lane == 0 && atomicSub(v->done_count, n) == n) {
         __threadfence_system();
