@@ -148,48 +148,91 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
             }
             const SceneDev& S = MULTI ? s_scene[threadIdx.x >> 5] : S0;
             do {  // the tile's pixel of this lane ("continue" leaves the block)
-            const int64_t tile = chunk - v.chunk_begin;
-            const int tx = (int)(tile % v.tiles_x), ty = (int)(tile / v.tiles_x);
-            const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
-            if (x >= v.W || y >= v.H) continue;
-            const int64_t p = (int64_t)y * v.W + x;
-            if (MS) {
-                // jittered samples (§2): each reads I_{n-1} at its own position
-                const int ns = v.spp > 0 ? v.spp : 1;
-                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                uint32_t code0 = 0;
-                int32_t prim0 = -1;
+                const int64_t tile = chunk - v.chunk_begin;
+                const int tx = (int)(tile % v.tiles_x), ty = (int)(tile / v.tiles_x);
+                const int x = tx * 8 + (lane & 7), y = ty * 4 + (lane >> 3);
+                if (x >= v.W || y >= v.H) continue;
+                const int64_t p = (int64_t)y * v.W + x;
+                if (MS) {
+                    // jittered samples (§2): each reads I_{n-1} at its own position
+                    const int ns = v.spp > 0 ? v.spp : 1;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    uint32_t code0 = 0;
+                    int32_t prim0 = -1;
+                    int2 hint = v.hint && stk.hints ? v.hint[p] : make_int2(-1, -1);
+                    if (!(stk.hints & 1)) hint.x = -1;
+                    if (!(stk.hints & 2)) hint.y = -1;
+                    prefetch_record(S, hint.x);
+                    for (int s = 0; s < ns; ++s) {
+                        const float jx = v.spp > 0 ? v.jit[2 * s] : 0.5f, jy = v.spp > 0 ? v.jit[2 * s + 1] : 0.5f;
+                        const float px = __fadd_rn((float)x, jx), py = __fadd_rn((float)y, jy);
+                        const float4 c = v.in ? sample_prev(v.in, v.W, v.H, px, py, v.mapping)
+                                              : make_float4(0.5f, 0.5f, 0.5f, 0.f);
+                        const RayF r = camera_ray(v, px, py, c, S.tmin);
+                        uint32_t code;
+                        int32_t prim;
+                        const float4 o = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc,
+                                                            n_shadow, code, prim, s_order, hint);
+                        ++n_primary;
+                        acc.x = __fadd_rn(acc.x, o.x);
+                        acc.y = __fadd_rn(acc.y, o.y);
+                        acc.z = __fadd_rn(acc.z, o.z);
+                        acc.w = __fadd_rn(acc.w, o.w);
+                        if (s == 0) {
+                            code0 = code;
+                            prim0 = prim;
+                        }
+                    }
+                    const float fn = (float)ns;
+                    float4 out = make_float4(__fdiv_rn(acc.x, fn), __fdiv_rn(acc.y, fn), __fdiv_rn(acc.z, fn),
+                                             __fdiv_rn(acc.w, fn));
+                    if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code0);
+                    v.out[p] = out;
+                    if (v.hint) v.hint[p] = hint;
+                    if (v.prim) v.prim[p] = prim0;
+                    if (v.rgb) {
+                        v.rgb[3 * p] = out.x;
+                        v.rgb[3 * p + 1] = out.y;
+                        v.rgb[3 * p + 2] = out.z;
+                    }
+                    if (overflow) {  // this view's image is incomplete
+                        *(volatile int*)v.status = 1;
+                        overflow = false;
+                    }
+                    continue;
+                }
                 int2 hint = v.hint && stk.hints ? v.hint[p] : make_int2(-1, -1);
                 if (!(stk.hints & 1)) hint.x = -1;
                 if (!(stk.hints & 2)) hint.y = -1;
-                prefetch_record(S, hint.x);
-                for (int s = 0; s < ns; ++s) {
-                    const float jx = v.spp > 0 ? v.jit[2 * s] : 0.5f, jy = v.spp > 0 ? v.jit[2 * s + 1] : 0.5f;
-                    const float px = __fadd_rn((float)x, jx), py = __fadd_rn((float)y, jy);
-                    const float4 c = v.in ? sample_prev(v.in, v.W, v.H, px, py, v.mapping)
-                                          : make_float4(0.5f, 0.5f, 0.5f, 0.f);
-                    const RayF r = camera_ray(v, px, py, c, S.tmin);
-                    uint32_t code;
-                    int32_t prim;
-                    const float4 o = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc,
-                                                        n_shadow, code, prim, s_order, hint);
-                    ++n_primary;
-                    acc.x = __fadd_rn(acc.x, o.x);
-                    acc.y = __fadd_rn(acc.y, o.y);
-                    acc.z = __fadd_rn(acc.z, o.z);
-                    acc.w = __fadd_rn(acc.w, o.w);
-                    if (s == 0) {
-                        code0 = code;
-                        prim0 = prim;
+                // CHAIN: passes 1..K, the camera reading this pixel's own previous value
+                float4 out = FUSED && v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
+                uint32_t code;
+                int32_t prim;
+                for (int n = 0; n < (CHAIN ? v.passes : 1); ++n) {
+                    prefetch_record(S, hint.x);  // its lines arrive while the camera ray is made
+                    RayF r;
+                    if (FUSED) {
+                        r = camera_ray(v, (float)x + 0.5f, (float)y + 0.5f, out, S.tmin);
+                    } else {
+                        const float4 a = __ldg(rays + 2 * (v.pix_begin + p));
+                        const float4 b = __ldg(rays + 2 * (v.pix_begin + p) + 1);
+                        r.ox = a.x;
+                        r.oy = a.y;
+                        r.oz = a.z;
+                        r.tmin = a.w;
+                        r.dx = b.x;
+                        r.dy = b.y;
+                        r.dz = b.z;
+                        r.tmax = b.w;
                     }
+                    out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc, n_shadow, code, prim,
+                                             s_order, hint);
+                    ++n_primary;
+                    if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
                 }
-                const float fn = (float)ns;
-                float4 out = make_float4(__fdiv_rn(acc.x, fn), __fdiv_rn(acc.y, fn), __fdiv_rn(acc.z, fn),
-                                         __fdiv_rn(acc.w, fn));
-                if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code0);
                 v.out[p] = out;
                 if (v.hint) v.hint[p] = hint;
-                if (v.prim) v.prim[p] = prim0;
+                if (v.prim) v.prim[p] = prim;
                 if (v.rgb) {
                     v.rgb[3 * p] = out.x;
                     v.rgb[3 * p + 1] = out.y;
@@ -199,49 +242,6 @@ __global__ void __launch_bounds__(BLOCK, CHAIN ? 640 / BLOCK : 0)  // CHAIN: 20 
                     *(volatile int*)v.status = 1;
                     overflow = false;
                 }
-                continue;
-            }
-            int2 hint = v.hint && stk.hints ? v.hint[p] : make_int2(-1, -1);
-            if (!(stk.hints & 1)) hint.x = -1;
-            if (!(stk.hints & 2)) hint.y = -1;
-            // CHAIN: passes 1..K, the camera reading this pixel's own previous value
-            float4 out = FUSED && v.in ? __ldg(v.in + p) : make_float4(0.5f, 0.5f, 0.5f, 0.f);
-            uint32_t code;
-            int32_t prim;
-            for (int n = 0; n < (CHAIN ? v.passes : 1); ++n) {
-                prefetch_record(S, hint.x);  // its lines arrive while the camera ray is made
-                RayF r;
-                if (FUSED) {
-                    r = camera_ray(v, (float)x + 0.5f, (float)y + 0.5f, out, S.tmin);
-                } else {
-                    const float4 a = __ldg(rays + 2 * (v.pix_begin + p));
-                    const float4 b = __ldg(rays + 2 * (v.pix_begin + p) + 1);
-                    r.ox = a.x;
-                    r.oy = a.y;
-                    r.oz = a.z;
-                    r.tmin = a.w;
-                    r.dx = b.x;
-                    r.dy = b.y;
-                    r.dz = b.z;
-                    r.tmax = b.w;
-                }
-                out = trace_shade<COUNT>(S, r, v.Fw, stack, BLOCK, stk, overflow, wc, n_shadow, code, prim,
-                                         s_order, hint);
-                ++n_primary;
-                if (v.mapping == RCP_MAP_NORMAL) out.w = __uint_as_float(code);
-            }
-            v.out[p] = out;
-            if (v.hint) v.hint[p] = hint;
-            if (v.prim) v.prim[p] = prim;
-            if (v.rgb) {
-                v.rgb[3 * p] = out.x;
-                v.rgb[3 * p + 1] = out.y;
-                v.rgb[3 * p + 2] = out.z;
-            }
-            if (overflow) {  // this view's image is incomplete
-                *(volatile int*)v.status = 1;
-                overflow = false;
-            }
             } while (0);
             if (SIGNAL && v.done_count) {  // counted when the warp leaves the view
                 const int w = threadIdx.x >> 5;
