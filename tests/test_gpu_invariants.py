@@ -258,6 +258,35 @@ def test_max_size_single_pass(tiny_g):
     del out
 
 
+def test_max_size_max_k_chained(tiny_g):
+    """The largest image and the most passes at once (8192 x 8192, K = 16):
+    the chained launch equals one launch per pass on every pixel (compared on
+    the device), and sampled pixels match the oracle's 16-pass chains."""
+    sc, g = tiny_g
+    cam = rcp.camera_from(sc.poses[0])
+    d = sc.diameter()
+    p = rcp.make_params(rcp.RCP_MAP_EYE, U.f32(0.05 * d), 6.0)
+    W = H = 8192
+    outs = []
+    try:
+        for chain in (1, 0):
+            rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, 0, 3, chain))
+            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+            rcp.rcp_render_device(g, cam, W, H, 16, p, None, out, None, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert len(rcp.rcp_last_pass_times(g)) == (1 if chain else 16)
+            outs.append(out)
+        assert torch.equal(outs[0].view(torch.int32), outs[1].view(torch.int32))
+        o = U.oracle_scene(sc)
+        pix = scenes.pixel_subset(W, H, 128, seed=2)
+        ref, _, _ = o.render(U.cam_f32(sc.poses[0]), W, H, 16, rcp.RCP_MAP_EYE, U.f32(0.05 * d), 6.0, pix=pix)
+        got = outs[0].reshape(-1, 4)[torch.from_numpy(pix).cuda()].cpu().numpy()
+        assert U.psnr(got[:, :3], ref[:, :3]) >= U.PSNR_MIN
+    finally:
+        rcp.rcp_set_tuning(g, rcp.rcp_tuning(128, 0, 32, 1, 0, 3, 1))
+        del outs
+
+
 def test_ray_counts_and_counters(tiny_g):
     sc, g = tiny_g
     cam = rcp.camera_from(sc.poses[0])
