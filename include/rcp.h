@@ -375,21 +375,25 @@ int64_t rcp_sort_static_capacity(void);
 /* ------------------------------------------------------------ serving ---
  * A request = one K-pass render of a resident scene. Requests are admitted
  * (first come first served) while a slot is free and their device memory (two
- * rgbz images, per-pixel hit hints and a status word) fits the budget. Each
+ * rgbz images, per-pixel hit hints, and an RGB staging buffer unless the last
+ * pass writes the caller's buffer) fits the budget; the server backs the
+ * device's stream-ordered memory pool with up to 8 GB of it at creation. Each
  * scheduler step advances admitted requests in ONE launch over all of their
  * views, whatever their scene, size or K (continuous batching): in admission
  * order, the oldest always (by one pass at least), each request by as many of
  * its remaining passes as the step's pixel-pass budget still holds
  * (rcp_server_set_step_pixels, at most rcp_server_set_max_chain), which run
  * chained (each pixel carried from pass to pass in registers); a step that
- * holds a multi-sample request advances every request by one pass. A finished
- * request's image is delivered to the caller's host buffer; a request whose
- * traversal stack overflowed fails with RCP_ERR_STACK. */
+ * holds a multi-sample request advances every request by one pass. A request
+ * is finished as soon as its own tiles of its final step are, not at the end
+ * of the step's launch (views are queued grouped by scene, oldest first); its
+ * image is then in the caller's host buffer. A request whose traversal stack
+ * overflowed fails with RCP_ERR_STACK. */
 typedef struct rcp_server rcp_server;
 
 typedef struct {
     int64_t submitted, completed, rejected, in_flight, queued;
-    int64_t steps;        /* scheduler steps (one pass of every in-flight request) */
+    int64_t steps;        /* scheduler steps (launches) */
     double p50_ms, p99_ms; /* submit-to-complete latency of completed requests */
     double frames_per_s;  /* completed requests per second since the first submit */
     double mrays_per_s;   /* primary + shadow rays per second over the same span */
