@@ -384,7 +384,8 @@ def roofline(work, pass_ms, frames, workload, clk, sms):
 def e2e_host(g, cams, W, H, K, params, flush, n):
     """Frames/s through rcp_render with a host RGB buffer: the per-call
     view-descriptor upload and the image's delivery to host memory are inside
-    the timed call."""
+    the timed call. One untimed call first, then n timed calls; with n =
+    len(cams) every camera is timed once."""
     import torch
 
     from paper_2312_12392_gb300 import rcp
@@ -470,8 +471,9 @@ def run_ours(args):
     # algorithmic work of the timed launches: the same poses, counted
     roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, len(cams), args.workload, clk,
                     sms)
-    e2e_fps, e2e_t = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, max(3, min(args.steps, 16)))
-    e2e_fps = world * max(3, min(args.steps, 16)) / max_over_ranks(e2e_t, "cuda")
+    # end to end over the same poses as the device-timed frames
+    e2e_fps, e2e_t = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, len(cams))
+    e2e_fps = world * len(cams) / max_over_ranks(e2e_t, "cuda")
     frames = args.steps * world
     value = frames / (tmax / 1000.0)
     res = {
@@ -555,7 +557,7 @@ def forest_summary(args):
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         roof = roofline(count_work(g, cams, W_IMG, H_IMG, K_PASSES, params), pass_ms, len(cams), "forest", clk,
                         sms)
-        e2e_fps, _ = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, 16)
+        e2e_fps, _ = e2e_host(g, cams, W_IMG, H_IMG, K_PASSES, params, flush, len(cams))
         tot = sum(ms) / 1000.0
         info = rcp.rcp_scene_get_info(g)
         return {"workload": desc, "frames_per_s": len(cams) / tot, "mrays_per_s": rays / tot / 1e6,
