@@ -96,6 +96,23 @@ def test_mid_end_to_end_psnr(mid, mid_gpu):
     assert p >= U.PSNR_MIN
 
 
+@pytest.mark.parametrize("mapping", [rcp.RCP_MAP_TARGET, rcp.RCP_MAP_DEPTH])
+def test_mid_other_mappings(mid, mid_gpu, mapping):
+    """The TARGET (§3) and DEPTH (§4, z0 at the focal distance) mappings at
+    the bench's size and parameters (1920x1080, K=6, k = 0.02 diam, f = 0.1
+    diam): per pass on 4,096 sampled pixels, and end to end by PSNR."""
+    d = mid.diameter()
+    W, H = 1920, 1080
+    k, f = 0.02 * d, 0.1 * d
+    z0 = f if mapping == rcp.RCP_MAP_DEPTH else 0.0
+    pix = scenes.pixel_subset(W, H, 4096, seed=300 + mapping)
+    rep = U.per_pass_parity(mid, mid.poses[9], W, H, 6, mapping, k, f, pix=pix, z0=z0, g=mid_gpu)
+    print(rep.assert_ok(f"mid mapping {mapping}"))
+    p, fl = U.end_to_end_psnr(mid, mid.poses[9], W, H, 6, mapping, k, f, pix=pix, z0=z0, g=mid_gpu)
+    print(f"mid mapping {mapping} K=6 PSNR {p:.1f} dB, flagged chains {fl:.4f}")
+    assert p >= U.PSNR_MIN
+
+
 @pytest.fixture(scope="module")
 def forest_golden():
     sc = scenes.forest_scene()
